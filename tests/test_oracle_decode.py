@@ -1,0 +1,135 @@
+"""Pins for oracle.decode: contractivity, convergence, the collage bound, a dense-matrix
+restatement on a tiny image, and the adjoint against central finite differences."""
+import numpy as np
+import pytest
+
+from oracle import decode, geometry
+from oracle import match as omatch
+from paper_1206_4880_gb300 import synth
+
+
+def _random_codes(rng, H, W, B, sigma, smax):
+    R = geometry.n_ranges(H, W, B)
+    Dn = geometry.n_domains(H, W, B, sigma)
+    return {"dom": rng.integers(0, Dn, R), "iso": rng.integers(0, 8, R),
+            "s": rng.uniform(-smax, smax, R), "o": rng.uniform(0, 128, R)}
+
+
+def test_nonexpansive():
+    rng = np.random.default_rng(0)
+    H = W = 32
+    c = _random_codes(rng, H, W, 8, 4, 0.9)
+    for _ in range(5):
+        x = rng.uniform(0, 255, (H, W))
+        y = rng.uniform(0, 255, (H, W))
+        a = decode.decode_step(x, c, 8, 4)
+        b = decode.decode_step(y, c, 8, 4)
+        assert np.max(np.abs(a - b)) <= np.max(np.abs(c["s"])) * np.max(np.abs(x - y)) + 1e-9
+
+
+def test_geometric_convergence():
+    rng = np.random.default_rng(1)
+    H = W = 32
+    c = _random_codes(rng, H, W, 8, 4, 0.9)
+    x = np.full((H, W), 128.0)
+    diffs = []
+    for _ in range(30):
+        y = decode.decode_step(x, c, 8, 4)
+        diffs.append(np.max(np.abs(y - x)))
+        x = y
+    for k in range(1, len(diffs)):
+        assert diffs[k] <= 0.9 * diffs[k - 1] + 1e-9
+
+
+def test_constant_image_decodes_exactly_after_one_iteration():
+    img = np.full((32, 48), 97, dtype=np.uint8)
+    codes = omatch.encode(img, B=8, sigma=4, K=4)
+    assert np.all(codes["s"] == 0) and np.all(codes["o"] == 97)
+    x = decode.decode(codes, 32, 48, 8, 4, 1)
+    assert np.array_equal(decode.to_u8(x), img)
+    assert decode.psnr(decode.to_u8(x), img) == float("inf")
+
+
+def test_collage_bound(pr1_img):
+    img = pr1_img[:64, :64]
+    codes = omatch.encode(img, B=8, sigma=4, K=1)
+    smax = np.max(np.abs(codes["s"]))
+    if smax >= 1.0:
+        # the theorem needs a strict contraction; restrict to ranges fitted with |s| < 1
+        codes["s"] = np.clip(codes["s"], -0.95, 0.95)
+        smax = 0.95
+    I = img.astype(np.float64)
+    coll = np.max(np.abs(decode.decode_step(I, codes, 8, 4) - I))
+    x = decode.decode(codes, 64, 64, 8, 4, 200, x0=I)
+    assert np.max(np.abs(I - x)) <= coll / (1 - smax) + 1e-6
+
+
+def _dense_step(H, W, B, sigma, codes):
+    """x -> M x + b as an explicit matrix over the H*W pixels."""
+    n = H * W
+    M = np.zeros((n, n))
+    b = np.zeros(n)
+    for r in range(geometry.n_ranges(H, W, B)):
+        ry, rx = geometry.range_origin(H, W, B, r)
+        dy, dx = geometry.domain_origin(H, W, B, sigma, int(codes["dom"][r]))
+        for y in range(B):
+            for x in range(B):
+                sy, sx = geometry.iso_source(B, int(codes["iso"][r]), y, x)
+                row = (ry + y) * W + rx + x
+                for a in (0, 1):
+                    for c in (0, 1):
+                        M[row, (dy + 2 * sy + a) * W + dx + 2 * sx + c] += codes["s"][r] / 4.0
+                b[row] = codes["o"][r]
+    return M, b
+
+
+def test_decode_equals_dense_matrix_iteration():
+    rng = np.random.default_rng(2)
+    H, W = 16, 24
+    c = _random_codes(rng, H, W, 8, 2, 1.0)
+    M, b = _dense_step(H, W, 8, 2, c)
+    x0 = rng.uniform(0, 255, H * W)
+    x = x0.copy()
+    for _ in range(6):
+        x = M @ x + b
+    got = decode.decode(c, H, W, 8, 2, 6, x0=x0.reshape(H, W))
+    assert np.allclose(got.reshape(-1), x, rtol=0, atol=1e-9)
+    # adjoint from the dense matrices: dL/dx_K = g
+    g = rng.normal(size=(H, W))
+    gs, go = decode.decode_adjoint(c, H, W, 8, 2, 6, g, x0=x0.reshape(H, W))
+    R = geometry.n_ranges(H, W, 8)
+    # derivative of x_K w.r.t. o_r: sum_{j<K} M^j e_r  (e_r = indicator of range r)
+    for r in range(R):
+        ry, rx = geometry.range_origin(H, W, 8, r)
+        e = np.zeros((H, W))
+        e[ry:ry + 8, rx:rx + 8] = 1
+        e = e.reshape(-1)
+        acc = np.zeros(H * W)
+        v = e.copy()
+        for _ in range(6):
+            acc += v
+            v = M @ v
+        assert abs(go[r] - g.reshape(-1) @ acc) <= 1e-9 * max(1, abs(go[r]))
+
+
+@pytest.mark.parametrize("iters", [1, 3, 8])
+def test_adjoint_against_central_differences(iters):
+    rng = np.random.default_rng(iters)
+    H, W = 32, 32
+    img = synth.fbm_image(40 + iters, H, W)
+    codes = omatch.encode(img, B=8, sigma=4, K=4)
+    codes = {k: np.array(codes[k], dtype=np.float64 if k in ("s", "o") else np.int64)
+             for k in ("dom", "iso", "s", "o")}
+    g = rng.normal(size=(H, W))
+    gs, go = decode.decode_adjoint(codes, H, W, 8, 4, iters, g)
+    h = 1e-4
+    for r in rng.choice(geometry.n_ranges(H, W, 8), 6, replace=False):
+        for key, grad in (("s", gs), ("o", go)):
+            cp = {k: v.copy() for k, v in codes.items()}
+            cm = {k: v.copy() for k, v in codes.items()}
+            cp[key][r] += h
+            cm[key][r] -= h
+            fp = np.sum(g * decode.decode(cp, H, W, 8, 4, iters))
+            fm = np.sum(g * decode.decode(cm, H, W, 8, 4, iters))
+            fdv = (fp - fm) / (2 * h)
+            assert abs(grad[r] - fdv) <= 1e-4 * max(1.0, abs(fdv)), (key, r, grad[r], fdv)
