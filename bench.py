@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of classified range-domain matching on GB300 (one JSON line on stdout).
+
+Workload (default): a seeded 1024x1024 8-bit fBm + ramp + rectangles image, 8x8 ranges
+(16384), 16x16 domains at stride 4 (64009) under 8 isometries, K = 16 LFD classes with pool
+half-width floor(K/3) = 5. A step is one fic_encode call (classification -> pools -> matching ->
+exact codes) with the image already resident in HBM; L2 is flushed (a 256 MiB write) before
+every step and the flush is not timed. The metric is range-domain-isometry matches per second,
+matches = sum over ranges of |Pool(r)| * 8.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--engine tensor|simt]
+  python bench.py --impl reference ...   (the CPU oracle, timed on the host cores)
+
+Under torchrun each rank encodes its own image (seed + rank) on its own GPU: independent
+problems, no data exchange, weak scaling; the timed region is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "encode-1024": dict(H=1024, W=1024, sigma=4, K=16, w=-1, seed=2000,
+                        desc="1024x1024 8-bit seeded fBm+edges image; 16384 8x8 ranges; 16x16 "
+                             "domains at stride 4 (64009) x 8 isometries; K=16 LFD classes, w=5"),
+    "encode-256": dict(H=256, W=256, sigma=8, K=8, w=-1, seed=1000,
+                       desc="256x256 8-bit seeded fBm+edges image; 1024 8x8 ranges; 16x16 domains "
+                            "at stride 8 (961) x 8 isometries; K=8 LFD classes, w=2"),
+}
+FLUSH_BYTES = 256 << 20
+FLOPS_PER_MATCH = 2 * 64  # one 64-term correlation: 64 multiply-adds
+N_SMS = 152
+FP32_LANES = 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _image(wl, rank):
+    from paper_1206_4880_gb300 import synth
+    if wl["seed"] == 1000 and rank == 0:
+        return synth.pr1_image()
+    return synth.fbm_image(wl["seed"] + rank, wl["H"], wl["W"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples (100 ms) for the GPU this rank uses."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark_begin(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.seek(0)
+        rows = []
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[3:]))
+            except ValueError:
+                continue
+        os.unlink(self.file.name)
+        inside = [r for r in rows if self.t0 - 1 <= r[0] <= self.t1 + 1] or rows
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in inside:
+            for name, v in zip(names, r[3][2:6]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "samples": len(inside),
+                "power_w_max": max((float(r[3][0]) for r in inside if r[3][0].replace(".", "").isdigit()), default=None),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(img, wl, budget_s: float):
+    """The oracle as it stands on a seeded sample of ranges (their full pools), all host cores."""
+    from oracle import match as omatch
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    cls = omatch.classify_image(img, 8, wl["sigma"], wl["K"])
+    t_cls = time.perf_counter() - t0
+    R = cls["range_bin"].size
+    order = np.random.default_rng(12345).permutation(R)
+    n = min(R, 2 * threads)
+    t0 = time.perf_counter()
+    omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=order[:n], n_threads=threads, cls=cls)
+    per = (time.perf_counter() - t0) / n
+    n = int(min(R, max(n, budget_s / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    c = omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=order[:n], n_threads=threads, cls=cls)
+    dt = time.perf_counter() - t0
+    matches = int(c["pool_size"].sum()) * 8
+    return {"value": matches / dt, "unit": "matches/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} of {R} ranges (seeded permutation), each over its full pool: "
+                      f"{matches} matches in {dt:.2f} s; whole-image classification "
+                      f"({t_cls:.2f} s) not included"}
+
+
+def run_reference(args, wl, world, rank):
+    """The CPU oracle as the reference arm: rank 0 only, each step a bounded sample."""
+    if rank != 0:
+        return 0
+    from oracle import match as omatch
+    img = _image(wl, 0)
+    threads = os.cpu_count() or 1
+    cls = omatch.classify_image(img, 8, wl["sigma"], wl["K"])
+    R = cls["range_bin"].size
+    order = np.random.default_rng(12345).permutation(R)
+    per_step = max(0.05, 90.0 / max(1, args.steps + args.warmup))
+    t0 = time.perf_counter()
+    omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=order[:threads], n_threads=threads, cls=cls)
+    per = (time.perf_counter() - t0) / threads
+    n = int(min(R, max(1, per_step / max(per, 1e-9))))
+    pos = 0
+    total_m, total_t = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        ids = order[(pos + np.arange(n)) % R]
+        pos += n
+        t0 = time.perf_counter()
+        c = omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=ids, n_threads=threads, cls=cls)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            total_m += int(c["pool_size"].sum()) * 8
+            total_t += dt
+    value = total_m / total_t
+    line = {"metric": "range-domain-isometry matches/s", "value": value, "unit": "matches/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": value, "unit": "matches/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{n} seeded ranges of {R} per step, each over its full pool"},
+            "e2e": {"value": value, "unit": "matches/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, wl, world, rank, local):
+    import torch
+
+    from paper_1206_4880_gb300 import fic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    img_np = _image(wl, rank)
+    H, W = img_np.shape
+    img = torch.from_numpy(img_np).to(dev)
+    p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=wl["K"], half_width=wl["w"],
+                         engine=args.engine)
+    R, Dn = fic.counts(H, W, p)
+    ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)
+    out = fic.alloc_codes(R, dev)
+    info = fic.new_info(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    fic.profile_enable(True)
+    for _ in range(args.warmup):
+        fic.encode(img, p, out=out, workspace=ws)
+    fic.encode(img, p, out=out, workspace=ws, info=info)
+    rep = fic.read_info(info)
+    matches = rep["matches"]
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    match_ms, launches = [], 0
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark_begin()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        ev0[k].record()
+        fic.encode(img, p, out=out, workspace=ws)
+        ev1[k].record()
+        stages, launches = fic.profile_read()
+        match_ms.append(stages["match"])
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks.mark_end()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_s = reduce_max(sum(step_ms) / 1e3, world)
+    all_matches = reduce_sum(float(matches) * args.steps, world)
+    clk = clocks.stop()
+
+    # end to end through the public API with host buffers: H2D image, encode, D2H codes
+    host_img = torch.from_numpy(img_np).pin_memory()
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    e2e_steps = min(args.steps, 50)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    for k in range(e2e_steps):
+        flush.fill_(k & 255)
+        e0[k].record()
+        img.copy_(host_img, non_blocking=True)
+        fic.encode(img, p, out=out, workspace=ws)
+        for key in out:
+            host_out[key].copy_(out[key], non_blocking=True)
+        e1[k].record()
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1e3, world)
+    e2e_value = reduce_sum(float(matches) * e2e_steps, world) / e2e_s
+
+    peaks, peak_src = _peaks()
+    mean_match_ms = statistics.mean(match_ms)
+    if args.engine == "tensor":
+        bound, unit = "tensor", "TFLOP/s"
+        peak = float(peaks["bf16_tflops"])  # FP16 dense = BF16 dense rate (nominal ratio 1)
+        peak_note = f"{peak_src} bf16 dense burst x nominal fp16/bf16 ratio 1.0"
+    else:
+        bound, unit = "alu", "TFLOP/s"
+        peak = N_SMS * FP32_LANES * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        peak_note = f"FP32 FMA: {N_SMS} SMs x {FP32_LANES} lanes x 2 flop x sm_max_mhz"
+    achieved = matches * FLOPS_PER_MATCH / (mean_match_ms / 1e3) / 1e12
+    line = {
+        "metric": "range-domain-isometry matches/s", "value": all_matches / total_s,
+        "unit": "matches/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp16-in/fp32-acc exact; int64/f64 re-eval" if args.engine == "tensor" else "f32-exact-int; int64/f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "engine": args.engine,
+                   "l2": "flushed (256 MiB write) before every step, untimed",
+                   "parallelism": f"independent images, 1 per GPU x {world}"},
+        "encode_ms": statistics.median(step_ms),
+        "matches_per_step": matches,
+        "pool_fraction": matches / (R * Dn * 8),
+        "fallback_ranges": rep["fallback_ranges"],
+        "roofline": {"kernel": "match", "bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "per_launch_ms": mean_match_ms, "peak_source": peak_note},
+        "e2e": {"value": e2e_value, "unit": "matches/s", "h2d_bytes_per_step": H * W,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_extras:
+        line["comparators"] = comparators(img, img_np, wl, args, dev)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(img_np, wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def comparators(img, img_np, wl, args, dev):
+    """Plain full search on CUDA cores (and on tensor cores when available) on the same image,
+    with decoded PSNR (8 iterations from mid-grey) of the full-search and classified codes."""
+    import torch
+
+    from paper_1206_4880_gb300 import fic
+    H, W = img_np.shape
+    res = {}
+
+    def timed(p, reps):
+        ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)
+        out = fic.encode(img, p, workspace=ws)
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fic.encode(img, p, out=out, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        x = fic.decode(out, H, W, p, 8)
+        xq = np.clip(np.rint(x.cpu().numpy().astype(np.float64)), 0, 255)
+        mse = np.mean((xq - img_np.astype(np.float64)) ** 2)
+        return statistics.median(ms), float(10 * np.log10(255.0 ** 2 / mse))
+
+    engines = ["simt", "tensor"] if args.engine == "tensor" else ["simt"]
+    for eng in engines:
+        for K, name in ((1, "full"), (wl["K"], "classified")):
+            p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=K, half_width=wl["w"], engine=eng)
+            ms, ps = timed(p, 3 if eng == "simt" else 10)
+            res[f"{eng}_{name}_ms"] = ms
+            res[f"{eng}_{name}_psnr_db"] = ps
+    res["plain_gpu_full_over_classified"] = res["simt_full_ms"] / res[f"{args.engine}_classified_ms"]
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--engine", choices=("tensor", "simt"), default="tensor")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="encode-1024")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, wl, world, rank)
+    return run_ours(args, wl, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

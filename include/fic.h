@@ -1,0 +1,192 @@
+/*
+ * fic.h - C ABI of the GB300 classified fractal image encoder.
+ *
+ * Method: K. Revathy and M. Jayamohan, "Dynamic Domain Classification for Fractal Image
+ * Compression". An 8-bit grayscale image is cut into non-overlapping B x B range blocks
+ * (Section 1); every 2B x 2B domain on a stride-sigma grid (Section 2) is contracted by 2x2
+ * averaging; ranges and domains are classified by their local fractal dimension estimated with
+ * differential box counting (Section 3.1); each range searches only the domains whose class is
+ * within the fractal distance D_f = (F_m - F_l)/3 of its own (Section 3.1, Eq. 2-3), under the
+ * 8 square isometries, with a least-squares contrast s (|s| <= 1) and brightness o, and keeps
+ * the (domain, isometry, s, o) of least collage error (Section 1). Decoding iterates the maps
+ * from an initial image (Section 1).
+ *
+ * Conventions for every entry point:
+ *  - Image, code, statistics and workspace pointers are DEVICE pointers owned by the caller.
+ *    The library allocates no memory and frees none; it keeps no state between calls except a
+ *    per-device cache of its own kernel attributes.
+ *  - `stream` is a cudaStream_t (passed as void*; NULL = the legacy default stream). All work
+ *    is enqueued asynchronously on it; nothing synchronises the host.
+ *  - Arguments are validated on the host before anything is enqueued; a failed validation
+ *    returns FIC_ERR_INVALID_ARG (or FIC_ERR_WORKSPACE) and enqueues nothing.
+ *  - A launch failure returns FIC_ERR_CUDA. fic_last_error() returns a message for the last
+ *    failure on the calling thread.
+ *  - Images are row-major uint8 with row pitch `pitch` >= W bytes. Ranges are numbered
+ *    row-major: range r covers rows (r / (W/B))*B .. +B-1 and columns (r % (W/B))*B .. +B-1.
+ *    Domains are numbered row-major over the stride grid: domain d has its top-left pixel at
+ *    ((d / nDx) * sigma, (d % nDx) * sigma), nDy = (H - 2B)/sigma + 1, nDx = (W - 2B)/sigma + 1.
+ *  - Isometry t maps a B x B block X to T_t X with (T_t X)[y][x] = X[sy][sx] where, with
+ *    N = B-1: t=0 (y,x); 1 rotate 90 clockwise (N-x,y); 2 rotate 180 (N-y,N-x);
+ *    3 rotate 270 clockwise (x,N-y); 4 mirror left-right (y,N-x); 5 mirror up-down (N-y,x);
+ *    6 transpose (x,y); 7 anti-transpose (N-x,N-y).
+ *
+ * Supported in this version: B = 8, 1 <= sigma, 1 <= K <= 255, s_max = 1.0.
+ */
+#ifndef FIC_H
+#define FIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FIC_OK = 0,
+    FIC_ERR_INVALID_ARG = 1,  /* bad geometry, parameters or null pointer */
+    FIC_ERR_WORKSPACE = 2,    /* workspace missing, too small or misaligned (256 B) */
+    FIC_ERR_CUDA = 3,         /* a CUDA runtime/driver call or launch failed */
+    FIC_ERR_DEVICE_TIMEOUT = 4, /* a bounded device-side wait gave up (see fic_check) */
+    FIC_ERR_UNSUPPORTED = 5   /* device or build lacks a required feature (sm_103a) */
+} fic_status;
+
+/* Matching engines. */
+enum {
+    FIC_ENGINE_TENSOR = 0, /* tcgen05 correlation GEMM + fused ranking + exact re-evaluation */
+    FIC_ENGINE_SIMT = 1    /* exact search on CUDA cores (the plain GPU search) */
+};
+
+typedef struct {
+    int32_t H, W;   /* image height and width in pixels: multiples of B, >= 2B */
+    int32_t pitch;  /* bytes between rows, >= W */
+} fic_geom;
+
+typedef struct {
+    int32_t block;         /* B, range side (8) */
+    int32_t domain_stride; /* sigma >= 1: domain grid step in pixels */
+    int32_t num_classes;   /* K in [1, 255]; K = 1 makes every pool the full domain set */
+    int32_t half_width;    /* w >= 0 classes on each side; -1 selects floor(K/3) (Eq. 2) */
+    double s_max;          /* contrast clamp; must be 1.0 */
+    int32_t engine;        /* FIC_ENGINE_TENSOR or FIC_ENGINE_SIMT */
+    int32_t flags;         /* reserved, must be 0 */
+} fic_params;
+
+/* Per-block statistics (Section 3.1: "the fractal dimension of the range blocks are calculated
+ * and listed in a linear array", then the FD values of the overlapping domains). Device
+ * arrays, R = (H/B)(W/B) entries for ranges and Dn = nDy*nDx for domains.
+ *  range_sum = sum r, range_sumsq = sum r^2 over the B x B pixels;
+ *  dom_sum = sum S, dom_sumsq = sum S^2 over the B x B integer 2x2 sums S of the domain;
+ *  *_counts[2*i + k] = differential box count N_s at s = 2 (k=0) and s = 4 (k=1);
+ *  *_fd = log2(N_2) - log2(N_4) in binary64 with correctly rounded log2;
+ *  fd_extent[0] = F_l (least domain FD), fd_extent[1] = F_m (largest domain FD);
+ *  *_bin = class in [0, K): min(K-1, max(0, floor(K * ((f - F_l) / (F_m - F_l))))), or 0 if
+ *  F_m == F_l, each operation a separate IEEE binary64 operation. */
+typedef struct {
+    int32_t *range_sum, *range_sumsq, *range_counts;
+    double *range_fd;
+    uint8_t *range_bin;
+    int32_t *dom_sum, *dom_sumsq, *dom_counts;
+    double *dom_fd;
+    uint8_t *dom_bin;
+    double *fd_extent;
+} fic_blockstats;
+
+/* Dynamic pools (Section 3.1 Eq. 3 in class units, replacing the paper's AVL tree by an
+ * ordered array: a range query of the tree is a contiguous slice of the class-sorted domains).
+ *  dom_order[Dn]   domain ids sorted by (class, id) - the in-order traversal of the tree;
+ *  bin_off[K+1]    dom_order[bin_off[b] .. bin_off[b+1]) holds class b;
+ *  range_order[R]  range ids sorted by (class, id); rbin_off[K+1] likewise;
+ *  win_lo[R], win_hi[R]  Pool(r) = dom_order[win_lo[r] .. win_hi[r]) = the domains with
+ *                  |bin_d - bin_r| <= w; when that set is empty the pool is every domain
+ *                  (win_lo = 0, win_hi = Dn). */
+typedef struct {
+    int32_t *dom_order, *bin_off, *range_order, *rbin_off, *win_lo, *win_hi;
+} fic_pools;
+
+/* Fractal code per range r (device arrays of R entries): the best domain id, isometry, contrast
+ * s, brightness o (binary64, unquantised) and collage error sse = sum (r - s T_t(D) - o)^2 with
+ * D the 2x2-averaged domain. Ties in sse go to the smaller domain id, then the smaller t. */
+typedef struct {
+    int32_t *dom;
+    int32_t *iso;
+    double *s, *o, *sse;
+} fic_codes;
+
+/* Optional encode report, written to DEVICE memory when the pointer is non-null. */
+typedef struct {
+    int64_t matches;          /* sum over ranges of |Pool(r)| * 8: range-domain-isometry fits */
+    int32_t fallback_ranges;  /* ranges re-searched exactly because ranking could not certify */
+    int32_t work_items;       /* tensor engine: (range tile, domain chunk) items */
+    int32_t device_error;     /* 0, or FIC_ERR_DEVICE_TIMEOUT if a bounded wait gave up */
+    int32_t reserved;
+} fic_encode_info;
+
+/* Bytes of workspace fic_encode / fic_classify / fic_build_pools need for this geometry. */
+size_t fic_encode_workspace_size(const fic_geom *g, const fic_params *p);
+
+/* Section 3.1: moments, differential box counts, FDs, F_l/F_m and classes of every range and
+ * domain of `img`. Workspace: fic_encode_workspace_size bytes (may be NULL/0 for this call). */
+fic_status fic_classify(const uint8_t *img, const fic_geom *g, const fic_params *p,
+                        const fic_blockstats *out, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* Section 3.1 Eq. 3: class-sorted domain and range orders and every range's pool window, from
+ * the classes in `st` (as written by fic_classify). Workspace: fic_encode_workspace_size. */
+fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *g, const fic_params *p,
+                           const fic_pools *out, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
+/* Sections 1 and 3: the whole encoder, image -> codes. Equal to the exact least-error search
+ * over each range's pool (ties as in fic_codes). `info` (device, nullable) receives the
+ * report. */
+fic_status fic_encode(const uint8_t *img, const fic_geom *g, const fic_params *p,
+                      const fic_codes *out, fic_encode_info *info, void *workspace,
+                      size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace fic_decode and fic_decode_backward need. */
+size_t fic_decode_workspace_size(const fic_geom *g, const fic_params *p, int32_t iters,
+                                 int32_t ckpt_every);
+
+/* Section 1: decoding. x_0 = x0 (H*W float, row-major, dense) or 128 everywhere when x0 is
+ * NULL; x_{k+1}[range r] = s_r T_{t_r}(D(x_k, dom_r)) + o_r for all ranges from x_k (Jacobi),
+ * D the 2x2 average of the 2B x 2B domain; `out` (H*W float) receives x_iters, unclamped.
+ * iters >= 0. Workspace: fic_decode_workspace_size. */
+fic_status fic_decode(const fic_codes *codes, const fic_geom *g, const fic_params *p,
+                      int32_t iters, const float *x0, float *out, void *workspace,
+                      size_t workspace_bytes, void *stream);
+
+/* Adjoint of fic_decode with respect to the per-range contrast and brightness: given
+ * grad_out = dL/dx_iters (H*W float), writes grad_s[r] = dL/ds_r and grad_o[r] = dL/do_r
+ * (R floats each). Iterates are recomputed from checkpoints kept every `ckpt_every` (>= 1)
+ * iterations. W^T is applied as a deterministic gather (no floating-point atomics). */
+fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *g, const fic_params *p,
+                               int32_t iters, int32_t ckpt_every, const float *x0,
+                               const float *grad_out, float *grad_s, float *grad_o,
+                               void *workspace, size_t workspace_bytes, void *stream);
+
+/* Instrumentation (not part of the method). When enabled on the calling thread, fic_encode
+ * records CUDA events on its stream around each stage; fic_profile_read waits for the last
+ * encode's events and writes the stage durations in milliseconds to ms[0..n):
+ *   ms[0] classification, ms[1] pool build, ms[2] operand packing, ms[3] matching,
+ *   ms[4] exact re-evaluation, ms[5] exact re-search of uncertified ranges
+ * (0 for stages the engine does not run), and the number of kernels the last fic_encode on
+ * this thread launched to *launches (nullable). Enabling creates the events on the current
+ * device; fic_profile_read returns FIC_ERR_INVALID_ARG if profiling is off. */
+fic_status fic_profile_enable(int32_t on);
+fic_status fic_profile_read(float *ms, int32_t n, int32_t *launches);
+
+/* 1 if `engine` (FIC_ENGINE_*) can run on the current device with this build, else 0. */
+int32_t fic_engine_available(int32_t engine);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *fic_last_error(void);
+
+/* Library version, (major << 16) | minor. */
+int32_t fic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIC_H */

@@ -1,0 +1,230 @@
+// Fractal decoding and its adjoint (Revathy & Jayamohan, Section 1: "the transformations are
+// applied on an initial image"; the adjoint differentiates a fixed number of iterations with
+// respect to the per-range contrast s and brightness o).
+//
+// One Jacobi step: x_{k+1}[p] = s_r * D(x_k, d_r)[src_{t_r}(p)] + o_r for every pixel p of range
+// r, with D the 2x2 average of the 2B x 2B domain. Adjoint of the linear part W:
+// (W^T l)[q] = sum over ranges r whose domain covers q of (s_r / 4) * l[p_r(q)], where p_r(q)
+// is the range pixel whose source cell contains q. It is evaluated as a gather per pixel q over
+// the (at most (2B/sigma)^2) domains covering q and, through a domain -> ranges CSR whose
+// segments are sorted, over the ranges using each domain: no atomics, so the result does not
+// depend on scheduling.
+#include "fic_internal.cuh"
+
+namespace fic {
+
+__global__ void k_fill(float *x, size_t n, float v) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, v);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+// One thread per output pixel.
+__global__ void k_decode_step(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                              const double *__restrict__ s, const double *__restrict__ o,
+                              const float *__restrict__ x, float *__restrict__ y) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.H * g.W) return;
+    const int py = idx / g.W, px = idx - py * g.W;
+    const int r = (py >> 3) * g.nRx + (px >> 3);
+    const int d = dom[r], t = iso[r];
+    int sy, sx;
+    iso_src(8, t, py & 7, px & 7, sy, sx);
+    const int qy = (d / g.nDx) * g.sigma + 2 * sy, qx = (d % g.nDx) * g.sigma + 2 * sx;
+    const float *p = x + (size_t)qy * g.W + qx;
+    const float v = (((p[0] + p[1]) + p[g.W]) + p[g.W + 1]) * 0.25f;
+    y[idx] = fmaf((float)s[r], v, (float)o[r]);
+}
+
+cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,
+                               cudaStream_t st) {
+    const int n = g.H * g.W;
+    k_decode_step<<<(n + 255) / 256, 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+// ---- adjoint -------------------------------------------------------------------------------
+// domain -> ranges CSR: cnt[d] = #ranges using d; off = exclusive scan; list sorted per segment.
+__global__ void k_dom_count(Geo g, const int32_t *__restrict__ dom, int32_t *cnt) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < g.R) atomicAdd(&cnt[dom[r]], 1);
+}
+
+// Single-block exclusive scan of cnt[0..n) into off[0..n], chunk by chunk.
+__global__ void k_scan_single(const int32_t *__restrict__ cnt, int n, int32_t *__restrict__ off,
+                              int32_t *__restrict__ cursor) {
+    __shared__ int buf[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? cnt[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int s = 1; s < 1024; s <<= 1) {
+            const int a = threadIdx.x >= s ? buf[threadIdx.x - s] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += a;
+            __syncthreads();
+        }
+        const int incl = buf[threadIdx.x];
+        if (i < n) {
+            off[i] = carry + incl - v;
+            cursor[i] = carry + incl - v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[n] = carry;
+}
+
+__global__ void k_dom_fill(Geo g, const int32_t *__restrict__ dom, int32_t *cursor,
+                           int32_t *__restrict__ list) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < g.R) list[atomicAdd(&cursor[dom[r]], 1)] = r;
+}
+
+// Insertion-sort each domain's segment so the gather order is fixed.
+__global__ void k_dom_sortseg(int Dn, const int32_t *__restrict__ off, int32_t *__restrict__ list) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= Dn) return;
+    const int a = off[d], b = off[d + 1];
+    for (int i = a + 1; i < b; ++i) {
+        const int v = list[i];
+        int j = i - 1;
+        while (j >= a && list[j] > v) {
+            list[j + 1] = list[j];
+            --j;
+        }
+        list[j + 1] = v;
+    }
+}
+
+// l_prev = W^T l, one thread per pixel q.
+__global__ void k_adjoint_gather(Geo g, const int32_t *__restrict__ iso, const double *__restrict__ s,
+                                 const int32_t *__restrict__ off, const int32_t *__restrict__ list,
+                                 const float *__restrict__ lam, float *__restrict__ lam_prev) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.H * g.W) return;
+    const int qy = idx / g.W, qx = idx - qy * g.W;
+    // domains (dy, dx) on the stride grid with dy <= qy < dy + 16, likewise x
+    const int jy_hi = min(qy / g.sigma, g.nDy - 1), jx_hi = min(qx / g.sigma, g.nDx - 1);
+    const int jy_lo = max(0, (qy - 15 + g.sigma - 1) / g.sigma);
+    const int jx_lo = max(0, (qx - 15 + g.sigma - 1) / g.sigma);
+    float acc = 0.f;
+    for (int jy = jy_lo; jy <= jy_hi; ++jy) {
+        const int dy = jy * g.sigma;
+        const int cy = (qy - dy) >> 1;
+        for (int jx = jx_lo; jx <= jx_hi; ++jx) {
+            const int dx = jx * g.sigma;
+            const int cx = (qx - dx) >> 1;
+            const int d = jy * g.nDx + jx;
+            for (int k = off[d]; k < off[d + 1]; ++k) {
+                const int r = list[k];
+                const int t = iso[r];
+                // range pixel p with src_t(p) = (cy, cx): p = src_{t^-1}(cy, cx)
+                const int tinv = (t == 1) ? 3 : (t == 3 ? 1 : t);
+                int py, px;
+                iso_src(8, tinv, cy, cx, py, px);
+                const int ry = (r / g.nRx) * 8, rx = (r % g.nRx) * 8;
+                acc = fmaf((float)s[r] * 0.25f, lam[(size_t)(ry + py) * g.W + rx + px], acc);
+            }
+        }
+    }
+    lam_prev[idx] = acc;
+}
+
+// grad_s[r] += sum_p l[p] * T(D x)[p], grad_o[r] += sum_p l[p]; one warp per range. The terms
+// are formed in FP32 and summed in FP64 (the sums cancel heavily: terms of a few hundred add up
+// to gradients of order one), into per-range FP64 accumulators.
+__global__ void k_adjoint_grads(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                                const float *__restrict__ x, const float *__restrict__ lam,
+                                double *__restrict__ gs, double *__restrict__ go) {
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= g.R) return;
+    const int d = dom[r], t = iso[r];
+    const int ry = (r / g.nRx) * 8, rx = (r % g.nRx) * 8;
+    const int dy = (d / g.nDx) * g.sigma, dx = (d % g.nDx) * g.sigma;
+    double a_s = 0.0, a_o = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = lane + 32 * h;
+        const int y = p >> 3, xx = p & 7;
+        int sy, sx;
+        iso_src(8, t, y, xx, sy, sx);
+        const float *q = x + (size_t)(dy + 2 * sy) * g.W + dx + 2 * sx;
+        const float v = (((q[0] + q[1]) + q[g.W]) + q[g.W + 1]) * 0.25f;
+        const float l = lam[(size_t)(ry + y) * g.W + rx + xx];
+        a_s += (double)l * (double)v;
+        a_o += (double)l;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a_s += __shfl_xor_sync(0xffffffffu, a_s, off);
+        a_o += __shfl_xor_sync(0xffffffffu, a_o, off);
+    }
+    if (lane == 0) {
+        gs[r] += a_s;
+        go[r] += a_o;
+    }
+}
+
+__global__ void k_grads_out(int R, const double *__restrict__ gs64, const double *__restrict__ go64,
+                            float *__restrict__ gs, float *__restrict__ go) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) {
+        gs[r] = (float)gs64[r];
+        go[r] = (float)go64[r];
+    }
+}
+
+cudaError_t launch_dom_csr(const Geo &g, const int32_t *dom, int32_t *cnt, int32_t *off,
+                           int32_t *cursor, int32_t *list, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * g.Dn, st))) return e;
+    k_dom_count<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, cnt);
+    ++g_launches;
+    k_scan_single<<<1, 1024, 0, st>>>(cnt, g.Dn, off, cursor);
+    ++g_launches;
+    k_dom_fill<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, cursor, list);
+    ++g_launches;
+    k_dom_sortseg<<<(g.Dn + 255) / 256, 256, 0, st>>>(g.Dn, off, list);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const int32_t *off,
+                                  const int32_t *list, const float *lam, float *lam_prev,
+                                  cudaStream_t st) {
+    const int n = g.H * g.W;
+    k_adjoint_gather<<<(n + 255) / 256, 256, 0, st>>>(g, c.iso, c.s, off, list, lam, lam_prev);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *x, const float *lam,
+                                 double *gs, double *go, cudaStream_t st) {
+    const long long threads = (long long)g.R * 32;
+    k_adjoint_grads<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grads_out(int R, const double *gs64, const double *go64, float *gs, float *go,
+                             cudaStream_t st) {
+    k_grads_out<<<(R + 255) / 256, 256, 0, st>>>(R, gs64, go64, gs, go);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace fic

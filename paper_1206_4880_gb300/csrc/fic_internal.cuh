@@ -1,0 +1,181 @@
+// Internal declarations of the fic CUDA library (sm_103a). Not part of the C ABI.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fic.h"
+
+namespace fic {
+
+constexpr int kMaxClasses = 255;
+
+// Kernels launched by the current fic_* call on this thread (reset at each entry point).
+extern thread_local int g_launches;
+
+// Derived geometry of one image (Section 1 range partition, Section 2 domain grid).
+struct Geo {
+    int H, W, pitch;
+    int B, n, sigma;     // range side, pixels per range, domain stride
+    int nRy, nRx, R;     // range grid
+    int nDy, nDx, Dn;    // domain grid
+    int K, w;            // classes and pool half-width (Section 3.1 Eq. 2-3)
+};
+
+// Correctly rounded log2(n) for n = 0..64 (entry 0 unused); passed to kernels by value.
+struct Log2Tab {
+    double v[65];
+};
+const Log2Tab &log2_table();
+double log2_correctly_rounded(int n);
+
+// ----------------------------------------------------------------------------------------
+// Square isometries: (T_t X)[y][x] = X[sy][sx], N = B - 1.
+__host__ __device__ __forceinline__ void iso_src(int B, int t, int y, int x, int &sy, int &sx) {
+    const int N = B - 1;
+    switch (t) {
+        case 0: sy = y; sx = x; break;
+        case 1: sy = N - x; sx = y; break;
+        case 2: sy = N - y; sx = N - x; break;
+        case 3: sy = x; sx = N - y; break;
+        case 4: sy = y; sx = N - x; break;
+        case 5: sy = N - y; sx = x; break;
+        case 6: sy = x; sx = y; break;
+        default: sy = N - x; sx = N - y; break;
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// Exact least-squares gain of one candidate (B = 8, n = 64).
+// With P = n X - A C and Q = n E - C^2, 16 n SSE = 16 (n Bs - A^2) - gain where
+//   gain = 16 P^2 / Q   (Q > 0, 4|P| <= Q; contrast s = 4P/Q not clamped)
+//   gain = 8 |P| - Q    (4|P| > Q; s clamped to sign(P))
+//   gain = 0            (Q = 0; flat domain, s = 0).
+// For n = 64: |P| < 2^28, 16 P^2 < 2^61, Q < 2^31, so num/den fit in int64 and cross products
+// in 128 bits.
+struct Gain {
+    long long num, den;  // gain = num / den, den > 0
+};
+
+__device__ __forceinline__ Gain exact_gain(long long P, long long Q) {
+    Gain g;
+    const long long aP = P < 0 ? -P : P;
+    if (Q == 0) {
+        g.num = 0;
+        g.den = 1;
+    } else if (4 * aP <= Q) {
+        g.num = 16 * P * P;
+        g.den = Q;
+    } else {
+        g.num = 8 * aP - Q;
+        g.den = 1;
+    }
+    return g;
+}
+
+__device__ __forceinline__ int gain_cmp(Gain a, Gain b) {
+    const __int128 l = (__int128)a.num * b.den, r = (__int128)b.num * a.den;
+    return l > r ? 1 : (l < r ? -1 : 0);
+}
+
+// Candidate order: larger gain, then smaller domain id, then smaller isometry.
+__device__ __forceinline__ bool cand_better(Gain ga, int da, int ta, Gain gb, int db, int tb) {
+    const int c = gain_cmp(ga, gb);
+    if (c != 0) return c > 0;
+    if (da != db) return da < db;
+    return ta < tb;
+}
+
+// Contrast, brightness and collage error of the chosen candidate in binary64, from exact
+// integers, with explicit rounding (no contraction).
+__device__ __forceinline__ void finalize_code(int n, long long A, long long Bs, long long C,
+                                              long long P, long long Q, Gain g, double &s,
+                                              double &o, double &sse) {
+    const long long aP = P < 0 ? -P : P;
+    if (Q == 0)
+        s = 0.0;
+    else if (4 * aP <= Q)
+        s = __ddiv_rn(__dmul_rn(4.0, (double)P), (double)Q);
+    else
+        s = P > 0 ? 1.0 : -1.0;
+    o = __ddiv_rn(__dsub_rn((double)A, __dmul_rn(s, __ddiv_rn((double)C, 4.0))), (double)n);
+    const long long base = 16 * ((long long)n * Bs - A * A);
+    const long long num = base * g.den - g.num;  // < 2^62 for n = 64
+    sse = __ddiv_rn((double)num, __dmul_rn(__dmul_rn(16.0, (double)n), (double)g.den));
+}
+
+// ----------------------------------------------------------------------------------------
+// Workspace carving.
+struct Carver {
+    char *base;
+    size_t off, cap;
+    bool ok;
+    explicit Carver(void *b, size_t c) : base((char *)b), off(0), cap(c), ok(true) {}
+    template <class T>
+    T *take(size_t count, size_t align = 256) {
+        off = (off + align - 1) / align * align;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        if (off > cap) ok = false;
+        return p;
+    }
+};
+
+// Encode-side internal buffers (all device, carved from the caller's workspace).
+struct EncodeBufs {
+    // classification
+    int32_t *range_sum, *range_sumsq, *range_counts;
+    double *range_fd;
+    uint8_t *range_bin;
+    int32_t *dom_sum, *dom_sumsq, *dom_counts;
+    double *dom_fd;
+    uint8_t *dom_bin;
+    double *fd_extent;
+    unsigned long long *extent_bits;  // [2] min/max FD bit patterns during the reduction
+    uint16_t *dom_S;                  // [Dn][64] integer 2x2 sums of every domain
+    // pools
+    int32_t *dom_order, *bin_off, *range_order, *rbin_off, *win_lo, *win_hi;
+    int32_t *sort_counts;  // [nblk][256] per-block class histograms
+    int32_t *sort_offs;    // [nblk][256] per-block scatter bases
+    // tensor engine
+    __half *A_mat;         // [R_pad][64]   64 * range pixels, class-sorted ranges
+    __half *B_mat;         // [8 Dn_aux][64] T_t(S_d), class-sorted domains x isometries
+    float4 *dom_aux;       // [Dn_aux] per sorted domain: C, Q/4, 2/Q (0 if Q = 0), unused
+    int4 *rng_info;        // [R_pad] per sorted range: A, pool start, pool end, range id
+    int4 *work;            // [max_items] (m_tile, first domain pos, end domain pos, chunk)
+    int4 *tile_win;        // [n_mtiles] union (x, y) and intersection (z, w) of row windows
+    int32_t *n_chunks;     // [n_mtiles] domain chunks per range tile
+    unsigned long long *cand;  // [R_pad][max_chunks][2] ranking keys
+    int32_t *fallback;     // [R] ranges to re-search exactly
+    int32_t *counters;     // [8] device counters (fallback count, work items, ...)
+    long long *matches;    // [1]
+    int R_pad, Dn_pad, Dn_aux, n_mtiles, max_chunks, max_items, sort_blocks_dom, sort_blocks_rng;
+};
+
+constexpr int kSortChunk = 2048;  // elements per counting-sort block
+constexpr int kTileM = 128;       // ranges per tensor-engine tile
+constexpr int kTileDom = 32;      // domains per accumulator tile (8 isometries -> N = 256)
+constexpr int kChunkTiles = 16;   // accumulator tiles per work item
+
+size_t encode_workspace(const Geo &g, EncodeBufs *b, void *ws, size_t cap, bool *ok);
+
+// Launchers (each returns cudaGetLastError()).
+cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &b,
+                            cudaStream_t st);
+cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st);
+cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs &b,
+                              const int32_t *list, const int32_t *list_count, int n_list_max,
+                              const fic_codes &out, cudaStream_t st);
+cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st);
+cudaError_t launch_match_tc(const Geo &g, const EncodeBufs &b, int num_sms, cudaStream_t st);
+cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b,
+                          const fic_codes &out, cudaStream_t st);
+cudaError_t launch_info(const EncodeBufs &b, fic_encode_info *info, cudaStream_t st);
+
+// decode
+cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,
+                               cudaStream_t st);
+cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st);
+
+}  // namespace fic

@@ -1,0 +1,102 @@
+"""The C ABI library builds, loads without a GPU, exports every entry point include/fic.h
+declares, and rejects bad arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import dbc
+from paper_1206_4880_gb300 import fic
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fic.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fic_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fic.load()
+    names = _declared()
+    assert {"fic_classify", "fic_build_pools", "fic_encode", "fic_decode",
+            "fic_decode_backward"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(fic.SIGNATURES)
+
+
+def test_log2_table_is_correctly_rounded():
+    lib = fic.load()
+    for n in range(1, 513):
+        assert lib.fic_debug_log2(n) == dbc.log2_cr(n), n
+
+
+def _ws_size(H, W, **kw):
+    p = fic.EncodeParams(**kw).c()
+    g = fic.geom(H, W)
+    return fic.load().fic_encode_workspace_size(ctypes.byref(g), ctypes.byref(p))
+
+
+def test_workspace_size_and_validation():
+    assert _ws_size(256, 256, domain_stride=8, num_classes=8) > 0
+    assert _ws_size(1024, 1024, domain_stride=4, num_classes=16) > _ws_size(256, 256)
+    for kw in ({"domain_stride": 0}, {"num_classes": 0}, {"num_classes": 256},
+               {"block": 16}, {"s_max": 0.5}, {"half_width": -2}):
+        assert _ws_size(64, 64, **kw) == 0, kw
+    assert _ws_size(12, 64) == 0 and _ws_size(64, 60) == 0 and _ws_size(8, 64) == 0
+
+
+def test_encode_rejects_before_any_launch():
+    lib = fic.load()
+    p = fic.EncodeParams(domain_stride=4, num_classes=8).c()
+    g = fic.geom(64, 64)
+    codes = fic.Codes(*(ctypes.c_void_p(0x1000) for _ in range(5)))
+    # null workspace
+    st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g), ctypes.byref(p),
+                        ctypes.byref(codes), None, None, 0, None)
+    assert st == fic.FIC_ERR_WORKSPACE and b"workspace" in lib.fic_last_error()
+    # misaligned workspace
+    st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g), ctypes.byref(p),
+                        ctypes.byref(codes), None, ctypes.c_void_p(0x1008), 1 << 30, None)
+    assert st == fic.FIC_ERR_WORKSPACE
+    # too small
+    st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g), ctypes.byref(p),
+                        ctypes.byref(codes), None, ctypes.c_void_p(0x1000), 1024, None)
+    assert st == fic.FIC_ERR_WORKSPACE
+    # bad geometry
+    g2 = fic.geom(60, 64)
+    st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g2), ctypes.byref(p),
+                        ctypes.byref(codes), None, ctypes.c_void_p(0x1000), 1 << 30, None)
+    assert st == fic.FIC_ERR_INVALID_ARG
+    # null code pointer
+    codes_bad = fic.Codes(None, None, None, None, None)
+    st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g), ctypes.byref(p),
+                        ctypes.byref(codes_bad), None, ctypes.c_void_p(0x1000), 1 << 30, None)
+    assert st == fic.FIC_ERR_INVALID_ARG
+
+
+def test_decode_rejects_bad_arguments():
+    lib = fic.load()
+    p = fic.EncodeParams(domain_stride=4).c()
+    g = fic.geom(64, 64)
+    codes = fic.Codes(*(ctypes.c_void_p(0x1000) for _ in range(5)))
+    assert lib.fic_decode_workspace_size(ctypes.byref(g), ctypes.byref(p), -1, 1) == 0
+    st = lib.fic_decode(ctypes.byref(codes), ctypes.byref(g), ctypes.byref(p), -1, None,
+                        ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000), 1 << 20, None)
+    assert st == fic.FIC_ERR_INVALID_ARG
+    st = lib.fic_decode_backward(ctypes.byref(codes), ctypes.byref(g), ctypes.byref(p), 4, 0,
+                                 None, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000),
+                                 ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000), 1 << 20, None)
+    assert st == fic.FIC_ERR_INVALID_ARG
+
+
+def test_no_cpu_fallback_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    img = torch.zeros(64, 64, dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        fic.encode(img, fic.EncodeParams())

@@ -1,0 +1,124 @@
+"""GPU parity of decoding and of its adjoint against the FP64 CPU oracle, through the C ABI.
+
+Bars: decoded PSNR within 0.01 dB of the oracle's; iterates within 2e-3 absolute (FP32 against
+FP64 over <= 8 contractive steps of values in [0, 255]); gradients within 1e-4 relative of the
+oracle's FP64 adjoint and of FP64 central finite differences (h = 1e-4).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import decode as odec
+from oracle import match as omatch
+from paper_1206_4880_gb300 import fic, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _codes_gpu(c):
+    return {"dom": torch.from_numpy(np.asarray(c["dom"], np.int32)).cuda(),
+            "iso": torch.from_numpy(np.asarray(c["iso"], np.int32)).cuda(),
+            "s": torch.from_numpy(np.asarray(c["s"], np.float64)).cuda(),
+            "o": torch.from_numpy(np.asarray(c["o"], np.float64)).cuda()}
+
+
+@pytest.fixture(scope="module")
+def pr1_codes():
+    img = synth.pr1_image()
+    return img, omatch.encode(img, B=8, sigma=8, K=8, n_threads=8)
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 5, 8])
+def test_decode_parity(pr1_codes, iters):
+    img, codes = pr1_codes
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    x = fic.decode(_codes_gpu(codes), 256, 256, p, iters)
+    torch.cuda.synchronize()
+    ref = odec.decode(codes, 256, 256, 8, 8, iters)
+    assert np.max(np.abs(x.cpu().numpy() - ref)) <= 2e-3
+    if iters >= 5:
+        pg = odec.psnr(odec.to_u8(x.cpu().numpy().astype(np.float64)), img)
+        po = odec.psnr(odec.to_u8(ref), img)
+        assert abs(pg - po) <= 0.01
+
+
+def test_decode_from_given_start(pr1_codes):
+    img, codes = pr1_codes
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    x0 = np.random.default_rng(0).uniform(0, 255, (256, 256)).astype(np.float32)
+    for iters in (1, 4):
+        x = fic.decode(_codes_gpu(codes), 256, 256, p, iters, x0=torch.from_numpy(x0).cuda())
+        torch.cuda.synchronize()
+        ref = odec.decode(codes, 256, 256, 8, 8, iters, x0=x0.astype(np.float64))
+        assert np.max(np.abs(x.cpu().numpy() - ref)) <= 2e-3
+
+
+@pytest.mark.parametrize("sigma", [8, 4, 3])
+def test_adjoint_parity(sigma):
+    H, W, iters = 64, 96, 6
+    img = synth.fbm_image(90 + sigma, H, W)
+    codes = omatch.encode(img, B=8, sigma=sigma, K=6, n_threads=8)
+    g = np.random.default_rng(sigma).normal(size=(H, W))
+    gs_ref, go_ref = odec.decode_adjoint(codes, H, W, 8, sigma, iters, g)
+    p = fic.EncodeParams(domain_stride=sigma, num_classes=6)
+    outs = []
+    for ck in (1, 2, 4, 6):
+        gs, go = fic.decode_backward(_codes_gpu(codes), H, W, p, iters, ck,
+                                     torch.from_numpy(g.astype(np.float32)).cuda())
+        torch.cuda.synchronize()
+        outs.append((gs.cpu().numpy(), go.cpu().numpy()))
+    for gs, go in outs:
+        assert np.array_equal(gs, outs[0][0]) and np.array_equal(go, outs[0][1])
+    gs, go = outs[0]
+    for a, b in ((gs, gs_ref), (go, go_ref)):
+        scale = np.max(np.abs(b))
+        assert np.max(np.abs(a - b)) <= 1e-4 * scale
+
+
+def test_adjoint_512_against_finite_differences():
+    """The 512x512 differentiation workload: 8 iterations from mid-grey, checkpoints every 2."""
+    img = synth.diff_image()
+    H = W = 512
+    iters = 8
+    codes = omatch.encode(img, B=8, sigma=8, K=16, n_threads=8)
+    cg = _codes_gpu(codes)
+    p = fic.EncodeParams(domain_stride=8, num_classes=16)
+    base = {k: np.asarray(codes[k], np.float64 if k in ("s", "o") else np.int64)
+            for k in ("dom", "iso", "s", "o")}
+    I = img.astype(np.float64)
+    # L = 0.5 * ||x_K - I||^2 ; dL/dx_K = x_K - I, with x_K the FP64 iterate the finite
+    # differences below differentiate
+    grad_out = torch.from_numpy((odec.decode(base, H, W, 8, 8, iters) - I).astype(np.float32)).cuda()
+    gs, go = fic.decode_backward(cg, H, W, p, iters, 2, grad_out)
+    torch.cuda.synchronize()
+    gs, go = gs.cpu().numpy(), go.cpu().numpy()
+    h = 1e-4
+
+    def loss(c):
+        x = odec.decode(c, H, W, 8, 8, iters)
+        return 0.5 * np.sum((x - I) ** 2)
+
+    rng = np.random.default_rng(4000)
+    for r in rng.choice(gs.size, 3, replace=False):
+        for key, grad in (("s", gs), ("o", go)):
+            cp = {k: v.copy() for k, v in base.items()}
+            cm = {k: v.copy() for k, v in base.items()}
+            cp[key][r] += h
+            cm[key][r] -= h
+            fd = (loss(cp) - loss(cm)) / (2 * h)
+            assert abs(grad[r] - fd) <= 1e-4 * max(abs(fd), 1.0), (key, r, grad[r], fd)
+
+
+def test_autograd_function(pr1_codes):
+    img, codes = pr1_codes
+    cg = _codes_gpu(codes)
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    s = cg["s"].clone().requires_grad_(True)
+    o = cg["o"].clone().requires_grad_(True)
+    x = fic.Decode.apply(s, o, cg["dom"], cg["iso"], 256, 256, p, 4, 2)
+    target = torch.from_numpy(img.astype(np.float32)).cuda()
+    loss = 0.5 * torch.sum((x - target) ** 2)
+    loss.backward()
+    gs, go = fic.decode_backward(cg, 256, 256, p, 4, 2, (x - target).detach())
+    torch.cuda.synchronize()
+    assert torch.allclose(s.grad.float(), gs) and torch.allclose(o.grad.float(), go)

@@ -1,0 +1,203 @@
+"""GPU parity of classification, pools and encoding against the CPU oracle, through the C ABI.
+
+Bars: block moments, box counts, FD bit patterns and classes bit-exact; pool orders and windows
+exact; chosen (domain, isometry) identical; s and o within 1e-6 (they are formed from the same
+exact integers, so in practice equal); sse within 1e-9 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dbc as odbc
+from oracle import match as omatch
+from oracle import pools as opools
+from paper_1206_4880_gb300 import fic, synth
+
+pytestmark = pytest.mark.gpu
+
+ENGINES = ["simt", "tensor"]
+
+# (H, W, sigma, K, w, seed): small ragged cases spanning several tensor tiles, odd strides
+SMALL = [
+    (32, 32, 1, 3, -1, 11),
+    (24, 40, 2, 4, 0, 12),
+    (64, 48, 3, 5, 1, 13),
+    (136, 200, 4, 7, -1, 14),
+    (96, 128, 8, 1, -1, 15),
+    (128, 96, 5, 16, 2, 16),
+    (256, 256, 8, 8, -1, 1000),
+]
+
+
+def _img(H, W, seed):
+    return synth.pr1_image() if seed == 1000 else synth.fbm_image(seed, H, W)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _params(sigma, K, w, engine="simt"):
+    return fic.EncodeParams(domain_stride=sigma, num_classes=K, half_width=w, engine=engine)
+
+
+def _need_tensor(engine):
+    if engine == "tensor":
+        major, minor = torch.cuda.get_device_capability()
+        if (major, minor) != (10, 3):
+            pytest.skip("tensor engine needs sm_103")
+        assert fic.engine_available("tensor"), "tensor engine missing on an sm_103 device"
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_classify_bit_exact(case):
+    H, W, sigma, K, w, seed = case
+    img = _img(H, W, seed)
+    st = fic.classify(_t(img), _params(sigma, K, w))
+    torch.cuda.synchronize()
+    cls = omatch.classify_image(img, 8, sigma, K)
+    g = {k: v.cpu().numpy() for k, v in st.items()}
+    assert np.array_equal(g["range_sum"], cls["range_sum"])
+    assert np.array_equal(g["range_sumsq"], cls["range_sumsq"])
+    assert np.array_equal(g["dom_sum"], cls["dom_sum"])
+    assert np.array_equal(g["dom_sumsq"], cls["dom_sumsq"])
+    assert np.array_equal(g["range_counts"], cls["range_counts"])
+    assert np.array_equal(g["dom_counts"], cls["dom_counts"])
+    assert np.array_equal(g["range_fd"].view(np.int64), cls["range_fd"].view(np.int64))
+    assert np.array_equal(g["dom_fd"].view(np.int64), cls["dom_fd"].view(np.int64))
+    assert g["fd_extent"][0] == cls["F_l"] and g["fd_extent"][1] == cls["F_m"]
+    assert np.array_equal(g["range_bin"], cls["range_bin"])
+    assert np.array_equal(g["dom_bin"], cls["dom_bin"])
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_pools_exact(case):
+    H, W, sigma, K, w, seed = case
+    img = _img(H, W, seed)
+    p = _params(sigma, K, w)
+    st = fic.classify(_t(img), p)
+    po = fic.build_pools(st, H, W, p)
+    torch.cuda.synchronize()
+    cls = omatch.classify_image(img, 8, sigma, K)
+    dom_order = po["dom_order"].cpu().numpy()
+    assert np.array_equal(dom_order, np.argsort(cls["dom_bin"], kind="stable"))
+    assert np.array_equal(po["range_order"].cpu().numpy(), np.argsort(cls["range_bin"], kind="stable"))
+    bo = np.concatenate([[0], np.cumsum(np.bincount(cls["dom_bin"], minlength=K))])
+    assert np.array_equal(po["bin_off"].cpu().numpy(), bo)
+    ww = odbc.default_half_width(K) if w < 0 else w
+    lo, hi = po["win_lo"].cpu().numpy(), po["win_hi"].cpu().numpy()
+    for r in range(lo.size):
+        pool = opools.class_pool(cls["range_bin"][r], cls["dom_bin"], ww)
+        assert np.array_equal(np.sort(dom_order[lo[r]:hi[r]]), pool), r
+
+
+def _compare_codes(gpu, ref, idx=None):
+    idx = np.arange(gpu["dom"].numel()) if idx is None else np.asarray(idx)
+    g = {k: v.cpu().numpy()[idx] for k, v in gpu.items()}
+    bad = np.nonzero((g["dom"] != ref["dom"]) | (g["iso"] != ref["iso"]))[0]
+    assert bad.size == 0, f"{bad.size} codes differ, first ranges {idx[bad[:8]]}: gpu " \
+        f"{list(zip(g['dom'][bad[:4]], g['iso'][bad[:4]], g['sse'][bad[:4]]))} ref " \
+        f"{list(zip(ref['dom'][bad[:4]], ref['iso'][bad[:4]], ref['sse'][bad[:4]]))}"
+    assert np.max(np.abs(g["s"] - ref["s"])) <= 1e-6
+    assert np.max(np.abs(g["o"] - ref["o"])) <= 1e-6
+    assert np.all(np.abs(g["sse"] - ref["sse"]) <= 1e-9 * np.maximum(1.0, ref["sse"]))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("case", SMALL)
+def test_encode_parity_small(case, engine):
+    _need_tensor(engine)
+    H, W, sigma, K, w, seed = case
+    img = _img(H, W, seed)
+    info = fic.new_info("cuda")
+    codes = fic.encode(_t(img), _params(sigma, K, w, engine), info=info)
+    torch.cuda.synchronize()
+    ref = omatch.encode(img, B=8, sigma=sigma, K=K, w=None if w < 0 else w, n_threads=8)
+    _compare_codes(codes, ref)
+    rep = fic.read_info(info)
+    assert rep["matches"] == int(ref["pool_size"].sum()) * 8
+    assert rep["device_error"] == 0
+    if engine == "tensor":
+        # the ranking must certify nearly every range by itself; a broken contraction would
+        # push them all to the exact re-search and still pass the code comparison
+        assert rep["fallback_ranges"] <= max(4, codes["dom"].numel() // 20), rep
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_encode_flat_and_edge_images(engine):
+    _need_tensor(engine)
+    cases = [np.full((48, 64), 200, np.uint8), np.zeros((32, 32), np.uint8)]
+    img = synth.fbm_image(77, 96, 96)
+    img[8:72, 16:64] = 31  # a large flat rectangle: flat ranges and flat (Q = 0) domains
+    cases.append(img)
+    chk = ((np.indices((64, 64)).sum(axis=0) % 2) * 255).astype(np.uint8)  # extreme values
+    cases.append(chk)
+    for im in cases:
+        H, W = im.shape
+        for K, sigma in ((4, 2), (1, 4), (255, 8)):
+            codes = fic.encode(_t(im), _params(sigma, K, -1, engine))
+            torch.cuda.synchronize()
+            ref = omatch.encode(im, B=8, sigma=sigma, K=K, n_threads=8)
+            _compare_codes(codes, ref)
+
+
+def test_encode_padded_pitch():
+    img = synth.fbm_image(21, 64, 80)
+    big = np.zeros((64, 96), np.uint8)
+    big[:, :80] = img
+    t = _t(big)[:, :80]
+    assert t.stride(0) == 96
+    codes = fic.encode(t, _params(4, 6, -1))
+    torch.cuda.synchronize()
+    ref = omatch.encode(img, B=8, sigma=4, K=6, n_threads=8)
+    _compare_codes(codes, ref)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_encode_deterministic(engine):
+    _need_tensor(engine)
+    img = _t(synth.fbm_image(3, 256, 192))
+    p = _params(4, 16, -1, engine)
+    a = fic.encode(img, p)
+    b = fic.encode(img, p)
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_encode_1024_sampled(engine):
+    """The 1024x1024, stride-4, K=16 workload at full size, in the bench's launch
+    configuration: classification bit-exact everywhere, codes on a seeded range sample."""
+    _need_tensor(engine)
+    img = synth.image_1024()
+    p = _params(4, 16, -1, engine)
+    info = fic.new_info("cuda")
+    codes = fic.encode(_t(img), p, info=info)
+    st = fic.classify(_t(img), p)
+    torch.cuda.synchronize()
+    cls = omatch.classify_image(img, 8, 4, 16)
+    assert np.array_equal(st["range_bin"].cpu().numpy(), cls["range_bin"])
+    assert np.array_equal(st["dom_bin"].cpu().numpy(), cls["dom_bin"])
+    rng = np.random.default_rng(2000)
+    R = 128 * 128
+    sample = np.unique(np.concatenate([[0, R - 1, 127, R - 128], rng.choice(R, 60, replace=False)]))
+    ref = omatch.encode(img, B=8, sigma=4, K=16, range_ids=sample, n_threads=8, cls=cls)
+    _compare_codes(codes, ref, sample)
+    rep = fic.read_info(info)
+    ww = odbc.default_half_width(16)
+    total = sum(opools.class_pool(b, cls["dom_bin"], ww).size for b in cls["range_bin"])
+    assert rep["matches"] == total * 8
+    assert rep["device_error"] == 0
+    if engine == "tensor":
+        assert rep["fallback_ranges"] <= R // 50, rep
+
+
+def test_full_search_simt_equals_k1_tensor():
+    _need_tensor("tensor")
+    img = _t(synth.fbm_image(8, 192, 256))
+    a = fic.encode(img, _params(4, 1, -1, "simt"))
+    b = fic.encode(img, _params(4, 1, -1, "tensor"))
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
