@@ -136,6 +136,7 @@ size_t encode_workspace(const Geo &g, EncodeBufs *b, void *ws, size_t cap, bool 
     b->n_chunks = c.take<int32_t>(b->n_mtiles);
     b->cand = c.take<unsigned long long>((size_t)b->R_pad * b->max_chunks * 2);
     b->fallback = c.take<int32_t>(g.R);
+    b->fb_best = c.take<FallbackBest>(g.R);
     b->counters = c.take<int32_t>(8);
     b->matches = c.take<long long>(1);
     if (ok) *ok = c.ok;
@@ -270,7 +271,7 @@ fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *
     FIC_TRY(mark(2), "event");
     if (p->engine == FIC_ENGINE_SIMT) {
         FIC_TRY(mark(3), "event");
-        FIC_TRY(launch_match_simt(img, g, b, nullptr, nullptr, 0, *out, st), "match_simt");
+        FIC_TRY(launch_match_simt(img, g, b, *out, st), "match_simt");
         FIC_TRY(mark(4), "event");
         FIC_TRY(mark(5), "event");
     } else {
@@ -282,7 +283,7 @@ fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *
         FIC_TRY(mark(4), "event");
         FIC_TRY(launch_reeval(img, g, b, *out, st), "reeval");
         FIC_TRY(mark(5), "event");
-        FIC_TRY(launch_match_simt(img, g, b, b.fallback, b.counters, g.R, *out, st), "fallback");
+        FIC_TRY(launch_rescan(img, g, b, *out, sms, st), "rescan");
     }
     FIC_TRY(mark(6), "event");
     if (info) FIC_TRY(launch_info(b, info, st), "info");

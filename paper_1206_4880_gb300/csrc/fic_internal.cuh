@@ -105,6 +105,12 @@ __device__ __forceinline__ void finalize_code(int n, long long A, long long Bs, 
     sse = __ddiv_rn((double)num, __dmul_rn(__dmul_rn(16.0, (double)n), (double)g.den));
 }
 
+// Exact best of the evaluated candidates of a range the ranking could not certify.
+struct FallbackBest {
+    long long num, den, P, Q;
+    int d, t, C, pad;
+};
+
 // ----------------------------------------------------------------------------------------
 // Workspace carving.
 struct Carver {
@@ -147,7 +153,8 @@ struct EncodeBufs {
     int4 *tile_win;        // [n_mtiles] union (x, y) and intersection (z, w) of row windows
     int32_t *n_chunks;     // [n_mtiles] domain chunks per range tile
     unsigned long long *cand;  // [R_pad][max_chunks][2] ranking keys
-    int32_t *fallback;     // [R] ranges to re-search exactly
+    int32_t *fallback;     // [R] class-sorted positions of ranges to re-search exactly
+    FallbackBest *fb_best; // [R] their exact best evaluated candidate
     int32_t *counters;     // [8] device counters (fallback count, work items, ...)
     long long *matches;    // [1]
     int R_pad, Dn_pad, Dn_aux, n_mtiles, max_chunks, max_items, sort_blocks_dom, sort_blocks_rng;
@@ -165,8 +172,9 @@ cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &
                             cudaStream_t st);
 cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st);
 cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs &b,
-                              const int32_t *list, const int32_t *list_count, int n_list_max,
                               const fic_codes &out, cudaStream_t st);
+cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const fic_codes &out,
+                          int num_sms, cudaStream_t st);
 cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st);
 cudaError_t launch_match_tc(const Geo &g, const EncodeBufs &b, int num_sms, cudaStream_t st);
 cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b,

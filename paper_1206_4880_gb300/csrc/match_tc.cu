@@ -501,9 +501,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // chunks, evaluates both candidates under all 8 isometries exactly, keeps the best (gain, then
 // smaller domain id, then smaller isometry) and certifies it: every other domain's FP32 score is
 // at most the runner-up's, and an FP32 score differs from that domain's exact gain / 8 by less
-// than a relative 2^-19 (it is formed from exact integers and 24-bit constants by a handful of
-// single-rounding operations), so if runner-up * (1 + 2^-12) < exact best, no other domain can
-// win or tie.
+// than a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
+// of single-rounding operations), so if runner-up * (1 + 2^-16) < exact best, no other domain
+// can win or tie. Otherwise the range is queued with its exact best for k_rescan.
 // Otherwise the range goes to the exact re-search list. Flat ranges (n Bs = A^2) have zero error
 // for every candidate; their code is the smallest domain id of the pool with t = 0.
 __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
@@ -512,7 +512,7 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
                          const int32_t *__restrict__ bin_off, const uint8_t *__restrict__ rbin,
                          const int4 *__restrict__ rng_info, const int4 *__restrict__ tile_win,
                          const unsigned long long *__restrict__ cand, int max_chunks, int32_t *__restrict__ fallback,
-                         int32_t *counters, fic_codes out) {
+                         FallbackBest *__restrict__ fb_best, int32_t *counters, fic_codes out) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= g.R) return;
@@ -612,11 +612,21 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     if (certified && b2 != 0) {
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
         const double g8 = (double)gg.num / (8.0 * (double)gg.den);
-        certified = u2 * (1.0 + 1.0 / 4096.0) < g8;
+        certified = u2 * (1.0 + 1.0 / 65536.0) < g8;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
-        fallback[slot] = r;
+        fallback[slot] = i;
+        FallbackBest fb;
+        fb.num = gg.num;
+        fb.den = gg.den;
+        fb.P = P;
+        fb.Q = Q;
+        fb.d = d;
+        fb.t = bt;
+        fb.C = (int)C;
+        fb.pad = 0;
+        fb_best[slot] = fb;
         return;
     }
     double s, o, sse;
@@ -708,7 +718,7 @@ cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b,
     const long long threads = (long long)g.R * 32;
     k_reeval<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
         g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, b.range_bin, b.rng_info,
-        b.tile_win, b.cand, b.max_chunks, b.fallback, b.counters, out);
+        b.tile_win, b.cand, b.max_chunks, b.fallback, b.fb_best, b.counters, out);
     ++g_launches;
     return cudaGetLastError();
 }

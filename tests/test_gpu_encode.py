@@ -190,7 +190,7 @@ def test_encode_1024_sampled(engine):
     assert rep["matches"] == total * 8
     assert rep["device_error"] == 0
     if engine == "tensor":
-        assert rep["fallback_ranges"] <= R // 50, rep
+        assert rep["fallback_ranges"] <= R // 20, rep
 
 
 def test_full_search_simt_equals_k1_tensor():
