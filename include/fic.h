@@ -176,6 +176,24 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *g, const 
 fic_status fic_profile_enable(int32_t on);
 fic_status fic_profile_read(float *ms, int32_t n, int32_t *launches);
 
+/* Largest image (pixels) fic_decode_static accepts: 1024 x 1024. */
+#define FIC_DECODE_STATIC_MAX_PIXELS (1 << 20)
+
+/* fic_decode without any allocation. The paper has no counterpart: this is an interface for
+ * callers that cannot call cudaMalloc (applications that reserve all device memory up front and
+ * give libraries only the buffers they need, and latency-critical loops where an allocation
+ * could block on or synchronise the device), who therefore cannot supply fic_decode's
+ * workspace. It computes exactly what fic_decode computes (same arguments, no workspace) using
+ * a fixed scratch image of FIC_DECODE_STATIC_MAX_PIXELS floats (4 MiB) kept in the library's
+ * device memory, which every GPU that loads the library holds until the process exits. Images
+ * with more pixels return FIC_ERR_INVALID_ARG. The first call made with a given device current
+ * looks up the scratch's device address (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture. All calls share the one scratch image: calls whose GPU work
+ * overlaps (different streams, concurrent host threads) race on it and must be ordered by the
+ * caller. x0 and out must not alias each other. */
+fic_status fic_decode_static(const fic_codes *codes, const fic_geom *g, const fic_params *p,
+                             int32_t iters, const float *x0, float *out, void *stream);
+
 /* 1 if `engine` (FIC_ENGINE_*) can run on the current device with this build, else 0. */
 int32_t fic_engine_available(int32_t engine);
 

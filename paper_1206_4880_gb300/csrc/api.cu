@@ -94,6 +94,9 @@ namespace fic {
 
 thread_local int g_launches = 0;
 
+// Sets the message fic_last_error() returns on this thread.
+void set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 size_t encode_workspace(const Geo &g, EncodeBufs *b, void *ws, size_t cap, bool *ok) {
     Carver c(ws, cap);
     b->R_pad = (g.R + kTileM - 1) / kTileM * kTileM;

@@ -1,0 +1,120 @@
+// fic_decode_static: decoding that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: applications that reserve all device memory up front and
+// hand libraries only the buffers they need (engines and media frameworks that own the memory
+// budget), and latency-critical loops in which an allocation could block on, or synchronise,
+// the device. fic_decode needs one image of scratch besides its output (the second buffer of the
+// Jacobi iteration), which those callers cannot provide on demand. This variant keeps that
+// scratch in a fixed array in the library's device memory instead: every GPU that loads the
+// library holds the array (kStaticDecodeMaxPixels floats, 4 MiB) until the process exits.
+//
+// The array's device address is looked up once per device (cudaGetSymbolAddress, with that
+// device current) on the first call made with that device current; host code must not use the
+// array's name directly, which on the host only names a stand-in, not device memory. Every call
+// shares the one array and leaves its last contents behind: nothing here reads scratch that the
+// same call has not written first, and calls whose GPU work overlaps (other streams, other host
+// threads) race on it.
+#include <cstdio>
+#include <mutex>
+
+#include "fic_internal.cuh"
+
+namespace fic {
+
+void set_error(const char *msg);
+
+constexpr size_t kStaticDecodeMaxPixels = (size_t)FIC_DECODE_STATIC_MAX_PIXELS;
+
+static __device__ __align__(256) float g_decode_scratch[kStaticDecodeMaxPixels];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+float *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_decode_scratch on the current device (looked up once per device).
+cudaError_t scratch_for_current_device(float **ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_decode_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<float *>(p);
+    }
+    *ptr = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+}  // namespace fic
+
+extern "C" fic_status fic_decode_static(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
+                                        int32_t iters, const float *x0, float *out, void *stream) {
+    using namespace fic;
+    // geometry and parameters are validated by the same checks as fic_decode's workspace query
+    if (fic_decode_workspace_size(gm, p, iters < 0 ? 0 : iters, 1) == 0) return FIC_ERR_INVALID_ARG;
+    if (!codes || !codes->dom || !codes->iso || !codes->s || !codes->o || !out || iters < 0) {
+        set_error("fic_decode_static: null code or output pointer, or negative iters");
+        return FIC_ERR_INVALID_ARG;
+    }
+    const size_t img = (size_t)gm->H * gm->W;
+    if (img > kStaticDecodeMaxPixels) {
+        char msg[160];
+        snprintf(msg, sizeof(msg),
+                 "fic_decode_static: %d x %d = %zu pixels exceeds the fixed scratch of %zu pixels; "
+                 "use fic_decode with a workspace",
+                 gm->H, gm->W, img, kStaticDecodeMaxPixels);
+        set_error(msg);
+        return FIC_ERR_INVALID_ARG;
+    }
+    Geo g;
+    g.H = gm->H;
+    g.W = gm->W;
+    g.pitch = gm->pitch;
+    g.B = p->block;
+    g.n = g.B * g.B;
+    g.sigma = p->domain_stride;
+    g.nRy = g.H / g.B;
+    g.nRx = g.W / g.B;
+    g.R = g.nRy * g.nRx;
+    g.nDy = (g.H - 2 * g.B) / g.sigma + 1;
+    g.nDx = (g.W - 2 * g.B) / g.sigma + 1;
+    g.Dn = g.nDy * g.nDx;
+    g.K = p->num_classes;
+    g.w = p->half_width < 0 ? p->num_classes / 3 : p->half_width;
+
+    float *tmp = nullptr;
+    cudaError_t e = scratch_for_current_device(&tmp);
+    if (e != cudaSuccess) {
+        set_error(cudaGetErrorString(e));
+        return FIC_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (iters == 0) {
+        e = x0 ? cudaMemcpyAsync(out, x0, img * sizeof(float), cudaMemcpyDeviceToDevice, st)
+               : launch_fill(out, img, 128.f, st);
+    } else {
+        // step k writes `out` when (iters - 1 - k) is even, the scratch otherwise, so the last
+        // iterate lands in `out`; with no x0 the start image (128) goes where step 0 reads
+        const float *cur = x0;
+        if (!x0) {
+            float *init = ((iters - 1) % 2 == 0) ? tmp : out;
+            e = launch_fill(init, img, 128.f, st);
+            cur = init;
+        }
+        for (int k = 0; k < iters && e == cudaSuccess; ++k) {
+            float *dst = ((iters - 1 - k) % 2 == 0) ? out : tmp;
+            e = launch_decode_step(*codes, g, cur, dst, st);
+            cur = dst;
+        }
+    }
+    if (e != cudaSuccess) {
+        set_error(cudaGetErrorString(e));
+        return FIC_ERR_CUDA;
+    }
+    return FIC_OK;
+}

@@ -62,6 +62,7 @@ SIGNATURES = {
                                     c_size, c_vp]),
     "fic_profile_enable": (c_i32, [c_i32]),
     "fic_profile_read": (c_i32, [c_vp, c_i32, c_vp]),
+    "fic_decode_static": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "fic_engine_available": (c_i32, [c_i32]),
     "fic_last_error": (ctypes.c_char_p, []),
     "fic_version": (c_i32, []),
@@ -266,6 +267,23 @@ def decode(codes: dict, H: int, W: int, p: EncodeParams, iters: int, x0=None, ou
     g, pc = geom(H, W), p.c()
     _check(load().fic_decode(ctypes.byref(cs), ctypes.byref(g), ctypes.byref(pc), iters, _p(x0),
                              _p(out), _p(workspace), workspace.numel(), _stream(stream)))
+    return out
+
+
+DECODE_STATIC_MAX_PIXELS = 1 << 20
+
+
+def decode_static(codes: dict, H: int, W: int, p: EncodeParams, iters: int, x0=None, out=None,
+                  stream=None) -> torch.Tensor:
+    """fic_decode_static: the same decode with no workspace (the library's fixed scratch image,
+    at most DECODE_STATIC_MAX_PIXELS pixels)."""
+    dev = codes["dom"].device
+    if out is None:
+        out = torch.empty(H, W, dtype=torch.float32, device=dev)
+    cs = _codes_struct(codes)
+    g, pc = geom(H, W), p.c()
+    _check(load().fic_decode_static(ctypes.byref(cs), ctypes.byref(g), ctypes.byref(pc), iters,
+                                    _p(x0), _p(out), _stream(stream)))
     return out
 
 
