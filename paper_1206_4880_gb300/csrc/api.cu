@@ -137,7 +137,7 @@ size_t encode_workspace(const Geo &g, EncodeBufs *b, void *ws, size_t cap, bool 
     b->work = c.take<int4>(b->max_items);
     b->tile_win = c.take<int4>(b->n_mtiles);
     b->n_chunks = c.take<int32_t>(b->n_mtiles);
-    b->cand = c.take<unsigned long long>((size_t)b->R_pad * b->max_chunks * 2);
+    b->cand = c.take<unsigned long long>((size_t)b->R_pad * b->max_chunks * 4);
     b->fallback = c.take<int32_t>(g.R);
     b->fb_best = c.take<FallbackBest>(g.R);
     b->counters = c.take<int32_t>(8);

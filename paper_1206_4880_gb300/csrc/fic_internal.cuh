@@ -152,7 +152,7 @@ struct EncodeBufs {
     int4 *work;            // [max_items] (m_tile, first domain pos, end domain pos, chunk)
     int4 *tile_win;        // [n_mtiles] union (x, y) and intersection (z, w) of row windows
     int32_t *n_chunks;     // [n_mtiles] domain chunks per range tile
-    unsigned long long *cand;  // [R_pad][max_chunks][2] ranking keys
+    unsigned long long *cand;  // [R_pad][max_chunks][2 column halves][2] ranking keys
     int32_t *fallback;     // [R] class-sorted positions of ranges to re-search exactly
     FallbackBest *fb_best; // [R] their exact best evaluated candidate
     int32_t *counters;     // [8] device counters (fallback count, work items, ...)

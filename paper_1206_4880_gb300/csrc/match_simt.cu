@@ -182,7 +182,9 @@ __global__ void __launch_bounds__(kSimtThreads)
         const int4 tw = tile_win[i / kTileM];
         const int nch = tw.y > tw.x ? (tw.y - tw.x + chunk - 1) / chunk : 0;
         for (int c = 0; c < nch; ++c) {
-            const unsigned long long key = cand[((size_t)i * max_chunks + c) * 2];
+            const unsigned long long k0 = cand[(((size_t)i * max_chunks + c) * 2 + 0) * 2];
+            const unsigned long long k1 = cand[(((size_t)i * max_chunks + c) * 2 + 1) * 2];
+            const unsigned long long key = k0 > k1 ? k0 : k1;
             if (key == 0) continue;
             const double s1 = (double)__uint_as_float((uint32_t)(key >> 32));
             if (s1 * (1.0 + 1.0 / 65536.0) < thr) continue;

@@ -16,10 +16,11 @@
 // exactly in integers and certifies that no other domain can be better (else the range is
 // re-searched exactly on CUDA cores).
 //
-// Kernel shape: persistent, one CTA per SM, 6 warps: warp 0 issues TMA loads (A tile 128 x 64,
+// Kernel shape: persistent, one CTA per SM, 10 warps: warp 0 issues TMA loads (A tile 128 x 64,
 // B tiles 256 x 64, 128-byte swizzle, 4-stage ring), warp 1 owns TMEM (two 128 x 256 FP32
-// accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16, four per tile), warps 2-5
-// (one thread per TMEM lane = range row) drain the accumulators with tcgen05.ld. Every wait is
+// accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16, four per tile), warps 2-9
+// (one thread per TMEM lane = range row, two warps per row group, one per column half) drain the
+// accumulators with tcgen05.ld. Every wait is
 // bounded by a wall-clock limit; a timeout sets an error word, lets in-flight copies and MMAs
 // finish (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -48,7 +49,9 @@ constexpr int kStages = 4;
 constexpr int kTileN = 8 * kTileDom;     // 256 accumulator columns
 constexpr int kABytes = kTileM * 128;    // 128 rows x 64 fp16
 constexpr int kBBytes = kTileN * 128;    // 256 rows x 64 fp16
-constexpr int kTcThreads = 192;
+constexpr int kEpiWarps = 8;             // two per TMEM lane group, one per column half
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);
+constexpr int kChunkDom = kTileDom * kChunkTiles;
 constexpr int kTmemCols = 2 * kTileN;    // two accumulators
 constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16 (0), both K-major,
@@ -58,8 +61,9 @@ constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint
 struct TcShared {
     uint8_t A[2][kABytes];
     uint8_t B[kStages][kBBytes];
+    float4 aux[2][kChunkDom];  // per-domain constants of the current and next work item
     unsigned long long full_a[2], empty_a[2], full_b[kStages], empty_b[kStages], tfull[2],
-        tempty[2], drain;
+        tempty[2], aux_ready[2], drain;
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -154,27 +158,102 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
           "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Waits for this thread's tcgen05.ld results; naming the destination registers as operands keeps
+// the compiler from reading them before the wait.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
+                   "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]),
+                   "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]),
+                   "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 
 __device__ __forceinline__ float max8(const uint32_t *v) {
-    float a = fmaxf(__uint_as_float(v[0]), __uint_as_float(v[1]));
-    float b = fmaxf(__uint_as_float(v[2]), __uint_as_float(v[3]));
-    float c = fmaxf(__uint_as_float(v[4]), __uint_as_float(v[5]));
-    float d = fmaxf(__uint_as_float(v[6]), __uint_as_float(v[7]));
-    return fmaxf(fmaxf(a, b), fmaxf(c, d));
+    const float a = fmax3f(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
+    const float b = fmax3f(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5]));
+    return fmax3f(a, b, fmaxf(__uint_as_float(v[6]), __uint_as_float(v[7])));
 }
 __device__ __forceinline__ float min8(const uint32_t *v) {
-    float a = fminf(__uint_as_float(v[0]), __uint_as_float(v[1]));
-    float b = fminf(__uint_as_float(v[2]), __uint_as_float(v[3]));
-    float c = fminf(__uint_as_float(v[4]), __uint_as_float(v[5]));
-    float d = fminf(__uint_as_float(v[6]), __uint_as_float(v[7]));
-    return fminf(fminf(a, b), fminf(c, d));
+    const float a = fmin3f(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
+    const float b = fmin3f(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5]));
+    return fmin3f(a, b, fminf(__uint_as_float(v[6]), __uint_as_float(v[7])));
 }
 
 __device__ __forceinline__ void top2(unsigned long long &b1, unsigned long long &b2, unsigned long long k) {
     const unsigned long long lo = k < b1 ? k : b1;
     b1 = k > b1 ? k : b1;
     b2 = lo > b2 ? lo : b2;
+}
+__device__ __forceinline__ void top2u(uint32_t &b1, uint32_t &b2, uint32_t k) {
+    const uint32_t lo = min(k, b1);
+    b1 = max(k, b1);
+    b2 = max(b2, lo);
+}
+
+// Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
+// range row. Per domain: p = max_t |P_t| from the max and min correlation, the clamped
+// least-squares gain / 8 estimate g8 = 2 m^2 / Q + (p - m), m = min(p, Q/4), and a 32-bit key
+// (g8's bits with the low 4 replaced by 15 - local index); t1, t2 keep the two largest keys.
+// MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
+template <bool MASK>
+__device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, float A, int jh, int lo_r,
+                                         int hi_r, uint32_t &t1, uint32_t &t2) {
+    uint32_t va[32], vb[32];
+    tmem_ld32(taddr, va);
+    tmem_ld_wait(va);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (c < 3) {
+            if (c & 1)
+                tmem_ld32(taddr + (c + 1) * 32, va);
+            else
+                tmem_ld32(taddr + (c + 1) * 32, vb);
+        }
+        const uint32_t *cur = (c & 1) ? vb : va;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = 4 * c + q;
+            const float4 a = auxp[l];
+            const float xmax = max8(cur + 8 * q), xmin = min8(cur + 8 * q);
+            const float p = fmaxf(fmaf(-A, a.x, xmax), fmaf(A, a.x, -xmin));
+            const float mm = fminf(p, a.y);
+            const float g8 = fmaf(mm, mm * a.z, p - mm);
+            uint32_t key = (__float_as_uint(g8) & 0xFFFFFFF0u) | (uint32_t)(15 - l);
+            if (MASK) {
+                const int j = jh + l;
+                key = (j >= lo_r && j < hi_r) ? key : 0u;
+            }
+            top2u(t1, t2, key);
+        }
+        if (c < 3) {
+            if (c & 1)
+                tmem_ld_wait(va);
+            else
+                tmem_ld_wait(vb);
+        }
+    }
+}
+
+// Folds a half-tile key (local index in the low 4 bits) into the running 64-bit keys
+// (score bits << 32 | ~domain position).
+__device__ __forceinline__ void merge_half_key(unsigned long long &b1, unsigned long long &b2, uint32_t t, int jh) {
+    const int j = jh + 15 - (int)(t & 15u);
+    const unsigned long long k =
+        t ? (((unsigned long long)(t & 0xFFFFFFF0u) << 32) | (unsigned long long)(uint32_t)(~j)) : 0ull;
+    top2(b1, b2, k);
 }
 
 }  // namespace
@@ -330,7 +409,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&sh.full_a[s], 1);
             mbar_init(&sh.empty_a[s], 1);
             mbar_init(&sh.tfull[s], 1);
-            mbar_init(&sh.tempty[s], 4);
+            mbar_init(&sh.tempty[s], kEpiWarps);
+            mbar_init(&sh.aux_ready[s], 32 * kEpiWarps);
         }
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sh.full_b[s], 1);
@@ -418,14 +498,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
     } else {
-        // ---- epilogue: warps 2..5, one thread per accumulator row
-        const int lg = warp & 3;  // TMEM lane group this warp may access
+        // ---- epilogue: warps 2..9. Warp w reads TMEM lane group (w & 3) (range rows) and column
+        // half (w - 2) >> 2 of every accumulator tile (16 domains x 8 isometries).
+        const int ew = warp - 2;
+        const int lg = warp & 3;
+        const int half = ew >> 2;
         const int row = lg * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
-        uint32_t gt = 0;
+        const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(half * (kTileN / 2));
+        uint32_t gt = 0, li = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
             const int4 w = work[it];
+            const int nt = (w.z - w.y + kTileDom - 1) / kTileDom;
+            // per-domain constants of this item into shared memory (double-buffered by item parity;
+            // a thread reaches item li + 2 only after every thread has left item li)
+            const int ab = li & 1;
+            for (int k = ew * 32 + lane; k < nt * kTileDom; k += 32 * kEpiWarps)
+                sh.aux[ab][k] = __ldg(&dom_aux[w.y + k]);
+            mbar_arrive(&sh.aux_ready[ab]);
+            ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (li >> 1) & 1, abort_flag));
+            if (!ok) break;
             const int i = w.x * kTileM + row;
             const int4 ri = rng_info[i];
             const bool valid = i < R;
@@ -434,41 +526,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int4 tw = tile_win[w.x];
             const int f_lo = max(tw.z, w.y), f_hi = min(tw.w, w.z);  // columns valid for every row
             unsigned long long b1 = 0, b2 = 0;
-            const int nt = (w.z - w.y + kTileDom - 1) / kTileDom;
             for (int k = 0; k < nt; ++k, ++gt) {
                 const int acc = gt & 1;
                 ok = __all_sync(0xffffffffu, mbar_wait(&sh.tfull[acc], (gt >> 1) & 1, abort_flag));
                 if (!ok) break;
                 tc_fence_after();
-                const int jt = w.y + k * kTileDom;
-                const bool fast = jt >= f_lo && jt + kTileDom <= f_hi;
-#pragma unroll 1
-                for (int c = 0; c < kTileN / 32; ++c) {
-                    uint32_t v[32];
-                    tmem_ld32(tbase + acc * kTileN + c * 32, v);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = jt + c * 4 + q;
-                        const float4 aux = __ldg(&dom_aux[j]);
-                        const float xmax = max8(v + 8 * q), xmin = min8(v + 8 * q);
-                        const float p1 = fmaf(-A, aux.x, xmax);
-                        const float p2 = fmaf(A, aux.x, -xmin);
-                        const float p = fmaxf(p1, p2);
-                        const float mm = fminf(p, aux.y);
-                        const float g8 = fmaf(mm, mm * aux.z, p - mm);
-                        unsigned long long key =
-                            ((unsigned long long)__float_as_uint(g8) << 32) | (unsigned long long)(uint32_t)(~j);
-                        if (!fast && !(j >= lo_r && j < hi_r)) key = 0;
-                        top2(b1, b2, key);
-                    }
-                }
+                const int jh = w.y + k * kTileDom + half * (kTileDom / 2);
+                const float4 *auxp = &sh.aux[ab][k * kTileDom + half * (kTileDom / 2)];
+                const uint32_t taddr = tbase + acc * kTileN;
+                uint32_t t1 = 0, t2 = 0;
+                if (jh >= f_lo && jh + kTileDom / 2 <= f_hi)
+                    epi_half<false>(taddr, auxp, A, jh, lo_r, hi_r, t1, t2);
+                else
+                    epi_half<true>(taddr, auxp, A, jh, lo_r, hi_r, t1, t2);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh.tempty[acc]);
+                merge_half_key(b1, b2, t1, jh);
+                merge_half_key(b1, b2, t2, jh);
             }
             if (ok && valid) {
-                unsigned long long *dst = cand + ((size_t)i * max_chunks + w.w) * 2;
+                unsigned long long *dst = cand + (((size_t)i * max_chunks + w.w) * 2 + half) * 2;
                 dst[0] = b1;
                 dst[1] = b2;
             }
@@ -555,10 +633,7 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     const int chunk = kTileDom * kChunkTiles;
     const int nch = tw.y > tw.x ? (tw.y - tw.x + chunk - 1) / chunk : 0;
     unsigned long long b1 = 0, b2 = 0;
-    for (int c = lane; c < nch; c += 32) {
-        top2(b1, b2, cand[((size_t)i * max_chunks + c) * 2]);
-        top2(b1, b2, cand[((size_t)i * max_chunks + c) * 2 + 1]);
-    }
+    for (int e = lane; e < 4 * nch; e += 32) top2(b1, b2, cand[(size_t)i * max_chunks * 4 + e]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, off);
