@@ -17,6 +17,8 @@
  *    per-device cache of its own kernel attributes.
  *  - `stream` is a cudaStream_t (passed as void*; NULL = the legacy default stream). All work
  *    is enqueued asynchronously on it; nothing synchronises the host.
+ *  - Decode workspaces must be 256-byte aligned; encode workspaces may have any alignment (the
+ *    library uses them from the first 1024-byte boundary; the size queries include that slack).
  *  - Arguments are validated on the host before anything is enqueued; a failed validation
  *    returns FIC_ERR_INVALID_ARG (or FIC_ERR_WORKSPACE) and enqueues nothing.
  *  - A launch failure returns FIC_ERR_CUDA. fic_last_error() returns a message for the last
@@ -45,7 +47,7 @@ extern "C" {
 typedef enum {
     FIC_OK = 0,
     FIC_ERR_INVALID_ARG = 1,  /* bad geometry, parameters or null pointer */
-    FIC_ERR_WORKSPACE = 2,    /* workspace missing, too small or misaligned (256 B) */
+    FIC_ERR_WORKSPACE = 2,    /* workspace missing, too small or (decode) not 256-byte aligned */
     FIC_ERR_CUDA = 3,         /* a CUDA runtime/driver call or launch failed */
     FIC_ERR_DEVICE_TIMEOUT = 4, /* a bounded device-side wait gave up (see fic_check) */
     FIC_ERR_UNSUPPORTED = 5   /* device or build lacks a required feature (sm_103a) */
@@ -70,6 +72,8 @@ typedef struct {
     double s_max;          /* contrast clamp; must be 1.0 */
     int32_t engine;        /* FIC_ENGINE_TENSOR or FIC_ENGINE_SIMT */
     int32_t flags;         /* reserved, must be 0 */
+    int32_t items_per_sm;  /* tensor engine scheduling: work items per SM the range tiles' domain
+                              chunks are split into, 1..64; 0 selects 16 */
 } fic_params;
 
 /* Per-block statistics (Section 3.1: "the fractal dimension of the range blocks are calculated
@@ -143,6 +147,18 @@ fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *g, const fi
 fic_status fic_encode(const uint8_t *img, const fic_geom *g, const fic_params *p,
                       const fic_codes *out, fic_encode_info *info, void *workspace,
                       size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace fic_encode_batched needs for these n images (1 <= n <= 4096). */
+size_t fic_encode_batched_workspace_size(const fic_geom *geoms, int32_t n, const fic_params *p);
+
+/* fic_encode over n images at once (Sections 1 and 3 applied to each image independently: every
+ * image has its own classes, F_l/F_m and pools). imgs, geoms and outs are HOST arrays of n
+ * entries (device image pointers, geometries, code structs of device arrays). The tensor engine
+ * matches all images' pools in one persistent launch. `info` (device, nullable) receives the
+ * totals over the batch. */
+fic_status fic_encode_batched(const uint8_t *const *imgs, const fic_geom *geoms, int32_t n,
+                              const fic_params *p, const fic_codes *outs, fic_encode_info *info,
+                              void *workspace, size_t workspace_bytes, void *stream);
 
 /* Bytes of workspace fic_decode and fic_decode_backward need. */
 size_t fic_decode_workspace_size(const fic_geom *g, const fic_params *p, int32_t iters,

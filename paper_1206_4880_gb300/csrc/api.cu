@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "fic_internal.cuh"
 
@@ -18,6 +19,7 @@ cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *
 cudaError_t launch_grads_out(int R, const double *gs64, const double *go64, float *gs, float *go,
                              cudaStream_t st);
 bool tensor_engine_available(int device);
+constexpr int kMaxBatch = 4096;
 }  // namespace fic
 
 using namespace fic;
@@ -71,6 +73,8 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
     if (p->engine != FIC_ENGINE_TENSOR && p->engine != FIC_ENGINE_SIMT)
         return fail(FIC_ERR_INVALID_ARG, "unknown engine %d", p->engine);
     if (p->flags != 0) return fail(FIC_ERR_INVALID_ARG, "flags must be 0");
+    if (p->items_per_sm < 0 || p->items_per_sm > 64)
+        return fail(FIC_ERR_INVALID_ARG, "items_per_sm must be in [0, 64]");
     g->H = gm->H;
     g->W = gm->W;
     g->pitch = gm->pitch;
@@ -97,65 +101,105 @@ thread_local int g_launches = 0;
 // Sets the message fic_last_error() returns on this thread.
 void set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
-size_t encode_workspace(const Geo &g, EncodeBufs *b, void *ws, size_t cap, bool *ok) {
+size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void *ws, size_t cap, bool *ok) {
     Carver c(ws, cap);
-    b->R_pad = (g.R + kTileM - 1) / kTileM * kTileM;
-    b->Dn_pad = (g.Dn + kTileDom - 1) / kTileDom * kTileDom;
-    b->Dn_aux = b->Dn_pad + kTileDom;  // a tile may start at any position < Dn
-    b->n_mtiles = b->R_pad / kTileM;
-    const int chunk_dom = kTileDom * kChunkTiles;
-    b->max_chunks = (g.Dn + chunk_dom - 1) / chunk_dom;
-    b->max_items = b->n_mtiles * b->max_chunks;
-    b->sort_blocks_dom = (g.Dn + kSortChunk - 1) / kSortChunk;
-    b->sort_blocks_rng = (g.R + kSortChunk - 1) / kSortChunk;
-    const int sort_blocks = b->sort_blocks_dom > b->sort_blocks_rng ? b->sort_blocks_dom : b->sort_blocks_rng;
-    b->range_sum = c.take<int32_t>(g.R);
-    b->range_sumsq = c.take<int32_t>(g.R);
-    b->range_counts = c.take<int32_t>(2 * (size_t)g.R);
-    b->range_fd = c.take<double>(g.R);
-    b->range_bin = c.take<uint8_t>(g.R);
-    b->dom_sum = c.take<int32_t>(g.Dn);
-    b->dom_sumsq = c.take<int32_t>(g.Dn);
-    b->dom_counts = c.take<int32_t>(2 * (size_t)g.Dn);
-    b->dom_fd = c.take<double>(g.Dn);
-    b->dom_bin = c.take<uint8_t>(g.Dn);
-    b->fd_extent = c.take<double>(2);
-    b->extent_bits = c.take<unsigned long long>(2);
-    b->dom_S = c.take<uint16_t>((size_t)g.Dn * 64);
-    b->dom_order = c.take<int32_t>(g.Dn);
-    b->bin_off = c.take<int32_t>(kMaxClasses + 2);
-    b->range_order = c.take<int32_t>(g.R);
-    b->rbin_off = c.take<int32_t>(kMaxClasses + 2);
-    b->win_lo = c.take<int32_t>(g.R);
-    b->win_hi = c.take<int32_t>(g.R);
-    b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 256);
-    b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 256);
-    b->A_mat = c.take<__half>((size_t)b->R_pad * 64, 1024);
-    b->B_mat = c.take<__half>((size_t)8 * b->Dn_aux * 64, 1024);
-    b->dom_aux = c.take<float4>(b->Dn_aux);
-    b->rng_info = c.take<int4>(b->R_pad);
-    b->work = c.take<int4>(b->max_items);
-    b->tile_win = c.take<int4>(b->n_mtiles);
-    b->n_chunks = c.take<int32_t>(b->n_mtiles);
-    b->cand = c.take<unsigned long long>((size_t)b->R_pad * b->max_chunks * 4);
-    b->fallback = c.take<int32_t>(g.R);
-    b->fb_best = c.take<FallbackBest>(g.R);
-    b->counters = c.take<int32_t>(8);
-    b->matches = c.take<long long>(1);
+    long long R_pad_tot = 0, Dn_aux_tot = 0, mt_tot = 0, chunks_tot = 0;
+    int32_t *img_counters = c.take<int32_t>(8 * (size_t)n);
+    long long *img_matches = c.take<long long>((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const Geo &g = gs[k];
+        EncodeBufs *b = &bs[k];
+        b->R_pad = (g.R + kTileM - 1) / kTileM * kTileM;
+        b->Dn_pad = (g.Dn + kTileDom - 1) / kTileDom * kTileDom;
+        b->Dn_aux = b->Dn_pad + kTileDom;  // a tile may start at any position < Dn
+        b->n_mtiles = b->R_pad / kTileM;
+        b->max_chunks = (g.Dn + kChunkDom - 1) / kChunkDom;
+        b->sort_blocks_dom = (g.Dn + kSortChunk - 1) / kSortChunk;
+        b->sort_blocks_rng = (g.R + kSortChunk - 1) / kSortChunk;
+        b->rng_off = (int)R_pad_tot;
+        b->dom_off = (int)Dn_aux_tot;
+        b->mt_off = (int)mt_tot;
+        R_pad_tot += b->R_pad;
+        Dn_aux_tot += b->Dn_aux;
+        mt_tot += b->n_mtiles;
+        chunks_tot += (long long)b->n_mtiles * b->max_chunks;
+        const int sort_blocks = b->sort_blocks_dom > b->sort_blocks_rng ? b->sort_blocks_dom : b->sort_blocks_rng;
+        b->range_sum = c.take<int32_t>(g.R);
+        b->range_sumsq = c.take<int32_t>(g.R);
+        b->range_counts = c.take<int32_t>(2 * (size_t)g.R);
+        b->range_fd = c.take<double>(g.R);
+        b->range_bin = c.take<uint8_t>(g.R);
+        b->dom_sum = c.take<int32_t>(g.Dn);
+        b->dom_sumsq = c.take<int32_t>(g.Dn);
+        b->dom_counts = c.take<int32_t>(2 * (size_t)g.Dn);
+        b->dom_fd = c.take<double>(g.Dn);
+        b->dom_bin = c.take<uint8_t>(g.Dn);
+        b->fd_extent = c.take<double>(2);
+        b->extent_bits = c.take<unsigned long long>(2);
+        b->dom_S = c.take<uint16_t>((size_t)g.Dn * 64);
+        b->dom_order = c.take<int32_t>(g.Dn);
+        b->bin_off = c.take<int32_t>(kMaxClasses + 2);
+        b->range_order = c.take<int32_t>(g.R);
+        b->rbin_off = c.take<int32_t>(kMaxClasses + 2);
+        b->win_lo = c.take<int32_t>(g.R);
+        b->win_hi = c.take<int32_t>(g.R);
+        b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 256);
+        b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 256);
+        b->fallback = c.take<int32_t>(g.R);
+        b->fb_best = c.take<FallbackBest>(g.R);
+        b->counters = img_counters ? img_counters + 8 * k : nullptr;
+        b->matches = img_matches ? img_matches + k : nullptr;
+    }
+    tb->R_pad = (int)R_pad_tot;
+    tb->Dn_aux = (int)Dn_aux_tot;
+    tb->n_mtiles = (int)mt_tot;
+    tb->max_items = (int)mt_tot + kMaxItemTarget;
+    tb->max_chunks = (int)chunks_tot;
+    tb->A_mat = c.take<__half>((size_t)R_pad_tot * 64, 1024);
+    tb->B_mat = c.take<__half>((size_t)8 * Dn_aux_tot * 64, 1024);
+    tb->A1_mat = c.take<__half>((size_t)R_pad_tot * 16, 1024);
+    tb->B1_mat = c.take<__half>((size_t)8 * Dn_aux_tot * 16, 1024);
+    tb->dom_aux = c.take<float4>((size_t)Dn_aux_tot);
+    tb->rng_info = c.take<int4>((size_t)R_pad_tot);
+    tb->tile_win = c.take<int4>((size_t)mt_tot);
+    tb->n_chunks = c.take<int32_t>((size_t)mt_tot);
+    tb->tile_items = c.take<int4>((size_t)mt_tot);
+    tb->work = c.take<int4>((size_t)tb->max_items);
+    tb->cand = c.take<unsigned long long>((size_t)tb->max_items * kTileM * 4);
+    tb->chunk_max = c.take<uint32_t>((size_t)chunks_tot * kTileM * 2);
+    tb->gcounters = c.take<int32_t>(8);
+    for (int k = 0; k < n; ++k) {
+        EncodeBufs *b = &bs[k];
+        const bool have = tb->A_mat != nullptr;
+        b->A_mat = have ? tb->A_mat + (size_t)b->rng_off * 64 : nullptr;
+        b->A1_mat = have ? tb->A1_mat + (size_t)b->rng_off * 16 : nullptr;
+        b->B_mat = have ? tb->B_mat + (size_t)b->dom_off * 8 * 64 : nullptr;
+        b->B1_mat = have ? tb->B1_mat + (size_t)b->dom_off * 8 * 16 : nullptr;
+        b->dom_aux = have ? tb->dom_aux + b->dom_off : nullptr;
+        b->rng_info = have ? tb->rng_info + b->rng_off : nullptr;
+    }
+    if (R_pad_tot >= (1LL << 31) / 64 || 8 * Dn_aux_tot >= (1LL << 31)) c.ok = false;
     if (ok) *ok = c.ok;
     return c.off + 256;
 }
 
-__global__ void k_write_info(const long long *matches, const int32_t *counters, fic_encode_info *info) {
-    info->matches = *matches;
-    info->fallback_ranges = counters[0];
-    info->work_items = counters[1];
-    info->device_error = counters[2];
+__global__ void k_write_info(const long long *matches, const int32_t *img_counters, int n,
+                             const int32_t *gcounters, fic_encode_info *info) {
+    long long m = 0;
+    int fb = 0;
+    for (int k = 0; k < n; ++k) {
+        m += matches[k];
+        fb += img_counters[8 * k];
+    }
+    info->matches = m;
+    info->fallback_ranges = fb;
+    info->work_items = gcounters[1];
+    info->device_error = gcounters[2];
     info->reserved = 0;
 }
 
-cudaError_t launch_info(const EncodeBufs &b, fic_encode_info *info, cudaStream_t st) {
-    k_write_info<<<1, 1, 0, st>>>(b.matches, b.counters, info);
+cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encode_info *info, cudaStream_t st) {
+    k_write_info<<<1, 1, 0, st>>>(b[0].matches, b[0].counters, n, tb.gcounters, info);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -183,31 +227,56 @@ int32_t fic_engine_available(int32_t engine) {
 double fic_debug_log2(int32_t n) { return log2_correctly_rounded(n); }
 
 size_t fic_encode_workspace_size(const fic_geom *gm, const fic_params *p) {
-    Geo g;
-    if (make_geo(gm, p, &g) != FIC_OK) return 0;
-    EncodeBufs b;
-    return encode_workspace(g, &b, nullptr, (size_t)-1, nullptr);
+    return fic_encode_batched_workspace_size(gm, 1, p);
 }
 
-static fic_status carve_encode(const fic_geom *gm, const fic_params *p, void *ws, size_t bytes,
-                               Geo *g, EncodeBufs *b) {
-    fic_status s = make_geo(gm, p, g);
-    if (s != FIC_OK) return s;
+size_t fic_encode_batched_workspace_size(const fic_geom *geoms, int32_t n, const fic_params *p) {
+    if (!geoms || n < 1 || n > kMaxBatch) {
+        fail(FIC_ERR_INVALID_ARG, "batch size must be in [1, %d]", kMaxBatch);
+        return 0;
+    }
+    std::vector<Geo> g(n);
+    for (int k = 0; k < n; ++k)
+        if (make_geo(&geoms[k], p, &g[k]) != FIC_OK) return 0;
+    std::vector<EncodeBufs> b(n);
+    TcBatch tb;
+    bool ok = true;
+    const size_t need = encode_workspace(g.data(), n, b.data(), &tb, nullptr, (size_t)-1, &ok);
+    if (!ok) {
+        fail(FIC_ERR_INVALID_ARG, "batch too large for 32-bit tile indexing");
+        return 0;
+    }
+    return need + 1024;
+}
+
+static fic_status carve_batch(const fic_geom *geoms, int n, const fic_params *p, void *ws, size_t bytes,
+                              std::vector<Geo> &g, std::vector<EncodeBufs> &b, TcBatch *tb) {
+    if (!geoms || n < 1 || n > kMaxBatch) return fail(FIC_ERR_INVALID_ARG, "batch size must be in [1, %d]", kMaxBatch);
+    g.resize(n);
+    b.resize(n);
+    for (int k = 0; k < n; ++k) {
+        fic_status s = make_geo(&geoms[k], p, &g[k]);
+        if (s != FIC_OK) return s;
+    }
     if (!ws) return fail(FIC_ERR_WORKSPACE, "workspace is null");
-    if ((uintptr_t)ws % 256) return fail(FIC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    // carve from the first 1024-byte boundary (TMA tiles); the size query includes the slack
+    char *base = (char *)(((uintptr_t)ws + 1023) & ~(uintptr_t)1023);
+    const size_t slack = (size_t)(base - (char *)ws);
     bool ok = false;
-    const size_t need = encode_workspace(*g, b, ws, bytes, &ok);
-    if (!ok || bytes < need)
-        return fail(FIC_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", bytes, need);
+    const size_t need = encode_workspace(g.data(), n, b.data(), tb, base, bytes > slack ? bytes - slack : 0, &ok);
+    if (!ok || bytes < need + 1024) return fail(FIC_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", bytes, need + 1024);
     return FIC_OK;
 }
 
 fic_status fic_classify(const uint8_t *img, const fic_geom *gm, const fic_params *p,
                         const fic_blockstats *out, void *ws, size_t bytes, void *stream) {
-    Geo g;
-    EncodeBufs b;
-    fic_status s = carve_encode(gm, p, ws, bytes, &g, &b);
+    std::vector<Geo> gv;
+    std::vector<EncodeBufs> bv;
+    TcBatch tb;
+    fic_status s = carve_batch(gm, 1, p, ws, bytes, gv, bv, &tb);
     if (s != FIC_OK) return s;
+    const Geo &g = gv[0];
+    EncodeBufs &b = bv[0];
     if (!img || !out || !out->range_sum || !out->range_sumsq || !out->range_counts ||
         !out->range_fd || !out->range_bin || !out->dom_sum || !out->dom_sumsq ||
         !out->dom_counts || !out->dom_fd || !out->dom_bin || !out->fd_extent)
@@ -223,16 +292,20 @@ fic_status fic_classify(const uint8_t *img, const fic_geom *gm, const fic_params
     b.dom_fd = out->dom_fd;
     b.dom_bin = out->dom_bin;
     b.fd_extent = out->fd_extent;
+    g_launches = 0;
     FIC_TRY(launch_classify(img, g, b, (cudaStream_t)stream), "classify");
     return FIC_OK;
 }
 
 fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *gm, const fic_params *p,
                            const fic_pools *out, void *ws, size_t bytes, void *stream) {
-    Geo g;
-    EncodeBufs b;
-    fic_status s = carve_encode(gm, p, ws, bytes, &g, &b);
+    std::vector<Geo> gv;
+    std::vector<EncodeBufs> bv;
+    TcBatch tb;
+    fic_status s = carve_batch(gm, 1, p, ws, bytes, gv, bv, &tb);
     if (s != FIC_OK) return s;
+    const Geo &g = gv[0];
+    EncodeBufs &b = bv[0];
     if (!st || !st->range_bin || !st->dom_bin || !out || !out->dom_order || !out->bin_off ||
         !out->range_order || !out->rbin_off || !out->win_lo || !out->win_hi)
         return fail(FIC_ERR_INVALID_ARG, "null statistics or pool pointer");
@@ -244,54 +317,77 @@ fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *gm, const f
     b.rbin_off = out->rbin_off;
     b.win_lo = out->win_lo;
     b.win_hi = out->win_hi;
+    g_launches = 0;
     FIC_TRY(launch_pools(g, b, (cudaStream_t)stream), "build_pools");
+    return FIC_OK;
+}
+
+static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms, int n, const fic_params *p,
+                               const fic_codes *outs, fic_encode_info *info, void *ws, size_t bytes,
+                               void *stream) {
+    std::vector<Geo> g;
+    std::vector<EncodeBufs> b;
+    TcBatch tb;
+    fic_status s = carve_batch(geoms, n, p, ws, bytes, g, b, &tb);
+    if (s != FIC_OK) return s;
+    if (!imgs || !outs) return fail(FIC_ERR_INVALID_ARG, "null image or code array");
+    for (int k = 0; k < n; ++k) {
+        const fic_codes &o = outs[k];
+        if (!imgs[k] || !o.dom || !o.iso || !o.s || !o.o || !o.sse)
+            return fail(FIC_ERR_INVALID_ARG, "null image or code pointer (image %d)", k);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    FIC_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (p->engine == FIC_ENGINE_TENSOR && !tensor_engine_available(dev))
+        return fail(FIC_ERR_UNSUPPORTED, "tensor engine needs an sm_103 device");
+    int sms = 0;
+    FIC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+    g_launches = 0;
+    auto mark = [&](int i) -> cudaError_t {
+        return g_prof.on ? cudaEventRecord(g_prof.ev[i], st) : cudaSuccess;
+    };
+    FIC_TRY(mark(0), "event");
+    FIC_TRY(cudaMemsetAsync(b[0].counters, 0, 8 * sizeof(int32_t) * n, st), "memset");
+    FIC_TRY(cudaMemsetAsync(tb.gcounters, 0, 8 * sizeof(int32_t), st), "memset");
+    for (int k = 0; k < n; ++k) FIC_TRY(launch_classify(imgs[k], g[k], b[k], st), "classify");
+    FIC_TRY(mark(1), "event");
+    for (int k = 0; k < n; ++k) FIC_TRY(launch_pools(g[k], b[k], st), "pools");
+    FIC_TRY(mark(2), "event");
+    if (p->engine == FIC_ENGINE_SIMT) {
+        FIC_TRY(mark(3), "event");
+        for (int k = 0; k < n; ++k) FIC_TRY(launch_match_simt(imgs[k], g[k], b[k], outs[k], st), "match_simt");
+        FIC_TRY(mark(4), "event");
+        FIC_TRY(mark(5), "event");
+    } else {
+        for (int k = 0; k < n; ++k) FIC_TRY(launch_pack(imgs[k], g[k], b[k], st), "pack");
+        FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), st),
+                "work_list");
+        FIC_TRY(mark(3), "event");
+        FIC_TRY(launch_match_tc(tb, sms, st), "match_tc");
+        FIC_TRY(mark(4), "event");
+        for (int k = 0; k < n; ++k) FIC_TRY(launch_reeval(imgs[k], g[k], b[k], tb, outs[k], st), "reeval");
+        FIC_TRY(mark(5), "event");
+        for (int k = 0; k < n; ++k) FIC_TRY(launch_rescan(imgs[k], g[k], b[k], tb, outs[k], sms, st), "rescan");
+    }
+    FIC_TRY(mark(6), "event");
+    if (info) FIC_TRY(launch_info(b.data(), n, tb, info, st), "info");
+    g_prof.launches = g_launches;
     return FIC_OK;
 }
 
 fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *p,
                       const fic_codes *out, fic_encode_info *info, void *ws, size_t bytes,
                       void *stream) {
-    Geo g;
-    EncodeBufs b;
-    fic_status s = carve_encode(gm, p, ws, bytes, &g, &b);
-    if (s != FIC_OK) return s;
-    if (!img || !out || !out->dom || !out->iso || !out->s || !out->o || !out->sse)
-        return fail(FIC_ERR_INVALID_ARG, "null image or code pointer");
-    cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0;
-    FIC_TRY(cudaGetDevice(&dev), "cudaGetDevice");
-    if (p->engine == FIC_ENGINE_TENSOR && !tensor_engine_available(dev))
-        return fail(FIC_ERR_UNSUPPORTED, "tensor engine needs an sm_103 device");
-    g_launches = 0;
-    auto mark = [&](int i) -> cudaError_t {
-        return g_prof.on ? cudaEventRecord(g_prof.ev[i], st) : cudaSuccess;
-    };
-    FIC_TRY(mark(0), "event");
-    FIC_TRY(cudaMemsetAsync(b.counters, 0, 8 * sizeof(int32_t), st), "memset");
-    FIC_TRY(launch_classify(img, g, b, st), "classify");
-    FIC_TRY(mark(1), "event");
-    FIC_TRY(launch_pools(g, b, st), "pools");
-    FIC_TRY(mark(2), "event");
-    if (p->engine == FIC_ENGINE_SIMT) {
-        FIC_TRY(mark(3), "event");
-        FIC_TRY(launch_match_simt(img, g, b, *out, st), "match_simt");
-        FIC_TRY(mark(4), "event");
-        FIC_TRY(mark(5), "event");
-    } else {
-        int sms = 0;
-        FIC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
-        FIC_TRY(launch_pack(img, g, b, st), "pack");
-        FIC_TRY(mark(3), "event");
-        FIC_TRY(launch_match_tc(g, b, sms, st), "match_tc");
-        FIC_TRY(mark(4), "event");
-        FIC_TRY(launch_reeval(img, g, b, *out, st), "reeval");
-        FIC_TRY(mark(5), "event");
-        FIC_TRY(launch_rescan(img, g, b, *out, sms, st), "rescan");
-    }
-    FIC_TRY(mark(6), "event");
-    if (info) FIC_TRY(launch_info(b, info, st), "info");
-    g_prof.launches = g_launches;
-    return FIC_OK;
+    const uint8_t *imgs[1] = {img};
+    if (!out) return fail(FIC_ERR_INVALID_ARG, "null code pointer");
+    return encode_batch(imgs, gm, 1, p, out, info, ws, bytes, stream);
+}
+
+fic_status fic_encode_batched(const uint8_t *const *imgs, const fic_geom *geoms, int32_t n,
+                              const fic_params *p, const fic_codes *outs, fic_encode_info *info,
+                              void *ws, size_t bytes, void *stream) {
+    return encode_batch(imgs, geoms, n, p, outs, info, ws, bytes, stream);
 }
 
 fic_status fic_profile_enable(int32_t on) {

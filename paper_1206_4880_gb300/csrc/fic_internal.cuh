@@ -144,28 +144,50 @@ struct EncodeBufs {
     int32_t *dom_order, *bin_off, *range_order, *rbin_off, *win_lo, *win_hi;
     int32_t *sort_counts;  // [nblk][256] per-block class histograms
     int32_t *sort_offs;    // [nblk][256] per-block scatter bases
-    // tensor engine
-    __half *A_mat;         // [R_pad][64]   64 * range pixels, class-sorted ranges
-    __half *B_mat;         // [8 Dn_aux][64] T_t(S_d), class-sorted domains x isometries
-    float4 *dom_aux;       // [Dn_aux] per sorted domain: C, Q/4, 2/Q (0 if Q = 0), unused
-    int4 *rng_info;        // [R_pad] per sorted range: A, pool start, pool end, range id
-    int4 *work;            // [max_items] (m_tile, first domain pos, end domain pos, chunk)
-    int4 *tile_win;        // [n_mtiles] union (x, y) and intersection (z, w) of row windows
-    int32_t *n_chunks;     // [n_mtiles] domain chunks per range tile
-    unsigned long long *cand;  // [R_pad][max_chunks][2 column halves][2] ranking keys
+    // tensor engine: this image's slice of the batch-wide arrays (TcBatch)
+    __half *A_mat;         // [R_pad][64]   range pixels - a, class-sorted ranges
+    __half *B_mat;         // [8 Dn_aux][64] T_t(S_d) - c, class-sorted domains x isometries
+    __half *A1_mat;        // [R_pad][16] (alpha, 0, ...): correction slice of the A operand
+    __half *B1_mat;        // [8 Dn_aux][16] (-gamma / 64, 0, ...): correction slice of B
+    float4 *dom_aux;       // [Dn_aux] per sorted domain: 0, Q / 256, 128 / Q (0 if Q = 0), 0
+    int4 *rng_info;        // [R_pad] per sorted range: A, pool start, pool end (batch-wide
+                           // domain positions), range id (-1 for padding rows)
+    int rng_off, dom_off, mt_off;  // first batch-wide sorted range, sorted domain, range tile
+    // exact re-search queue of this image
     int32_t *fallback;     // [R] class-sorted positions of ranges to re-search exactly
     FallbackBest *fb_best; // [R] their exact best evaluated candidate
-    int32_t *counters;     // [8] device counters (fallback count, work items, ...)
-    long long *matches;    // [1]
-    int R_pad, Dn_pad, Dn_aux, n_mtiles, max_chunks, max_items, sort_blocks_dom, sort_blocks_rng;
+    int32_t *counters;     // [8] this image: [0] re-search count
+    long long *matches;    // [1] sum of this image's pool sizes x 8
+    int R_pad, Dn_pad, Dn_aux, n_mtiles, max_chunks, sort_blocks_dom, sort_blocks_rng;
+};
+
+// Tensor-engine arrays shared by every image of a batch: class-sorted ranges and domains of all
+// images concatenated, so one persistent kernel launch serves the whole batch.
+struct TcBatch {
+    __half *A_mat, *B_mat, *A1_mat, *B1_mat;
+    float4 *dom_aux;
+    int4 *rng_info;
+    int4 *tile_win;        // [n_mtiles] union (x, y) and intersection (z, w) of row windows
+    int32_t *n_chunks;     // [n_mtiles] 512-domain chunks per range tile
+    int4 *tile_items;      // [n_mtiles] first work item, items, first chunk, chunks
+    int4 *work;            // [max_items] (range tile, first domain, end domain, first chunk)
+    unsigned long long *cand;  // [max_items][128 rows][2 column halves][2] top-2 keys
+    uint32_t *chunk_max;   // [max_chunks][128 rows][2 column halves] best key per chunk
+    int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks
+    int R_pad, Dn_aux, n_mtiles, max_items, max_chunks;
 };
 
 constexpr int kSortChunk = 2048;  // elements per counting-sort block
 constexpr int kTileM = 128;       // ranges per tensor-engine tile
 constexpr int kTileDom = 32;      // domains per accumulator tile (8 isometries -> N = 256)
-constexpr int kChunkTiles = 16;   // accumulator tiles per work item
+constexpr int kChunkTiles = 16;   // accumulator tiles per chunk (the re-search granule)
+constexpr int kChunkDom = kTileDom * kChunkTiles;
+constexpr int kItemsPerSm = 16;   // default work items per SM the work list aims for
+constexpr int kMaxItemTarget = 64 * 256;  // items_per_sm <= 64, SMs <= 256
 
-size_t encode_workspace(const Geo &g, EncodeBufs *b, void *ws, size_t cap, bool *ok);
+// Carves the workspace for n images: per-image buffers, then the batch-wide arrays. Returns the
+// bytes needed (with base == nullptr, only the size).
+size_t encode_workspace(const Geo *g, int n, EncodeBufs *b, TcBatch *tb, void *ws, size_t cap, bool *ok);
 
 // Launchers (each returns cudaGetLastError()).
 cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &b,
@@ -173,13 +195,14 @@ cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &
 cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st);
 cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                               const fic_codes &out, cudaStream_t st);
-cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const fic_codes &out,
-                          int num_sms, cudaStream_t st);
+cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
+                          const fic_codes &out, int num_sms, cudaStream_t st);
 cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st);
-cudaError_t launch_match_tc(const Geo &g, const EncodeBufs &b, int num_sms, cudaStream_t st);
-cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b,
+cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st);
+cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st);
+cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, cudaStream_t st);
-cudaError_t launch_info(const EncodeBufs &b, fic_encode_info *info, cudaStream_t st);
+cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encode_info *info, cudaStream_t st);
 
 // decode
 cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,

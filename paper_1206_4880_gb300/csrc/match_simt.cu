@@ -24,6 +24,8 @@ struct ScanShared {
     float rp[8][64];
     long long num[kSimtThreads], den[kSimtThreads], P[kSimtThreads], Q[kSimtThreads];
     int d[kSimtThreads], t[kSimtThreads], C[kSimtThreads];
+    int flagged[kSimtThreads];
+    int n_flagged;
 };
 
 struct Best {
@@ -155,20 +157,20 @@ __global__ void __launch_bounds__(kSimtThreads)
     reduce_and_write(sh, b, r, A, Bs, out);
 }
 
-// Re-search of uncertified ranges. Slot k holds class-sorted range position fb_pos[k] and the
-// exact best of its evaluated candidates; the chunks of the range's tile whose best FP32 score
-// could still reach that best (score * (1 + 2^-16) >= best gain / 8) are scanned exactly.
+// Re-search of uncertified ranges of one image. Slot k holds class-sorted position fb_pos[k] and
+// the exact best of its evaluated candidates; the 512-domain chunks of the range's tile whose best
+// FP32 score (an upper bound of exact gain / 512) could still reach that best (score * (1 + 2^-16)
+// >= best gain / 512) are scanned exactly.
 __global__ void __launch_bounds__(kSimtThreads)
     k_rescan(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
              const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
              const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
-             const int4 *__restrict__ rng_info, const int4 *__restrict__ tile_win,
-             const unsigned long long *__restrict__ cand, int max_chunks,
+             const int4 *__restrict__ rng_info, int rng_off, int dom_off, const int4 *__restrict__ tile_win,
+             const int4 *__restrict__ tile_items, const uint32_t *__restrict__ chunk_max,
              const int32_t *__restrict__ fb_pos, const FallbackBest *__restrict__ fb_best,
              const int32_t *__restrict__ counters, fic_codes out) {
     __shared__ __align__(16) ScanShared sh;
     const int n = min(counters[0], g.R);
-    const int chunk = kTileDom * kChunkTiles;
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int i = fb_pos[k];
         const int4 ri = rng_info[i];
@@ -177,20 +179,34 @@ __global__ void __launch_bounds__(kSimtThreads)
         __syncthreads();
         const FallbackBest fb = fb_best[k];
         Best b{{fb.num, fb.den}, fb.d, fb.t, fb.C, fb.P, fb.Q};
-        const double thr = fb.num < 0 ? -1.0 : (double)fb.num / (8.0 * (double)fb.den);
+        const double thr = fb.num < 0 ? -1.0 : (double)fb.num / (512.0 * (double)fb.den);
         const long long A = ri.x, Bs = rsumsq[r];
-        const int4 tw = tile_win[i / kTileM];
-        const int nch = tw.y > tw.x ? (tw.y - tw.x + chunk - 1) / chunk : 0;
-        for (int c = 0; c < nch; ++c) {
-            const unsigned long long k0 = cand[(((size_t)i * max_chunks + c) * 2 + 0) * 2];
-            const unsigned long long k1 = cand[(((size_t)i * max_chunks + c) * 2 + 1) * 2];
-            const unsigned long long key = k0 > k1 ? k0 : k1;
-            if (key == 0) continue;
-            const double s1 = (double)__uint_as_float((uint32_t)(key >> 32));
-            if (s1 * (1.0 + 1.0 / 65536.0) < thr) continue;
-            const int j0 = max(ri.y, tw.x + c * chunk), j1 = min(ri.z, min(tw.x + (c + 1) * chunk, tw.y));
-            for (int j = j0 + threadIdx.x; j < j1; j += kSimtThreads)
-                scan_domain(sh, dom_order[j], A, domS, dsum, dsumsq, b);
+        const int ig = rng_off + i, row = ig % kTileM;
+        const int4 tw = tile_win[ig / kTileM];
+        const int4 ti = tile_items[ig / kTileM];
+        const int nch = ti.w;
+        // flag the chunks whose best score reaches the threshold (256 chunks at a time, in
+        // parallel), then scan the flagged chunks' domains with all threads
+        for (int base = 0; base < nch; base += kSimtThreads) {
+            if (threadIdx.x == 0) sh.n_flagged = 0;
+            __syncthreads();
+            const int c = base + threadIdx.x;
+            if (c < nch) {
+                const size_t e = ((size_t)(ti.z + c) * kTileM + row) * 2;
+                const uint32_t key = max(chunk_max[e], chunk_max[e + 1]);
+                const double s1 = (double)__uint_as_float(key);
+                if (key != 0 && s1 * (1.0 + 1.0 / 65536.0) >= thr) sh.flagged[atomicAdd(&sh.n_flagged, 1)] = c;
+            }
+            __syncthreads();
+            const int nf = sh.n_flagged;
+            for (int f = 0; f < nf; ++f) {
+                const int cc = sh.flagged[f];
+                const int j0 = max(ri.y, tw.x + cc * kChunkDom);
+                const int j1 = min(ri.z, min(tw.x + (cc + 1) * kChunkDom, tw.y));
+                for (int j = j0 + threadIdx.x; j < j1; j += kSimtThreads)
+                    scan_domain(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
+            }
+            __syncthreads();
         }
         reduce_and_write(sh, b, r, A, Bs, out);
     }
@@ -204,11 +220,12 @@ cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs
     return cudaGetLastError();
 }
 
-cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const fic_codes &out,
-                          int num_sms, cudaStream_t st) {
+cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
+                          const fic_codes &out, int num_sms, cudaStream_t st) {
     k_rescan<<<4 * num_sms, kSimtThreads, 0, st>>>(g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq,
-                                                   b.dom_order, b.rng_info, b.tile_win, b.cand, b.max_chunks,
-                                                   b.fallback, b.fb_best, b.counters, out);
+                                                   b.dom_order, b.rng_info, b.rng_off, b.dom_off, tb.tile_win,
+                                                   tb.tile_items, tb.chunk_max, b.fallback, b.fb_best, b.counters,
+                                                   out);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -4,17 +4,22 @@
 // comparison is a least-squares fit whose only range x domain term is the correlation
 // X = sum_p r[p] * T_t(S_d)[p]. Here that term is one dense contraction per tile:
 //
-//   A_mat[i][p]          = 64 * r_i[p]             (class-sorted range i, fp16, exact <= 16320)
-//   B_mat[8 j + t][p]    = T_t(S_{d_j})[p]         (class-sorted domain j, isometry t, fp16,
-//                                                   exact <= 1020)
-//   D[i][8 j + t]        = sum_p A_mat[i][p] * B_mat[8 j + t][p] = 64 X
+//   A_mat[i][p]          = r_i[p] - a_i            (class-sorted range i, fp16, |.| <= 255)
+//   B_mat[8 j + t][p]    = T_t(S_{d_j})[p] - c_j   (class-sorted domain j, isometry t, fp16,
+//                                                   |.| <= 1020)
+//   D[i][8 j + t] = Y    = sum_p A_mat[i][p] * B_mat[8 j + t][p]
 //
-// 64 X < 2^30 is a multiple of 64 and every partial sum is a non-negative integer multiple of
-// 64 below 2^30, so FP32 accumulation is exact. The fused epilogue turns each row's 8 isometry
-// columns of domain j into an FP32 estimate of the best least-squares gain (Section 1's intensity
-// map with |s| <= 1) and keeps the two best (gain, j) keys per range; `k_reeval` evaluates those
-// exactly in integers and certifies that no other domain can be better (else the range is
-// re-searched exactly on CUDA cores).
+// with a = round(A / 64) and c = round(C / 64) the integer means (A = sum r, C = sum S). Every
+// product and partial sum is an integer of magnitude < 64 * 255 * 1020 < 2^24, so the FP32
+// accumulator holds Y exactly, and with alpha = A - 64 a and gamma = C - 64 c (both in
+// [-32, 32]) the least-squares numerator is P = 64 X - A C = 64 Y - alpha gamma. A fifth K = 16
+// step adds alpha_i * (-gamma_j / 64) (both exact in FP16; only column 64 of the slice is
+// non-zero), so the accumulator ends as P / 64 with a relative error of a few 2^-24. The fused
+// epilogue takes max_t |P_t| / 64 over the 8 isometry columns, inflates it to cover that error,
+// forms the clamped least-squares gain (Section 1's intensity map with |s| <= 1) of it, an upper
+// bound of the exact best gain of the pair, and keeps the two best (bound, j) keys per range;
+// `k_reeval` evaluates those exactly in integers and certifies that no other domain can be better
+// (else the range is re-searched exactly on CUDA cores).
 //
 // Kernel shape: persistent, one CTA per SM, 10 warps: warp 0 issues TMA loads (A tile 128 x 64,
 // B tiles 256 x 64, 128-byte swizzle, 4-stage ring), warp 1 owns TMEM (two 128 x 256 FP32
@@ -49,9 +54,10 @@ constexpr int kStages = 4;
 constexpr int kTileN = 8 * kTileDom;     // 256 accumulator columns
 constexpr int kABytes = kTileM * 128;    // 128 rows x 64 fp16
 constexpr int kBBytes = kTileN * 128;    // 256 rows x 64 fp16
+constexpr int kA1Bytes = kTileM * 32;    // 128 rows x 16 fp16 (correction slice)
+constexpr int kB1Bytes = kTileN * 32;    // 256 rows x 16 fp16
 constexpr int kEpiWarps = 8;             // two per TMEM lane group, one per column half
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);
-constexpr int kChunkDom = kTileDom * kChunkTiles;
 constexpr int kTmemCols = 2 * kTileN;    // two accumulators
 constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16 (0), both K-major,
@@ -61,6 +67,8 @@ constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint
 struct TcShared {
     uint8_t A[2][kABytes];
     uint8_t B[kStages][kBBytes];
+    uint8_t A1[2][kA1Bytes];
+    uint8_t B1[kStages][kB1Bytes];
     float4 aux[2][kChunkDom];  // per-domain constants of the current and next work item
     unsigned long long full_a[2], empty_a[2], full_b[kStages], empty_b[kStages], tfull[2],
         tempty[2], aux_ready[2], drain;
@@ -143,6 +151,12 @@ __device__ __forceinline__ void umma_commit(unsigned long long *bar) {
 // K-major operand tile in shared memory, rows of 128 bytes, 128-byte swizzle, 8-row groups
 // 1024 bytes apart; bits: start >> 4 [0,14), leading offset >> 4 [16,30) (unused for this
 // layout), stride offset >> 4 [32,46), descriptor version 1 [46,48), swizzle mode 2 [61,64).
+// The same for the 16-column correction slice: 32-byte rows, 32-byte swizzle (mode 6), 8-row
+// groups 256 bytes apart.
+__device__ __forceinline__ unsigned long long sw32_desc(uint32_t saddr) {
+    return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((unsigned long long)(256 >> 4) << 32) |
+           (1ull << 46) | (6ull << 61);
+}
 __device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
     return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
            (1ull << 46) | (2ull << 61);
@@ -170,27 +184,7 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[32]) {
                  :
                  : "memory");
 }
-__device__ __forceinline__ float fmax3f(float a, float b, float c) {
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-__device__ __forceinline__ float fmin3f(float a, float b, float c) {
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
 
-__device__ __forceinline__ float max8(const uint32_t *v) {
-    const float a = fmax3f(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
-    const float b = fmax3f(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5]));
-    return fmax3f(a, b, fmaxf(__uint_as_float(v[6]), __uint_as_float(v[7])));
-}
-__device__ __forceinline__ float min8(const uint32_t *v) {
-    const float a = fmin3f(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
-    const float b = fmin3f(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5]));
-    return fmin3f(a, b, fminf(__uint_as_float(v[6]), __uint_as_float(v[7])));
-}
 
 __device__ __forceinline__ void top2(unsigned long long &b1, unsigned long long &b2, unsigned long long k) {
     const unsigned long long lo = k < b1 ? k : b1;
@@ -204,13 +198,23 @@ __device__ __forceinline__ void top2u(uint32_t &b1, uint32_t &b2, uint32_t k) {
 }
 
 // Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
-// range row. Per domain: p = max_t |P_t| from the max and min correlation, the clamped
-// least-squares gain / 8 estimate g8 = 2 m^2 / Q + (p - m), m = min(p, Q/4), and a 32-bit key
-// (g8's bits with the low 4 replaced by 15 - local index); t1, t2 keep the two largest keys.
+// range row. Per domain: p = max_t |P_t| / 64 (inflated by a relative 2^-18 and 2^-14 to cover
+// the accumulation error), the clamped least-squares gain / 512 of p: s = 128 m^2 / Q + (p - m),
+// m = min(p, Q / 256) (an upper bound of the exact gain / 512, since the gain grows with |P|),
+// and a 32-bit key (s's bits with the low 4 replaced by 15 - local index); t1, t2 keep the two
+// largest keys.
 // MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
+__device__ __forceinline__ float absmax8(const uint32_t *v) {
+    const float a = fmaxf(fabsf(__uint_as_float(v[0])), fabsf(__uint_as_float(v[1])));
+    const float b = fmaxf(fabsf(__uint_as_float(v[2])), fabsf(__uint_as_float(v[3])));
+    const float c = fmaxf(fabsf(__uint_as_float(v[4])), fabsf(__uint_as_float(v[5])));
+    const float d = fmaxf(fabsf(__uint_as_float(v[6])), fabsf(__uint_as_float(v[7])));
+    return fmaxf(fmaxf(a, b), fmaxf(c, d));
+}
+
 template <bool MASK>
-__device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, float A, int jh, int lo_r,
-                                         int hi_r, uint32_t &t1, uint32_t &t2) {
+__device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int jh, int lo_r, int hi_r,
+                                         uint32_t &t1, uint32_t &t2) {
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
@@ -227,11 +231,11 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, flo
         for (int q = 0; q < 4; ++q) {
             const int l = 4 * c + q;
             const float4 a = auxp[l];
-            const float xmax = max8(cur + 8 * q), xmin = min8(cur + 8 * q);
-            const float p = fmaxf(fmaf(-A, a.x, xmax), fmaf(A, a.x, -xmin));
+            // accumulator = P / 64 up to the FP32 accumulation error, covered by the inflation
+            const float p = fmaf(absmax8(cur + 8 * q), 1.0f + 0x1p-18f, 0x1p-14f);
             const float mm = fminf(p, a.y);
-            const float g8 = fmaf(mm, mm * a.z, p - mm);
-            uint32_t key = (__float_as_uint(g8) & 0xFFFFFFF0u) | (uint32_t)(15 - l);
+            const float sc = fmaf(mm, mm * a.z, p - mm);
+            uint32_t key = (__float_as_uint(sc) & 0xFFFFFFF0u) | (uint32_t)(15 - l);
             if (MASK) {
                 const int j = jh + l;
                 key = (j >= lo_r && j < hi_r) ? key : 0u;
@@ -259,12 +263,14 @@ __device__ __forceinline__ void merge_half_key(unsigned long long &b1, unsigned 
 }  // namespace
 
 // ---- operand packing ------------------------------------------------------------------------
-// One thread per (sorted range i, pixel row y): A_mat row i = 64 * pixels; rng_info[i] =
-// (A, pool start, pool end, range id). Rows i >= R are zero with an empty window.
+// One thread per (sorted range i, pixel row y): A_mat row i = pixels - round(A / 64), A1 row i =
+// (A - 64 round(A / 64), 0, ...); rng_info[i] = (A, pool start, pool end, range id) with the pool
+// in batch-wide domain positions (dom_off + position in this image's dom_order). Rows i >= R are
+// zero with an empty window and range id -1.
 __global__ void k_pack_ranges(Geo g, const uint8_t *__restrict__ img, const int32_t *__restrict__ range_order,
                               const int32_t *__restrict__ rsum, const int32_t *__restrict__ win_lo,
-                              const int32_t *__restrict__ win_hi, int R_pad, __half *__restrict__ A_mat,
-                              int4 *__restrict__ rng_info) {
+                              const int32_t *__restrict__ win_hi, int R_pad, int dom_off,
+                              __half *__restrict__ A_mat, uint4 *__restrict__ A1, int4 *__restrict__ rng_info) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gid >> 3, y = gid & 7;
     if (i >= R_pad) return;
@@ -272,26 +278,35 @@ __global__ void k_pack_ranges(Geo g, const uint8_t *__restrict__ img, const int3
     if (i < g.R) {
         const int r = range_order[i];
         const uint8_t *row = img + (size_t)((r / g.nRx) * 8 + y) * g.pitch + (r % g.nRx) * 8;
+        const int abar = (rsum[r] + 32) >> 6;  // round(A / 64)
         uint32_t w[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-            const __half a = __float2half_rn(64.f * (float)row[2 * h]);
-            const __half b = __float2half_rn(64.f * (float)row[2 * h + 1]);
+            const __half a = __int2half_rn((int)row[2 * h] - abar);
+            const __half b = __int2half_rn((int)row[2 * h + 1] - abar);
             w[h] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
         }
         pk = make_uint4(w[0], w[1], w[2], w[3]);
-        if (y == 0) rng_info[i] = make_int4(rsum[r], win_lo[r], win_hi[r], r);
+        if (y == 0) {
+            rng_info[i] = make_int4(rsum[r], win_lo[r] + dom_off, win_hi[r] + dom_off, r);
+            const int alpha = rsum[r] - 64 * abar;
+            A1[2 * i] = make_uint4((uint32_t)__half_as_ushort(__int2half_rn(alpha)), 0, 0, 0);
+            A1[2 * i + 1] = make_uint4(0, 0, 0, 0);
+        }
     } else if (y == 0) {
         rng_info[i] = make_int4(0, 0, 0, -1);
+        A1[2 * i] = make_uint4(0, 0, 0, 0);
+        A1[2 * i + 1] = make_uint4(0, 0, 0, 0);
     }
     reinterpret_cast<uint4 *>(A_mat + (size_t)i * 64)[y] = pk;
 }
 
-// One thread per (sorted domain j, isometry t, row y): B_mat row 8j+t = T_t(S_{dom_order[j]});
-// dom_aux[j] = (C, Q/4, 2/Q or 0, 0). Entries j >= Dn are zero.
+// One thread per (sorted domain j, isometry t, row y): B_mat row 8j+t = T_t(S_{dom_order[j]}) -
+// round(C / 64); dom_aux[j] = (|gamma|, Q / 256, 128 / Q or 0, 0) with gamma = C - 64 round(C/64).
+// Entries j >= Dn are zero.
 __global__ void k_pack_domains(Geo g, const uint16_t *__restrict__ domS, const int32_t *__restrict__ dom_order,
                                const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq, int n_pad,
-                               __half *__restrict__ B_mat, float4 *__restrict__ dom_aux) {
+                               __half *__restrict__ B_mat, uint4 *__restrict__ B1, float4 *__restrict__ dom_aux) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = (int)(gid >> 6), t = (int)(gid >> 3) & 7, y = (int)gid & 7;
     if (j >= n_pad) return;
@@ -299,35 +314,49 @@ __global__ void k_pack_domains(Geo g, const uint16_t *__restrict__ domS, const i
     if (j < g.Dn) {
         const int d = dom_order[j];
         const uint16_t *S = domS + (size_t)d * 64;
+        const int cbar = (dsum[d] + 32) >> 6;  // round(C / 64)
         uint32_t w[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             int sy, sx;
             iso_src(8, t, y, 2 * h, sy, sx);
-            const __half a = __float2half_rn((float)S[sy * 8 + sx]);
+            const __half a = __int2half_rn((int)S[sy * 8 + sx] - cbar);
             iso_src(8, t, y, 2 * h + 1, sy, sx);
-            const __half b = __float2half_rn((float)S[sy * 8 + sx]);
+            const __half b = __int2half_rn((int)S[sy * 8 + sx] - cbar);
             w[h] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
         }
         pk = make_uint4(w[0], w[1], w[2], w[3]);
+        if (y == 0) {
+            const int gamma = dsum[d] - 64 * cbar;
+            const __half cg = __float2half_rn(-(float)gamma * (1.0f / 64.0f));  // exact: |gamma| <= 32
+            B1[2 * ((size_t)j * 8 + t)] = make_uint4((uint32_t)__half_as_ushort(cg), 0, 0, 0);
+            B1[2 * ((size_t)j * 8 + t) + 1] = make_uint4(0, 0, 0, 0);
+        }
         if (t == 0 && y == 0) {
             const long long C = dsum[d];
             const long long Q = 64LL * dsumsq[d] - C * C;
-            dom_aux[j] = make_float4((float)C, (float)Q * 0.25f, Q > 0 ? 2.0f / (float)Q : 0.f, 0.f);
+            const int gamma = (int)C - 64 * cbar;
+            dom_aux[j] = make_float4(0.f, (float)Q * (1.0f / 256.0f), Q > 0 ? 128.0f / (float)Q : 0.f, 0.f);
+            (void)gamma;
         }
-    } else if (t == 0 && y == 0) {
-        dom_aux[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        if (y == 0) {
+            B1[2 * ((size_t)j * 8 + t)] = make_uint4(0, 0, 0, 0);
+            B1[2 * ((size_t)j * 8 + t) + 1] = make_uint4(0, 0, 0, 0);
+        }
+        if (t == 0 && y == 0) dom_aux[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     reinterpret_cast<uint4 *>(B_mat + ((size_t)j * 8 + t) * 64)[y] = pk;
 }
 
-// One block (128 threads) per range tile: the union [lo_u, hi_u) of its rows' pool windows and
-// the intersection [lo_i, hi_i) over its valid rows; tile_win[m] = (lo_u, hi_u, lo_i, hi_i).
-__global__ void k_tile_windows(int R, const int4 *__restrict__ rng_info, int4 *__restrict__ tile_win,
+// One block (128 threads) per range tile of the batch: the union [lo_u, hi_u) of its rows' pool
+// windows and the intersection [lo_i, hi_i) over its valid rows; tile_win[m] = (lo_u, hi_u, lo_i,
+// hi_i); n_chunks[m] = number of 512-domain chunks of the union.
+__global__ void k_tile_windows(const int4 *__restrict__ rng_info, int4 *__restrict__ tile_win,
                                int32_t *__restrict__ n_chunks) {
     const int m = blockIdx.x, i = m * kTileM + threadIdx.x;
-    const bool valid = i < R;
     const int4 ri = rng_info[i];
+    const bool valid = ri.w >= 0;
     int lo_u = valid ? ri.y : INT_MAX, hi_u = valid ? ri.z : INT_MIN;
     int lo_i = valid ? ri.y : INT_MIN, hi_i = valid ? ri.z : INT_MAX;
 #pragma unroll
@@ -349,54 +378,77 @@ __global__ void k_tile_windows(int R, const int4 *__restrict__ rng_info, int4 *_
             t.w = min(t.w, w[k].w);
         }
         tile_win[m] = t;
-        const int chunk = kTileDom * kChunkTiles;
-        n_chunks[m] = t.y > t.x ? (t.y - t.x + chunk - 1) / chunk : 0;
+        n_chunks[m] = t.y > t.x ? (t.y - t.x + kChunkDom - 1) / kChunkDom : 0;
     }
 }
 
-// One block: work items (m, j0, j1, chunk) for every tile's chunks, tile-major; the count goes
-// to counters[1].
-__global__ void k_work_list(int n_mtiles, const int4 *__restrict__ tile_win, const int32_t *__restrict__ n_chunks,
-                            int4 *__restrict__ work, int32_t *counters) {
-    __shared__ int base_s;
-    if (threadIdx.x == 0) base_s = 0;
+// Block-wide exclusive scan of one int per thread (blockDim.x == 1024); returns the thread's
+// exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ int block_scan_1024(int v, int *sc, int *total) {
+    sc[threadIdx.x] = v;
     __syncthreads();
-    const int chunk = kTileDom * kChunkTiles;
-    for (int m0 = 0; m0 < n_mtiles; m0 += blockDim.x) {
-        const int m = m0 + threadIdx.x;
-        const int c = m < n_mtiles ? n_chunks[m] : 0;
-        // inclusive scan over the block (Hillis-Steele in shared memory)
-        __shared__ int sc[1024];
-        sc[threadIdx.x] = c;
+    for (int s = 1; s < 1024; s <<= 1) {
+        const int a = threadIdx.x >= (unsigned)s ? sc[threadIdx.x - s] : 0;
         __syncthreads();
-        for (int s = 1; s < (int)blockDim.x; s <<= 1) {
-            const int a = threadIdx.x >= (unsigned)s ? sc[threadIdx.x - s] : 0;
-            __syncthreads();
-            sc[threadIdx.x] += a;
-            __syncthreads();
-        }
-        const int start = base_s + sc[threadIdx.x] - c;
-        if (m < n_mtiles) {
-            const int4 t = tile_win[m];
-            for (int k = 0; k < c; ++k) {
-                const int j0 = t.x + k * chunk;
-                work[start + k] = make_int4(m, j0, min(j0 + chunk, t.y), k);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) base_s += sc[threadIdx.x];
+        sc[threadIdx.x] += a;
         __syncthreads();
     }
-    if (threadIdx.x == 0) counters[1] = base_s;
+    const int incl = sc[threadIdx.x];
+    *total = sc[1023];
+    __syncthreads();
+    return incl - v;
+}
+
+// One block of 1024 threads. Every range tile's chunks are split into work items of `cpi`
+// consecutive chunks, cpi chosen so that the batch has about `target` items; items are written
+// tile-major as (tile, first domain, end domain, first chunk id), tile_items[m] = (first item,
+// items, first chunk id, chunks); gcounters[1] = items, gcounters[3] = chunks.
+__global__ void k_work_list(int n_mtiles, int target, const int4 *__restrict__ tile_win,
+                            const int32_t *__restrict__ n_chunks, int4 *__restrict__ work,
+                            int4 *__restrict__ tile_items, int32_t *gcounters) {
+    __shared__ int sc[1024];
+    __shared__ int total_chunks_s;
+    int tot = 0;
+    for (int m = threadIdx.x; m < n_mtiles; m += 1024) tot += n_chunks[m];
+    int all = 0;
+    block_scan_1024(tot, sc, &all);
+    if (threadIdx.x == 0) total_chunks_s = all;
+    __syncthreads();
+    const int total = total_chunks_s;
+    const int cpi = max(1, (total + target - 1) / max(1, target));
+    int item_base = 0, chunk_base = 0;
+    for (int m0 = 0; m0 < n_mtiles; m0 += 1024) {
+        const int m = m0 + threadIdx.x;
+        const int c = m < n_mtiles ? n_chunks[m] : 0;
+        const int q = (c + cpi - 1) / cpi;
+        int q_all = 0, c_all = 0;
+        const int q_off = item_base + block_scan_1024(q, sc, &q_all);
+        const int c_off = chunk_base + block_scan_1024(c, sc, &c_all);
+        if (m < n_mtiles) {
+            const int4 t = tile_win[m];
+            for (int k = 0; k < q; ++k) {
+                const int c0 = k * cpi, c1 = min(c0 + cpi, c);
+                work[q_off + k] = make_int4(m, t.x + c0 * kChunkDom, min(t.x + c1 * kChunkDom, t.y), c_off + c0);
+            }
+            tile_items[m] = make_int4(q_off, q, c_off, c);
+        }
+        item_base += q_all;
+        chunk_base += c_all;
+    }
+    if (threadIdx.x == 0) {
+        gcounters[1] = item_base;
+        gcounters[3] = chunk_base;
+    }
 }
 
 // ---- the matching kernel ----------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int R,
+    k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
                const int4 *__restrict__ work, const int32_t *__restrict__ counters_in,
                const int4 *__restrict__ tile_win, const int4 *__restrict__ rng_info,
-               const float4 *__restrict__ dom_aux, int max_chunks, unsigned long long *__restrict__ cand,
-               int32_t *err) {
+               const float4 *__restrict__ dom_aux, unsigned long long *__restrict__ cand,
+               uint32_t *__restrict__ chunk_max, int32_t *err) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
     TcShared &sh = *reinterpret_cast<TcShared *>(smem_raw + pad);
@@ -442,15 +494,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int ab = li & 1;
                 ok = mbar_wait(&sh.empty_a[ab], ((li >> 1) & 1) ^ 1, abort_flag);
                 if (!ok) break;
-                mbar_expect_tx(&sh.full_a[ab], kABytes);
+                mbar_expect_tx(&sh.full_a[ab], kABytes + kA1Bytes);
                 tma_load_2d(sh.A[ab], &tmA, &sh.full_a[ab], 0, w.x * kTileM);
+                tma_load_2d(sh.A1[ab], &tmA1, &sh.full_a[ab], 0, w.x * kTileM);
                 const int nt = (w.z - w.y + kTileDom - 1) / kTileDom;
                 for (int k = 0; k < nt; ++k, ++gt) {
                     const int s = gt % kStages;
                     ok = mbar_wait(&sh.empty_b[s], ((gt / kStages) & 1) ^ 1, abort_flag);
                     if (!ok) break;
-                    mbar_expect_tx(&sh.full_b[s], kBBytes);
+                    mbar_expect_tx(&sh.full_b[s], kBBytes + kB1Bytes);
                     tma_load_2d(sh.B[s], &tmB, &sh.full_b[s], 0, 8 * (w.y + k * kTileDom));
+                    tma_load_2d(sh.B1[s], &tmB1, &sh.full_b[s], 0, 8 * (w.y + k * kTileDom));
                 }
             }
             if (!ok) {
@@ -483,6 +537,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int kk = 0; kk < 4; ++kk)
                         umma_f16(tmem + acc * kTileN, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), kIdesc,
                                  kk > 0 ? 1u : 0u);
+                    // K = 64..79: alpha_i * (-gamma_j / 64), turning Y into P / 64
+                    umma_f16(tmem + acc * kTileN, sw32_desc(su32(sh.A1[ab])), sw32_desc(su32(sh.B1[s])), kIdesc, 1u);
                     umma_commit(&sh.empty_b[s]);
                     umma_commit(&sh.tfull[acc]);
                 }
@@ -505,48 +561,55 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int half = ew >> 2;
         const int row = lg * 32 + lane;
         const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(half * (kTileN / 2));
-        uint32_t gt = 0, li = 0;
+        uint32_t gt = 0, lc = 0;  // accumulator tiles and chunks this CTA has processed
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const int4 w = work[it];
             const int nt = (w.z - w.y + kTileDom - 1) / kTileDom;
-            // per-domain constants of this item into shared memory (double-buffered by item parity;
-            // a thread reaches item li + 2 only after every thread has left item li)
-            const int ab = li & 1;
-            for (int k = ew * 32 + lane; k < nt * kTileDom; k += 32 * kEpiWarps)
-                sh.aux[ab][k] = __ldg(&dom_aux[w.y + k]);
-            mbar_arrive(&sh.aux_ready[ab]);
-            ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (li >> 1) & 1, abort_flag));
-            if (!ok) break;
             const int i = w.x * kTileM + row;
             const int4 ri = rng_info[i];
-            const bool valid = i < R;
-            const float A = (float)ri.x;
+            const bool valid = ri.w >= 0;
             const int lo_r = ri.y, hi_r = min(ri.z, w.z);
             const int4 tw = tile_win[w.x];
             const int f_lo = max(tw.z, w.y), f_hi = min(tw.w, w.z);  // columns valid for every row
             unsigned long long b1 = 0, b2 = 0;
-            for (int k = 0; k < nt; ++k, ++gt) {
-                const int acc = gt & 1;
-                ok = __all_sync(0xffffffffu, mbar_wait(&sh.tfull[acc], (gt >> 1) & 1, abort_flag));
+            for (int k0 = 0; k0 < nt && ok; k0 += kChunkTiles, ++lc) {
+                const int ntc = min(kChunkTiles, nt - k0);
+                const int jc = w.y + k0 * kTileDom;
+                // per-domain constants of this chunk into shared memory (double-buffered by chunk
+                // parity; a thread reaches chunk lc + 2 only after every thread has left chunk lc)
+                const int ab = lc & 1;
+                for (int k = ew * 32 + lane; k < ntc * kTileDom; k += 32 * kEpiWarps)
+                    sh.aux[ab][k] = __ldg(&dom_aux[jc + k]);
+                mbar_arrive(&sh.aux_ready[ab]);
+                ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (lc >> 1) & 1, abort_flag));
                 if (!ok) break;
-                tc_fence_after();
-                const int jh = w.y + k * kTileDom + half * (kTileDom / 2);
-                const float4 *auxp = &sh.aux[ab][k * kTileDom + half * (kTileDom / 2)];
-                const uint32_t taddr = tbase + acc * kTileN;
-                uint32_t t1 = 0, t2 = 0;
-                if (jh >= f_lo && jh + kTileDom / 2 <= f_hi)
-                    epi_half<false>(taddr, auxp, A, jh, lo_r, hi_r, t1, t2);
-                else
-                    epi_half<true>(taddr, auxp, A, jh, lo_r, hi_r, t1, t2);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sh.tempty[acc]);
-                merge_half_key(b1, b2, t1, jh);
-                merge_half_key(b1, b2, t2, jh);
+                uint32_t cmax = 0;
+                for (int k = 0; k < ntc; ++k, ++gt) {
+                    const int acc = gt & 1;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sh.tfull[acc], (gt >> 1) & 1, abort_flag));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const int jh = jc + k * kTileDom + half * (kTileDom / 2);
+                    const float4 *auxp = &sh.aux[ab][k * kTileDom + half * (kTileDom / 2)];
+                    const uint32_t taddr = tbase + acc * kTileN;
+                    uint32_t t1 = 0, t2 = 0;
+                    if (jh >= f_lo && jh + kTileDom / 2 <= f_hi)
+                        epi_half<false>(taddr, auxp, jh, lo_r, hi_r, t1, t2);
+                    else
+                        epi_half<true>(taddr, auxp, jh, lo_r, hi_r, t1, t2);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.tempty[acc]);
+                    merge_half_key(b1, b2, t1, jh);
+                    merge_half_key(b1, b2, t2, jh);
+                    cmax = max(cmax, t1);
+                }
+                if (ok && valid)
+                    chunk_max[((size_t)(w.w + k0 / kChunkTiles) * kTileM + row) * 2 + half] = cmax & 0xFFFFFFF0u;
             }
             if (ok && valid) {
-                unsigned long long *dst = cand + (((size_t)i * max_chunks + w.w) * 2 + half) * 2;
+                unsigned long long *dst = cand + (((size_t)it * kTileM + row) * 2 + half) * 2;
                 dst[0] = b1;
                 dst[1] = b2;
             }
@@ -575,26 +638,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---- exact re-evaluation and certification ----------------------------------------------------
-// One warp per class-sorted range position i. Merges the range's top-2 keys over its tile's
-// chunks, evaluates both candidates under all 8 isometries exactly, keeps the best (gain, then
+// One warp per class-sorted range position i of one image. Merges the range's top-2 keys over its
+// tile's work items, evaluates both candidates under all 8 isometries exactly, keeps the best (gain, then
 // smaller domain id, then smaller isometry) and certifies it: every other domain's FP32 score is
-// at most the runner-up's, and an FP32 score differs from that domain's exact gain / 8 by less
-// than a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
+// at most the runner-up's, and an FP32 score is an upper bound of that domain's exact gain / 512
+// up to a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
 // of single-rounding operations), so if runner-up * (1 + 2^-16) < exact best, no other domain
-// can win or tie. Otherwise the range is queued with its exact best for k_rescan.
-// Otherwise the range goes to the exact re-search list. Flat ranges (n Bs = A^2) have zero error
+// can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
+// (n Bs = A^2) have zero error
 // for every candidate; their code is the smallest domain id of the pool with t = 0.
 __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                          const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                          const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
                          const int32_t *__restrict__ bin_off, const uint8_t *__restrict__ rbin,
-                         const int4 *__restrict__ rng_info, const int4 *__restrict__ tile_win,
-                         const unsigned long long *__restrict__ cand, int max_chunks, int32_t *__restrict__ fallback,
+                         const int4 *__restrict__ rng_info, int rng_off, int dom_off,
+                         const int4 *__restrict__ tile_items, const unsigned long long *__restrict__ cand,
+                         const int32_t *__restrict__ gcounters, int32_t *__restrict__ fallback,
                          FallbackBest *__restrict__ fb_best, int32_t *counters, fic_codes out) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // sorted position in this image
     const int lane = threadIdx.x & 31;
     if (i >= g.R) return;
-    if (counters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
     const int4 ri = rng_info[i];
     const int r = ri.w;
     const long long A = ri.x, Bs = rsumsq[r];
@@ -627,13 +691,13 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
         return;
     }
 
-    // merge the top-2 keys of all chunks
-    const int m = i / kTileM;
-    const int4 tw = tile_win[m];
-    const int chunk = kTileDom * kChunkTiles;
-    const int nch = tw.y > tw.x ? (tw.y - tw.x + chunk - 1) / chunk : 0;
+    // merge the top-2 keys of all work items of this range's tile
+    const int ig = rng_off + i;
+    const int row = ig % kTileM;
+    const int4 ti = tile_items[ig / kTileM];
     unsigned long long b1 = 0, b2 = 0;
-    for (int e = lane; e < 4 * nch; e += 32) top2(b1, b2, cand[(size_t)i * max_chunks * 4 + e]);
+    for (int e = lane; e < 4 * ti.y; e += 32)
+        top2(b1, b2, cand[((size_t)(ti.x + (e >> 2)) * kTileM + row) * 4 + (e & 3)]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, off);
@@ -644,13 +708,13 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     // exact evaluation: lane = 8 * candidate + t for lanes 0..15
     const int cidx = lane >> 3, t = lane & 7;
     const unsigned long long key = cidx == 0 ? b1 : b2;
-    const bool has = lane < 16 && key != 0 && (int)(~(uint32_t)(key & 0xffffffffu)) < g.Dn;
+    const int jl = (int)(~(uint32_t)(key & 0xffffffffu)) - dom_off;  // position in this image
+    const bool has = lane < 16 && key != 0 && jl >= 0 && jl < g.Dn;
     Gain gg{-1, 1};
     int d = INT_MAX;
     long long P = 0, Q = 0, C = 0;
     if (has) {
-        const int j = (int)(~(uint32_t)(key & 0xffffffffu));
-        d = dom_order[j];
+        d = dom_order[jl];
         const uint16_t *S = domS + (size_t)d * 64;
         long long X = 0;
         for (int y = 0; y < 8; ++y) {
@@ -686,8 +750,8 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     bool certified = b1 != 0 && gg.num >= 0;
     if (certified && b2 != 0) {
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
-        const double g8 = (double)gg.num / (8.0 * (double)gg.den);
-        certified = u2 * (1.0 + 1.0 / 65536.0) < g8;
+        const double sc = (double)gg.num / (512.0 * (double)gg.den);  // exact gain / 512
+        certified = u2 * (1.0 + 1.0 / 65536.0) < sc;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
@@ -734,17 +798,18 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// rows x 64 fp16, row-major (128-byte rows); box = box_rows x 64; 128-byte swizzle.
-cudaError_t make_map(CUtensorMap *map, void *base, unsigned long long rows, unsigned box_rows) {
+// rows x cols fp16, row-major (cols = 64: 128-byte rows, 128-byte swizzle; cols = 16: 32-byte
+// rows, 32-byte swizzle); box = box_rows x cols.
+cudaError_t make_map(CUtensorMap *map, void *base, unsigned long long rows, unsigned box_rows, unsigned cols) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {64, rows};
-    const cuuint64_t strides[1] = {128};
-    const cuuint32_t box[2] = {64, box_rows};
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 }  // namespace
@@ -753,47 +818,57 @@ cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, c
     {
         const long long n = (long long)b.R_pad * 8;
         k_pack_ranges<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, img, b.range_order, b.range_sum, b.win_lo,
-                                                                  b.win_hi, b.R_pad, b.A_mat, b.rng_info);
+                                                                  b.win_hi, b.R_pad, b.dom_off, b.A_mat,
+                                                                  (uint4 *)b.A1_mat, b.rng_info);
         ++g_launches;
     }
     {
         const long long n = (long long)b.Dn_aux * 64;
         k_pack_domains<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, b.dom_S, b.dom_order, b.dom_sum,
-                                                                   b.dom_sumsq, b.Dn_aux, b.B_mat, b.dom_aux);
+                                                                   b.dom_sumsq, b.Dn_aux, b.B_mat, (uint4 *)b.B1_mat,
+                                                                   b.dom_aux);
         ++g_launches;
     }
-    k_tile_windows<<<b.n_mtiles, kTileM, 0, st>>>(g.R, b.rng_info, b.tile_win, b.n_chunks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st) {
+    k_tile_windows<<<tb.n_mtiles, kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
     ++g_launches;
-    k_work_list<<<1, 1024, 0, st>>>(b.n_mtiles, b.tile_win, b.n_chunks, b.work, b.counters);
+    const int target = max(1, min(target_items, kMaxItemTarget));
+    k_work_list<<<1, 1024, 0, st>>>(tb.n_mtiles, target, tb.tile_win, tb.n_chunks, tb.work, tb.tile_items,
+                                    tb.gcounters);
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_match_tc(const Geo &g, const EncodeBufs &b, int num_sms, cudaStream_t st) {
-    CUtensorMap tmA, tmB;
+cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
+    CUtensorMap tmA, tmB, tmA1, tmB1;
     cudaError_t e;
-    if ((e = make_map(&tmA, b.A_mat, (unsigned long long)b.R_pad, kTileM))) return e;
-    if ((e = make_map(&tmB, b.B_mat, (unsigned long long)b.Dn_aux * 8, kTileN))) return e;
+    if ((e = make_map(&tmA, tb.A_mat, (unsigned long long)tb.R_pad, kTileM, 64))) return e;
+    if ((e = make_map(&tmB, tb.B_mat, (unsigned long long)tb.Dn_aux * 8, kTileN, 64))) return e;
+    if ((e = make_map(&tmA1, tb.A1_mat, (unsigned long long)tb.R_pad, kTileM, 16))) return e;
+    if ((e = make_map(&tmB1, tb.B1_mat, (unsigned long long)tb.Dn_aux * 8, kTileN, 16))) return e;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         attr_err = cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     });
     if (attr_err) return attr_err;
-    const int grid = num_sms < b.max_items ? num_sms : b.max_items;
+    const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
     if (grid <= 0) return cudaSuccess;
-    k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, g.R, b.work, b.counters, b.tile_win, b.rng_info,
-                                                   b.dom_aux, b.max_chunks, b.cand, b.counters + 2);
+    k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.gcounters, tb.tile_win,
+                                                   tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max, tb.gcounters + 2);
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const fic_codes &out,
-                          cudaStream_t st) {
+cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
+                          const fic_codes &out, cudaStream_t st) {
     const long long threads = (long long)g.R * 32;
     k_reeval<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
         g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, b.range_bin, b.rng_info,
-        b.tile_win, b.cand, b.max_chunks, b.fallback, b.fb_best, b.counters, out);
+        b.rng_off, b.dom_off, tb.tile_items, tb.cand, tb.gcounters, b.fallback, b.fb_best, b.counters, out);
     ++g_launches;
     return cudaGetLastError();
 }

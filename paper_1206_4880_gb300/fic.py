@@ -27,7 +27,8 @@ class Geom(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("block", c_i32), ("domain_stride", c_i32), ("num_classes", c_i32),
-                ("half_width", c_i32), ("s_max", c_dbl), ("engine", c_i32), ("flags", c_i32)]
+                ("half_width", c_i32), ("s_max", c_dbl), ("engine", c_i32), ("flags", c_i32),
+                ("items_per_sm", c_i32)]
 
 
 class BlockStats(ctypes.Structure):
@@ -56,6 +57,8 @@ SIGNATURES = {
     "fic_classify": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_build_pools": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_encode": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
+    "fic_encode_batched_workspace_size": (c_size, [c_vp, c_i32, c_vp]),
+    "fic_encode_batched": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_decode_workspace_size": (c_size, [c_vp, c_vp, c_i32, c_i32]),
     "fic_decode": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_decode_backward": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp,
@@ -114,10 +117,11 @@ class EncodeParams:
     engine: str = "tensor"
     block: int = 8
     s_max: float = 1.0
+    items_per_sm: int = 0
 
     def c(self) -> Params:
         return Params(self.block, self.domain_stride, self.num_classes, self.half_width,
-                      self.s_max, ENGINES[self.engine], 0)
+                      self.s_max, ENGINES[self.engine], 0, self.items_per_sm)
 
 
 def geom(H: int, W: int, pitch: int | None = None) -> Geom:
@@ -188,6 +192,38 @@ def encode(img: torch.Tensor, p: EncodeParams, out: dict | None = None,
 def engine_available(engine: str) -> bool:
     """Whether the library can run `engine` on the current CUDA device."""
     return bool(load().fic_engine_available(ENGINES[engine]))
+
+
+def encode_batched_workspace_size(shapes, p: EncodeParams) -> int:
+    n = len(shapes)
+    geoms = (Geom * n)(*[geom(H, W) for H, W in shapes])
+    pc = p.c()
+    size = load().fic_encode_batched_workspace_size(geoms, n, ctypes.byref(pc))
+    if size == 0:
+        raise FicError(FIC_ERR_INVALID_ARG, load().fic_last_error().decode())
+    return size
+
+
+def encode_batched(imgs, p: EncodeParams, outs=None, workspace=None, info=None, stream=None):
+    """fic_encode_batched over a list of uint8 CUDA images (any sizes); returns one code dict per
+    image. The tensor engine matches all images in one persistent launch."""
+    n = len(imgs)
+    for t in imgs:
+        _require_cuda(t, "img")
+        if t.dtype != torch.uint8 or t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError("images must be 2-D uint8 tensors with unit column stride")
+    geoms = (Geom * n)(*[geom(t.shape[0], t.shape[1], t.stride(0)) for t in imgs])
+    if outs is None:
+        outs = [alloc_codes(counts(t.shape[0], t.shape[1], p)[0], t.device) for t in imgs]
+    if workspace is None:
+        workspace = torch.empty(encode_batched_workspace_size([tuple(t.shape) for t in imgs], p),
+                                dtype=torch.uint8, device=imgs[0].device)
+    ptrs = (c_vp * n)(*[t.data_ptr() for t in imgs])
+    cs = (Codes * n)(*[_codes_struct(o) for o in outs])
+    pc = p.c()
+    _check(load().fic_encode_batched(ptrs, geoms, n, ctypes.byref(pc), cs, _p(info), _p(workspace),
+                                     workspace.numel(), _stream(stream)))
+    return outs
 
 
 def new_info(device) -> torch.Tensor:

@@ -58,10 +58,14 @@ def test_encode_rejects_before_any_launch():
     st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g), ctypes.byref(p),
                         ctypes.byref(codes), None, None, 0, None)
     assert st == fic.FIC_ERR_WORKSPACE and b"workspace" in lib.fic_last_error()
-    # misaligned workspace
+    # a workspace too small once aligned to 1024 bytes
+    need = lib.fic_encode_workspace_size(ctypes.byref(g), ctypes.byref(p))
     st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g), ctypes.byref(p),
-                        ctypes.byref(codes), None, ctypes.c_void_p(0x1008), 1 << 30, None)
+                        ctypes.byref(codes), None, ctypes.c_void_p(0x1008), need - 1024, None)
     assert st == fic.FIC_ERR_WORKSPACE
+    # batched: bad count
+    assert lib.fic_encode_batched_workspace_size(ctypes.byref(g), 0, ctypes.byref(p)) == 0
+    assert lib.fic_encode_batched_workspace_size(ctypes.byref(g), 1, ctypes.byref(p)) == need
     # too small
     st = lib.fic_encode(ctypes.c_void_p(0x1000), ctypes.byref(g), ctypes.byref(p),
                         ctypes.byref(codes), None, ctypes.c_void_p(0x1000), 1024, None)

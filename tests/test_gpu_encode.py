@@ -201,3 +201,29 @@ def test_full_search_simt_equals_k1_tensor():
     torch.cuda.synchronize()
     for k in a:
         assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_encode_batched_equals_oracle(engine):
+    """Several images of different sizes in one fic_encode_batched call (one tensor-engine launch
+    for all of them): each image's codes equal the oracle's for that image alone."""
+    _need_tensor(engine)
+    shapes = [(64, 48, 31), (136, 200, 32), (96, 128, 33), (32, 32, 34), (256, 256, 35), (48, 64, 36)]
+    imgs = [synth.fbm_image(seed, H, W) for H, W, seed in shapes]
+    p = _params(4, 7, -1, engine)
+    info = fic.new_info("cuda")
+    outs = fic.encode_batched([_t(im) for im in imgs], p, info=info)
+    torch.cuda.synchronize()
+    total = 0
+    for im, out in zip(imgs, outs):
+        ref = omatch.encode(im, B=8, sigma=4, K=7, n_threads=8)
+        _compare_codes(out, ref)
+        total += int(ref["pool_size"].sum()) * 8
+    rep = fic.read_info(info)
+    assert rep["matches"] == total and rep["device_error"] == 0
+    # the same images one at a time give the same codes
+    for im, out in zip(imgs, outs):
+        single = fic.encode(_t(im), p)
+        torch.cuda.synchronize()
+        for k in ("dom", "iso", "s", "o", "sse"):
+            assert torch.equal(single[k], out[k]), k
