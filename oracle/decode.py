@@ -16,6 +16,11 @@ The adjoint: with W the linear part of one step (x -> s * T(D(x))), lambda_K = d
 lambda_k = W^T lambda_{k+1}, the gradients are
     dL/ds_r = sum_k sum_{p in r} lambda_{k+1}[p] * T_{t_r}(D(x_k, d_r))[p]
     dL/do_r = sum_k sum_{p in r} lambda_{k+1}[p].
+Resolution independence (Section 1: the initial image "can be of any size", decoding
+reconstructs "to any size"): decode_scaled applies the same codes on a z-times larger grid:
+range r covers the (8z) x (8z) block at z times its position, domain d the (16z) x (16z) block at
+z times its position, contracted by 2x2 averaging, with the isometries of the larger square.
+
 Everything is binary64.
 """
 from __future__ import annotations
@@ -84,3 +89,18 @@ def decode_adjoint(codes: dict, H: int, W: int, B: int, sigma: int, iters: int,
                     prev[dy + a:dy + 2 * B:2, dx + b:dx + 2 * B:2] += G
         lam = prev
     return gs, go
+
+
+def decode_scaled(codes: dict, H: int, W: int, B: int, sigma: int, iters: int, z: int, x0=None) -> np.ndarray:
+    """Decode codes of an H x W encoding on the (zH) x (zW) grid (module docstring)."""
+    Bz = B * z
+    x = np.full((z * H, z * W), 128.0) if x0 is None else np.array(x0, dtype=np.float64)
+    for _ in range(iters):
+        y = np.empty_like(x)
+        for r in range(geometry.n_ranges(H, W, B)):
+            dy, dx = geometry.domain_origin(H, W, B, sigma, int(codes["dom"][r]))
+            ry, rx = geometry.range_origin(H, W, B, r)
+            D = _contract(x, Bz, z * dy, z * dx)
+            y[z * ry:z * ry + Bz, z * rx:z * rx + Bz] = codes["s"][r] * geometry.isometry(D, int(codes["iso"][r])) + codes["o"][r]
+        x = y
+    return x

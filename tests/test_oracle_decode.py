@@ -133,3 +133,19 @@ def test_adjoint_against_central_differences(iters):
             fm = np.sum(g * decode.decode(cm, H, W, 8, 4, iters))
             fdv = (fp - fm) / (2 * h)
             assert abs(grad[r] - fdv) <= 1e-4 * max(1.0, abs(fdv)), (key, r, grad[r], fdv)
+
+
+def test_scaled_decode_pins():
+    """z = 1 is the ordinary decode; 2x2 averaging of the 2x decode is the 1x decode (the maps
+    commute with block averaging: isometries move aligned 2x2 blocks to aligned 2x2 blocks and the
+    brightness is constant over a block)."""
+    rng = np.random.default_rng(5)
+    H, W = 32, 48
+    c = _random_codes(rng, H, W, 8, 4, 0.9)
+    x1 = decode.decode(c, H, W, 8, 4, 5)
+    assert np.allclose(decode.decode_scaled(c, H, W, 8, 4, 5, 1), x1, rtol=0, atol=1e-12)
+    x2 = decode.decode_scaled(c, H, W, 8, 4, 5, 2)
+    down = x2.reshape(H, 2, W, 2).mean(axis=(1, 3))
+    assert np.allclose(down, x1, rtol=0, atol=1e-9)
+    x3 = decode.decode_scaled(c, H, W, 8, 4, 3, 3)
+    assert np.allclose(x3.reshape(H, 3, W, 3).mean(axis=(1, 3)), decode.decode(c, H, W, 8, 4, 3), atol=1e-9)
