@@ -418,9 +418,7 @@ def comparators(img, img_np, wl, args, dev):
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
         x = fic.decode(out, H, W, p, 8)
-        xq = np.clip(np.rint(x.cpu().numpy().astype(np.float64)), 0, 255)
-        mse = np.mean((xq - img_np.astype(np.float64)) ** 2)
-        return statistics.median(ms), float(10 * np.log10(255.0 ** 2 / mse))
+        return statistics.median(ms), fic.quality(x, img)[1]
 
     engines = ["simt", "tensor"] if args.engine == "tensor" else ["simt"]
     for eng in engines:

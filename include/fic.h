@@ -59,6 +59,13 @@ enum {
     FIC_ENGINE_SIMT = 1    /* exact search on CUDA cores (the plain GPU search) */
 };
 
+/* Pool window (fic_params.flags). Default: the class window |bin_d - bin_r| <= w. With
+ * FIC_FLAG_LITERAL_WINDOW the pool is Section 3.1 Eq. 3 on the FD values themselves,
+ * Pool(r) = {d : FD_r - D_f <= FD_d <= FD_r + D_f}, D_f = (F_m - F_l) / 3 (Eq. 2), each bound one
+ * binary64 operation; domains and ranges are then ordered by FD value instead of class, and
+ * num_classes / half_width only shape the reported classes. */
+#define FIC_FLAG_LITERAL_WINDOW 1
+
 typedef struct {
     int32_t H, W;   /* image height and width in pixels: multiples of B, >= 2B */
     int32_t pitch;  /* bytes between rows, >= W */
@@ -71,7 +78,7 @@ typedef struct {
     int32_t half_width;    /* w >= 0 classes on each side; -1 selects floor(K/3) (Eq. 2) */
     double s_max;          /* contrast clamp; must be 1.0 */
     int32_t engine;        /* FIC_ENGINE_TENSOR or FIC_ENGINE_SIMT */
-    int32_t flags;         /* reserved, must be 0 */
+    int32_t flags;         /* 0, or FIC_FLAG_LITERAL_WINDOW */
     int32_t items_per_sm;  /* tensor engine scheduling: work items per SM the range tiles' domain
                               chunks are split into, 1..64; 0 selects 16 */
 } fic_params;
@@ -99,8 +106,10 @@ typedef struct {
 /* Dynamic pools (Section 3.1 Eq. 3 in class units, replacing the paper's AVL tree by an
  * ordered array: a range query of the tree is a contiguous slice of the class-sorted domains).
  *  dom_order[Dn]   domain ids sorted by (class, id) - the in-order traversal of the tree;
- *  bin_off[K+1]    dom_order[bin_off[b] .. bin_off[b+1]) holds class b;
- *  range_order[R]  range ids sorted by (class, id); rbin_off[K+1] likewise;
+ *  bin_off[257]    (257 entries) dom_order[bin_off[b] .. bin_off[b+1]) holds class b (with
+ *                  FIC_FLAG_LITERAL_WINDOW: the b-th smallest distinct FD value that 8x8 box
+ *                  counts can produce, up to 245 + 1 entries);
+ *  range_order[R]  range ids sorted by (class, id); rbin_off[257] likewise;
  *  win_lo[R], win_hi[R]  Pool(r) = dom_order[win_lo[r] .. win_hi[r]) = the domains with
  *                  |bin_d - bin_r| <= w; when that set is empty the pool is every domain
  *                  (win_lo = 0, win_hi = Dn). */
@@ -160,6 +169,32 @@ fic_status fic_encode_batched(const uint8_t *const *imgs, const fic_geom *geoms,
                               const fic_params *p, const fic_codes *outs, fic_encode_info *info,
                               void *workspace, size_t workspace_bytes, void *stream);
 
+/* Doubles `out` must hold for fic_quality. */
+#define FIC_QUALITY_OUT_DOUBLES 1026
+
+/* Table 4's quality metric: decoded 8-bit image clamp(round-half-even(x), 0, 255) (x: H*W floats,
+ * dense) against the original `ref` (H x W bytes, row pitch g->pitch). Writes out[0] = mean
+ * squared error, out[1] = PSNR = 10 log10(255^2 / MSE) in dB (+inf when MSE = 0); out[2..] is
+ * scratch (FIC_QUALITY_OUT_DOUBLES entries in all, device memory). The sum runs in binary64 in
+ * a fixed order, so the result does not depend on scheduling. */
+fic_status fic_quality(const float *x, const uint8_t *ref, const fic_geom *g, double *out, void *stream);
+
+/* Doubles `header` must hold for fic_quantize. */
+#define FIC_QUANT_HEADER_DOUBLES 514
+
+/* A code format for Section 1's "transformation coefficients" (the paper fixes none): contrast
+ * s in [-1, 1] quantised uniformly to 2^bits_s levels including both endpoints, brightness o
+ * quantised uniformly to 2^bits_o levels over the codes' own [min o, max o]; 1 <= bits <= 16.
+ * With Ls = 2^bits_s - 1 and Lo = 2^bits_o - 1, each a separate binary64 operation:
+ *   q_s = clamp(rint(((s + 1) / 2) * Ls), 0, Ls),  s' = (q_s * 2) / Ls - 1,
+ *   q_o = clamp(rint(((o - lo) / (hi - lo)) * Lo), 0, Lo) (0 if hi == lo),
+ *   o' = lo + (q_o * (hi - lo)) / Lo,  rint rounding half to even.
+ * Writes q_s, q_o (n entries), header[0] = lo, header[1] = hi (header holds
+ * FIC_QUANT_HEADER_DOUBLES device doubles, the rest scratch) and the dequantised codes to `out`
+ * (dom and iso copied from `in`; `out` may be `in`). All pointers are device pointers. */
+fic_status fic_quantize(const fic_codes *in, int32_t n, int32_t bits_s, int32_t bits_o, uint16_t *q_s,
+                        uint16_t *q_o, double *header, const fic_codes *out, void *stream);
+
 /* Bytes of workspace fic_decode and fic_decode_backward need. */
 size_t fic_decode_workspace_size(const fic_geom *g, const fic_params *p, int32_t iters,
                                  int32_t ckpt_every);
@@ -171,6 +206,19 @@ size_t fic_decode_workspace_size(const fic_geom *g, const fic_params *p, int32_t
 fic_status fic_decode(const fic_codes *codes, const fic_geom *g, const fic_params *p,
                       int32_t iters, const float *x0, float *out, void *workspace,
                       size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace fic_decode_scaled needs at this scale. */
+size_t fic_decode_scaled_workspace_size(const fic_geom *g, const fic_params *p, int32_t scale);
+
+/* Section 1, resolution independence ("the initial image can be of any size"): decodes the codes
+ * of the H x W encoding g on the (scale*H) x (scale*W) grid, 1 <= scale <= 16: range r covers the
+ * (8 scale)^2 block at scale times its position, domain d the (16 scale)^2 block at scale times its
+ * position, contracted by 2x2 averaging, under the isometries of the larger square. x0 and out
+ * are (scale H) x (scale W) floats (x0 NULL: 128 everywhere). With scale = 1 it is fic_decode;
+ * 2x2 block averages of a scale-2 decode equal the scale-1 decode from the same constant start. */
+fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *g, const fic_params *p,
+                             int32_t scale, int32_t iters, const float *x0, float *out,
+                             void *workspace, size_t workspace_bytes, void *stream);
 
 /* Adjoint of fic_decode with respect to the per-range contrast and brightness: given
  * grad_out = dL/dx_iters (H*W float), writes grad_s[r] = dL/ds_r and grad_o[r] = dL/do_r

@@ -18,6 +18,12 @@ cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *
                                  double *gs, double *go, cudaStream_t st);
 cudaError_t launch_grads_out(int R, const double *gs64, const double *go64, float *gs, float *go,
                              cudaStream_t st);
+cudaError_t launch_quality(const float *x, const uint8_t *ref, int H, int W, int pitch, double *out,
+                           cudaStream_t st);
+cudaError_t launch_decode_step_scaled(const fic_codes &c, const Geo &g, int z, const float *x, float *y,
+                                      cudaStream_t st);
+cudaError_t launch_quantize(const fic_codes &in, int n, int bits_s, int bits_o, uint16_t *q_s, uint16_t *q_o,
+                            double *header, const fic_codes &out, cudaStream_t st);
 bool tensor_engine_available(int device);
 constexpr int kMaxBatch = 4096;
 }  // namespace fic
@@ -72,7 +78,8 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
     if (p->s_max != 1.0) return fail(FIC_ERR_INVALID_ARG, "s_max must be 1.0");
     if (p->engine != FIC_ENGINE_TENSOR && p->engine != FIC_ENGINE_SIMT)
         return fail(FIC_ERR_INVALID_ARG, "unknown engine %d", p->engine);
-    if (p->flags != 0) return fail(FIC_ERR_INVALID_ARG, "flags must be 0");
+    if (p->flags != 0 && p->flags != FIC_FLAG_LITERAL_WINDOW)
+        return fail(FIC_ERR_INVALID_ARG, "flags must be 0 or FIC_FLAG_LITERAL_WINDOW");
     if (p->items_per_sm < 0 || p->items_per_sm > 64)
         return fail(FIC_ERR_INVALID_ARG, "items_per_sm must be in [0, 64]");
     g->H = gm->H;
@@ -89,6 +96,7 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
     g->Dn = g->nDy * g->nDx;
     g->K = p->num_classes;
     g->w = p->half_width < 0 ? p->num_classes / 3 : p->half_width;
+    g->literal = (p->flags & FIC_FLAG_LITERAL_WINDOW) ? 1 : 0;
     return FIC_OK;
 }
 
@@ -143,6 +151,8 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->rbin_off = c.take<int32_t>(kMaxClasses + 2);
         b->win_lo = c.take<int32_t>(g.R);
         b->win_hi = c.take<int32_t>(g.R);
+        b->dom_key = c.take<uint8_t>(g.Dn);
+        b->range_key = c.take<uint8_t>(g.R);
         b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 256);
         b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 256);
         b->fallback = c.take<int32_t>(g.R);
@@ -311,6 +321,14 @@ fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *gm, const f
         return fail(FIC_ERR_INVALID_ARG, "null statistics or pool pointer");
     b.range_bin = st->range_bin;
     b.dom_bin = st->dom_bin;
+    if (g.literal) {
+        if (!st->range_counts || !st->dom_counts || !st->range_fd || !st->fd_extent)
+            return fail(FIC_ERR_INVALID_ARG, "the literal window needs box counts, range FDs and F_l/F_m");
+        b.range_counts = st->range_counts;
+        b.dom_counts = st->dom_counts;
+        b.range_fd = st->range_fd;
+        b.fd_extent = st->fd_extent;
+    }
     b.dom_order = out->dom_order;
     b.bin_off = out->bin_off;
     b.range_order = out->range_order;
@@ -390,6 +408,26 @@ fic_status fic_encode_batched(const uint8_t *const *imgs, const fic_geom *geoms,
     return encode_batch(imgs, geoms, n, p, outs, info, ws, bytes, stream);
 }
 
+fic_status fic_quality(const float *x, const uint8_t *ref, const fic_geom *gm, double *out, void *stream) {
+    if (!x || !ref || !gm || !out) return fail(FIC_ERR_INVALID_ARG, "null pointer");
+    if (gm->H < 1 || gm->W < 1 || gm->pitch < gm->W) return fail(FIC_ERR_INVALID_ARG, "bad geometry");
+    g_launches = 0;
+    FIC_TRY(launch_quality(x, ref, gm->H, gm->W, gm->pitch, out, (cudaStream_t)stream), "quality");
+    return FIC_OK;
+}
+
+fic_status fic_quantize(const fic_codes *in, int32_t n, int32_t bits_s, int32_t bits_o, uint16_t *q_s,
+                        uint16_t *q_o, double *header, const fic_codes *out, void *stream) {
+    if (!in || !in->dom || !in->iso || !in->s || !in->o || !out || !out->dom || !out->iso || !out->s ||
+        !out->o || !q_s || !q_o || !header)
+        return fail(FIC_ERR_INVALID_ARG, "null pointer");
+    if (n < 1 || bits_s < 1 || bits_s > 16 || bits_o < 1 || bits_o > 16)
+        return fail(FIC_ERR_INVALID_ARG, "n must be >= 1 and bits in [1, 16]");
+    g_launches = 0;
+    FIC_TRY(launch_quantize(*in, n, bits_s, bits_o, q_s, q_o, header, *out, (cudaStream_t)stream), "quantize");
+    return FIC_OK;
+}
+
 fic_status fic_profile_enable(int32_t on) {
     if (on && !g_prof.on) {
         for (auto &e : g_prof.ev) FIC_TRY(cudaEventCreate(&e), "cudaEventCreate");
@@ -465,6 +503,45 @@ fic_status fic_decode(const fic_codes *codes, const fic_geom *gm, const fic_para
     for (int k = 0; k < iters; ++k) {
         float *dst = ((iters - 1 - k) % 2 == 0) ? out : tmp;
         FIC_TRY(launch_decode_step(*codes, g, cur, dst, st), "decode_step");
+        cur = dst;
+    }
+    return FIC_OK;
+}
+
+size_t fic_decode_scaled_workspace_size(const fic_geom *gm, const fic_params *p, int32_t scale) {
+    Geo g;
+    if (make_geo(gm, p, &g) != FIC_OK || scale < 1 || scale > 16) return 0;
+    return (size_t)g.H * g.W * scale * scale * sizeof(float) + 256;
+}
+
+fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *gm, const fic_params *p, int32_t scale,
+                             int32_t iters, const float *x0, float *out, void *ws, size_t bytes, void *stream) {
+    Geo g;
+    fic_status s = make_geo(gm, p, &g);
+    if (s != FIC_OK) return s;
+    if ((s = check_codes(codes)) != FIC_OK) return s;
+    if (!out || iters < 0 || scale < 1 || scale > 16)
+        return fail(FIC_ERR_INVALID_ARG, "null output, negative iters or scale outside [1, 16]");
+    const size_t img = (size_t)g.H * g.W * scale * scale;
+    if (!ws || (uintptr_t)ws % 256 || bytes < img * sizeof(float))
+        return fail(FIC_ERR_WORKSPACE, "workspace null, misaligned or below %zu bytes", img * sizeof(float));
+    cudaStream_t st = (cudaStream_t)stream;
+    g_launches = 0;
+    float *tmp = (float *)ws;
+    if (iters == 0) {
+        if (x0) FIC_TRY(cudaMemcpyAsync(out, x0, img * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy");
+        else FIC_TRY(launch_fill(out, img, 128.f, st), "fill");
+        return FIC_OK;
+    }
+    const float *cur = x0;
+    if (!x0) {
+        float *init = ((iters - 1) % 2 == 0) ? tmp : out;
+        FIC_TRY(launch_fill(init, img, 128.f, st), "fill");
+        cur = init;
+    }
+    for (int k = 0; k < iters; ++k) {
+        float *dst = ((iters - 1 - k) % 2 == 0) ? out : tmp;
+        FIC_TRY(launch_decode_step_scaled(*codes, g, scale, cur, dst, st), "decode_step_scaled");
         cur = dst;
     }
     return FIC_OK;

@@ -50,6 +50,35 @@ cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x,
     return cudaGetLastError();
 }
 
+// Resolution-independent step (Section 1): the codes of an H x W encoding applied on the
+// (zH) x (zW) grid; range r covers the (8z)^2 block at z times its position, domain d the (16z)^2
+// block at z times its position, contracted by 2x2 averaging, with the isometries of the
+// (8z) x (8z) square. One thread per output pixel.
+__global__ void k_decode_step_scaled(Geo g, int z, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                                     const double *__restrict__ s, const double *__restrict__ o,
+                                     const float *__restrict__ x, float *__restrict__ y) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Wz = g.W * z, Bz = 8 * z;
+    if (idx >= (long long)g.H * z * Wz) return;
+    const int py = (int)(idx / Wz), px = (int)(idx - (long long)py * Wz);
+    const int r = (py / Bz) * g.nRx + px / Bz;
+    const int d = dom[r], t = iso[r];
+    int sy, sx;
+    iso_src(Bz, t, py % Bz, px % Bz, sy, sx);
+    const int qy = (d / g.nDx) * g.sigma * z + 2 * sy, qx = (d % g.nDx) * g.sigma * z + 2 * sx;
+    const float *p = x + (size_t)qy * Wz + qx;
+    const float v = (((p[0] + p[1]) + p[Wz]) + p[Wz + 1]) * 0.25f;
+    y[idx] = fmaf((float)s[r], v, (float)o[r]);
+}
+
+cudaError_t launch_decode_step_scaled(const fic_codes &c, const Geo &g, int z, const float *x, float *y,
+                                      cudaStream_t st) {
+    const long long n = (long long)g.H * g.W * z * z;
+    k_decode_step_scaled<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, z, c.dom, c.iso, c.s, c.o, x, y);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
 // ---- adjoint -------------------------------------------------------------------------------
 // domain -> ranges CSR: cnt[d] = #ranges using d; off = exclusive scan; list sorted per segment.
 __global__ void k_dom_count(Geo g, const int32_t *__restrict__ dom, int32_t *cnt) {
@@ -223,6 +252,56 @@ cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *
 cudaError_t launch_grads_out(int R, const double *gs64, const double *go64, float *gs, float *go,
                              cudaStream_t st) {
     k_grads_out<<<(R + 255) / 256, 256, 0, st>>>(R, gs64, go64, gs, go);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+// ---- quality (PSNR) --------------------------------------------------------------------------
+constexpr int kQualBlocks = 1024;
+
+__global__ void k_sqerr_partial(const float *__restrict__ x, const uint8_t *__restrict__ ref, int H, int W,
+                                int pitch, double *__restrict__ partial) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    const long long n = (long long)H * W;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int py = (int)(i / W), px = (int)(i - (long long)py * W);
+        const float q = fminf(fmaxf(rintf(x[i]), 0.f), 255.f);
+        const double e = (double)q - (double)ref[(size_t)py * pitch + px];
+        acc += e * e;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sqerr_final(const double *__restrict__ partial, int nb, long long n, double *out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mse = red[0] / (double)n;
+        out[0] = mse;
+        out[1] = mse > 0.0 ? 10.0 * log10(255.0 * 255.0 / mse) : __longlong_as_double(0x7ff0000000000000LL);
+    }
+}
+
+cudaError_t launch_quality(const float *x, const uint8_t *ref, int H, int W, int pitch, double *out,
+                           cudaStream_t st) {
+    k_sqerr_partial<<<kQualBlocks, 256, 0, st>>>(x, ref, H, W, pitch, out + 2);
+    ++g_launches;
+    k_sqerr_final<<<1, 256, 0, st>>>(out + 2, kQualBlocks, (long long)H * W, out);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -21,6 +21,7 @@ struct Geo {
     int nRy, nRx, R;     // range grid
     int nDy, nDx, Dn;    // domain grid
     int K, w;            // classes and pool half-width (Section 3.1 Eq. 2-3)
+    int literal;         // 1: Eq. 3 window on FD values (FIC_FLAG_LITERAL_WINDOW)
 };
 
 // Correctly rounded log2(n) for n = 0..64 (entry 0 unused); passed to kernels by value.
@@ -31,19 +32,16 @@ const Log2Tab &log2_table();
 double log2_correctly_rounded(int n);
 
 // ----------------------------------------------------------------------------------------
-// Square isometries: (T_t X)[y][x] = X[sy][sx], N = B - 1.
+// Square isometries: (T_t X)[y][x] = X[sy][sx], N = B - 1:
+//   t: 0 (y, x)  1 (N-x, y)  2 (N-y, N-x)  3 (x, N-y)  4 (y, N-x)  5 (N-y, x)  6 (x, y)  7 (N-x, N-y).
+// Written without branches (threads of a warp often hold different t): (u, v) = (y, x), swapped
+// for t in {1, 3, 6, 7}; sy = u mirrored for t in {1, 2, 5, 7}; sx = v mirrored for t in {2, 3, 4, 7}.
 __host__ __device__ __forceinline__ void iso_src(int B, int t, int y, int x, int &sy, int &sx) {
     const int N = B - 1;
-    switch (t) {
-        case 0: sy = y; sx = x; break;
-        case 1: sy = N - x; sx = y; break;
-        case 2: sy = N - y; sx = N - x; break;
-        case 3: sy = x; sx = N - y; break;
-        case 4: sy = y; sx = N - x; break;
-        case 5: sy = N - y; sx = x; break;
-        case 6: sy = x; sx = y; break;
-        default: sy = N - x; sx = N - y; break;
-    }
+    const bool swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
+    const int u = swap ? x : y, v = swap ? y : x;
+    sy = fy ? N - u : u;
+    sx = fx ? N - v : v;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -142,6 +140,8 @@ struct EncodeBufs {
     uint16_t *dom_S;                  // [Dn][64] integer 2x2 sums of every domain
     // pools
     int32_t *dom_order, *bin_off, *range_order, *rbin_off, *win_lo, *win_hi;
+    uint8_t *dom_key, *range_key;  // [Dn], [R] sort keys (class, or FD rank in literal mode)
+    int nbuckets;          // sort buckets: K, or the number of distinct FD values
     int32_t *sort_counts;  // [nblk][256] per-block class histograms
     int32_t *sort_offs;    // [nblk][256] per-block scatter bases
     // tensor engine: this image's slice of the batch-wide arrays (TcBatch)
@@ -193,6 +193,7 @@ size_t encode_workspace(const Geo *g, int n, EncodeBufs *b, TcBatch *tb, void *w
 cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                             cudaStream_t st);
 cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st);
+int sort_buckets(const Geo &g);  // buckets of the pool sort: K, or distinct FD values
 cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                               const fic_codes &out, cudaStream_t st);
 cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,

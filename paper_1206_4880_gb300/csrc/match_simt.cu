@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(kSimtThreads)
 
 // Re-search of uncertified ranges of one image. Slot k holds class-sorted position fb_pos[k] and
 // the exact best of its evaluated candidates; the 512-domain chunks of the range's tile whose best
-// FP32 score (an upper bound of exact gain / 512) could still reach that best (score * (1 + 2^-16)
-// >= best gain / 512) are scanned exactly.
+// FP32 score could still reach that best (score * (1 + 2^-16) + 2^-8 >= best gain / 512, the
+// bound k_reeval certifies with) are scanned exactly.
 __global__ void __launch_bounds__(kSimtThreads)
     k_rescan(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
              const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(kSimtThreads)
                 const size_t e = ((size_t)(ti.z + c) * kTileM + row) * 2;
                 const uint32_t key = max(chunk_max[e], chunk_max[e + 1]);
                 const double s1 = (double)__uint_as_float(key);
-                if (key != 0 && s1 * (1.0 + 1.0 / 65536.0) >= thr) sh.flagged[atomicAdd(&sh.n_flagged, 1)] = c;
+                if (key != 0 && s1 * (1.0 + 1.0 / 65536.0) + 1.0 / 256.0 >= thr)
+                    sh.flagged[atomicAdd(&sh.n_flagged, 1)] = c;
             }
             __syncthreads();
             const int nf = sh.n_flagged;

@@ -198,11 +198,10 @@ __device__ __forceinline__ void top2u(uint32_t &b1, uint32_t &b2, uint32_t k) {
 }
 
 // Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
-// range row. Per domain: p = max_t |P_t| / 64 (inflated by a relative 2^-18 and 2^-14 to cover
-// the accumulation error), the clamped least-squares gain / 512 of p: s = 128 m^2 / Q + (p - m),
-// m = min(p, Q / 256) (an upper bound of the exact gain / 512, since the gain grows with |P|),
-// and a 32-bit key (s's bits with the low 4 replaced by 15 - local index); t1, t2 keep the two
-// largest keys.
+// range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
+// s = 128 m^2 / Q + (p - m), m = min(p, Q / 256) (the exact gain / 512 up to the accumulator's
+// and this formula's rounding), and a 32-bit key (s's bits with the low 4 replaced by 15 - local
+// index); t1, t2 keep the two largest keys.
 // MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
 __device__ __forceinline__ float absmax8(const uint32_t *v) {
     const float a = fmaxf(fabsf(__uint_as_float(v[0])), fabsf(__uint_as_float(v[1])));
@@ -231,8 +230,9 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
         for (int q = 0; q < 4; ++q) {
             const int l = 4 * c + q;
             const float4 a = auxp[l];
-            // accumulator = P / 64 up to the FP32 accumulation error, covered by the inflation
-            const float p = fmaf(absmax8(cur + 8 * q), 1.0f + 0x1p-18f, 0x1p-14f);
+            // accumulator = P / 64 up to the FP32 accumulation error, which k_reeval's
+            // certification margin covers
+            const float p = absmax8(cur + 8 * q);
             const float mm = fminf(p, a.y);
             const float sc = fmaf(mm, mm * a.z, p - mm);
             uint32_t key = (__float_as_uint(sc) & 0xFFFFFFF0u) | (uint32_t)(15 - l);
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                          const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                          const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
-                         const int32_t *__restrict__ bin_off, const uint8_t *__restrict__ rbin,
+                         const int32_t *__restrict__ bin_off, int nbuckets,
                          const int4 *__restrict__ rng_info, int rng_off, int dom_off,
                          const int4 *__restrict__ tile_items, const unsigned long long *__restrict__ cand,
                          const int32_t *__restrict__ gcounters, int32_t *__restrict__ fallback,
@@ -665,17 +665,15 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     const int ry = (r / g.nRx) * 8, rx = (r % g.nRx) * 8;
 
     if (64LL * Bs - A * A == 0) {  // flat range
+        // the pool is a union of whole sort buckets, each holding ascending domain ids: the
+        // smallest id of the pool is the smallest first entry of a bucket inside the window
         int dmin = INT_MAX;
-        const int b = rbin[r];
-        const int blo = max(0, b - g.w), bhi = min(g.K - 1, b + g.w);
-        if (bin_off[blo] == bin_off[bhi + 1]) {
-            dmin = 0;  // empty class window: the pool is every domain
-        } else {
-            for (int bb = blo + lane; bb <= bhi; bb += 32)
-                if (bin_off[bb] < bin_off[bb + 1]) dmin = min(dmin, dom_order[bin_off[bb]]);
+        const int wlo = ri.y - dom_off, whi = ri.z - dom_off;
+        for (int bb = lane; bb < nbuckets; bb += 32)
+            if (bin_off[bb] < bin_off[bb + 1] && bin_off[bb] >= wlo && bin_off[bb] < whi)
+                dmin = min(dmin, dom_order[bin_off[bb]]);
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
-        }
+        for (int off = 16; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
         if (lane == 0) {
             const long long C = dsum[dmin];
             const long long Q = 64LL * dsumsq[dmin] - C * C;
@@ -705,29 +703,35 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
         top2(b1, b2, o1);
         top2(b1, b2, o2);
     }
-    // exact evaluation: lane = 8 * candidate + t for lanes 0..15
-    const int cidx = lane >> 3, t = lane & 7;
+    // exact evaluation: lanes 2 (8 c + t) and 2 (8 c + t) + 1 form X of candidate c, isometry t
+    // over range rows 0-3 and 4-7
+    const int cidx = lane >> 4, t = (lane >> 1) & 7, hrow = (lane & 1) * 4;
     const unsigned long long key = cidx == 0 ? b1 : b2;
     const int jl = (int)(~(uint32_t)(key & 0xffffffffu)) - dom_off;  // position in this image
-    const bool has = lane < 16 && key != 0 && jl >= 0 && jl < g.Dn;
+    const bool has = key != 0 && jl >= 0 && jl < g.Dn;
     Gain gg{-1, 1};
     int d = INT_MAX;
     long long P = 0, Q = 0, C = 0;
+    int X = 0;
     if (has) {
         d = dom_order[jl];
         const uint16_t *S = domS + (size_t)d * 64;
-        long long X = 0;
-        for (int y = 0; y < 8; ++y) {
+#pragma unroll
+        for (int y = hrow; y < hrow + 4; ++y) {
             const uint8_t *row = img + (size_t)(ry + y) * g.pitch + rx;
+#pragma unroll
             for (int x = 0; x < 8; ++x) {
                 int sy, sx;
                 iso_src(8, t, y, x, sy, sx);
-                X += (long long)row[x] * S[sy * 8 + sx];
+                X += (int)row[x] * (int)S[sy * 8 + sx];
             }
         }
+    }
+    X += __shfl_xor_sync(0xffffffffu, X, 1);
+    if (has) {
         C = dsum[d];
         Q = 64LL * dsumsq[d] - C * C;
-        P = 64LL * X - A * C;
+        P = 64LL * (long long)X - A * C;
         gg = exact_gain(P, Q);
     }
     int bt = t;
@@ -749,9 +753,13 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     if (lane != 0) return;
     bool certified = b1 != 0 && gg.num >= 0;
     if (certified && b2 != 0) {
+        // runner-up score (truncated key) * (1 + 2^-16) + 2^-8 bounds every other domain's exact
+        // gain / 512: the key drops < 2^-19 relatively, the FP32 score formula errs < 20 * 2^-24
+        // relatively, and the accumulator's P / 64 errs < 2^-22 (|P / 64| + 16), which moves the
+        // score by < 2^-19 relatively plus < 2^-11 absolutely (Q >= 63 when Q > 0)
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
         const double sc = (double)gg.num / (512.0 * (double)gg.den);  // exact gain / 512
-        certified = u2 * (1.0 + 1.0 / 65536.0) < sc;
+        certified = u2 * (1.0 + 1.0 / 65536.0) + 1.0 / 256.0 < sc;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
@@ -867,7 +875,7 @@ cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                           const fic_codes &out, cudaStream_t st) {
     const long long threads = (long long)g.R * 32;
     k_reeval<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, b.range_bin, b.rng_info,
+        g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, sort_buckets(g), b.rng_info,
         b.rng_off, b.dom_off, tb.tile_items, tb.cand, tb.gcounters, b.fallback, b.fb_best, b.counters, out);
     ++g_launches;
     return cudaGetLastError();

@@ -7,6 +7,11 @@
 // (`dom_order`, `bin_off`), built in O(Dn), and each range's pool is the contiguous slice of the
 // classes within w of its own. Ranges are sorted the same way so that ranges sharing a pool are
 // adjacent (the tensor engine tiles them together).
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
 #include "fic_internal.cuh"
 
 namespace fic {
@@ -110,6 +115,86 @@ __global__ void k_windows(Geo g, const uint8_t *__restrict__ rbin, const int32_t
     if ((threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long *)matches, (unsigned long long)m);
 }
 
+// ---- literal window (Eq. 3 on FD values) ----------------------------------------------------
+// An 8x8 block's FD is L[N_2] - L[N_4] with 16 <= N_2 <= 64, 4 <= N_4 <= 8, so at most 245
+// distinct values exist. They are sorted once on the host (computed with the same correctly
+// rounded log2 table and one binary64 subtraction as the kernels), giving each (N_2, N_4) pair
+// the rank of its value; domains and ranges are counting-sorted by that rank.
+struct FdRanks {
+    double vals[256];       // distinct FD values, ascending
+    int n;
+    uint8_t rank[65][9];    // rank[N_2][N_4]
+};
+
+static const FdRanks &fd_ranks() {
+    static FdRanks t;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const Log2Tab &L = log2_table();
+        std::vector<double> v;
+        for (int n2 = 16; n2 <= 64; ++n2)
+            for (int n4 = 4; n4 <= 8; ++n4) v.push_back(L.v[n2] - L.v[n4]);
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        t.n = (int)v.size();
+        for (int i = 0; i < 256; ++i) t.vals[i] = i < t.n ? v[i] : 0.0;
+        memset(t.rank, 0, sizeof(t.rank));
+        for (int n2 = 16; n2 <= 64; ++n2)
+            for (int n4 = 4; n4 <= 8; ++n4)
+                t.rank[n2][n4] = (uint8_t)(std::lower_bound(v.begin(), v.end(), L.v[n2] - L.v[n4]) - v.begin());
+    });
+    return t;
+}
+
+struct RankTab {
+    uint8_t rank[65][9];
+};
+
+__global__ void k_fd_keys(int n, const int32_t *__restrict__ counts, RankTab t, uint8_t *__restrict__ key) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) key[i] = t.rank[counts[2 * i]][counts[2 * i + 1]];
+}
+
+struct ValTab {
+    double vals[256];
+};
+
+// Pool window of every range: the domains (FD-rank-sorted) whose FD lies in
+// [FD_r - D_f, FD_r + D_f], D_f = (F_m - F_l) / 3; all domains when that set is empty.
+__global__ void k_windows_literal(Geo g, const double *__restrict__ rfd, const double *__restrict__ fd_extent,
+                                  ValTab t, int nvals, const int32_t *__restrict__ off,
+                                  int32_t *__restrict__ win_lo, int32_t *__restrict__ win_hi, long long *matches) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    long long m = 0;
+    if (r < g.R) {
+        const double Df = __ddiv_rn(__dsub_rn(fd_extent[1], fd_extent[0]), 3.0);
+        const double lo_v = __dsub_rn(rfd[r], Df), hi_v = __dadd_rn(rfd[r], Df);
+        int a = 0, b = nvals;  // first rank with value >= lo_v
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (t.vals[mid] >= lo_v) b = mid; else a = mid + 1;
+        }
+        const int rlo = a;
+        a = 0;
+        b = nvals;  // first rank with value > hi_v
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (t.vals[mid] > hi_v) b = mid; else a = mid + 1;
+        }
+        int lo = off[rlo], hi = off[a];
+        if (lo >= hi) {
+            lo = 0;
+            hi = g.Dn;
+        }
+        win_lo[r] = lo;
+        win_hi[r] = hi;
+        m = (long long)(hi - lo) * 8;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long *)matches, (unsigned long long)m);
+}
+
 static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *counts, int32_t *offs,
                                  int32_t *order, int32_t *bin_off, cudaStream_t st) {
     const int nblk = (n + kSortChunk - 1) / kSortChunk;
@@ -124,6 +209,27 @@ static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *cou
 
 cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
     cudaError_t e;
+    if (g.literal) {
+        const FdRanks &fr = fd_ranks();
+        RankTab rt;
+        memcpy(rt.rank, fr.rank, sizeof(rt.rank));
+        ValTab vt;
+        memcpy(vt.vals, fr.vals, sizeof(vt.vals));
+        k_fd_keys<<<(g.Dn + 255) / 256, 256, 0, st>>>(g.Dn, b.dom_counts, rt, b.dom_key);
+        ++g_launches;
+        k_fd_keys<<<(g.R + 255) / 256, 256, 0, st>>>(g.R, b.range_counts, rt, b.range_key);
+        ++g_launches;
+        if ((e = counting_sort(b.dom_key, g.Dn, fr.n, b.sort_counts, b.sort_offs, b.dom_order, b.bin_off, st)))
+            return e;
+        if ((e = counting_sort(b.range_key, g.R, fr.n, b.sort_counts, b.sort_offs, b.range_order, b.rbin_off,
+                               st)))
+            return e;
+        if ((e = cudaMemsetAsync(b.matches, 0, sizeof(long long), st))) return e;
+        k_windows_literal<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_fd, b.fd_extent, vt, fr.n, b.bin_off,
+                                                             b.win_lo, b.win_hi, b.matches);
+        ++g_launches;
+        return cudaGetLastError();
+    }
     if ((e = counting_sort(b.dom_bin, g.Dn, g.K, b.sort_counts, b.sort_offs, b.dom_order,
                            b.bin_off, st)))
         return e;
@@ -136,5 +242,7 @@ cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
     ++g_launches;
     return cudaGetLastError();
 }
+
+int sort_buckets(const Geo &g) { return g.literal ? fd_ranks().n : g.K; }
 
 }  // namespace fic

@@ -17,6 +17,7 @@ from . import _build
 FIC_OK, FIC_ERR_INVALID_ARG, FIC_ERR_WORKSPACE, FIC_ERR_CUDA, FIC_ERR_DEVICE_TIMEOUT, \
     FIC_ERR_UNSUPPORTED = range(6)
 ENGINES = {"tensor": 0, "simt": 1}
+FLAG_LITERAL_WINDOW = 1
 
 c_i32, c_i64, c_dbl, c_vp, c_size = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -66,6 +67,10 @@ SIGNATURES = {
     "fic_profile_enable": (c_i32, [c_i32]),
     "fic_profile_read": (c_i32, [c_vp, c_i32, c_vp]),
     "fic_decode_static": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "fic_quality": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "fic_quantize": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "fic_decode_scaled_workspace_size": (c_size, [c_vp, c_vp, c_i32]),
+    "fic_decode_scaled": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_engine_available": (c_i32, [c_i32]),
     "fic_last_error": (ctypes.c_char_p, []),
     "fic_version": (c_i32, []),
@@ -118,10 +123,12 @@ class EncodeParams:
     block: int = 8
     s_max: float = 1.0
     items_per_sm: int = 0
+    literal: bool = False   # Eq. 3's window on FD values instead of the class window
 
     def c(self) -> Params:
         return Params(self.block, self.domain_stride, self.num_classes, self.half_width,
-                      self.s_max, ENGINES[self.engine], 0, self.items_per_sm)
+                      self.s_max, ENGINES[self.engine], FLAG_LITERAL_WINDOW if self.literal else 0,
+                      self.items_per_sm)
 
 
 def geom(H: int, W: int, pitch: int | None = None) -> Geom:
@@ -267,10 +274,12 @@ def build_pools(stats: dict, H: int, W: int, p: EncodeParams, workspace=None, st
     R, Dn = counts(H, W, p)
     dev = stats["range_bin"].device
     i32 = torch.int32
+    # bucket offsets: K + 1 entries, or one per distinct FD value (+1) with the literal window;
+    # the library documents 257 as the size that covers both
     out = {"dom_order": torch.empty(Dn, dtype=i32, device=dev),
-           "bin_off": torch.empty(p.num_classes + 1, dtype=i32, device=dev),
+           "bin_off": torch.empty(257, dtype=i32, device=dev),
            "range_order": torch.empty(R, dtype=i32, device=dev),
-           "rbin_off": torch.empty(p.num_classes + 1, dtype=i32, device=dev),
+           "rbin_off": torch.empty(257, dtype=i32, device=dev),
            "win_lo": torch.empty(R, dtype=i32, device=dev),
            "win_hi": torch.empty(R, dtype=i32, device=dev)}
     s = BlockStats(*[_p(stats[n]) for n, _ in BlockStats._fields_])
@@ -306,6 +315,38 @@ def decode(codes: dict, H: int, W: int, p: EncodeParams, iters: int, x0=None, ou
     return out
 
 
+def quality(x: torch.Tensor, ref: torch.Tensor, stream=None) -> tuple[float, float]:
+    """(MSE, PSNR dB) of the decoded image clamp(round-half-even(x)) against the uint8 original,
+    computed by the library on the GPU (Table 4's metric)."""
+    _require_cuda(x, "x")
+    _require_cuda(ref, "ref")
+    H, W = ref.shape
+    out = torch.empty(1026, dtype=torch.float64, device=x.device)
+    g = geom(H, W, ref.stride(0))
+    _check(load().fic_quality(_p(x.contiguous()), _p(ref), ctypes.byref(g), _p(out), _stream(stream)))
+    mse, psnr = out[:2].tolist()
+    return mse, psnr
+
+
+def quantize(codes: dict, bits_s: int = 5, bits_o: int = 7, stream=None):
+    """fic_quantize: (dequantised codes, q_s, q_o, (o_lo, o_hi)); the integer codes are uint16
+    tensors stored as int16 bit patterns (torch has no uint16 arithmetic)."""
+    dev = codes["s"].device
+    n = codes["s"].numel()
+    out = {"dom": torch.empty_like(codes["dom"]), "iso": torch.empty_like(codes["iso"]),
+           "s": torch.empty_like(codes["s"]), "o": torch.empty_like(codes["o"])}
+    if "sse" in codes:
+        out["sse"] = codes["sse"].clone()
+    q_s = torch.empty(n, dtype=torch.int16, device=dev)
+    q_o = torch.empty(n, dtype=torch.int16, device=dev)
+    header = torch.empty(514, dtype=torch.float64, device=dev)
+    ci, co = _codes_struct(codes), _codes_struct(out)
+    _check(load().fic_quantize(ctypes.byref(ci), n, bits_s, bits_o, _p(q_s), _p(q_o), _p(header),
+                               ctypes.byref(co), _stream(stream)))
+    lo, hi = header[:2].tolist()
+    return out, q_s, q_o, (lo, hi)
+
+
 DECODE_STATIC_MAX_PIXELS = 1 << 20
 
 
@@ -320,6 +361,23 @@ def decode_static(codes: dict, H: int, W: int, p: EncodeParams, iters: int, x0=N
     g, pc = geom(H, W), p.c()
     _check(load().fic_decode_static(ctypes.byref(cs), ctypes.byref(g), ctypes.byref(pc), iters,
                                     _p(x0), _p(out), _stream(stream)))
+    return out
+
+
+def decode_scaled(codes: dict, H: int, W: int, p: EncodeParams, scale: int, iters: int, x0=None,
+                  out=None, stream=None) -> torch.Tensor:
+    """fic_decode_scaled: the codes of an H x W encoding decoded on the (scale H) x (scale W) grid."""
+    dev = codes["dom"].device
+    if out is None:
+        out = torch.empty(scale * H, scale * W, dtype=torch.float32, device=dev)
+    g, pc = geom(H, W), p.c()
+    n = load().fic_decode_scaled_workspace_size(ctypes.byref(g), ctypes.byref(pc), scale)
+    if n == 0:
+        raise FicError(FIC_ERR_INVALID_ARG, load().fic_last_error().decode())
+    ws = torch.empty(n, dtype=torch.uint8, device=dev)
+    cs = _codes_struct(codes)
+    _check(load().fic_decode_scaled(ctypes.byref(cs), ctypes.byref(g), ctypes.byref(pc), scale, iters, _p(x0),
+                                    _p(out), _p(ws), ws.numel(), _stream(stream)))
     return out
 
 

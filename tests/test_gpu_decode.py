@@ -42,6 +42,18 @@ def test_decode_parity(pr1_codes, iters):
         assert abs(pg - po) <= 0.01
 
 
+def test_quality_matches_oracle_psnr(pr1_codes):
+    img, codes = pr1_codes
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    x = fic.decode(_codes_gpu(codes), 256, 256, p, 8)
+    mse, psnr = fic.quality(x, torch.from_numpy(img).cuda())
+    xq = odec.to_u8(x.cpu().numpy().astype(np.float64))
+    assert abs(psnr - odec.psnr(xq, img)) <= 1e-9
+    assert abs(mse - np.mean((xq.astype(np.float64) - img) ** 2)) <= 1e-9
+    m0, p0 = fic.quality(torch.from_numpy(img.astype(np.float32)).cuda(), torch.from_numpy(img).cuda())
+    assert m0 == 0.0 and p0 == float("inf")
+
+
 def test_decode_from_given_start(pr1_codes):
     img, codes = pr1_codes
     p = fic.EncodeParams(domain_stride=8, num_classes=8)
@@ -122,3 +134,50 @@ def test_autograd_function(pr1_codes):
     gs, go = fic.decode_backward(cg, 256, 256, p, 4, 2, (x - target).detach())
     torch.cuda.synchronize()
     assert torch.allclose(s.grad.float(), gs) and torch.allclose(o.grad.float(), go)
+
+
+@pytest.mark.parametrize("scale", [1, 2, 3])
+def test_decode_scaled(pr1_codes, scale):
+    """Resolution-independent decode against the oracle, and 2x2 block averages of the 2x decode
+    against the 1x decode."""
+    img, codes = pr1_codes
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    cg = _codes_gpu(codes)
+    x = fic.decode_scaled(cg, 256, 256, p, scale, 6)
+    torch.cuda.synchronize()
+    ref = odec.decode_scaled(codes, 256, 256, 8, 8, 6, scale)
+    assert np.max(np.abs(x.cpu().numpy() - ref)) <= 2e-3
+    if scale == 2:
+        x1 = fic.decode(cg, 256, 256, p, 6).cpu().numpy()
+        down = x.cpu().numpy().astype(np.float64).reshape(256, 2, 256, 2).mean(axis=(1, 3))
+        assert np.max(np.abs(down - x1)) <= 2e-3
+
+
+def test_quantize_bit_exact_against_oracle(pr1_codes):
+    from oracle import quantize as oq
+    img, codes = pr1_codes
+    rng = np.random.default_rng(9)
+    cases = [codes, {"dom": codes["dom"], "iso": codes["iso"], "s": rng.uniform(-1, 1, 1024),
+                     "o": rng.uniform(-50, 300, 1024)}]
+    for c in cases:
+        for bs, bo in ((5, 7), (4, 6), (16, 16)):
+            out, qs, qo, (lo, hi) = fic.quantize(_codes_gpu(c), bs, bo)
+            torch.cuda.synchronize()
+            rqs, rqo, rs, ro, rlo, rhi = oq.quantize(c["s"], c["o"], bs, bo)
+            assert lo == rlo and hi == rhi
+            assert np.array_equal(qs.cpu().numpy().view(np.uint16), rqs.astype(np.uint16))
+            assert np.array_equal(qo.cpu().numpy().view(np.uint16), rqo.astype(np.uint16))
+            assert np.array_equal(out["s"].cpu().numpy(), rs) and np.array_equal(out["o"].cpu().numpy(), ro)
+            assert np.array_equal(out["dom"].cpu().numpy(), np.asarray(c["dom"], np.int32))
+
+
+def test_refinement_improves_decoded_psnr(pr1_codes):
+    from paper_1206_4880_gb300 import refine
+    img, codes = pr1_codes
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    cg = _codes_gpu(codes)
+    rep = refine.refine_and_quantize(cg, torch.from_numpy(img).cuda(), p, steps=15)
+    assert rep["psnr_refined"] > rep["psnr_encoded"] + 0.05, rep
+    assert rep["psnr_refined_quantized"] > rep["psnr_quantized"], rep
+    r = refine.refine(cg, torch.from_numpy(img).cuda(), p, steps=3)
+    assert float(r["s"].abs().max()) <= 1.0

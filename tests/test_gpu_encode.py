@@ -83,7 +83,7 @@ def test_pools_exact(case):
     assert np.array_equal(dom_order, np.argsort(cls["dom_bin"], kind="stable"))
     assert np.array_equal(po["range_order"].cpu().numpy(), np.argsort(cls["range_bin"], kind="stable"))
     bo = np.concatenate([[0], np.cumsum(np.bincount(cls["dom_bin"], minlength=K))])
-    assert np.array_equal(po["bin_off"].cpu().numpy(), bo)
+    assert np.array_equal(po["bin_off"].cpu().numpy()[:K + 1], bo)
     ww = odbc.default_half_width(K) if w < 0 else w
     lo, hi = po["win_lo"].cpu().numpy(), po["win_hi"].cpu().numpy()
     for r in range(lo.size):
@@ -227,3 +227,46 @@ def test_encode_batched_equals_oracle(engine):
         torch.cuda.synchronize()
         for k in ("dom", "iso", "s", "o", "sse"):
             assert torch.equal(single[k], out[k]), k
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("case", [c for c in SMALL if c[3] > 1])
+def test_encode_literal_window(case, engine):
+    """Section 3.1 Eq. 3 on FD values: FD_r - D_f <= FD_d <= FD_r + D_f, against the oracle's
+    literal mode."""
+    _need_tensor(engine)
+    H, W, sigma, K, w, seed = case
+    img = _img(H, W, seed)
+    p = fic.EncodeParams(domain_stride=sigma, num_classes=K, half_width=w, engine=engine, literal=True)
+    info = fic.new_info("cuda")
+    codes = fic.encode(_t(img), p, info=info)
+    st = fic.classify(_t(img), p)
+    po = fic.build_pools(st, H, W, p)
+    torch.cuda.synchronize()
+    ref = omatch.encode(img, B=8, sigma=sigma, K=K, mode="literal", n_threads=8)
+    _compare_codes(codes, ref)
+    assert fic.read_info(info)["matches"] == int(ref["pool_size"].sum()) * 8
+    cls = ref["cls"]
+    Df = opools.fractal_distance(cls["F_l"], cls["F_m"])
+    dom_order = po["dom_order"].cpu().numpy()
+    fd_sorted = cls["dom_fd"][dom_order]
+    assert np.all(np.diff(fd_sorted) >= 0)  # ordered by FD value
+    same = np.diff(fd_sorted) == 0
+    assert np.all(np.diff(dom_order)[same] > 0)  # stable: equal FDs keep ascending ids
+    lo, hi = po["win_lo"].cpu().numpy(), po["win_hi"].cpu().numpy()
+    for r in range(lo.size):
+        pool = opools.literal_pool(cls["range_fd"][r], cls["dom_fd"], Df)
+        assert np.array_equal(np.sort(dom_order[lo[r]:hi[r]]), pool), r
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_conci_two_groups(engine):
+    """Conci and Aquino's static classification (Section 2, ref. [8]) split the domains into two
+    FD groups and searched the range's own group: K = 2 classes, half-width 0."""
+    _need_tensor(engine)
+    img = synth.fbm_image(88, 192, 160)
+    p = fic.EncodeParams(domain_stride=4, num_classes=2, half_width=0, engine=engine)
+    codes = fic.encode(_t(img), p)
+    torch.cuda.synchronize()
+    ref = omatch.encode(img, B=8, sigma=4, K=2, w=0, n_threads=8)
+    _compare_codes(codes, ref)
