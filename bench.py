@@ -32,15 +32,25 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "encode-1024": dict(H=1024, W=1024, sigma=4, K=16, w=-1, seed=2000,
+    "encode-1024": dict(H=1024, W=1024, sigma=4, K=16, w=-1, seed=2000, block=8,
                         desc="1024x1024 8-bit seeded fBm+edges image; 16384 8x8 ranges; 16x16 "
                              "domains at stride 4 (64009) x 8 isometries; K=16 LFD classes, w=5"),
-    "encode-256": dict(H=256, W=256, sigma=8, K=8, w=-1, seed=1000,
+    "encode-256": dict(H=256, W=256, sigma=8, K=8, w=-1, seed=1000, block=8,
                        desc="256x256 8-bit seeded fBm+edges image; 1024 8x8 ranges; 16x16 domains "
                             "at stride 8 (961) x 8 isometries; K=8 LFD classes, w=2"),
+    "encode-4096": dict(H=4096, W=4096, sigma=8, K=32, w=-1, seed=5000, block=8,
+                        desc="4096x4096 8-bit seeded fBm+edges image; 262144 8x8 ranges; 16x16 "
+                             "domains at stride 8 (261121) x 8 isometries; K=32 LFD classes, w=10"),
+    "encode-4096-b16": dict(H=4096, W=4096, sigma=8, K=32, w=-1, seed=5000, block=16,
+                            desc="4096x4096 8-bit seeded fBm+edges image; 65536 16x16 ranges; 32x32 "
+                                 "domains at stride 8 (259081) x 8 isometries; K=32 LFD classes, w=10"),
 }
 FLUSH_BYTES = 256 << 20
-FLOPS_PER_MATCH = 2 * 64  # one 64-term correlation: 64 multiply-adds
+
+
+def flops_per_match(block: int) -> int:
+    """One B*B-term correlation: B*B multiply-adds."""
+    return 2 * block * block
 N_SMS = 152
 FP32_LANES = 128
 
@@ -59,6 +69,8 @@ def _image(wl, rank):
     from paper_1206_4880_gb300 import synth
     if wl["seed"] == 1000 and rank == 0:
         return synth.pr1_image()
+    if wl["seed"] == 5000 and rank == 0:
+        return synth.large_image()
     return synth.fbm_image(wl["seed"] + rank, wl["H"], wl["W"])
 
 
@@ -175,17 +187,18 @@ def cpu_baseline(img, wl, budget_s: float):
     from oracle import match as omatch
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    cls = omatch.classify_image(img, 8, wl["sigma"], wl["K"])
+    B = wl["block"]
+    cls = omatch.classify_image(img, B, wl["sigma"], wl["K"])
     t_cls = time.perf_counter() - t0
     R = cls["range_bin"].size
     order = np.random.default_rng(12345).permutation(R)
     n = min(R, 2 * threads)
     t0 = time.perf_counter()
-    omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=order[:n], n_threads=threads, cls=cls)
+    omatch.encode(img, B=B, sigma=wl["sigma"], K=wl["K"], range_ids=order[:n], n_threads=threads, cls=cls)
     per = (time.perf_counter() - t0) / n
     n = int(min(R, max(n, budget_s / max(per, 1e-9))))
     t0 = time.perf_counter()
-    c = omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=order[:n], n_threads=threads, cls=cls)
+    c = omatch.encode(img, B=B, sigma=wl["sigma"], K=wl["K"], range_ids=order[:n], n_threads=threads, cls=cls)
     dt = time.perf_counter() - t0
     matches = int(c["pool_size"].sum()) * 8
     return {"value": matches / dt, "unit": "matches/s", "cores": threads, "kind": "oracle",
@@ -201,12 +214,13 @@ def run_reference(args, wl, world, rank):
     from oracle import match as omatch
     img = _image(wl, 0)
     threads = os.cpu_count() or 1
-    cls = omatch.classify_image(img, 8, wl["sigma"], wl["K"])
+    B = wl["block"]
+    cls = omatch.classify_image(img, B, wl["sigma"], wl["K"])
     R = cls["range_bin"].size
     order = np.random.default_rng(12345).permutation(R)
     per_step = max(0.05, 90.0 / max(1, args.steps + args.warmup))
     t0 = time.perf_counter()
-    omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=order[:threads], n_threads=threads, cls=cls)
+    omatch.encode(img, B=B, sigma=wl["sigma"], K=wl["K"], range_ids=order[:threads], n_threads=threads, cls=cls)
     per = (time.perf_counter() - t0) / threads
     n = int(min(R, max(1, per_step / max(per, 1e-9))))
     pos = 0
@@ -215,7 +229,7 @@ def run_reference(args, wl, world, rank):
         ids = order[(pos + np.arange(n)) % R]
         pos += n
         t0 = time.perf_counter()
-        c = omatch.encode(img, B=8, sigma=wl["sigma"], K=wl["K"], range_ids=ids, n_threads=threads, cls=cls)
+        c = omatch.encode(img, B=B, sigma=wl["sigma"], K=wl["K"], range_ids=ids, n_threads=threads, cls=cls)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             total_m += int(c["pool_size"].sum()) * 8
@@ -245,7 +259,7 @@ def run_ours(args, wl, world, rank, local):
     H, W = img_np.shape
     img = torch.from_numpy(img_np).to(dev)
     p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=wl["K"], half_width=wl["w"],
-                         engine=args.engine)
+                         engine=args.engine, block=wl["block"])
     R, Dn = fic.counts(H, W, p)
     ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)
     out = fic.alloc_codes(R, dev)
@@ -311,7 +325,7 @@ def run_ours(args, wl, world, rank, local):
         bound, unit = "alu", "TFLOP/s"
         peak = N_SMS * FP32_LANES * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         peak_note = f"FP32 FMA: {N_SMS} SMs x {FP32_LANES} lanes x 2 flop x sm_max_mhz"
-    achieved = matches * FLOPS_PER_MATCH / (mean_match_ms / 1e3) / 1e12
+    achieved = matches * flops_per_match(wl["block"]) / (mean_match_ms / 1e3) / 1e12
     line = {
         "metric": "range-domain-isometry matches/s", "value": all_matches / total_s,
         "unit": "matches/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -337,6 +351,8 @@ def run_ours(args, wl, world, rank, local):
         line["comparators"] = comparators(img, img_np, wl, args, dev)
         if args.engine == "tensor":
             line["batched"] = batched(args, dev)
+            if args.workload == "encode-1024":
+                line["large"] = large(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img_np, wl, args.cpu_seconds)
     if rank == 0:
@@ -397,6 +413,54 @@ def batched(args, dev):
             "autotune_ms": tune_ms, "autotune_s": tune_s}
 
 
+def large(args, dev):
+    """The 4096x4096 workload (stride-8 domains, K = 32, w = 10) in both range sizes: 8x8 ranges
+    against 16x16 domains and 16x16 ranges against 32x32 domains, each one fic_encode per step,
+    L2 flushed before every step; with the decoded PSNR of each pass (8 iterations)."""
+    import torch
+
+    from paper_1206_4880_gb300 import fic, synth
+    img_np = synth.large_image()
+    H, W = img_np.shape
+    img = torch.from_numpy(img_np).to(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peaks, peak_src = _peaks()
+    peak = float(peaks["bf16_tflops"])
+    res = {"image": "4096x4096 seeded fBm+edges (seed 5000); stride-8 domains, K=32, w=10"}
+    for B in (8, 16):
+        p = fic.EncodeParams(domain_stride=8, num_classes=32, half_width=-1, engine=args.engine, block=B)
+        R, Dn = fic.counts(H, W, p)
+        ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)
+        info = fic.new_info(dev)
+        out = fic.encode(img, p, workspace=ws, info=info)
+        rep = fic.read_info(info)
+        for _ in range(2):
+            fic.encode(img, p, out=out, workspace=ws)
+        ms, mm = [], []
+        for k in range(3):
+            flush.fill_(k & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fic.encode(img, p, out=out, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            mm.append(fic.profile_read()[0]["match"])
+        x = fic.decode(out, H, W, p, 8)
+        psnr = fic.quality(x, img)[1]
+        med, mmatch = statistics.median(ms), statistics.median(mm)
+        tf = rep["matches"] * flops_per_match(B) / (mmatch / 1e3) / 1e12
+        res[f"b{B}"] = {"ranges": R, "domains": Dn, "matches_per_step": rep["matches"],
+                        "pool_fraction": rep["matches"] / (R * Dn * 8), "encode_ms": med,
+                        "matches_per_s": rep["matches"] / (med / 1e3), "match_ms": mmatch,
+                        "match_tflops": tf, "match_frac_of_peak": tf / peak,
+                        "fallback_ranges": rep["fallback_ranges"], "work_items": rep["work_items"],
+                        "device_error": rep["device_error"], "psnr_db": psnr}
+        del ws, out
+    res["peak_source"] = f"{peak_src} bf16 dense burst x nominal fp16/bf16 ratio 1.0"
+    return res
+
+
 def comparators(img, img_np, wl, args, dev):
     """Plain full search on CUDA cores (and on tensor cores when available) on the same image,
     with decoded PSNR (8 iterations from mid-grey) of the full-search and classified codes."""
@@ -423,7 +487,8 @@ def comparators(img, img_np, wl, args, dev):
     engines = ["simt", "tensor"] if args.engine == "tensor" else ["simt"]
     for eng in engines:
         for K, name in ((1, "full"), (wl["K"], "classified")):
-            p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=K, half_width=wl["w"], engine=eng)
+            p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=K, half_width=wl["w"], engine=eng,
+                                 block=wl["block"])
             ms, ps = timed(p, 3 if eng == "simt" else 10)
             res[f"{eng}_{name}_ms"] = ms
             res[f"{eng}_{name}_psnr_db"] = ps

@@ -32,7 +32,9 @@
  *    3 rotate 270 clockwise (x,N-y); 4 mirror left-right (y,N-x); 5 mirror up-down (N-y,x);
  *    6 transpose (x,y); 7 anti-transpose (N-x,N-y).
  *
- * Supported in this version: B = 8, 1 <= sigma, 1 <= K <= 255, s_max = 1.0.
+ * Supported in this version: B = 8 or 16 (16x16 ranges against 32x32 domains: the paper's
+ * method at a second range size, with n = 256 pixels per block), 1 <= sigma, 1 <= K <= 255,
+ * s_max = 1.0. The literal FD window (FIC_FLAG_LITERAL_WINDOW) needs B = 8.
  */
 #ifndef FIC_H
 #define FIC_H
@@ -72,7 +74,7 @@ typedef struct {
 } fic_geom;
 
 typedef struct {
-    int32_t block;         /* B, range side (8) */
+    int32_t block;         /* B, range side: 8 or 16 */
     int32_t domain_stride; /* sigma >= 1: domain grid step in pixels */
     int32_t num_classes;   /* K in [1, 255]; K = 1 makes every pool the full domain set */
     int32_t half_width;    /* w >= 0 classes on each side; -1 selects floor(K/3) (Eq. 2) */
@@ -88,8 +90,12 @@ typedef struct {
  * arrays, R = (H/B)(W/B) entries for ranges and Dn = nDy*nDx for domains.
  *  range_sum = sum r, range_sumsq = sum r^2 over the B x B pixels;
  *  dom_sum = sum S, dom_sumsq = sum S^2 over the B x B integer 2x2 sums S of the domain;
- *  *_counts[2*i + k] = differential box count N_s at s = 2 (k=0) and s = 4 (k=1);
- *  *_fd = log2(N_2) - log2(N_4) in binary64 with correctly rounded log2;
+ *  *_counts[ns*i + k] = differential box count N_s at s = 2^(k+1): ns = 2 scales (s = 2, 4)
+ *  for B = 8, ns = 3 (s = 2, 4, 8) for B = 16; box height s*G/B with G = 256 grey levels for
+ *  range pixels and G = 1024 for the domains' 2x2 sums;
+ *  *_fd = the least-squares slope of log2 N_s against log2(B/s) in binary64 with correctly
+ *  rounded log2: log2(N_2) - log2(N_4) for B = 8, (log2(N_2) - log2(N_8)) / 2 for B = 16 (the
+ *  middle of three equally spaced abscissae has zero weight);
  *  fd_extent[0] = F_l (least domain FD), fd_extent[1] = F_m (largest domain FD);
  *  *_bin = class in [0, K): min(K-1, max(0, floor(K * ((f - F_l) / (F_m - F_l))))), or 0 if
  *  F_m == F_l, each operation a separate IEEE binary64 operation. */
@@ -212,8 +218,8 @@ size_t fic_decode_scaled_workspace_size(const fic_geom *g, const fic_params *p, 
 
 /* Section 1, resolution independence ("the initial image can be of any size"): decodes the codes
  * of the H x W encoding g on the (scale*H) x (scale*W) grid, 1 <= scale <= 16: range r covers the
- * (8 scale)^2 block at scale times its position, domain d the (16 scale)^2 block at scale times its
- * position, contracted by 2x2 averaging, under the isometries of the larger square. x0 and out
+ * (B scale)^2 block at scale times its position, domain d the (2B scale)^2 block at scale times
+ * its position, contracted by 2x2 averaging, under the isometries of the larger square. x0 and out
  * are (scale H) x (scale W) floats (x0 NULL: 128 everywhere). With scale = 1 it is fic_decode;
  * 2x2 block averages of a scale-2 decode equal the scale-1 decode from the same constant start. */
 fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *g, const fic_params *p,

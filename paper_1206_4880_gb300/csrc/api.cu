@@ -63,7 +63,7 @@ fic_status cuda_fail(cudaError_t e, const char *where) {
 
 fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
     if (!gm || !p) return fail(FIC_ERR_INVALID_ARG, "null geometry or parameters");
-    if (p->block != 8) return fail(FIC_ERR_INVALID_ARG, "block must be 8 (got %d)", p->block);
+    if (p->block != 8 && p->block != 16) return fail(FIC_ERR_INVALID_ARG, "block must be 8 or 16 (got %d)", p->block);
     const int B = p->block;
     if (gm->H < 2 * B || gm->W < 2 * B || gm->H % B || gm->W % B)
         return fail(FIC_ERR_INVALID_ARG, "H and W must be multiples of %d and >= %d (got %dx%d)",
@@ -80,6 +80,8 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
         return fail(FIC_ERR_INVALID_ARG, "unknown engine %d", p->engine);
     if (p->flags != 0 && p->flags != FIC_FLAG_LITERAL_WINDOW)
         return fail(FIC_ERR_INVALID_ARG, "flags must be 0 or FIC_FLAG_LITERAL_WINDOW");
+    if ((p->flags & FIC_FLAG_LITERAL_WINDOW) && p->block != 8)
+        return fail(FIC_ERR_INVALID_ARG, "the literal FD window is implemented for block 8 only");
     if (p->items_per_sm < 0 || p->items_per_sm > 64)
         return fail(FIC_ERR_INVALID_ARG, "items_per_sm must be in [0, 64]");
     g->H = gm->H;
@@ -112,15 +114,16 @@ void set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void *ws, size_t cap, bool *ok) {
     Carver c(ws, cap);
     long long R_pad_tot = 0, Dn_aux_tot = 0, mt_tot = 0, chunks_tot = 0;
+    const int B = gs[0].B, TM = tile_rows(B), npx = B * B, H = B == 16 ? 1 : 2, NS = n_scales(B);
     int32_t *img_counters = c.take<int32_t>(8 * (size_t)n);
     long long *img_matches = c.take<long long>((size_t)n);
     for (int k = 0; k < n; ++k) {
         const Geo &g = gs[k];
         EncodeBufs *b = &bs[k];
-        b->R_pad = (g.R + kTileM - 1) / kTileM * kTileM;
+        b->R_pad = (g.R + TM - 1) / TM * TM;
         b->Dn_pad = (g.Dn + kTileDom - 1) / kTileDom * kTileDom;
         b->Dn_aux = b->Dn_pad + kTileDom;  // a tile may start at any position < Dn
-        b->n_mtiles = b->R_pad / kTileM;
+        b->n_mtiles = b->R_pad / TM;
         b->max_chunks = (g.Dn + kChunkDom - 1) / kChunkDom;
         b->sort_blocks_dom = (g.Dn + kSortChunk - 1) / kSortChunk;
         b->sort_blocks_rng = (g.R + kSortChunk - 1) / kSortChunk;
@@ -134,17 +137,17 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         const int sort_blocks = b->sort_blocks_dom > b->sort_blocks_rng ? b->sort_blocks_dom : b->sort_blocks_rng;
         b->range_sum = c.take<int32_t>(g.R);
         b->range_sumsq = c.take<int32_t>(g.R);
-        b->range_counts = c.take<int32_t>(2 * (size_t)g.R);
+        b->range_counts = c.take<int32_t>((size_t)NS * g.R);
         b->range_fd = c.take<double>(g.R);
         b->range_bin = c.take<uint8_t>(g.R);
         b->dom_sum = c.take<int32_t>(g.Dn);
         b->dom_sumsq = c.take<int32_t>(g.Dn);
-        b->dom_counts = c.take<int32_t>(2 * (size_t)g.Dn);
+        b->dom_counts = c.take<int32_t>((size_t)NS * g.Dn);
         b->dom_fd = c.take<double>(g.Dn);
         b->dom_bin = c.take<uint8_t>(g.Dn);
         b->fd_extent = c.take<double>(2);
         b->extent_bits = c.take<unsigned long long>(2);
-        b->dom_S = c.take<uint16_t>((size_t)g.Dn * 64);
+        b->dom_S = c.take<uint16_t>((size_t)g.Dn * npx);
         b->dom_order = c.take<int32_t>(g.Dn);
         b->bin_off = c.take<int32_t>(kMaxClasses + 2);
         b->range_order = c.take<int32_t>(g.R);
@@ -160,35 +163,39 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->counters = img_counters ? img_counters + 8 * k : nullptr;
         b->matches = img_matches ? img_matches + k : nullptr;
     }
+    tb->B = B;
+    tb->tm = TM;
+    tb->halves = H;
     tb->R_pad = (int)R_pad_tot;
     tb->Dn_aux = (int)Dn_aux_tot;
     tb->n_mtiles = (int)mt_tot;
     tb->max_items = (int)mt_tot + kMaxItemTarget;
     tb->max_chunks = (int)chunks_tot;
-    tb->A_mat = c.take<__half>((size_t)R_pad_tot * 64, 1024);
-    tb->B_mat = c.take<__half>((size_t)8 * Dn_aux_tot * 64, 1024);
-    tb->A1_mat = c.take<__half>((size_t)R_pad_tot * 16, 1024);
-    tb->B1_mat = c.take<__half>((size_t)8 * Dn_aux_tot * 16, 1024);
+    const size_t slice = B == 8 ? 16 : 0;  // correction slice columns (B = 16 corrects in the epilogue)
+    tb->A_mat = c.take<__half>((size_t)R_pad_tot * npx, 1024);
+    tb->B_mat = c.take<__half>((size_t)8 * Dn_aux_tot * npx, 1024);
+    tb->A1_mat = c.take<__half>((size_t)R_pad_tot * slice, 1024);
+    tb->B1_mat = c.take<__half>((size_t)8 * Dn_aux_tot * slice, 1024);
     tb->dom_aux = c.take<float4>((size_t)Dn_aux_tot);
     tb->rng_info = c.take<int4>((size_t)R_pad_tot);
     tb->tile_win = c.take<int4>((size_t)mt_tot);
     tb->n_chunks = c.take<int32_t>((size_t)mt_tot);
     tb->tile_items = c.take<int4>((size_t)mt_tot);
     tb->work = c.take<int4>((size_t)tb->max_items);
-    tb->cand = c.take<unsigned long long>((size_t)tb->max_items * kTileM * 4);
-    tb->chunk_max = c.take<uint32_t>((size_t)chunks_tot * kTileM * 2);
+    tb->cand = c.take<unsigned long long>((size_t)tb->max_items * TM * H * 2);
+    tb->chunk_max = c.take<uint32_t>((size_t)chunks_tot * TM * H);
     tb->gcounters = c.take<int32_t>(8);
     for (int k = 0; k < n; ++k) {
         EncodeBufs *b = &bs[k];
         const bool have = tb->A_mat != nullptr;
-        b->A_mat = have ? tb->A_mat + (size_t)b->rng_off * 64 : nullptr;
-        b->A1_mat = have ? tb->A1_mat + (size_t)b->rng_off * 16 : nullptr;
-        b->B_mat = have ? tb->B_mat + (size_t)b->dom_off * 8 * 64 : nullptr;
-        b->B1_mat = have ? tb->B1_mat + (size_t)b->dom_off * 8 * 16 : nullptr;
+        b->A_mat = have ? tb->A_mat + (size_t)b->rng_off * npx : nullptr;
+        b->A1_mat = have ? tb->A1_mat + (size_t)b->rng_off * slice : nullptr;
+        b->B_mat = have ? tb->B_mat + (size_t)b->dom_off * 8 * npx : nullptr;
+        b->B1_mat = have ? tb->B1_mat + (size_t)b->dom_off * 8 * slice : nullptr;
         b->dom_aux = have ? tb->dom_aux + b->dom_off : nullptr;
         b->rng_info = have ? tb->rng_info + b->rng_off : nullptr;
     }
-    if (R_pad_tot >= (1LL << 31) / 64 || 8 * Dn_aux_tot >= (1LL << 31)) c.ok = false;
+    if (R_pad_tot * npx >= (1LL << 31) || 8 * Dn_aux_tot >= (1LL << 31)) c.ok = false;
     if (ok) *ok = c.ok;
     return c.off + 256;
 }
@@ -378,13 +385,18 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(mark(4), "event");
         FIC_TRY(mark(5), "event");
     } else {
-        for (int k = 0; k < n; ++k) FIC_TRY(launch_pack(imgs[k], g[k], b[k], st), "pack");
+        const bool b16 = g[0].B == 16;
+        for (int k = 0; k < n; ++k)
+            FIC_TRY(b16 ? launch_pack16(imgs[k], g[k], b[k], st) : launch_pack(imgs[k], g[k], b[k], st), "pack");
         FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), st),
                 "work_list");
         FIC_TRY(mark(3), "event");
-        FIC_TRY(launch_match_tc(tb, sms, st), "match_tc");
+        FIC_TRY(b16 ? launch_match_tc16(tb, sms, st) : launch_match_tc(tb, sms, st), "match_tc");
         FIC_TRY(mark(4), "event");
-        for (int k = 0; k < n; ++k) FIC_TRY(launch_reeval(imgs[k], g[k], b[k], tb, outs[k], st), "reeval");
+        for (int k = 0; k < n; ++k)
+            FIC_TRY(b16 ? launch_reeval16(imgs[k], g[k], b[k], tb, outs[k], st)
+                        : launch_reeval(imgs[k], g[k], b[k], tb, outs[k], st),
+                    "reeval");
         FIC_TRY(mark(5), "event");
         for (int k = 0; k < n; ++k) FIC_TRY(launch_rescan(imgs[k], g[k], b[k], tb, outs[k], sms, st), "rescan");
     }

@@ -2,12 +2,16 @@
 // dimension and LFD classes (Revathy & Jayamohan, Section 3.1, Eq. 2-3).
 //
 // DBC reading used throughout the library (the paper cites Sarkar & Chaudhuri without
-// restating the estimator): an 8x8 block with G grey levels is covered by s x s cells,
-// s in {2, 4}; a cell contributes floor(max/h) - floor(min/h) + 1 boxes of height
-// h = s*G/8; N_s sums the cells; FD = log2 N_2 - log2 N_4 (the least-squares slope of
-// log N_s against log(8/s) through two points). Ranges use their pixels (G = 256, h = 64, 128:
+// restating the estimator): an M x M block with G grey levels is covered by s x s cells,
+// s = 2, 4, ..., M/2; a cell contributes floor(max/h) - floor(min/h) + 1 boxes of height
+// h = s*G/M; N_s sums the cells; FD is the least-squares slope of log2 N_s against log2(M/s).
+// M = 8: s in {2, 4}, FD = log2 N_2 - log2 N_4. Ranges use their pixels (G = 256, h = 64, 128:
 // shifts 6 and 7); domains use their contracted block of integer 2x2 sums (G = 1024, shifts 8
 // and 9, identical to the 2x2 average with G = 256).
+// M = 16: s in {2, 4, 8} at equally spaced abscissae, where the middle point has zero weight and
+// FD = (log2 N_2 - log2 N_8) / 2; pixel box heights 32, 64, 128 (shifts 5, 6, 7), sums 128, 256,
+// 512 (shifts 7, 8, 9). Counts are stored per block as n_scales(B) consecutive int32.
+#include <climits>
 #include <cmath>
 #include <mutex>
 
@@ -82,7 +86,7 @@ const Log2Tab &log2_table() {
     static std::once_flag once;
     std::call_once(once, [] {
         tab.v[0] = 0.0;
-        for (int i = 1; i <= 64; ++i) tab.v[i] = log2_correctly_rounded(i);
+        for (int i = 1; i <= 512; ++i) tab.v[i] = log2_correctly_rounded(i);
     });
     return tab;
 }
@@ -249,6 +253,144 @@ __global__ void k_bins(Geo g, const double *__restrict__ rfd, const double *__re
         dbin[i - g.R] = (uint8_t)b;
 }
 
+// ---- B = 16 -----------------------------------------------------------------------------------
+__device__ __forceinline__ double fd16_of(const Log2Tab &L, int n2, int n8) {
+    return __dmul_rn(__dsub_rn(L.v[n2], L.v[n8]), 0.5);
+}
+
+// Box counts of a 16x16 block streamed two rows at a time: the 2x2 cells of each row pair
+// complete at once; 4x4 and 8x8 cells gather their 2x2 cells' extremes until they close.
+// SH is the box-height shift of s = 2 (5 for pixels, 7 for sums); s = 4, 8 use SH + 1, SH + 2.
+template <int SH>
+struct Dbc16 {
+    int n2 = 0, n4 = 0, n8 = 0;
+    int mx4[4], mn4[4], mx8[2], mn8[2];
+    __device__ __forceinline__ void reset4() {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            mx4[k] = INT_MIN;
+            mn4[k] = INT_MAX;
+        }
+    }
+    __device__ __forceinline__ void reset8() {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            mx8[k] = INT_MIN;
+            mn8[k] = INT_MAX;
+        }
+    }
+    // rows a[16], b[16] of row pair p (0..7)
+    __device__ __forceinline__ void row_pair(int p, const int *a, const int *b) {
+        if ((p & 1) == 0) reset4();
+        if ((p & 3) == 0) reset8();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int mx = max(max(a[2 * c], a[2 * c + 1]), max(b[2 * c], b[2 * c + 1]));
+            const int mn = min(min(a[2 * c], a[2 * c + 1]), min(b[2 * c], b[2 * c + 1]));
+            n2 += (mx >> SH) - (mn >> SH) + 1;
+            mx4[c >> 1] = max(mx4[c >> 1], mx);
+            mn4[c >> 1] = min(mn4[c >> 1], mn);
+            mx8[c >> 2] = max(mx8[c >> 2], mx);
+            mn8[c >> 2] = min(mn8[c >> 2], mn);
+        }
+        if (p & 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) n4 += (mx4[k] >> (SH + 1)) - (mn4[k] >> (SH + 1)) + 1;
+        if ((p & 3) == 3)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) n8 += (mx8[k] >> (SH + 2)) - (mn8[k] >> (SH + 2)) + 1;
+    }
+};
+
+// One thread per 16x16 range.
+__global__ void k_range_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
+                                int32_t *__restrict__ rsum, int32_t *__restrict__ rsumsq,
+                                int32_t *__restrict__ rcounts, double *__restrict__ rfd) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.R) return;
+    const int y0 = (r / g.nRx) * 16, x0 = (r % g.nRx) * 16;
+    Dbc16<5> dbc;
+    int A = 0, Bs = 0;
+    for (int p = 0; p < 8; ++p) {
+        int a[16], b[16];
+        const uint8_t *r0 = img + (size_t)(y0 + 2 * p) * g.pitch + x0;
+        const uint8_t *r1 = r0 + g.pitch;
+#pragma unroll
+        for (int x = 0; x < 16; ++x) {
+            a[x] = __ldg(r0 + x);
+            b[x] = __ldg(r1 + x);
+            A += a[x] + b[x];
+            Bs += a[x] * a[x] + b[x] * b[x];
+        }
+        dbc.row_pair(p, a, b);
+    }
+    rsum[r] = A;
+    rsumsq[r] = Bs;
+    rcounts[3 * r] = dbc.n2;
+    rcounts[3 * r + 1] = dbc.n4;
+    rcounts[3 * r + 2] = dbc.n8;
+    rfd[r] = fd16_of(L, dbc.n2, dbc.n8);
+}
+
+// One thread per 32x32 domain: its 16x16 block of 2x2 sums S (stored), C, E, counts and FD; the
+// FD extent as in k_dom_stats.
+__global__ void k_dom_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
+                              uint16_t *__restrict__ domS, int32_t *__restrict__ dsum,
+                              int32_t *__restrict__ dsumsq, int32_t *__restrict__ dcounts,
+                              double *__restrict__ dfd, unsigned long long *extent_bits) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long fbits_min = ~0ull, fbits_max = 0ull;
+    if (d < g.Dn) {
+        const int y0 = (d / g.nDx) * g.sigma, x0 = (d % g.nDx) * g.sigma;
+        Dbc16<7> dbc;
+        int C = 0, E = 0;
+        uint4 *dst = reinterpret_cast<uint4 *>(domS + (size_t)d * 256);
+        for (int p = 0; p < 8; ++p) {
+            int a[16], b[16];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int *S = h ? b : a;
+                const uint8_t *q0 = img + (size_t)(y0 + 4 * p + 2 * h) * g.pitch + x0;
+                const uint8_t *q1 = q0 + g.pitch;
+#pragma unroll
+                for (int x = 0; x < 16; ++x) {
+                    S[x] = (int)__ldg(q0 + 2 * x) + __ldg(q0 + 2 * x + 1) + __ldg(q1 + 2 * x) +
+                           __ldg(q1 + 2 * x + 1);
+                    C += S[x];
+                    E += S[x] * S[x];
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    uint4 pk;
+                    pk.x = (uint32_t)S[8 * k + 0] | ((uint32_t)S[8 * k + 1] << 16);
+                    pk.y = (uint32_t)S[8 * k + 2] | ((uint32_t)S[8 * k + 3] << 16);
+                    pk.z = (uint32_t)S[8 * k + 4] | ((uint32_t)S[8 * k + 5] << 16);
+                    pk.w = (uint32_t)S[8 * k + 6] | ((uint32_t)S[8 * k + 7] << 16);
+                    dst[(2 * p + h) * 2 + k] = pk;
+                }
+            }
+            dbc.row_pair(p, a, b);
+        }
+        const double f = fd16_of(L, dbc.n2, dbc.n8);
+        dsum[d] = C;
+        dsumsq[d] = E;
+        dcounts[3 * d] = dbc.n2;
+        dcounts[3 * d + 1] = dbc.n4;
+        dcounts[3 * d + 2] = dbc.n8;
+        dfd[d] = f;
+        fbits_min = fbits_max = (unsigned long long)__double_as_longlong(f);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        fbits_min = min(fbits_min, __shfl_xor_sync(0xffffffffu, fbits_min, off));
+        fbits_max = max(fbits_max, __shfl_xor_sync(0xffffffffu, fbits_max, off));
+    }
+    if ((threadIdx.x & 31) == 0 && fbits_max != 0ull) {
+        atomicMin(&extent_bits[0], fbits_min);
+        atomicMax(&extent_bits[1], fbits_max);
+    }
+}
+
 cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                             cudaStream_t st) {
     const Log2Tab &L = log2_table();
@@ -256,12 +398,21 @@ cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &
     // extent_bits[0] = all ones (min identity), extent_bits[1] = 0 (max identity)
     if ((e = cudaMemsetAsync(b.extent_bits, 0xff, sizeof(unsigned long long), st))) return e;
     if ((e = cudaMemsetAsync(b.extent_bits + 1, 0, sizeof(unsigned long long), st))) return e;
-    k_range_stats<<<(g.R + 127) / 128, 128, 0, st>>>(img, g, L, b.range_sum, b.range_sumsq,
-                                                     b.range_counts, b.range_fd);
-    ++g_launches;
-    k_dom_stats<<<(g.Dn + 127) / 128, 128, 0, st>>>(img, g, L, b.dom_S, b.dom_sum, b.dom_sumsq,
-                                                    b.dom_counts, b.dom_fd, b.extent_bits);
-    ++g_launches;
+    if (g.B == 16) {
+        k_range_stats16<<<(g.R + 127) / 128, 128, 0, st>>>(img, g, L, b.range_sum, b.range_sumsq,
+                                                           b.range_counts, b.range_fd);
+        ++g_launches;
+        k_dom_stats16<<<(g.Dn + 127) / 128, 128, 0, st>>>(img, g, L, b.dom_S, b.dom_sum, b.dom_sumsq,
+                                                          b.dom_counts, b.dom_fd, b.extent_bits);
+        ++g_launches;
+    } else {
+        k_range_stats<<<(g.R + 127) / 128, 128, 0, st>>>(img, g, L, b.range_sum, b.range_sumsq,
+                                                         b.range_counts, b.range_fd);
+        ++g_launches;
+        k_dom_stats<<<(g.Dn + 127) / 128, 128, 0, st>>>(img, g, L, b.dom_S, b.dom_sum, b.dom_sumsq,
+                                                        b.dom_counts, b.dom_fd, b.extent_bits);
+        ++g_launches;
+    }
     const int n = g.R + g.Dn;
     k_bins<<<(n + 255) / 256, 256, 0, st>>>(g, b.range_fd, b.dom_fd, b.extent_bits, b.fd_extent,
                                             b.range_bin, b.dom_bin);

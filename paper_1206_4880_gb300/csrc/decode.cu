@@ -26,16 +26,17 @@ cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st) {
 }
 
 // One thread per output pixel.
+template <int B>
 __global__ void k_decode_step(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
                               const double *__restrict__ s, const double *__restrict__ o,
                               const float *__restrict__ x, float *__restrict__ y) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.H * g.W) return;
     const int py = idx / g.W, px = idx - py * g.W;
-    const int r = (py >> 3) * g.nRx + (px >> 3);
+    const int r = (py / B) * g.nRx + (px / B);
     const int d = dom[r], t = iso[r];
     int sy, sx;
-    iso_src(8, t, py & 7, px & 7, sy, sx);
+    iso_src(B, t, py % B, px % B, sy, sx);
     const int qy = (d / g.nDx) * g.sigma + 2 * sy, qx = (d % g.nDx) * g.sigma + 2 * sx;
     const float *p = x + (size_t)qy * g.W + qx;
     const float v = (((p[0] + p[1]) + p[g.W]) + p[g.W + 1]) * 0.25f;
@@ -45,20 +46,23 @@ __global__ void k_decode_step(Geo g, const int32_t *__restrict__ dom, const int3
 cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,
                                cudaStream_t st) {
     const int n = g.H * g.W;
-    k_decode_step<<<(n + 255) / 256, 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+    if (g.B == 16)
+        k_decode_step<16><<<(n + 255) / 256, 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+    else
+        k_decode_step<8><<<(n + 255) / 256, 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
     ++g_launches;
     return cudaGetLastError();
 }
 
 // Resolution-independent step (Section 1): the codes of an H x W encoding applied on the
-// (zH) x (zW) grid; range r covers the (8z)^2 block at z times its position, domain d the (16z)^2
+// (zH) x (zW) grid; range r covers the (Bz)^2 block at z times its position, domain d the (2Bz)^2
 // block at z times its position, contracted by 2x2 averaging, with the isometries of the
-// (8z) x (8z) square. One thread per output pixel.
+// (Bz) x (Bz) square. One thread per output pixel.
 __global__ void k_decode_step_scaled(Geo g, int z, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
                                      const double *__restrict__ s, const double *__restrict__ o,
                                      const float *__restrict__ x, float *__restrict__ y) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Wz = g.W * z, Bz = 8 * z;
+    const int Wz = g.W * z, Bz = g.B * z;
     if (idx >= (long long)g.H * z * Wz) return;
     const int py = (int)(idx / Wz), px = (int)(idx - (long long)py * Wz);
     const int r = (py / Bz) * g.nRx + px / Bz;
@@ -139,16 +143,17 @@ __global__ void k_dom_sortseg(int Dn, const int32_t *__restrict__ off, int32_t *
 }
 
 // l_prev = W^T l, one thread per pixel q.
+template <int B>
 __global__ void k_adjoint_gather(Geo g, const int32_t *__restrict__ iso, const double *__restrict__ s,
                                  const int32_t *__restrict__ off, const int32_t *__restrict__ list,
                                  const float *__restrict__ lam, float *__restrict__ lam_prev) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.H * g.W) return;
     const int qy = idx / g.W, qx = idx - qy * g.W;
-    // domains (dy, dx) on the stride grid with dy <= qy < dy + 16, likewise x
+    // domains (dy, dx) on the stride grid with dy <= qy < dy + 2B, likewise x
     const int jy_hi = min(qy / g.sigma, g.nDy - 1), jx_hi = min(qx / g.sigma, g.nDx - 1);
-    const int jy_lo = max(0, (qy - 15 + g.sigma - 1) / g.sigma);
-    const int jx_lo = max(0, (qx - 15 + g.sigma - 1) / g.sigma);
+    const int jy_lo = max(0, (qy - (2 * B - 1) + g.sigma - 1) / g.sigma);
+    const int jx_lo = max(0, (qx - (2 * B - 1) + g.sigma - 1) / g.sigma);
     float acc = 0.f;
     for (int jy = jy_lo; jy <= jy_hi; ++jy) {
         const int dy = jy * g.sigma;
@@ -163,8 +168,8 @@ __global__ void k_adjoint_gather(Geo g, const int32_t *__restrict__ iso, const d
                 // range pixel p with src_t(p) = (cy, cx): p = src_{t^-1}(cy, cx)
                 const int tinv = (t == 1) ? 3 : (t == 3 ? 1 : t);
                 int py, px;
-                iso_src(8, tinv, cy, cx, py, px);
-                const int ry = (r / g.nRx) * 8, rx = (r % g.nRx) * 8;
+                iso_src(B, tinv, cy, cx, py, px);
+                const int ry = (r / g.nRx) * B, rx = (r % g.nRx) * B;
                 acc = fmaf((float)s[r] * 0.25f, lam[(size_t)(ry + py) * g.W + rx + px], acc);
             }
         }
@@ -175,6 +180,7 @@ __global__ void k_adjoint_gather(Geo g, const int32_t *__restrict__ iso, const d
 // grad_s[r] += sum_p l[p] * T(D x)[p], grad_o[r] += sum_p l[p]; one warp per range. The terms
 // are formed in FP32 and summed in FP64 (the sums cancel heavily: terms of a few hundred add up
 // to gradients of order one), into per-range FP64 accumulators.
+template <int B>
 __global__ void k_adjoint_grads(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
                                 const float *__restrict__ x, const float *__restrict__ lam,
                                 double *__restrict__ gs, double *__restrict__ go) {
@@ -182,15 +188,15 @@ __global__ void k_adjoint_grads(Geo g, const int32_t *__restrict__ dom, const in
     const int lane = threadIdx.x & 31;
     if (r >= g.R) return;
     const int d = dom[r], t = iso[r];
-    const int ry = (r / g.nRx) * 8, rx = (r % g.nRx) * 8;
+    const int ry = (r / g.nRx) * B, rx = (r % g.nRx) * B;
     const int dy = (d / g.nDx) * g.sigma, dx = (d % g.nDx) * g.sigma;
     double a_s = 0.0, a_o = 0.0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < B * B / 32; ++h) {
         const int p = lane + 32 * h;
-        const int y = p >> 3, xx = p & 7;
+        const int y = p / B, xx = p % B;
         int sy, sx;
-        iso_src(8, t, y, xx, sy, sx);
+        iso_src(B, t, y, xx, sy, sx);
         const float *q = x + (size_t)(dy + 2 * sy) * g.W + dx + 2 * sx;
         const float v = (((q[0] + q[1]) + q[g.W]) + q[g.W + 1]) * 0.25f;
         const float l = lam[(size_t)(ry + y) * g.W + rx + xx];
@@ -236,7 +242,10 @@ cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const int32_
                                   const int32_t *list, const float *lam, float *lam_prev,
                                   cudaStream_t st) {
     const int n = g.H * g.W;
-    k_adjoint_gather<<<(n + 255) / 256, 256, 0, st>>>(g, c.iso, c.s, off, list, lam, lam_prev);
+    if (g.B == 16)
+        k_adjoint_gather<16><<<(n + 255) / 256, 256, 0, st>>>(g, c.iso, c.s, off, list, lam, lam_prev);
+    else
+        k_adjoint_gather<8><<<(n + 255) / 256, 256, 0, st>>>(g, c.iso, c.s, off, list, lam, lam_prev);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -244,7 +253,10 @@ cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const int32_
 cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *x, const float *lam,
                                  double *gs, double *go, cudaStream_t st) {
     const long long threads = (long long)g.R * 32;
-    k_adjoint_grads<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
+    if (g.B == 16)
+        k_adjoint_grads<16><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
+    else
+        k_adjoint_grads<8><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
     ++g_launches;
     return cudaGetLastError();
 }

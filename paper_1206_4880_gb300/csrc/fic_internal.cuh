@@ -24,9 +24,10 @@ struct Geo {
     int literal;         // 1: Eq. 3 window on FD values (FIC_FLAG_LITERAL_WINDOW)
 };
 
-// Correctly rounded log2(n) for n = 0..64 (entry 0 unused); passed to kernels by value.
+// Correctly rounded log2(n) for n = 0..512 (entry 0 unused; box counts of 16x16 blocks reach
+// 512); passed to kernels by value.
 struct Log2Tab {
-    double v[65];
+    double v[513];
 };
 const Log2Tab &log2_table();
 double log2_correctly_rounded(int n);
@@ -103,9 +104,96 @@ __device__ __forceinline__ void finalize_code(int n, long long A, long long Bs, 
     sse = __ddiv_rn((double)num, __dmul_rn(__dmul_rn(16.0, (double)n), (double)g.den));
 }
 
-// Exact best of the evaluated candidates of a range the ranking could not certify.
-struct FallbackBest {
-    long long num, den, P, Q;
+// ----------------------------------------------------------------------------------------
+// The same for B = 16 (n = 256): |P| < 2^35 and Q < 2^37, so 16 P^2 needs 128 bits.
+struct GainW {
+    __int128 num;
+    long long den;
+};
+
+__device__ __forceinline__ GainW exact_gain_w(long long P, long long Q) {
+    GainW g;
+    const long long aP = P < 0 ? -P : P;
+    if (Q == 0) {
+        g.num = 0;
+        g.den = 1;
+    } else if (4 * aP <= Q) {
+        g.num = (__int128)16 * ((__int128)P * (__int128)P);
+        g.den = Q;
+    } else {
+        g.num = (__int128)(8 * aP - Q);
+        g.den = 1;
+    }
+    return g;
+}
+
+__device__ __forceinline__ int gain_cmp(GainW a, GainW b) {
+    const __int128 l = a.num * (__int128)b.den, r = b.num * (__int128)a.den;  // < 2^113
+    return l > r ? 1 : (l < r ? -1 : 0);
+}
+
+__device__ __forceinline__ bool cand_better(GainW ga, int da, int ta, GainW gb, int db, int tb) {
+    const int c = gain_cmp(ga, gb);
+    if (c != 0) return c > 0;
+    if (da != db) return da < db;
+    return ta < tb;
+}
+
+// Round-to-nearest-even conversion of a 128-bit integer: the top 64 significant bits with the
+// dropped bits folded into bit 0 (a sticky bit well below the rounding position) convert to the
+// same double as the whole value; the power-of-two scaling is exact.
+__device__ __forceinline__ double i128_to_double_rn(__int128 v) {
+    const bool neg = v < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    double r;
+    if (hi == 0) {
+        r = __ull2double_rn(lo);
+    } else {
+        const int sh = 64 - __clzll((long long)hi);  // 1..64 bits above the low word
+        unsigned long long top = (unsigned long long)(u >> sh);
+        const unsigned long long dropped = sh == 64 ? lo : (lo & ((1ull << sh) - 1ull));
+        top |= dropped != 0ull ? 1ull : 0ull;
+        r = __dmul_rn(__ull2double_rn(top), __longlong_as_double((long long)(1023 + sh) << 52));
+    }
+    return neg ? -r : r;
+}
+
+__device__ __forceinline__ void finalize_code(int n, long long A, long long Bs, long long C,
+                                              long long P, long long Q, GainW g, double &s,
+                                              double &o, double &sse) {
+    const long long aP = P < 0 ? -P : P;
+    if (Q == 0)
+        s = 0.0;
+    else if (4 * aP <= Q)
+        s = __ddiv_rn(__dmul_rn(4.0, (double)P), (double)Q);
+    else
+        s = P > 0 ? 1.0 : -1.0;
+    o = __ddiv_rn(__dsub_rn((double)A, __dmul_rn(s, __ddiv_rn((double)C, 4.0))), (double)n);
+    const long long base = 16 * ((long long)n * Bs - A * A);  // < 2^37
+    const __int128 num = (__int128)base * (__int128)g.den - g.num;
+    sse = __ddiv_rn(i128_to_double_rn(num), __dmul_rn(__dmul_rn(16.0, (double)n), (double)g.den));
+}
+
+// Gain type and exact gain of a B x B block.
+template <int B>
+struct FitOf;
+template <>
+struct FitOf<8> {
+    using G = Gain;
+    __device__ static __forceinline__ G gain(long long P, long long Q) { return exact_gain(P, Q); }
+};
+template <>
+struct FitOf<16> {
+    using G = GainW;
+    __device__ static __forceinline__ G gain(long long P, long long Q) { return exact_gain_w(P, Q); }
+};
+
+// Exact best of the evaluated candidates of a range the ranking could not certify (num < 0:
+// none).
+struct __align__(16) FallbackBest {
+    __int128 num;
+    long long den, P, Q;
     int d, t, C, pad;
 };
 
@@ -137,7 +225,7 @@ struct EncodeBufs {
     uint8_t *dom_bin;
     double *fd_extent;
     unsigned long long *extent_bits;  // [2] min/max FD bit patterns during the reduction
-    uint16_t *dom_S;                  // [Dn][64] integer 2x2 sums of every domain
+    uint16_t *dom_S;                  // [Dn][n] integer 2x2 sums of every domain (n = B^2)
     // pools
     int32_t *dom_order, *bin_off, *range_order, *rbin_off, *win_lo, *win_hi;
     uint8_t *dom_key, *range_key;  // [Dn], [R] sort keys (class, or FD rank in literal mode)
@@ -145,11 +233,12 @@ struct EncodeBufs {
     int32_t *sort_counts;  // [nblk][256] per-block class histograms
     int32_t *sort_offs;    // [nblk][256] per-block scatter bases
     // tensor engine: this image's slice of the batch-wide arrays (TcBatch)
-    __half *A_mat;         // [R_pad][64]   range pixels - a, class-sorted ranges
-    __half *B_mat;         // [8 Dn_aux][64] T_t(S_d) - c, class-sorted domains x isometries
-    __half *A1_mat;        // [R_pad][16] (alpha, 0, ...): correction slice of the A operand
-    __half *B1_mat;        // [8 Dn_aux][16] (-gamma / 64, 0, ...): correction slice of B
-    float4 *dom_aux;       // [Dn_aux] per sorted domain: 0, Q / 256, 128 / Q (0 if Q = 0), 0
+    __half *A_mat;         // [R_pad][n]   range pixels - a, class-sorted ranges
+    __half *B_mat;         // [8 Dn_aux][n] T_t(S_d) - c, class-sorted domains x isometries
+    __half *A1_mat;        // [R_pad][16] (alpha, 0, ...): correction slice of the A operand (B = 8)
+    __half *B1_mat;        // [8 Dn_aux][16] (-gamma / 64, 0, ...): correction slice of B (B = 8)
+    float4 *dom_aux;       // [Dn_aux] per sorted domain: B = 8: (0, Q / 256, 128 / Q, 0);
+                           // B = 16: (-gamma / 256, Q / 1024, 512 / Q, 0) (1/Q terms 0 if Q = 0)
     int4 *rng_info;        // [R_pad] per sorted range: A, pool start, pool end (batch-wide
                            // domain positions), range id (-1 for padding rows)
     int rng_off, dom_off, mt_off;  // first batch-wide sorted range, sorted domain, range tile
@@ -164,6 +253,9 @@ struct EncodeBufs {
 // Tensor-engine arrays shared by every image of a batch: class-sorted ranges and domains of all
 // images concatenated, so one persistent kernel launch serves the whole batch.
 struct TcBatch {
+    int B;                 // range side: 8 or 16
+    int tm;                // ranges per range tile: 128 (B = 8) or 256 (B = 16, two MMA row tiles)
+    int halves;            // key columns per row: 2 (B = 8: two column halves), 1 (B = 16)
     __half *A_mat, *B_mat, *A1_mat, *B1_mat;
     float4 *dom_aux;
     int4 *rng_info;
@@ -171,19 +263,23 @@ struct TcBatch {
     int32_t *n_chunks;     // [n_mtiles] 512-domain chunks per range tile
     int4 *tile_items;      // [n_mtiles] first work item, items, first chunk, chunks
     int4 *work;            // [max_items] (range tile, first domain, end domain, first chunk)
-    unsigned long long *cand;  // [max_items][128 rows][2 column halves][2] top-2 keys
-    uint32_t *chunk_max;   // [max_chunks][128 rows][2 column halves] best key per chunk
+    unsigned long long *cand;  // [max_items][tm rows][halves][2] top-2 keys
+    uint32_t *chunk_max;   // [max_chunks][tm rows][halves] best key per chunk
     int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks
     int R_pad, Dn_aux, n_mtiles, max_items, max_chunks;
 };
 
 constexpr int kSortChunk = 2048;  // elements per counting-sort block
-constexpr int kTileM = 128;       // ranges per tensor-engine tile
+constexpr int kTileM = 128;       // rows of one MMA (ranges per B = 8 range tile)
 constexpr int kTileDom = 32;      // domains per accumulator tile (8 isometries -> N = 256)
 constexpr int kChunkTiles = 16;   // accumulator tiles per chunk (the re-search granule)
 constexpr int kChunkDom = kTileDom * kChunkTiles;
 constexpr int kItemsPerSm = 16;   // default work items per SM the work list aims for
 constexpr int kMaxItemTarget = 64 * 256;  // items_per_sm <= 64, SMs <= 256
+
+// Ranges per range tile of the tensor engine and box-count scales of a B x B block.
+__host__ __device__ constexpr int tile_rows(int B) { return B == 16 ? 2 * kTileM : kTileM; }
+__host__ __device__ constexpr int n_scales(int B) { return B == 16 ? 3 : 2; }
 
 // Carves the workspace for n images: per-image buffers, then the batch-wide arrays. Returns the
 // bytes needed (with base == nullptr, only the size).
@@ -203,6 +299,11 @@ cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t s
 cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st);
 cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, cudaStream_t st);
+// B = 16 tensor engine (match_tc16.cu)
+cudaError_t launch_pack16(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st);
+cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st);
+cudaError_t launch_reeval16(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
+                            const fic_codes &out, cudaStream_t st);
 cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encode_info *info, cudaStream_t st);
 
 // decode

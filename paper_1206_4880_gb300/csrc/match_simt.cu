@@ -3,9 +3,10 @@
 // (restricted to the domain chunks that could still hold the winner).
 //
 // For a range r, a domain d of its pool (Section 3.1 Eq. 3) and an isometry t, the correlation
-// X_t = sum_p r[p] * (T_t S_d)[p] is formed exactly (integer products <= 255*1020 and sums
-// < 2^24 are exact in FP32 FMA), then P = 64 X - A C and Q = 64 E - C^2 give the exact
-// least-squares gain (Section 1's intensity map with |s| <= 1); the best (gain, -d, -t) wins.
+// X_t = sum_p r[p] * (T_t S_d)[p] is formed exactly (integer products <= 255*1020; FP32 FMA sums
+// over at most 64 pixels stay below 2^24 and are exact, and B = 16 adds four such partial sums in
+// integers), then P = n X - A C and Q = n E - C^2 give the exact least-squares gain (Section 1's
+// intensity map with |s| <= 1); the best (gain, -d, -t) wins.
 //
 // One CTA per range: the range's 8 inverse-permuted copies sit in shared memory, each thread
 // walks every 256th domain, and a shared-memory tree picks the block's best.
@@ -19,74 +20,92 @@ namespace {
 
 constexpr int kSimtThreads = 256;
 
+template <int B>
 struct ScanShared {
+    using G = typename FitOf<B>::G;
     // rp[t][q] = r[p] with src_t(p) = q, so that X_t = sum_q S[q] * rp[t][q]
-    float rp[8][64];
-    long long num[kSimtThreads], den[kSimtThreads], P[kSimtThreads], Q[kSimtThreads];
+    float rp[8][B * B];
+    G g[kSimtThreads];
+    long long P[kSimtThreads], Q[kSimtThreads];
     int d[kSimtThreads], t[kSimtThreads], C[kSimtThreads];
     int flagged[kSimtThreads];
     int n_flagged;
 };
 
+template <int B>
 struct Best {
-    Gain g;
+    typename FitOf<B>::G g;
     int d, t, C;
     long long P, Q;
 };
 
-__device__ __forceinline__ void load_range(ScanShared &sh, const Geo &g, const uint8_t *img, int r) {
-    const int tid = threadIdx.x;
-    if (tid < 64) {
-        const int y = tid >> 3, x = tid & 7;
-        const int ry = (r / g.nRx) * 8, rx = (r % g.nRx) * 8;
+template <int B>
+__device__ __forceinline__ void load_range(ScanShared<B> &sh, const Geo &g, const uint8_t *img, int r) {
+    for (int p = threadIdx.x; p < B * B; p += kSimtThreads) {
+        const int y = p / B, x = p % B;
+        const int ry = (r / g.nRx) * B, rx = (r % g.nRx) * B;
         const float v = (float)img[(size_t)(ry + y) * g.pitch + rx + x];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             int sy, sx;
-            iso_src(8, t, y, x, sy, sx);
-            sh.rp[t][sy * 8 + sx] = v;
+            iso_src(B, t, y, x, sy, sx);
+            sh.rp[t][sy * B + sx] = v;
         }
     }
 }
 
-// Exact evaluation of domain d under all 8 isometries against the range in sh.rp.
-__device__ __forceinline__ void scan_domain(const ScanShared &sh, int d, long long A,
-                                            const uint16_t *__restrict__ domS,
-                                            const int32_t *__restrict__ dsum,
-                                            const int32_t *__restrict__ dsumsq, Best &b) {
-    float S[64];
-    const uint4 *src = reinterpret_cast<const uint4 *>(domS + (size_t)d * 64);
+// X_t over source indices [q0, q0 + 64) of domain d (a 64-entry slice of S), exact in FP32.
+template <int B>
+__device__ __forceinline__ void slice_dot(const ScanShared<B> &sh, const uint16_t *__restrict__ Sd, int q0,
+                                          float (&acc)[8]) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(Sd + q0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const uint4 u = __ldg(src + k);
         const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            S[8 * k + 2 * h] = (float)(w4[h] & 0xffffu);
-            S[8 * k + 2 * h + 1] = (float)(w4[h] >> 16);
+        for (int h = 0; h < 2; ++h) {
+            const float s0 = (float)(w4[2 * h] & 0xffffu), s1 = (float)(w4[2 * h] >> 16);
+            const float s2 = (float)(w4[2 * h + 1] & 0xffffu), s3 = (float)(w4[2 * h + 1] >> 16);
+            const int q = q0 + 8 * k + 4 * h;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float4 rv = *reinterpret_cast<const float4 *>(&sh.rp[t][q]);
+                acc[t] = fmaf(s0, rv.x, acc[t]);
+                acc[t] = fmaf(s1, rv.y, acc[t]);
+                acc[t] = fmaf(s2, rv.z, acc[t]);
+                acc[t] = fmaf(s3, rv.w, acc[t]);
+            }
         }
     }
-    float acc[8];
+}
+
+// Exact evaluation of domain d under all 8 isometries against the range in sh.rp.
+template <int B>
+__device__ __forceinline__ void scan_domain(const ScanShared<B> &sh, int d, long long A,
+                                            const uint16_t *__restrict__ domS,
+                                            const int32_t *__restrict__ dsum,
+                                            const int32_t *__restrict__ dsumsq, Best<B> &b) {
+    constexpr int n = B * B;
+    const uint16_t *Sd = domS + (size_t)d * n;
+    int X[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+    for (int t = 0; t < 8; ++t) X[t] = 0;
+#pragma unroll 1
+    for (int q0 = 0; q0 < n; q0 += 64) {
+        float acc[8];
 #pragma unroll
-    for (int q = 0; q < 64; q += 4) {
+        for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+        slice_dot<B>(sh, Sd, q0, acc);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const float4 rv = *reinterpret_cast<const float4 *>(&sh.rp[t][q]);
-            acc[t] = fmaf(S[q], rv.x, acc[t]);
-            acc[t] = fmaf(S[q + 1], rv.y, acc[t]);
-            acc[t] = fmaf(S[q + 2], rv.z, acc[t]);
-            acc[t] = fmaf(S[q + 3], rv.w, acc[t]);
-        }
+        for (int t = 0; t < 8; ++t) X[t] += (int)acc[t];
     }
     const long long C = dsum[d];
-    const long long Q = 64LL * dsumsq[d] - C * C;
+    const long long Q = (long long)n * dsumsq[d] - C * C;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        const long long X = (long long)acc[t];
-        const long long P = 64LL * X - A * C;
-        const Gain gg = exact_gain(P, Q);
+        const long long P = (long long)n * X[t] - A * C;
+        const auto gg = FitOf<B>::gain(P, Q);
         if (cand_better(gg, d, t, b.g, b.d, b.t)) {
             b.g = gg;
             b.d = d;
@@ -99,11 +118,11 @@ __device__ __forceinline__ void scan_domain(const ScanShared &sh, int d, long lo
 }
 
 // Block-wide best and the code of range r (thread 0 writes it).
-__device__ __forceinline__ void reduce_and_write(ScanShared &sh, const Best &b, int r, long long A,
+template <int B>
+__device__ __forceinline__ void reduce_and_write(ScanShared<B> &sh, const Best<B> &b, int r, long long A,
                                                  long long Bs, const fic_codes &out) {
     const int tid = threadIdx.x;
-    sh.num[tid] = b.g.num;
-    sh.den[tid] = b.g.den;
+    sh.g[tid] = b.g;
     sh.d[tid] = b.d;
     sh.t[tid] = b.t;
     sh.P[tid] = b.P;
@@ -112,10 +131,8 @@ __device__ __forceinline__ void reduce_and_write(ScanShared &sh, const Best &b, 
     __syncthreads();
     for (int s = kSimtThreads / 2; s > 0; s >>= 1) {
         if (tid < s) {
-            const Gain ga{sh.num[tid], sh.den[tid]}, gb{sh.num[tid + s], sh.den[tid + s]};
-            if (cand_better(gb, sh.d[tid + s], sh.t[tid + s], ga, sh.d[tid], sh.t[tid])) {
-                sh.num[tid] = gb.num;
-                sh.den[tid] = gb.den;
+            if (cand_better(sh.g[tid + s], sh.d[tid + s], sh.t[tid + s], sh.g[tid], sh.d[tid], sh.t[tid])) {
+                sh.g[tid] = sh.g[tid + s];
                 sh.d[tid] = sh.d[tid + s];
                 sh.t[tid] = sh.t[tid + s];
                 sh.P[tid] = sh.P[tid + s];
@@ -127,7 +144,7 @@ __device__ __forceinline__ void reduce_and_write(ScanShared &sh, const Best &b, 
     }
     if (tid == 0) {
         double s, o, sse;
-        finalize_code(64, A, Bs, sh.C[0], sh.P[0], sh.Q[0], Gain{sh.num[0], sh.den[0]}, s, o, sse);
+        finalize_code(B * B, A, Bs, sh.C[0], sh.P[0], sh.Q[0], sh.g[0], s, o, sse);
         out.dom[r] = sh.d[0];
         out.iso[r] = sh.t[0];
         out.s[r] = s;
@@ -137,30 +154,41 @@ __device__ __forceinline__ void reduce_and_write(ScanShared &sh, const Best &b, 
     __syncthreads();
 }
 
+template <class G>
+__device__ __forceinline__ G no_gain() {
+    G g;
+    g.num = -1;
+    g.den = 1;
+    return g;
+}
+
 }  // namespace
 
 // Plain search: CTA r scans the whole pool of range r.
+template <int B>
 __global__ void __launch_bounds__(kSimtThreads)
     k_match_simt(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                  const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                  const int32_t *__restrict__ rsum, const int32_t *__restrict__ rsumsq,
                  const int32_t *__restrict__ dom_order, const int32_t *__restrict__ win_lo,
                  const int32_t *__restrict__ win_hi, fic_codes out) {
-    __shared__ __align__(16) ScanShared sh;
+    __shared__ __align__(16) ScanShared<B> sh;
     const int r = blockIdx.x;
-    load_range(sh, g, img, r);
+    load_range<B>(sh, g, img, r);
     __syncthreads();
     const long long A = rsum[r], Bs = rsumsq[r];
-    Best b{{-1, 1}, INT_MAX, 0, 0, 0, 0};
+    Best<B> b{no_gain<typename FitOf<B>::G>(), INT_MAX, 0, 0, 0, 0};
     for (int j = win_lo[r] + threadIdx.x; j < win_hi[r]; j += kSimtThreads)
-        scan_domain(sh, dom_order[j], A, domS, dsum, dsumsq, b);
-    reduce_and_write(sh, b, r, A, Bs, out);
+        scan_domain<B>(sh, dom_order[j], A, domS, dsum, dsumsq, b);
+    reduce_and_write<B>(sh, b, r, A, Bs, out);
 }
 
 // Re-search of uncertified ranges of one image. Slot k holds class-sorted position fb_pos[k] and
 // the exact best of its evaluated candidates; the 512-domain chunks of the range's tile whose best
-// FP32 score could still reach that best (score * (1 + 2^-16) + 2^-8 >= best gain / 512, the
-// bound k_reeval certifies with) are scanned exactly.
+// FP32 score could still reach that best (score * (1 + 2^-16) + 2^-8 >= best gain / (8 n), the
+// bound the re-evaluation certifies with) are scanned exactly. TM ranges per tile, H key columns
+// per row (chunk_max layout [chunk][TM][H]).
+template <int B, int TM, int H>
 __global__ void __launch_bounds__(kSimtThreads)
     k_rescan(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
              const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
@@ -169,21 +197,25 @@ __global__ void __launch_bounds__(kSimtThreads)
              const int4 *__restrict__ tile_items, const uint32_t *__restrict__ chunk_max,
              const int32_t *__restrict__ fb_pos, const FallbackBest *__restrict__ fb_best,
              const int32_t *__restrict__ counters, fic_codes out) {
-    __shared__ __align__(16) ScanShared sh;
+    __shared__ __align__(16) ScanShared<B> sh;
+    using G = typename FitOf<B>::G;
     const int n = min(counters[0], g.R);
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int i = fb_pos[k];
         const int4 ri = rng_info[i];
         const int r = ri.w;
-        load_range(sh, g, img, r);
+        load_range<B>(sh, g, img, r);
         __syncthreads();
         const FallbackBest fb = fb_best[k];
-        Best b{{fb.num, fb.den}, fb.d, fb.t, fb.C, fb.P, fb.Q};
-        const double thr = fb.num < 0 ? -1.0 : (double)fb.num / (512.0 * (double)fb.den);
+        G g0;
+        g0.num = fb.num;
+        g0.den = fb.den;
+        Best<B> b{g0, fb.d, fb.t, fb.C, fb.P, fb.Q};
+        const double thr = fb.num < 0 ? -1.0 : i128_to_double_rn(fb.num) / (8.0 * B * B * (double)fb.den);
         const long long A = ri.x, Bs = rsumsq[r];
-        const int ig = rng_off + i, row = ig % kTileM;
-        const int4 tw = tile_win[ig / kTileM];
-        const int4 ti = tile_items[ig / kTileM];
+        const int ig = rng_off + i, row = ig % TM;
+        const int4 tw = tile_win[ig / TM];
+        const int4 ti = tile_items[ig / TM];
         const int nch = ti.w;
         // flag the chunks whose best score reaches the threshold (256 chunks at a time, in
         // parallel), then scan the flagged chunks' domains with all threads
@@ -192,8 +224,10 @@ __global__ void __launch_bounds__(kSimtThreads)
             __syncthreads();
             const int c = base + threadIdx.x;
             if (c < nch) {
-                const size_t e = ((size_t)(ti.z + c) * kTileM + row) * 2;
-                const uint32_t key = max(chunk_max[e], chunk_max[e + 1]);
+                const size_t e = ((size_t)(ti.z + c) * TM + row) * H;
+                uint32_t key = chunk_max[e];
+#pragma unroll
+                for (int h = 1; h < H; ++h) key = max(key, chunk_max[e + h]);
                 const double s1 = (double)__uint_as_float(key);
                 if (key != 0 && s1 * (1.0 + 1.0 / 65536.0) + 1.0 / 256.0 >= thr)
                     sh.flagged[atomicAdd(&sh.n_flagged, 1)] = c;
@@ -205,28 +239,36 @@ __global__ void __launch_bounds__(kSimtThreads)
                 const int j0 = max(ri.y, tw.x + cc * kChunkDom);
                 const int j1 = min(ri.z, min(tw.x + (cc + 1) * kChunkDom, tw.y));
                 for (int j = j0 + threadIdx.x; j < j1; j += kSimtThreads)
-                    scan_domain(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
+                    scan_domain<B>(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
             }
             __syncthreads();
         }
-        reduce_and_write(sh, b, r, A, Bs, out);
+        reduce_and_write<B>(sh, b, r, A, Bs, out);
     }
 }
 
 cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                               const fic_codes &out, cudaStream_t st) {
-    k_match_simt<<<g.R, kSimtThreads, 0, st>>>(g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sum,
-                                               b.range_sumsq, b.dom_order, b.win_lo, b.win_hi, out);
+    if (g.B == 16)
+        k_match_simt<16><<<g.R, kSimtThreads, 0, st>>>(g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sum,
+                                                       b.range_sumsq, b.dom_order, b.win_lo, b.win_hi, out);
+    else
+        k_match_simt<8><<<g.R, kSimtThreads, 0, st>>>(g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sum,
+                                                      b.range_sumsq, b.dom_order, b.win_lo, b.win_hi, out);
     ++g_launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, int num_sms, cudaStream_t st) {
-    k_rescan<<<4 * num_sms, kSimtThreads, 0, st>>>(g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq,
-                                                   b.dom_order, b.rng_info, b.rng_off, b.dom_off, tb.tile_win,
-                                                   tb.tile_items, tb.chunk_max, b.fallback, b.fb_best, b.counters,
-                                                   out);
+    if (g.B == 16)
+        k_rescan<16, 2 * kTileM, 1><<<4 * num_sms, kSimtThreads, 0, st>>>(
+            g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.rng_info, b.rng_off, b.dom_off,
+            tb.tile_win, tb.tile_items, tb.chunk_max, b.fallback, b.fb_best, b.counters, out);
+    else
+        k_rescan<8, kTileM, 2><<<4 * num_sms, kSimtThreads, 0, st>>>(
+            g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.rng_info, b.rng_off, b.dom_off,
+            tb.tile_win, tb.tile_items, tb.chunk_max, b.fallback, b.fb_best, b.counters, out);
     ++g_launches;
     return cudaGetLastError();
 }

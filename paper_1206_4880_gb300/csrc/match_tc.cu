@@ -35,6 +35,7 @@
 #include <mutex>
 
 #include "fic_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace fic {
 
@@ -59,7 +60,6 @@ constexpr int kB1Bytes = kTileN * 32;    // 256 rows x 16 fp16
 constexpr int kEpiWarps = 8;             // two per TMEM lane group, one per column half
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 constexpr int kTmemCols = 2 * kTileN;    // two accumulators
-constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per wait
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16 (0), both K-major,
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
@@ -76,126 +76,6 @@ struct TcShared {
     int abort_flag;
 };
 constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
-
-// ---- PTX wrappers ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of parity `parity`; false on timeout or when another role gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_test(b, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    for (uint32_t i = 1;; ++i) {
-        if (mbar_test(b, parity)) return true;
-        if ((i & 63) == 0) {
-            if (*abort_flag) return false;
-            if (gtimer() - t0 > kTimeoutNs) return false;
-        }
-    }
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, unsigned long long *bar,
-                                            int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            su32(dst)),
-        "l"((unsigned long long)map), "r"(su32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, unsigned long long adesc, unsigned long long bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-// K-major operand tile in shared memory, rows of 128 bytes, 128-byte swizzle, 8-row groups
-// 1024 bytes apart; bits: start >> 4 [0,14), leading offset >> 4 [16,30) (unused for this
-// layout), stride offset >> 4 [32,46), descriptor version 1 [46,48), swizzle mode 2 [61,64).
-// The same for the 16-column correction slice: 32-byte rows, 32-byte swizzle (mode 6), 8-row
-// groups 256 bytes apart.
-__device__ __forceinline__ unsigned long long sw32_desc(uint32_t saddr) {
-    return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((unsigned long long)(256 >> 4) << 32) |
-           (1ull << 46) | (6ull << 61);
-}
-__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
-    return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
-           (1ull << 46) | (2ull << 61);
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-}
-// Waits for this thread's tcgen05.ld results; naming the destination registers as operands keeps
-// the compiler from reading them before the wait.
-__device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
-                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
-                   "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]),
-                   "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]),
-                   "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
-                 :
-                 : "memory");
-}
-
-
-__device__ __forceinline__ void top2(unsigned long long &b1, unsigned long long &b2, unsigned long long k) {
-    const unsigned long long lo = k < b1 ? k : b1;
-    b1 = k > b1 ? k : b1;
-    b2 = lo > b2 ? lo : b2;
-}
-__device__ __forceinline__ void top2u(uint32_t &b1, uint32_t &b2, uint32_t k) {
-    const uint32_t lo = min(k, b1);
-    b1 = max(k, b1);
-    b2 = max(b2, lo);
-}
 
 // Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
 // range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
@@ -249,15 +129,6 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 tmem_ld_wait(vb);
         }
     }
-}
-
-// Folds a half-tile key (local index in the low 4 bits) into the running 64-bit keys
-// (score bits << 32 | ~domain position).
-__device__ __forceinline__ void merge_half_key(unsigned long long &b1, unsigned long long &b2, uint32_t t, int jh) {
-    const int j = jh + 15 - (int)(t & 15u);
-    const unsigned long long k =
-        t ? (((unsigned long long)(t & 0xFFFFFFF0u) << 32) | (unsigned long long)(uint32_t)(~j)) : 0ull;
-    top2(b1, b2, k);
 }
 
 }  // namespace
@@ -349,12 +220,13 @@ __global__ void k_pack_domains(Geo g, const uint16_t *__restrict__ domS, const i
     reinterpret_cast<uint4 *>(B_mat + ((size_t)j * 8 + t) * 64)[y] = pk;
 }
 
-// One block (128 threads) per range tile of the batch: the union [lo_u, hi_u) of its rows' pool
+// One block (TM threads) per range tile of the batch: the union [lo_u, hi_u) of its rows' pool
 // windows and the intersection [lo_i, hi_i) over its valid rows; tile_win[m] = (lo_u, hi_u, lo_i,
 // hi_i); n_chunks[m] = number of 512-domain chunks of the union.
+template <int TM>
 __global__ void k_tile_windows(const int4 *__restrict__ rng_info, int4 *__restrict__ tile_win,
                                int32_t *__restrict__ n_chunks) {
-    const int m = blockIdx.x, i = m * kTileM + threadIdx.x;
+    const int m = blockIdx.x, i = m * TM + threadIdx.x;
     const int4 ri = rng_info[i];
     const bool valid = ri.w >= 0;
     int lo_u = valid ? ri.y : INT_MAX, hi_u = valid ? ri.z : INT_MIN;
@@ -366,12 +238,12 @@ __global__ void k_tile_windows(const int4 *__restrict__ rng_info, int4 *__restri
         lo_i = max(lo_i, __shfl_xor_sync(0xffffffffu, lo_i, off));
         hi_i = min(hi_i, __shfl_xor_sync(0xffffffffu, hi_i, off));
     }
-    __shared__ int4 w[4];
+    __shared__ int4 w[TM / 32];
     if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = make_int4(lo_u, hi_u, lo_i, hi_i);
     __syncthreads();
     if (threadIdx.x == 0) {
         int4 t = w[0];
-        for (int k = 1; k < 4; ++k) {
+        for (int k = 1; k < TM / 32; ++k) {
             t.x = min(t.x, w[k].x);
             t.y = max(t.y, w[k].y);
             t.z = max(t.z, w[k].z);
@@ -806,20 +678,24 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// rows x cols fp16, row-major (cols = 64: 128-byte rows, 128-byte swizzle; cols = 16: 32-byte
-// rows, 32-byte swizzle); box = box_rows x cols.
-cudaError_t make_map(CUtensorMap *map, void *base, unsigned long long rows, unsigned box_rows, unsigned cols) {
+}  // namespace
+
+cudaError_t make_map_f16(CUtensorMap *map, void *base, unsigned long long rows, unsigned cols, unsigned box_rows,
+                         unsigned box_cols) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {cols, box_rows};
+    const cuuint32_t box[2] = {box_cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+namespace {
 }  // namespace
 
 cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st) {
@@ -841,7 +717,10 @@ cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, c
 }
 
 cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st) {
-    k_tile_windows<<<tb.n_mtiles, kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
+    if (tb.tm == 2 * kTileM)
+        k_tile_windows<2 * kTileM><<<tb.n_mtiles, 2 * kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
+    else
+        k_tile_windows<kTileM><<<tb.n_mtiles, kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
     ++g_launches;
     const int target = max(1, min(target_items, kMaxItemTarget));
     k_work_list<<<1, 1024, 0, st>>>(tb.n_mtiles, target, tb.tile_win, tb.n_chunks, tb.work, tb.tile_items,
@@ -853,10 +732,10 @@ cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t s
 cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
     CUtensorMap tmA, tmB, tmA1, tmB1;
     cudaError_t e;
-    if ((e = make_map(&tmA, tb.A_mat, (unsigned long long)tb.R_pad, kTileM, 64))) return e;
-    if ((e = make_map(&tmB, tb.B_mat, (unsigned long long)tb.Dn_aux * 8, kTileN, 64))) return e;
-    if ((e = make_map(&tmA1, tb.A1_mat, (unsigned long long)tb.R_pad, kTileM, 16))) return e;
-    if ((e = make_map(&tmB1, tb.B1_mat, (unsigned long long)tb.Dn_aux * 8, kTileN, 16))) return e;
+    if ((e = make_map_f16(&tmA, tb.A_mat, (unsigned long long)tb.R_pad, 64, kTileM, 64))) return e;
+    if ((e = make_map_f16(&tmB, tb.B_mat, (unsigned long long)tb.Dn_aux * 8, 64, kTileN, 64))) return e;
+    if ((e = make_map_f16(&tmA1, tb.A1_mat, (unsigned long long)tb.R_pad, 16, kTileM, 16))) return e;
+    if ((e = make_map_f16(&tmB1, tb.B1_mat, (unsigned long long)tb.Dn_aux * 8, 16, kTileN, 16))) return e;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {

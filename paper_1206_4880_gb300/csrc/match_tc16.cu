@@ -1,0 +1,568 @@
+// Tensor-core engine for 16x16 ranges and 32x32 domains (sm_103a: TMA, tcgen05, TMEM).
+//
+// The same contraction as the B = 8 engine with n = 256 pixels per block:
+//
+//   A_mat[i][p]       = r_i[p] - a_i             (class-sorted range i, fp16, |.| <= 255)
+//   B_mat[8 j + t][p] = T_t(S_{d_j})[p] - c_j    (class-sorted domain j, isometry t, |.| <= 1020)
+//   D[i][8 j + t] = Y = sum_p A_mat[i][p] * B_mat[8 j + t][p]
+//
+// with a = round(A / 256), c = round(C / 256). The products are integers, so exactness needs every
+// partial sum below 2^24. By Cauchy-Schwarz any partial sum is at most
+// sqrt(sum (r - a)^2) sqrt(sum (S - c)^2); with the variance bound (max - min)^2 / 4 and the mean
+// rounding (|A/256 - a| <= 1/2), sum (r - a)^2 <= 256 (127.5^2 + 1/4) = 4,161,664 and
+// sum (S - c)^2 <= 256 (510^2 + 1/4) = 66,585,664, so |partial| <= 2040.02 * 8160.01
+// < 16,646,600 < 2^24 = 16,777,216: the FP32 accumulator holds Y exactly whatever the order of
+// additions. With alpha = A - 256 a and gamma = C - 256 c (both in [-128, 128]),
+// P = 256 X - A C = 256 Y - alpha gamma, and the epilogue forms P / 256 = fma(alpha, -gamma/256, Y)
+// with one rounding (the product is exact in FP32), so no correction slice is needed.
+//
+// Scores: with p = |P| / 256, the clamped least-squares gain / 2048 (Section 1's intensity map,
+// |s| <= 1) is 512 p^2 / Q for p <= Q / 1024 and p - Q / 2048 beyond; s = fma(m, m (512/Q), p - m)
+// with m = min(p, Q / 1024) covers both. Keys and certification as in the B = 8 engine, with
+// gain / 2048 in place of gain / 512.
+//
+// Kernel shape: persistent, one CTA per SM, 10 warps. A range tile is 256 class-sorted ranges,
+// two M = 128 MMA operands resident in shared memory (4 K-quarters of 64 columns each, 128-byte
+// swizzle); every B stage (one K-quarter of 16 domains x 8 isometries = 128 rows) feeds both, so a
+// streamed byte of B serves 256 ranges. TMEM holds four 128 x 128 FP32 accumulators (two range
+// tiles x double buffering). Warp 0 issues TMA loads, warp 1 the MMAs (M = 128, N = 128, K = 16,
+// 16 per accumulator), warps 2-9 drain: warp w reads TMEM lane group w & 3 of range tile
+// (w - 2) >> 2. Every wait is bounded as in the B = 8 engine.
+#include <cuda.h>
+
+#include <climits>
+#include <mutex>
+
+#include "fic_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fic {
+
+namespace {
+
+constexpr int kTm16 = 2 * kTileM;                   // 256 ranges per range tile
+constexpr int kDom16 = 16;                          // domains per accumulator tile
+constexpr int kN16 = 8 * kDom16;                    // 128 accumulator columns
+constexpr int kChunkTiles16 = kChunkDom / kDom16;   // 32 accumulator tiles per chunk
+constexpr int kStages16 = 5;
+constexpr int kQA = kTileM * 128;                   // one K-quarter of one MMA row tile: 16 KB
+constexpr int kQB = kN16 * 128;                     // one K-quarter of one domain tile: 16 KB
+constexpr int kEpi16 = 8;
+constexpr int kTc16Threads = 32 * (2 + kEpi16);
+constexpr int kTmem16 = 4 * kN16;                   // 512 columns
+constexpr uint32_t kIdesc16 = (1u << 4) | ((uint32_t)(kN16 >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+
+struct Tc16Shared {
+    uint8_t A[2][4][kQA];          // [MMA row tile][K-quarter]
+    uint8_t B[kStages16][kQB];     // ring of K-quarters
+    float4 aux[2][kChunkDom];      // per-domain constants of the current and next chunk
+    unsigned long long full_a, empty_a, full_b[kStages16], empty_b[kStages16], tfull[2], tempty[2], aux_ready[2],
+        drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+constexpr size_t kTc16Smem = sizeof(Tc16Shared) + 1024;
+static_assert(kTc16Smem <= 232448, "shared memory per CTA");
+
+// Scores of one accumulator tile for this thread's range row: 16 domains x 8 isometries.
+template <bool MASK>
+__device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float alpha, int jh, int lo_r, int hi_r,
+                                      uint32_t &t1, uint32_t &t2) {
+    uint32_t va[32], vb[32];
+    tmem_ld32(taddr, va);
+    tmem_ld_wait(va);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (c < 3) {
+            if (c & 1)
+                tmem_ld32(taddr + (c + 1) * 32, va);
+            else
+                tmem_ld32(taddr + (c + 1) * 32, vb);
+        }
+        const uint32_t *cur = (c & 1) ? vb : va;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = 4 * c + q;
+            const float4 a = auxp[l];
+            float p = 0.f;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) p = fmaxf(p, fabsf(fmaf(alpha, a.x, __uint_as_float(cur[8 * q + t]))));
+            const float mm = fminf(p, a.y);
+            const float sc = fmaf(mm, mm * a.z, p - mm);
+            uint32_t key = (__float_as_uint(sc) & 0xFFFFFFF0u) | (uint32_t)(15 - l);
+            if (MASK) {
+                const int j = jh + l;
+                key = (j >= lo_r && j < hi_r) ? key : 0u;
+            }
+            top2u(t1, t2, key);
+        }
+        if (c < 3) {
+            if (c & 1)
+                tmem_ld_wait(va);
+            else
+                tmem_ld_wait(vb);
+        }
+    }
+}
+
+}  // namespace
+
+// ---- operand packing ------------------------------------------------------------------------
+// One thread per (sorted range i, pixel row y): A_mat row i = pixels - round(A / 256);
+// rng_info[i] = (A, pool start, pool end, range id), pools in batch-wide domain positions. Rows
+// i >= R are zero with an empty window and range id -1.
+__global__ void k_pack_ranges16(Geo g, const uint8_t *__restrict__ img, const int32_t *__restrict__ range_order,
+                                const int32_t *__restrict__ rsum, const int32_t *__restrict__ win_lo,
+                                const int32_t *__restrict__ win_hi, int R_pad, int dom_off,
+                                __half *__restrict__ A_mat, int4 *__restrict__ rng_info) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gid >> 4, y = gid & 15;
+    if (i >= R_pad) return;
+    uint4 pk[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+    if (i < g.R) {
+        const int r = range_order[i];
+        const uint8_t *row = img + (size_t)((r / g.nRx) * 16 + y) * g.pitch + (r % g.nRx) * 16;
+        const int abar = (rsum[r] + 128) >> 8;  // round(A / 256)
+        uint32_t w[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const __half a = __int2half_rn((int)row[2 * h] - abar);
+            const __half b = __int2half_rn((int)row[2 * h + 1] - abar);
+            w[h] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+        }
+        pk[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        pk[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        if (y == 0) rng_info[i] = make_int4(rsum[r], win_lo[r] + dom_off, win_hi[r] + dom_off, r);
+    } else if (y == 0) {
+        rng_info[i] = make_int4(0, 0, 0, -1);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(A_mat + (size_t)i * 256 + y * 16);
+    dst[0] = pk[0];
+    dst[1] = pk[1];
+}
+
+// One thread per (sorted domain j, isometry t, row y): B_mat row 8j+t = T_t(S_{dom_order[j]}) -
+// round(C / 256); dom_aux[j] = (-gamma / 256, Q / 1024, 512 / Q or 0, 0), gamma = C - 256 round(C/256).
+// Entries j >= Dn are zero.
+__global__ void k_pack_domains16(Geo g, const uint16_t *__restrict__ domS, const int32_t *__restrict__ dom_order,
+                                 const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq, int n_pad,
+                                 __half *__restrict__ B_mat, float4 *__restrict__ dom_aux) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (int)(gid >> 7), t = (int)(gid >> 4) & 7, y = (int)gid & 15;
+    if (j >= n_pad) return;
+    uint4 pk[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+    if (j < g.Dn) {
+        const int d = dom_order[j];
+        const uint16_t *S = domS + (size_t)d * 256;
+        const int cbar = (dsum[d] + 128) >> 8;  // round(C / 256)
+        uint32_t w[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            int sy, sx;
+            iso_src(16, t, y, 2 * h, sy, sx);
+            const __half a = __int2half_rn((int)S[sy * 16 + sx] - cbar);
+            iso_src(16, t, y, 2 * h + 1, sy, sx);
+            const __half b = __int2half_rn((int)S[sy * 16 + sx] - cbar);
+            w[h] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+        }
+        pk[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        pk[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        if (t == 0 && y == 0) {
+            const long long C = dsum[d];
+            const long long Q = 256LL * dsumsq[d] - C * C;
+            const int gamma = (int)C - 256 * cbar;
+            dom_aux[j] = make_float4(-(float)gamma * (1.0f / 256.0f), (float)Q * (1.0f / 1024.0f),
+                                     Q > 0 ? 512.0f / (float)Q : 0.f, 0.f);
+        }
+    } else if (t == 0 && y == 0) {
+        dom_aux[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(B_mat + ((size_t)j * 8 + t) * 256 + y * 16);
+    dst[0] = pk[0];
+    dst[1] = pk[1];
+}
+
+// ---- the matching kernel ----------------------------------------------------------------------
+__global__ void __launch_bounds__(kTc16Threads, 1)
+    k_match_tc16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const int4 *__restrict__ work, const int32_t *__restrict__ counters_in,
+                 const int4 *__restrict__ tile_win, const int4 *__restrict__ rng_info,
+                 const float4 *__restrict__ dom_aux, unsigned long long *__restrict__ cand,
+                 uint32_t *__restrict__ chunk_max, int32_t *err) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
+    Tc16Shared &sh = *reinterpret_cast<Tc16Shared *>(smem_raw + pad);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_items = counters_in[1];
+    volatile int *abort_flag = &sh.abort_flag;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.full_a, 1);
+        mbar_init(&sh.empty_a, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&sh.tfull[s], 1);
+            mbar_init(&sh.tempty[s], kEpi16);
+            mbar_init(&sh.aux_ready[s], 32 * kEpi16);
+        }
+        for (int s = 0; s < kStages16; ++s) {
+            mbar_init(&sh.full_b[s], 1);
+            mbar_init(&sh.empty_b[s], 1);
+        }
+        mbar_init(&sh.drain, 1);
+        sh.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(&sh.tmem_base, kTmem16);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
+            uint32_t gs = 0, li = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+                const int4 w = work[it];
+                ok = mbar_wait(&sh.empty_a, (li & 1) ^ 1, abort_flag);
+                if (!ok) break;
+                mbar_expect_tx(&sh.full_a, 8 * kQA);
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_2d(sh.A[m][q], &tmA, &sh.full_a, 64 * q, w.x * kTm16 + m * kTileM);
+                const int nt = (w.z - w.y + kDom16 - 1) / kDom16;
+                for (int k = 0; k < nt && ok; ++k) {
+                    for (int q = 0; q < 4; ++q, ++gs) {
+                        const int s = gs % kStages16;
+                        ok = mbar_wait(&sh.empty_b[s], ((gs / kStages16) & 1) ^ 1, abort_flag);
+                        if (!ok) break;
+                        mbar_expect_tx(&sh.full_b[s], kQB);
+                        tma_load_2d(sh.B[s], &tmB, &sh.full_b[s], 64 * q, 8 * (w.y + k * kDom16));
+                    }
+                }
+            }
+            if (!ok) {
+                atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
+                *abort_flag = 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            uint32_t gs = 0, gt = 0, li = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+                const int4 w = work[it];
+                ok = mbar_wait(&sh.full_a, li & 1, abort_flag);
+                if (!ok) break;
+                tc_fence_after();
+                const int nt = (w.z - w.y + kDom16 - 1) / kDom16;
+                for (int k = 0; k < nt && ok; ++k, ++gt) {
+                    const int acc = gt & 1;
+                    ok = mbar_wait(&sh.tempty[acc], ((gt >> 1) & 1) ^ 1, abort_flag);
+                    if (!ok) break;
+                    tc_fence_after();
+                    for (int q = 0; q < 4; ++q, ++gs) {
+                        const int s = gs % kStages16;
+                        ok = mbar_wait(&sh.full_b[s], (gs / kStages16) & 1, abort_flag);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t b0 = su32(sh.B[s]);
+#pragma unroll
+                        for (int m = 0; m < 2; ++m) {
+                            const uint32_t a0 = su32(sh.A[m][q]);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                umma_f16(tmem + (uint32_t)((2 * acc + m) * kN16), sw128_desc(a0 + kk * 32),
+                                         sw128_desc(b0 + kk * 32), kIdesc16, (q | kk) ? 1u : 0u);
+                        }
+                        umma_commit(&sh.empty_b[s]);
+                    }
+                    if (!ok) break;
+                    umma_commit(&sh.tfull[acc]);
+                }
+                if (!ok) break;
+                umma_commit(&sh.empty_a);
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            umma_commit(&sh.drain);
+            if (!mbar_wait(&sh.drain, 0, abort_flag) && !*abort_flag) ok = false;
+            if (!ok) {
+                atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
+                *abort_flag = 1;
+            }
+        }
+    } else {
+        // ---- epilogue: warps 2..9; warp w reads TMEM lane group (w & 3) of MMA row tile
+        // (w - 2) >> 2, i.e. range rows m * 128 + lane group * 32 + lane of the range tile
+        const int ew = warp - 2;
+        const int lg = warp & 3;
+        const int m = ew >> 2;
+        const int row = m * kTileM + lg * 32 + lane;
+        const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(m * kN16);
+        uint32_t gt = 0, lc = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const int4 w = work[it];
+            const int nt = (w.z - w.y + kDom16 - 1) / kDom16;
+            const int i = w.x * kTm16 + row;
+            const int4 ri = rng_info[i];
+            const bool valid = ri.w >= 0;
+            const float alpha = (float)(ri.x - 256 * ((ri.x + 128) >> 8));
+            const int lo_r = ri.y, hi_r = min(ri.z, w.z);
+            const int4 tw = tile_win[w.x];
+            const int f_lo = max(tw.z, w.y), f_hi = min(tw.w, w.z);  // columns valid for every row
+            unsigned long long b1 = 0, b2 = 0;
+            for (int k0 = 0; k0 < nt && ok; k0 += kChunkTiles16, ++lc) {
+                const int ntc = min(kChunkTiles16, nt - k0);
+                const int jc = w.y + k0 * kDom16;
+                const int ab = lc & 1;
+                for (int k = ew * 32 + lane; k < ntc * kDom16; k += 32 * kEpi16) sh.aux[ab][k] = __ldg(&dom_aux[jc + k]);
+                mbar_arrive(&sh.aux_ready[ab]);
+                ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (lc >> 1) & 1, abort_flag));
+                if (!ok) break;
+                uint32_t cmax = 0;
+                for (int k = 0; k < ntc; ++k, ++gt) {
+                    const int acc = gt & 1;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sh.tfull[acc], (gt >> 1) & 1, abort_flag));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const int jh = jc + k * kDom16;
+                    const float4 *auxp = &sh.aux[ab][k * kDom16];
+                    const uint32_t taddr = tbase + (uint32_t)(acc * 2 * kN16);
+                    uint32_t t1 = 0, t2 = 0;
+                    if (jh >= f_lo && jh + kDom16 <= f_hi)
+                        epi16<false>(taddr, auxp, alpha, jh, lo_r, hi_r, t1, t2);
+                    else
+                        epi16<true>(taddr, auxp, alpha, jh, lo_r, hi_r, t1, t2);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.tempty[acc]);
+                    merge_half_key(b1, b2, t1, jh);
+                    merge_half_key(b1, b2, t2, jh);
+                    cmax = max(cmax, t1);
+                }
+                if (ok && valid) chunk_max[(size_t)(w.w + k0 / kChunkTiles16) * kTm16 + row] = cmax & 0xFFFFFFF0u;
+            }
+            if (ok && valid) {
+                unsigned long long *dst = cand + ((size_t)it * kTm16 + row) * 2;
+                dst[0] = b1;
+                dst[1] = b2;
+            }
+        }
+        if (!ok) {
+            atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
+            *abort_flag = 1;
+        }
+    }
+
+    // ---- teardown: copies in flight complete (bounded), then TMEM is freed
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        const unsigned long long t0 = gtimer();
+        while (gtimer() - t0 < 5000000ull) {
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmem16);
+    }
+}
+
+// ---- exact re-evaluation and certification ----------------------------------------------------
+// One warp per class-sorted range position i of one image, as the B = 8 re-evaluation: the two
+// best keys over the tile's work items are evaluated exactly under all 8 isometries (lane
+// (candidate, t, half) sums X over 8 of the 16 rows), the best is certified if the runner-up's
+// score * (1 + 2^-16) + 2^-8 < exact best gain / 2048 (the key truncation, the score formula and
+// the accumulator's single rounding err by less than 2^-17 relatively, the latter also by less
+// than 2^-16 absolutely), else the range is queued for the exact re-search.
+__global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
+                           const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
+                           const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
+                           const int32_t *__restrict__ bin_off, int nbuckets, const int4 *__restrict__ rng_info,
+                           int rng_off, int dom_off, const int4 *__restrict__ tile_items,
+                           const unsigned long long *__restrict__ cand, const int32_t *__restrict__ gcounters,
+                           int32_t *__restrict__ fallback, FallbackBest *__restrict__ fb_best, int32_t *counters,
+                           fic_codes out) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= g.R) return;
+    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+    const int4 ri = rng_info[i];
+    const int r = ri.w;
+    const long long A = ri.x, Bs = rsumsq[r];
+    const int ry = (r / g.nRx) * 16, rx = (r % g.nRx) * 16;
+
+    if (256LL * Bs - A * A == 0) {  // flat range: every candidate has P = 0
+        int dmin = INT_MAX;
+        const int wlo = ri.y - dom_off, whi = ri.z - dom_off;
+        for (int bb = lane; bb < nbuckets; bb += 32)
+            if (bin_off[bb] < bin_off[bb + 1] && bin_off[bb] >= wlo && bin_off[bb] < whi)
+                dmin = min(dmin, dom_order[bin_off[bb]]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
+        if (lane == 0) {
+            const long long C = dsum[dmin];
+            const long long Q = 256LL * dsumsq[dmin] - C * C;
+            double s, o, sse;
+            finalize_code(256, A, Bs, C, 0, Q, exact_gain_w(0, Q), s, o, sse);
+            out.dom[r] = dmin;
+            out.iso[r] = 0;
+            out.s[r] = s;
+            out.o[r] = o;
+            out.sse[r] = sse;
+        }
+        return;
+    }
+
+    const int ig = rng_off + i;
+    const int row = ig % kTm16;
+    const int4 ti = tile_items[ig / kTm16];
+    unsigned long long b1 = 0, b2 = 0;
+    for (int e = lane; e < 2 * ti.y; e += 32) top2(b1, b2, cand[((size_t)(ti.x + (e >> 1)) * kTm16 + row) * 2 + (e & 1)]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, off);
+        const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, b2, off);
+        top2(b1, b2, o1);
+        top2(b1, b2, o2);
+    }
+    const int cidx = lane >> 4, t = (lane >> 1) & 7, hrow = (lane & 1) * 8;
+    const unsigned long long key = cidx == 0 ? b1 : b2;
+    const int jl = (int)(~(uint32_t)(key & 0xffffffffu)) - dom_off;
+    const bool has = key != 0 && jl >= 0 && jl < g.Dn;
+    GainW gg{-1, 1};
+    int d = INT_MAX;
+    long long P = 0, Q = 0, C = 0;
+    int X = 0;
+    if (has) {
+        d = dom_order[jl];
+        const uint16_t *S = domS + (size_t)d * 256;
+        for (int y = hrow; y < hrow + 8; ++y) {
+            const uint8_t *prow = img + (size_t)(ry + y) * g.pitch + rx;
+#pragma unroll
+            for (int x = 0; x < 16; ++x) {
+                int sy, sx;
+                iso_src(16, t, y, x, sy, sx);
+                X += (int)prow[x] * (int)S[sy * 16 + sx];
+            }
+        }
+    }
+    X += __shfl_xor_sync(0xffffffffu, X, 1);
+    if (has) {
+        C = dsum[d];
+        Q = 256LL * dsumsq[d] - C * C;
+        P = 256LL * (long long)X - A * C;
+        gg = exact_gain_w(P, Q);
+    }
+    int bt = t;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        GainW og;
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)gg.num, off);
+        const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(gg.num >> 64), off);
+        og.num = (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned __int128)lo);
+        og.den = __shfl_xor_sync(0xffffffffu, gg.den, off);
+        const int od = __shfl_xor_sync(0xffffffffu, d, off), ot = __shfl_xor_sync(0xffffffffu, bt, off);
+        const long long oP = __shfl_xor_sync(0xffffffffu, P, off), oQ = __shfl_xor_sync(0xffffffffu, Q, off);
+        const long long oC = __shfl_xor_sync(0xffffffffu, C, off);
+        if (cand_better(og, od, ot, gg, d, bt)) {
+            gg = og;
+            d = od;
+            bt = ot;
+            P = oP;
+            Q = oQ;
+            C = oC;
+        }
+    }
+    if (lane != 0) return;
+    bool certified = b1 != 0 && gg.num >= 0;
+    if (certified && b2 != 0) {
+        const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
+        const double sc = i128_to_double_rn(gg.num) / (2048.0 * (double)gg.den);
+        certified = u2 * (1.0 + 1.0 / 65536.0) + 1.0 / 256.0 < sc;
+    }
+    if (!certified) {
+        const int slot = atomicAdd(&counters[0], 1);
+        fallback[slot] = i;
+        FallbackBest fb;
+        fb.num = gg.num;
+        fb.den = gg.den;
+        fb.P = P;
+        fb.Q = Q;
+        fb.d = d;
+        fb.t = bt;
+        fb.C = (int)C;
+        fb.pad = 0;
+        fb_best[slot] = fb;
+        return;
+    }
+    double s, o, sse;
+    finalize_code(256, A, Bs, C, P, Q, gg, s, o, sse);
+    out.dom[r] = d;
+    out.iso[r] = bt;
+    out.s[r] = s;
+    out.o[r] = o;
+    out.sse[r] = sse;
+}
+
+// ---- host side -------------------------------------------------------------------------------
+cudaError_t launch_pack16(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st) {
+    {
+        const long long n = (long long)b.R_pad * 16;
+        k_pack_ranges16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, img, b.range_order, b.range_sum, b.win_lo,
+                                                                    b.win_hi, b.R_pad, b.dom_off, b.A_mat,
+                                                                    b.rng_info);
+        ++g_launches;
+    }
+    {
+        const long long n = (long long)b.Dn_aux * 128;
+        k_pack_domains16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, b.dom_S, b.dom_order, b.dom_sum,
+                                                                     b.dom_sumsq, b.Dn_aux, b.B_mat, b.dom_aux);
+        ++g_launches;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st) {
+    CUtensorMap tmA, tmB;
+    cudaError_t e;
+    if ((e = make_map_f16(&tmA, tb.A_mat, (unsigned long long)tb.R_pad, 256, kTileM, 64))) return e;
+    if ((e = make_map_f16(&tmB, tb.B_mat, (unsigned long long)tb.Dn_aux * 8, 256, kN16, 64))) return e;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(k_match_tc16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc16Smem);
+    });
+    if (attr_err) return attr_err;
+    const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
+    if (grid <= 0) return cudaSuccess;
+    k_match_tc16<<<grid, kTc16Threads, kTc16Smem, st>>>(tmA, tmB, tb.work, tb.gcounters, tb.tile_win, tb.rng_info,
+                                                         tb.dom_aux, tb.cand, tb.chunk_max, tb.gcounters + 2);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reeval16(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
+                            const fic_codes &out, cudaStream_t st) {
+    const long long threads = (long long)g.R * 32;
+    k_reeval16<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+        g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, sort_buckets(g), b.rng_info,
+        b.rng_off, b.dom_off, tb.tile_items, tb.cand, tb.gcounters, b.fallback, b.fb_best, b.counters, out);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace fic

@@ -149,6 +149,11 @@ def _require_cuda(t: torch.Tensor, name: str):
         raise ValueError(f"{name} must be a CUDA tensor")
 
 
+def n_scales(block: int) -> int:
+    """Box-count scales per block: s = 2, 4 for 8x8 blocks; s = 2, 4, 8 for 16x16 blocks."""
+    return 3 if block == 16 else 2
+
+
 def counts(H: int, W: int, p: EncodeParams) -> tuple[int, int]:
     B = p.block
     R = (H // B) * (W // B)
@@ -252,12 +257,12 @@ def classify(img: torch.Tensor, p: EncodeParams, workspace=None, stream=None) ->
     i32, f64, u8 = torch.int32, torch.float64, torch.uint8
     st = {"range_sum": torch.empty(R, dtype=i32, device=dev),
           "range_sumsq": torch.empty(R, dtype=i32, device=dev),
-          "range_counts": torch.empty(R, 2, dtype=i32, device=dev),
+          "range_counts": torch.empty(R, n_scales(p.block), dtype=i32, device=dev),
           "range_fd": torch.empty(R, dtype=f64, device=dev),
           "range_bin": torch.empty(R, dtype=u8, device=dev),
           "dom_sum": torch.empty(Dn, dtype=i32, device=dev),
           "dom_sumsq": torch.empty(Dn, dtype=i32, device=dev),
-          "dom_counts": torch.empty(Dn, 2, dtype=i32, device=dev),
+          "dom_counts": torch.empty(Dn, n_scales(p.block), dtype=i32, device=dev),
           "dom_fd": torch.empty(Dn, dtype=f64, device=dev),
           "dom_bin": torch.empty(Dn, dtype=u8, device=dev),
           "fd_extent": torch.empty(2, dtype=f64, device=dev)}

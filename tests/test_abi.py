@@ -44,9 +44,14 @@ def test_workspace_size_and_validation():
     assert _ws_size(256, 256, domain_stride=8, num_classes=8) > 0
     assert _ws_size(1024, 1024, domain_stride=4, num_classes=16) > _ws_size(256, 256)
     for kw in ({"domain_stride": 0}, {"num_classes": 0}, {"num_classes": 256},
-               {"block": 16}, {"s_max": 0.5}, {"half_width": -2}):
+               {"block": 12}, {"s_max": 0.5}, {"half_width": -2},
+               {"block": 16, "literal": True}):
         assert _ws_size(64, 64, **kw) == 0, kw
     assert _ws_size(12, 64) == 0 and _ws_size(64, 60) == 0 and _ws_size(8, 64) == 0
+    # 16x16 ranges: sides multiples of 16 and at least 32
+    assert _ws_size(64, 64, block=16) > 0
+    assert _ws_size(24, 64, block=16) == 0 and _ws_size(64, 48, block=16) > 0 and _ws_size(16, 64, block=16) == 0
+    assert _ws_size(1024, 1024, block=16) > _ws_size(512, 512, block=16)
 
 
 def test_encode_rejects_before_any_launch():
