@@ -41,6 +41,12 @@ WORKLOADS = {
     "encode-4096": dict(H=4096, W=4096, sigma=8, K=32, w=-1, seed=5000, block=8,
                         desc="4096x4096 8-bit seeded fBm+edges image; 262144 8x8 ranges; 16x16 "
                              "domains at stride 8 (261121) x 8 isometries; K=32 LFD classes, w=10"),
+    "encode-2048-s4": dict(H=2048, W=2048, sigma=4, K=32, w=-1, seed=2100, block=8,
+                           desc="2048x2048 8-bit seeded fBm+edges image; 65536 8x8 ranges; 16x16 "
+                                "domains at stride 4 (259081) x 8 isometries; K=32 LFD classes, w=10"),
+    "encode-2048-s4-b16": dict(H=2048, W=2048, sigma=4, K=32, w=-1, seed=2100, block=16,
+                               desc="2048x2048 8-bit seeded fBm+edges image; 16384 16x16 ranges; 32x32 "
+                                    "domains at stride 4 (255025) x 8 isometries; K=32 LFD classes, w=10"),
     "encode-4096-b16": dict(H=4096, W=4096, sigma=8, K=32, w=-1, seed=5000, block=16,
                             desc="4096x4096 8-bit seeded fBm+edges image; 65536 16x16 ranges; 32x32 "
                                  "domains at stride 8 (259081) x 8 isometries; K=32 LFD classes, w=10"),

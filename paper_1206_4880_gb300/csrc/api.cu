@@ -124,7 +124,8 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->Dn_pad = (g.Dn + kTileDom - 1) / kTileDom * kTileDom;
         b->Dn_aux = b->Dn_pad + kTileDom;  // a tile may start at any position < Dn
         b->n_mtiles = b->R_pad / TM;
-        b->max_chunks = (g.Dn + kChunkDom - 1) / kChunkDom;
+        // chunks of the absolute grid a tile's window (within this image's Dn domains) can meet
+        b->max_chunks = (g.Dn + kChunkDom - 1) / kChunkDom + 1;
         b->sort_blocks_dom = (g.Dn + kSortChunk - 1) / kSortChunk;
         b->sort_blocks_rng = (g.R + kSortChunk - 1) / kSortChunk;
         b->rng_off = (int)R_pad_tot;
@@ -169,8 +170,14 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
     tb->R_pad = (int)R_pad_tot;
     tb->Dn_aux = (int)Dn_aux_tot;
     tb->n_mtiles = (int)mt_tot;
-    tb->max_items = (int)mt_tot + kMaxItemTarget;
+    // cpi_cap chunks per domain group: about 32 MB of B rows (512 KB per chunk for B = 8, 2 MB
+    // for B = 16). A tile meets at most chunks / cpi + 2 groups, and cpi >= min(cap, total /
+    // target), so items <= 2 tiles + max(target, chunks / cap).
+    tb->cpi_cap = B == 16 ? 16 : 64;
+    tb->max_items = (int)(2 * mt_tot + (chunks_tot / tb->cpi_cap + 1 > kMaxItemTarget ? chunks_tot / tb->cpi_cap + 1
+                                                                                        : kMaxItemTarget));
     tb->max_chunks = (int)chunks_tot;
+    tb->ng_max = (int)(Dn_aux_tot / kChunkDom + 2);
     const size_t slice = B == 8 ? 16 : 0;  // correction slice columns (B = 16 corrects in the epilogue)
     tb->A_mat = c.take<__half>((size_t)R_pad_tot * npx, 1024);
     tb->B_mat = c.take<__half>((size_t)8 * Dn_aux_tot * npx, 1024);
@@ -182,6 +189,8 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
     tb->n_chunks = c.take<int32_t>((size_t)mt_tot);
     tb->tile_items = c.take<int4>((size_t)mt_tot);
     tb->work = c.take<int4>((size_t)tb->max_items);
+    tb->work_slot = c.take<int32_t>((size_t)tb->max_items);
+    tb->grp = c.take<int32_t>((size_t)tb->ng_max);
     tb->cand = c.take<unsigned long long>((size_t)tb->max_items * TM * H * 2);
     tb->chunk_max = c.take<uint32_t>((size_t)chunks_tot * TM * H);
     tb->gcounters = c.take<int32_t>(8);

@@ -260,13 +260,16 @@ struct TcBatch {
     float4 *dom_aux;
     int4 *rng_info;
     int4 *tile_win;        // [n_mtiles] union (x, y) and intersection (z, w) of row windows
-    int32_t *n_chunks;     // [n_mtiles] 512-domain chunks per range tile
-    int4 *tile_items;      // [n_mtiles] first work item, items, first chunk, chunks
-    int4 *work;            // [max_items] (range tile, first domain, end domain, first chunk)
-    unsigned long long *cand;  // [max_items][tm rows][halves][2] top-2 keys
+    int32_t *n_chunks;     // [n_mtiles] 512-domain chunks (absolute grid) the union window meets
+    int4 *tile_items;      // [n_mtiles] first key slot, items, first chunk, chunks
+    int4 *work;            // [max_items] (range tile, first domain, end domain, first chunk),
+                           // in schedule order (by domain group)
+    int32_t *work_slot;    // [max_items] key slot of each scheduled item
+    int32_t *grp;          // [ng_max] per domain group: item count, then schedule cursor
+    unsigned long long *cand;  // [max_items][tm rows][halves][2] top-2 keys, by key slot
     uint32_t *chunk_max;   // [max_chunks][tm rows][halves] best key per chunk
-    int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks
-    int R_pad, Dn_aux, n_mtiles, max_items, max_chunks;
+    int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks, [4] chunks per group
+    int R_pad, Dn_aux, n_mtiles, max_items, max_chunks, ng_max, cpi_cap;
 };
 
 constexpr int kSortChunk = 2048;  // elements per counting-sort block

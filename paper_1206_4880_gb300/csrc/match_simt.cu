@@ -234,10 +234,11 @@ __global__ void __launch_bounds__(kSimtThreads)
             }
             __syncthreads();
             const int nf = sh.n_flagged;
+            const int c_lo = tw.x / kChunkDom;  // the tile's first chunk of the absolute grid
             for (int f = 0; f < nf; ++f) {
-                const int cc = sh.flagged[f];
-                const int j0 = max(ri.y, tw.x + cc * kChunkDom);
-                const int j1 = min(ri.z, min(tw.x + (cc + 1) * kChunkDom, tw.y));
+                const int cc = sh.flagged[f] + c_lo;
+                const int j0 = max(ri.y, cc * kChunkDom);
+                const int j1 = min(ri.z, (cc + 1) * kChunkDom);
                 for (int j = j0 + threadIdx.x; j < j1; j += kSimtThreads)
                     scan_domain<B>(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
             }

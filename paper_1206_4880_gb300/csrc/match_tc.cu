@@ -222,7 +222,8 @@ __global__ void k_pack_domains(Geo g, const uint16_t *__restrict__ domS, const i
 
 // One block (TM threads) per range tile of the batch: the union [lo_u, hi_u) of its rows' pool
 // windows and the intersection [lo_i, hi_i) over its valid rows; tile_win[m] = (lo_u, hi_u, lo_i,
-// hi_i); n_chunks[m] = number of 512-domain chunks of the union.
+// hi_i); n_chunks[m] = number of chunks of the absolute grid (batch-wide domain positions
+// [512 c, 512 (c + 1))) the union meets.
 template <int TM>
 __global__ void k_tile_windows(const int4 *__restrict__ rng_info, int4 *__restrict__ tile_win,
                                int32_t *__restrict__ n_chunks) {
@@ -250,7 +251,7 @@ __global__ void k_tile_windows(const int4 *__restrict__ rng_info, int4 *__restri
             t.w = min(t.w, w[k].w);
         }
         tile_win[m] = t;
-        n_chunks[m] = t.y > t.x ? (t.y - t.x + kChunkDom - 1) / kChunkDom : 0;
+        n_chunks[m] = t.y > t.x ? (t.y - 1) / kChunkDom - t.x / kChunkDom + 1 : 0;
     }
 }
 
@@ -271,13 +272,24 @@ __device__ __forceinline__ int block_scan_1024(int v, int *sc, int *total) {
     return incl - v;
 }
 
-// One block of 1024 threads. Every range tile's chunks are split into work items of `cpi`
-// consecutive chunks, cpi chosen so that the batch has about `target` items; items are written
-// tile-major as (tile, first domain, end domain, first chunk id), tile_items[m] = (first item,
-// items, first chunk id, chunks); gcounters[1] = items, gcounters[3] = chunks.
-__global__ void k_work_list(int n_mtiles, int target, const int4 *__restrict__ tile_win,
-                            const int32_t *__restrict__ n_chunks, int4 *__restrict__ work,
-                            int4 *__restrict__ tile_items, int32_t *gcounters) {
+// One block of 1024 threads: the work list and its schedule. Chunks of the absolute grid are
+// grouped cpi at a time (domain group G = positions [512 cpi G, 512 cpi (G + 1))), cpi chosen so
+// the batch has about `target` items but at most cpi_cap (so one group's B rows stay L2-resident
+// while every range tile meeting the group streams them). A work item is (range tile m, group G):
+// the part of m's union window inside G, its first domain rounded down to the accumulator tile
+// width td (the extra columns lie below every row's window and are masked). tile_items[m] =
+// (first key slot, items, first chunk id, chunks): m's items own consecutive key slots in group
+// order and its chunks consecutive chunk ids. The schedule (work, work_slot) is group-major, so
+// the SMs working at the same time read the same B rows; within a group the order is that of
+// the atomic cursor (results do not depend on it: every item writes its own key slot and chunk
+// entries). gcounters[1] = items, [3] = chunks, [4] = cpi.
+__device__ __forceinline__ int tile_chunk_lo(int4 t) { return t.x / kChunkDom; }
+__device__ __forceinline__ int tile_chunk_hi(int4 t) { return (t.y - 1) / kChunkDom + 1; }  // exclusive
+
+__global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int ng_max,
+                            const int4 *__restrict__ tile_win, const int32_t *__restrict__ n_chunks,
+                            int4 *__restrict__ work, int32_t *__restrict__ work_slot,
+                            int4 *__restrict__ tile_items, int32_t *__restrict__ grp, int32_t *gcounters) {
     __shared__ int sc[1024];
     __shared__ int total_chunks_s;
     int tot = 0;
@@ -287,29 +299,61 @@ __global__ void k_work_list(int n_mtiles, int target, const int4 *__restrict__ t
     if (threadIdx.x == 0) total_chunks_s = all;
     __syncthreads();
     const int total = total_chunks_s;
-    const int cpi = max(1, (total + target - 1) / max(1, target));
+    const int cpi = max(1, min(cpi_cap, (total + target - 1) / max(1, target)));
+    const int gdom = cpi * kChunkDom;  // domains per group
+    for (int G = threadIdx.x; G < ng_max; G += 1024) grp[G] = 0;
+    __syncthreads();
+    // key slots and chunk ids per tile (tile-major); group counts
     int item_base = 0, chunk_base = 0;
     for (int m0 = 0; m0 < n_mtiles; m0 += 1024) {
         const int m = m0 + threadIdx.x;
         const int c = m < n_mtiles ? n_chunks[m] : 0;
-        const int q = (c + cpi - 1) / cpi;
+        int q = 0, glo = 0;
+        if (c > 0) {
+            const int4 t = tile_win[m];
+            glo = tile_chunk_lo(t) / cpi;
+            q = (tile_chunk_hi(t) - 1) / cpi - glo + 1;
+        }
         int q_all = 0, c_all = 0;
         const int q_off = item_base + block_scan_1024(q, sc, &q_all);
         const int c_off = chunk_base + block_scan_1024(c, sc, &c_all);
         if (m < n_mtiles) {
-            const int4 t = tile_win[m];
-            for (int k = 0; k < q; ++k) {
-                const int c0 = k * cpi, c1 = min(c0 + cpi, c);
-                work[q_off + k] = make_int4(m, t.x + c0 * kChunkDom, min(t.x + c1 * kChunkDom, t.y), c_off + c0);
-            }
             tile_items[m] = make_int4(q_off, q, c_off, c);
+            for (int k = 0; k < q; ++k) atomicAdd(&grp[glo + k], 1);
         }
         item_base += q_all;
         chunk_base += c_all;
     }
+    __syncthreads();
+    // exclusive scan of the group counts: grp[G] becomes group G's schedule cursor
+    int carry = 0;
+    for (int g0 = 0; g0 < ng_max; g0 += 1024) {
+        const int G = g0 + threadIdx.x;
+        const int v = G < ng_max ? grp[G] : 0;
+        int g_all = 0;
+        const int off = carry + block_scan_1024(v, sc, &g_all);
+        if (G < ng_max) grp[G] = off;
+        carry += g_all;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < n_mtiles; m += 1024) {
+        const int4 ti = tile_items[m];
+        if (ti.y == 0) continue;
+        const int4 t = tile_win[m];
+        const int c_lo = tile_chunk_lo(t), glo = c_lo / cpi;
+        for (int k = 0; k < ti.y; ++k) {
+            const int G = glo + k;
+            const int d0 = max(t.x, G * gdom) / td * td;
+            const int d1 = min(t.y, (G + 1) * gdom);
+            const int pos = atomicAdd(&grp[G], 1);
+            work[pos] = make_int4(m, d0, d1, ti.z + d0 / kChunkDom - c_lo);
+            work_slot[pos] = ti.x + k;
+        }
+    }
     if (threadIdx.x == 0) {
         gcounters[1] = item_base;
         gcounters[3] = chunk_base;
+        gcounters[4] = cpi;
     }
 }
 
@@ -317,10 +361,10 @@ __global__ void k_work_list(int n_mtiles, int target, const int4 *__restrict__ t
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
-               const int4 *__restrict__ work, const int32_t *__restrict__ counters_in,
-               const int4 *__restrict__ tile_win, const int4 *__restrict__ rng_info,
-               const float4 *__restrict__ dom_aux, unsigned long long *__restrict__ cand,
-               uint32_t *__restrict__ chunk_max, int32_t *err) {
+               const int4 *__restrict__ work, const int32_t *__restrict__ work_slot,
+               const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
+               const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
+               unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *err) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
     TcShared &sh = *reinterpret_cast<TcShared *>(smem_raw + pad);
@@ -445,9 +489,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int4 tw = tile_win[w.x];
             const int f_lo = max(tw.z, w.y), f_hi = min(tw.w, w.z);  // columns valid for every row
             unsigned long long b1 = 0, b2 = 0;
-            for (int k0 = 0; k0 < nt && ok; k0 += kChunkTiles, ++lc) {
-                const int ntc = min(kChunkTiles, nt - k0);
+            // accumulator tiles grouped by chunk of the absolute grid (the first chunk of an item
+            // may be partial: items start where the tile's window or the domain group starts)
+            for (int k0 = 0, ntc = 0; k0 < nt && ok; k0 += ntc, ++lc) {
                 const int jc = w.y + k0 * kTileDom;
+                const int cabs = jc / kChunkDom;
+                ntc = min(nt - k0, ((cabs + 1) * kChunkDom - jc) / kTileDom);
                 // per-domain constants of this chunk into shared memory (double-buffered by chunk
                 // parity; a thread reaches chunk lc + 2 only after every thread has left chunk lc)
                 const int ab = lc & 1;
@@ -478,10 +525,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     cmax = max(cmax, t1);
                 }
                 if (ok && valid)
-                    chunk_max[((size_t)(w.w + k0 / kChunkTiles) * kTileM + row) * 2 + half] = cmax & 0xFFFFFFF0u;
+                    chunk_max[((size_t)(w.w + cabs - w.y / kChunkDom) * kTileM + row) * 2 + half] =
+                        cmax & 0xFFFFFFF0u;
             }
             if (ok && valid) {
-                unsigned long long *dst = cand + (((size_t)it * kTileM + row) * 2 + half) * 2;
+                unsigned long long *dst = cand + (((size_t)work_slot[it] * kTileM + row) * 2 + half) * 2;
                 dst[0] = b1;
                 dst[1] = b2;
             }
@@ -723,7 +771,8 @@ cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t s
         k_tile_windows<kTileM><<<tb.n_mtiles, kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
     ++g_launches;
     const int target = max(1, min(target_items, kMaxItemTarget));
-    k_work_list<<<1, 1024, 0, st>>>(tb.n_mtiles, target, tb.tile_win, tb.n_chunks, tb.work, tb.tile_items,
+    k_work_list<<<1, 1024, 0, st>>>(tb.n_mtiles, target, tb.cpi_cap, tb.B == 16 ? 16 : kTileDom, tb.ng_max,
+                                    tb.tile_win, tb.n_chunks, tb.work, tb.work_slot, tb.tile_items, tb.grp,
                                     tb.gcounters);
     ++g_launches;
     return cudaGetLastError();
@@ -744,8 +793,9 @@ cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
     if (attr_err) return attr_err;
     const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
     if (grid <= 0) return cudaSuccess;
-    k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.gcounters, tb.tile_win,
-                                                   tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max, tb.gcounters + 2);
+    k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.work_slot, tb.gcounters,
+                                                   tb.tile_win, tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
+                                                   tb.gcounters + 2);
     ++g_launches;
     return cudaGetLastError();
 }

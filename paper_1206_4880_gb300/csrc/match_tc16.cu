@@ -43,7 +43,6 @@ namespace {
 constexpr int kTm16 = 2 * kTileM;                   // 256 ranges per range tile
 constexpr int kDom16 = 16;                          // domains per accumulator tile
 constexpr int kN16 = 8 * kDom16;                    // 128 accumulator columns
-constexpr int kChunkTiles16 = kChunkDom / kDom16;   // 32 accumulator tiles per chunk
 constexpr int kStages16 = 5;
 constexpr int kQA = kTileM * 128;                   // one K-quarter of one MMA row tile: 16 KB
 constexpr int kQB = kN16 * 128;                     // one K-quarter of one domain tile: 16 KB
@@ -185,10 +184,10 @@ __global__ void k_pack_domains16(Geo g, const uint16_t *__restrict__ domS, const
 // ---- the matching kernel ----------------------------------------------------------------------
 __global__ void __launch_bounds__(kTc16Threads, 1)
     k_match_tc16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const int4 *__restrict__ work, const int32_t *__restrict__ counters_in,
-                 const int4 *__restrict__ tile_win, const int4 *__restrict__ rng_info,
-                 const float4 *__restrict__ dom_aux, unsigned long long *__restrict__ cand,
-                 uint32_t *__restrict__ chunk_max, int32_t *err) {
+                 const int4 *__restrict__ work, const int32_t *__restrict__ work_slot,
+                 const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
+                 const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
+                 unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *err) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
     Tc16Shared &sh = *reinterpret_cast<Tc16Shared *>(smem_raw + pad);
@@ -322,9 +321,10 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
             const int4 tw = tile_win[w.x];
             const int f_lo = max(tw.z, w.y), f_hi = min(tw.w, w.z);  // columns valid for every row
             unsigned long long b1 = 0, b2 = 0;
-            for (int k0 = 0; k0 < nt && ok; k0 += kChunkTiles16, ++lc) {
-                const int ntc = min(kChunkTiles16, nt - k0);
+            for (int k0 = 0, ntc = 0; k0 < nt && ok; k0 += ntc, ++lc) {
                 const int jc = w.y + k0 * kDom16;
+                const int cabs = jc / kChunkDom;
+                ntc = min(nt - k0, ((cabs + 1) * kChunkDom - jc) / kDom16);
                 const int ab = lc & 1;
                 for (int k = ew * 32 + lane; k < ntc * kDom16; k += 32 * kEpi16) sh.aux[ab][k] = __ldg(&dom_aux[jc + k]);
                 mbar_arrive(&sh.aux_ready[ab]);
@@ -351,10 +351,11 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                     merge_half_key(b1, b2, t2, jh);
                     cmax = max(cmax, t1);
                 }
-                if (ok && valid) chunk_max[(size_t)(w.w + k0 / kChunkTiles16) * kTm16 + row] = cmax & 0xFFFFFFF0u;
+                if (ok && valid)
+                    chunk_max[(size_t)(w.w + cabs - w.y / kChunkDom) * kTm16 + row] = cmax & 0xFFFFFFF0u;
             }
             if (ok && valid) {
-                unsigned long long *dst = cand + ((size_t)it * kTm16 + row) * 2;
+                unsigned long long *dst = cand + ((size_t)work_slot[it] * kTm16 + row) * 2;
                 dst[0] = b1;
                 dst[1] = b2;
             }
@@ -549,8 +550,9 @@ cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st) {
     if (attr_err) return attr_err;
     const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
     if (grid <= 0) return cudaSuccess;
-    k_match_tc16<<<grid, kTc16Threads, kTc16Smem, st>>>(tmA, tmB, tb.work, tb.gcounters, tb.tile_win, tb.rng_info,
-                                                         tb.dom_aux, tb.cand, tb.chunk_max, tb.gcounters + 2);
+    k_match_tc16<<<grid, kTc16Threads, kTc16Smem, st>>>(tmA, tmB, tb.work, tb.work_slot, tb.gcounters, tb.tile_win,
+                                                         tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
+                                                         tb.gcounters + 2);
     ++g_launches;
     return cudaGetLastError();
 }
