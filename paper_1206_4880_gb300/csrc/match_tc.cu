@@ -80,9 +80,9 @@ constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 // Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
 // range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
 // s = 128 m^2 / Q + (p - m), m = min(p, Q / 256) (the exact gain / 512 up to the accumulator's
-// and this formula's rounding), and a 32-bit key (s's bits with the low 4 replaced by 15 - local
-// index); t1, t2 keep the two largest keys.
-// MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
+// and this formula's rounding), and a 32-bit key (s's bits with the low 9 replaced by 511 - the
+// domain's offset in its 512-domain chunk, jrel + l); t1, t2 keep the two largest keys of the
+// chunk. MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
 __device__ __forceinline__ float absmax8(const uint32_t *v) {
     const float a = fmaxf(fabsf(__uint_as_float(v[0])), fabsf(__uint_as_float(v[1])));
     const float b = fmaxf(fabsf(__uint_as_float(v[2])), fabsf(__uint_as_float(v[3])));
@@ -92,7 +92,7 @@ __device__ __forceinline__ float absmax8(const uint32_t *v) {
 }
 
 template <bool MASK>
-__device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int jh, int lo_r, int hi_r,
+__device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int jh, int jrel, int lo_r, int hi_r,
                                          uint32_t &t1, uint32_t &t2) {
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
@@ -115,7 +115,7 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
             const float p = absmax8(cur + 8 * q);
             const float mm = fminf(p, a.y);
             const float sc = fmaf(mm, mm * a.z, p - mm);
-            uint32_t key = (__float_as_uint(sc) & 0xFFFFFFF0u) | (uint32_t)(15 - l);
+            uint32_t key = (__float_as_uint(sc) & 0xFFFFFE00u) | (uint32_t)(511 - jrel - l);
             if (MASK) {
                 const int j = jh + l;
                 key = (j >= lo_r && j < hi_r) ? key : 0u;
@@ -503,7 +503,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 mbar_arrive(&sh.aux_ready[ab]);
                 ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (lc >> 1) & 1, abort_flag));
                 if (!ok) break;
-                uint32_t cmax = 0;
+                // the chunk's two best 32-bit keys, folded into the 64-bit keys once per chunk
+                uint32_t t1 = 0, t2 = 0;
+                const int jrel0 = jc - cabs * kChunkDom + half * (kTileDom / 2);
                 for (int k = 0; k < ntc; ++k, ++gt) {
                     const int acc = gt & 1;
                     ok = __all_sync(0xffffffffu, mbar_wait(&sh.tfull[acc], (gt >> 1) & 1, abort_flag));
@@ -512,21 +514,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int jh = jc + k * kTileDom + half * (kTileDom / 2);
                     const float4 *auxp = &sh.aux[ab][k * kTileDom + half * (kTileDom / 2)];
                     const uint32_t taddr = tbase + acc * kTileN;
-                    uint32_t t1 = 0, t2 = 0;
+                    const int jrel = jrel0 + k * kTileDom;
                     if (jh >= f_lo && jh + kTileDom / 2 <= f_hi)
-                        epi_half<false>(taddr, auxp, jh, lo_r, hi_r, t1, t2);
+                        epi_half<false>(taddr, auxp, jh, jrel, lo_r, hi_r, t1, t2);
                     else
-                        epi_half<true>(taddr, auxp, jh, lo_r, hi_r, t1, t2);
+                        epi_half<true>(taddr, auxp, jh, jrel, lo_r, hi_r, t1, t2);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh.tempty[acc]);
-                    merge_half_key(b1, b2, t1, jh);
-                    merge_half_key(b1, b2, t2, jh);
-                    cmax = max(cmax, t1);
                 }
+                merge_chunk_key(b1, b2, t1, cabs * kChunkDom);
+                merge_chunk_key(b1, b2, t2, cabs * kChunkDom);
                 if (ok && valid)
-                    chunk_max[((size_t)(w.w + cabs - w.y / kChunkDom) * kTileM + row) * 2 + half] =
-                        cmax & 0xFFFFFFF0u;
+                    chunk_max[((size_t)(w.w + cabs - w.y / kChunkDom) * kTileM + row) * 2 + half] = t1 & 0xFFFFFE00u;
             }
             if (ok && valid) {
                 unsigned long long *dst = cand + (((size_t)work_slot[it] * kTileM + row) * 2 + half) * 2;
@@ -563,8 +563,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // smaller domain id, then smaller isometry) and certifies it: every other domain's FP32 score is
 // at most the runner-up's, and an FP32 score is an upper bound of that domain's exact gain / 512
 // up to a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
-// of single-rounding operations), so if runner-up * (1 + 2^-16) < exact best, no other domain
-// can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
+// of single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-8 < exact best, no other
+// domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
 // (n Bs = A^2) have zero error
 // for every candidate; their code is the smallest domain id of the pool with t = 0.
 __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
@@ -673,13 +673,14 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     if (lane != 0) return;
     bool certified = b1 != 0 && gg.num >= 0;
     if (certified && b2 != 0) {
-        // runner-up score (truncated key) * (1 + 2^-16) + 2^-8 bounds every other domain's exact
-        // gain / 512: the key drops < 2^-19 relatively, the FP32 score formula errs < 20 * 2^-24
-        // relatively, and the accumulator's P / 64 errs < 2^-22 (|P / 64| + 16), which moves the
-        // score by < 2^-19 relatively plus < 2^-11 absolutely (Q >= 63 when Q > 0)
+        // runner-up score (truncated key) * (1 + 2^-13) + 2^-8 bounds every other domain's exact
+        // gain / 512: the key drops < 2^-14 relatively (9 low bits hold the chunk offset), the
+        // FP32 score formula errs < 20 * 2^-24 relatively, and the accumulator's P / 64 errs
+        // < 2^-22 (|P / 64| + 16), which moves the score by < 2^-19 relatively plus < 2^-11
+        // absolutely (Q >= 63 when Q > 0)
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
         const double sc = (double)gg.num / (512.0 * (double)gg.den);  // exact gain / 512
-        certified = u2 * (1.0 + 1.0 / 65536.0) + 1.0 / 256.0 < sc;
+        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 256.0 < sc;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);

@@ -65,8 +65,8 @@ static_assert(kTc16Smem <= 232448, "shared memory per CTA");
 
 // Scores of one accumulator tile for this thread's range row: 16 domains x 8 isometries.
 template <bool MASK>
-__device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float alpha, int jh, int lo_r, int hi_r,
-                                      uint32_t &t1, uint32_t &t2) {
+__device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float alpha, int jh, int jrel, int lo_r,
+                                      int hi_r, uint32_t &t1, uint32_t &t2) {
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
@@ -88,7 +88,7 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
             for (int t = 0; t < 8; ++t) p = fmaxf(p, fabsf(fmaf(alpha, a.x, __uint_as_float(cur[8 * q + t]))));
             const float mm = fminf(p, a.y);
             const float sc = fmaf(mm, mm * a.z, p - mm);
-            uint32_t key = (__float_as_uint(sc) & 0xFFFFFFF0u) | (uint32_t)(15 - l);
+            uint32_t key = (__float_as_uint(sc) & 0xFFFFFE00u) | (uint32_t)(511 - jrel - l);
             if (MASK) {
                 const int j = jh + l;
                 key = (j >= lo_r && j < hi_r) ? key : 0u;
@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                 mbar_arrive(&sh.aux_ready[ab]);
                 ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (lc >> 1) & 1, abort_flag));
                 if (!ok) break;
-                uint32_t cmax = 0;
+                uint32_t t1 = 0, t2 = 0;
+                const int jrel0 = jc - cabs * kChunkDom;
                 for (int k = 0; k < ntc; ++k, ++gt) {
                     const int acc = gt & 1;
                     ok = __all_sync(0xffffffffu, mbar_wait(&sh.tfull[acc], (gt >> 1) & 1, abort_flag));
@@ -339,20 +340,18 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                     const int jh = jc + k * kDom16;
                     const float4 *auxp = &sh.aux[ab][k * kDom16];
                     const uint32_t taddr = tbase + (uint32_t)(acc * 2 * kN16);
-                    uint32_t t1 = 0, t2 = 0;
+                    const int jrel = jrel0 + k * kDom16;
                     if (jh >= f_lo && jh + kDom16 <= f_hi)
-                        epi16<false>(taddr, auxp, alpha, jh, lo_r, hi_r, t1, t2);
+                        epi16<false>(taddr, auxp, alpha, jh, jrel, lo_r, hi_r, t1, t2);
                     else
-                        epi16<true>(taddr, auxp, alpha, jh, lo_r, hi_r, t1, t2);
+                        epi16<true>(taddr, auxp, alpha, jh, jrel, lo_r, hi_r, t1, t2);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh.tempty[acc]);
-                    merge_half_key(b1, b2, t1, jh);
-                    merge_half_key(b1, b2, t2, jh);
-                    cmax = max(cmax, t1);
                 }
-                if (ok && valid)
-                    chunk_max[(size_t)(w.w + cabs - w.y / kChunkDom) * kTm16 + row] = cmax & 0xFFFFFFF0u;
+                merge_chunk_key(b1, b2, t1, cabs * kChunkDom);
+                merge_chunk_key(b1, b2, t2, cabs * kChunkDom);
+                if (ok && valid) chunk_max[(size_t)(w.w + cabs - w.y / kChunkDom) * kTm16 + row] = t1 & 0xFFFFFE00u;
             }
             if (ok && valid) {
                 unsigned long long *dst = cand + ((size_t)work_slot[it] * kTm16 + row) * 2;
@@ -386,9 +385,9 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
 // One warp per class-sorted range position i of one image, as the B = 8 re-evaluation: the two
 // best keys over the tile's work items are evaluated exactly under all 8 isometries (lane
 // (candidate, t, half) sums X over 8 of the 16 rows), the best is certified if the runner-up's
-// score * (1 + 2^-16) + 2^-8 < exact best gain / 2048 (the key truncation, the score formula and
-// the accumulator's single rounding err by less than 2^-17 relatively, the latter also by less
-// than 2^-16 absolutely), else the range is queued for the exact re-search.
+// score * (1 + 2^-13) + 2^-8 < exact best gain / 2048 (the key truncation errs by less than 2^-14,
+// the score formula and the accumulator's single rounding by less than 2^-18 relatively, the
+// latter also by less than 2^-16 absolutely), else the range is queued for the exact re-search.
 __global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                            const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                            const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
@@ -493,7 +492,7 @@ __global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_
     if (certified && b2 != 0) {
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
         const double sc = i128_to_double_rn(gg.num) / (2048.0 * (double)gg.den);
-        certified = u2 * (1.0 + 1.0 / 65536.0) + 1.0 / 256.0 < sc;
+        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 256.0 < sc;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);

@@ -111,6 +111,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
           "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
+                   "+r"(v[14]), "+r"(v[15])
+                 :
+                 : "memory");
+}
 // Waits for this thread's tcgen05.ld results; naming the destination registers as operands keeps
 // the compiler from reading them before the wait.
 __device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[32]) {
@@ -136,12 +153,13 @@ __device__ __forceinline__ void top2u(uint32_t &b1, uint32_t &b2, uint32_t k) {
     b2 = max(b2, lo);
 }
 
-// Folds a half-tile key (local index in the low 4 bits) into the running 64-bit keys
-// (score bits << 32 | ~domain position).
-__device__ __forceinline__ void merge_half_key(unsigned long long &b1, unsigned long long &b2, uint32_t t, int jh) {
-    const int j = jh + 15 - (int)(t & 15u);
+// Folds a chunk's 32-bit key (score bits, low 9 bits = 511 - domain offset in the chunk starting
+// at batch-wide position cbase) into the running 64-bit keys (score bits << 32 | ~position).
+__device__ __forceinline__ void merge_chunk_key(unsigned long long &b1, unsigned long long &b2, uint32_t t,
+                                                int cbase) {
+    const int j = cbase + 511 - (int)(t & 511u);
     const unsigned long long k =
-        t ? (((unsigned long long)(t & 0xFFFFFFF0u) << 32) | (unsigned long long)(uint32_t)(~j)) : 0ull;
+        t ? (((unsigned long long)(t & 0xFFFFFE00u) << 32) | (unsigned long long)(uint32_t)(~j)) : 0ull;
     top2(b1, b2, k);
 }
 
