@@ -52,6 +52,10 @@ WORKLOADS = {
                                  "domains at stride 8 (259081) x 8 isometries; K=32 LFD classes, w=10"),
 }
 FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one matcher launch from an ncu capture of the current kernel on the
+# workload (profiles/match_tc_encode1024.md); set to None whenever the kernel changes until it is
+# captured again.
+MEASURED_TRAFFIC = {("encode-1024", "tensor"): 85.948672e6 + 12.945664e6}
 
 
 def flops_per_match(block: int) -> int:
@@ -283,7 +287,7 @@ def run_ours(args, wl, world, rank, local):
     clocks.start()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    match_ms, launches = [], 0
+    match_ms, stage_ms, launches = [], [], 0
     barrier(world)
     torch.cuda.synchronize()
     clocks.mark_begin()
@@ -294,6 +298,7 @@ def run_ours(args, wl, world, rank, local):
         ev1[k].record()
         stages, launches = fic.profile_read()
         match_ms.append(stages["match"])
+        stage_ms.append(stages)
     torch.cuda.synchronize()
     barrier(world)
     clocks.mark_end()
@@ -345,8 +350,10 @@ def run_ours(args, wl, world, rank, local):
         "matches_per_step": matches,
         "pool_fraction": matches / (R * Dn * 8),
         "fallback_ranges": rep["fallback_ranges"],
+        "stages_ms": {k: statistics.median(st[k] for st in stage_ms) for k in fic.STAGES},
         "roofline": {"kernel": "match", "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "unit": unit, "frac": achieved / peak,
+                     "traffic": MEASURED_TRAFFIC.get((args.workload, args.engine)), "traffic_unit": "bytes per launch",
                      "per_launch_ms": mean_match_ms, "peak_source": peak_note},
         "e2e": {"value": e2e_value, "unit": "matches/s", "h2d_bytes_per_step": H * W,
                 "d2h_bytes_per_step": d2h},
