@@ -266,7 +266,8 @@ struct TcBatch {
                            // in schedule order (by domain group)
     int32_t *work_slot;    // [max_items] key slot of each scheduled item
     int32_t *grp;          // [ng_max] per domain group: item count, then schedule cursor
-    unsigned long long *cand;  // [max_items][tm rows][halves][2] top-2 keys, by key slot
+    unsigned long long *cand;  // top-2 keys: range tile m owns [first slot, + items) x tm x halves x 2
+                               // entries, ordered (row, item, half, key)
     uint32_t *chunk_max;   // [max_chunks][tm rows][halves] best key per chunk
     int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks, [4] chunks per group
     int R_pad, Dn_aux, n_mtiles, max_items, max_chunks, ng_max, cpi_cap;

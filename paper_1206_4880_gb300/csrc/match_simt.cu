@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kSimtThreads)
 
 // Re-search of uncertified ranges of one image. Slot k holds class-sorted position fb_pos[k] and
 // the exact best of its evaluated candidates; the 512-domain chunks of the range's tile whose best
-// FP32 score could still reach that best (score * (1 + 2^-13) + 2^-8 >= best gain / (8 n), the
+// FP32 score could still reach that best (score * (1 + 2^-13) + 2^-16 >= best gain / (8 n), the
 // bound the re-evaluation certifies with) are scanned exactly. TM ranges per tile, H key columns
 // per row (chunk_max layout [chunk][TM][H]).
 template <int B, int TM, int H>
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kSimtThreads)
 #pragma unroll
                 for (int h = 1; h < H; ++h) key = max(key, chunk_max[e + h]);
                 const double s1 = (double)__uint_as_float(key);
-                if (key != 0 && s1 * (1.0 + 1.0 / 8192.0) + 1.0 / 256.0 >= thr)
+                if (key != 0 && s1 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0 >= thr)
                     sh.flagged[atomicAdd(&sh.n_flagged, 1)] = c;
             }
             __syncthreads();

@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
                const int4 *__restrict__ work, const int32_t *__restrict__ work_slot,
+               const int4 *__restrict__ tile_items,
                const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
                const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
                unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *err) {
@@ -529,7 +530,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     chunk_max[((size_t)(w.w + cabs - w.y / kChunkDom) * kTileM + row) * 2 + half] = t1 & 0xFFFFFE00u;
             }
             if (ok && valid) {
-                unsigned long long *dst = cand + (((size_t)work_slot[it] * kTileM + row) * 2 + half) * 2;
+                // the tile's keys are row-major (row, item, half, 2): a range reads its keys at once
+                const int4 ti = tile_items[w.x];
+                unsigned long long *dst =
+                    cand + (size_t)ti.x * kTileM * 4 + (((size_t)row * ti.y + (work_slot[it] - ti.x)) * 2 + half) * 2;
                 dst[0] = b1;
                 dst[1] = b2;
             }
@@ -558,12 +562,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---- exact re-evaluation and certification ----------------------------------------------------
+constexpr int kReevalThreads = 256;
+// Per-warp staging of one range (8x8 pixels) and its two candidates' 8x8 blocks of 2x2 sums in
+// four layouts each.
+struct __align__(16) ReevalStage {
+    uint16_t S[2][4][64];
+    uint8_t r[64];
+};
+
 // One warp per class-sorted range position i of one image. Merges the range's top-2 keys over its
 // tile's work items, evaluates both candidates under all 8 isometries exactly, keeps the best (gain, then
 // smaller domain id, then smaller isometry) and certifies it: every other domain's FP32 score is
 // at most the runner-up's, and an FP32 score is an upper bound of that domain's exact gain / 512
 // up to a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
-// of single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-8 < exact best, no other
+// of single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other
 // domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
 // (n Bs = A^2) have zero error
 // for every candidate; their code is the smallest domain id of the pool with t = 0.
@@ -575,6 +587,7 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
                          const int4 *__restrict__ tile_items, const unsigned long long *__restrict__ cand,
                          const int32_t *__restrict__ gcounters, int32_t *__restrict__ fallback,
                          FallbackBest *__restrict__ fb_best, int32_t *counters, fic_codes out) {
+    __shared__ ReevalStage stage[kReevalThreads / 32];
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // sorted position in this image
     const int lane = threadIdx.x & 31;
     if (i >= g.R) return;
@@ -614,8 +627,8 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     const int row = ig % kTileM;
     const int4 ti = tile_items[ig / kTileM];
     unsigned long long b1 = 0, b2 = 0;
-    for (int e = lane; e < 4 * ti.y; e += 32)
-        top2(b1, b2, cand[((size_t)(ti.x + (e >> 2)) * kTileM + row) * 4 + (e & 3)]);
+    const unsigned long long *ck = cand + (size_t)ti.x * kTileM * 4 + (size_t)row * ti.y * 4;
+    for (int e = lane; e < 4 * ti.y; e += 32) top2(b1, b2, ck[e]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, off);
@@ -623,29 +636,55 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
         top2(b1, b2, o1);
         top2(b1, b2, o2);
     }
-    // exact evaluation: lanes 2 (8 c + t) and 2 (8 c + t) + 1 form X of candidate c, isometry t
-    // over range rows 0-3 and 4-7
+    // exact evaluation. The warp stages the range's pixels and both candidates' blocks of 2x2
+    // sums in shared memory, each block in four layouts (as stored, transposed, rows reversed,
+    // transposed with rows reversed), so that row y of T_t(S) is one contiguous 16-byte row of one
+    // layout: layout swap + 2 rev, row (swap ? fx : fy) ? 7 - y : y, with rev = swap ? fy : fx and
+    // swap, fy, fx the isometry's flags. Lanes 2 (8 c + t) and 2 (8 c + t) + 1 then form X of
+    // candidate c, isometry t over range rows 0-3 and 4-7 with packed byte x halfword dot products.
+    ReevalStage &sg = stage[threadIdx.x >> 5];
+    const int j0 = (int)(~(uint32_t)(b1 & 0xffffffffu)) - dom_off;  // positions in this image
+    const int j1 = (int)(~(uint32_t)(b2 & 0xffffffffu)) - dom_off;
+    const bool h0 = b1 != 0 && j0 >= 0 && j0 < g.Dn, h1 = b2 != 0 && j1 >= 0 && j1 < g.Dn;
+    const int d0 = h0 ? dom_order[j0] : INT_MAX, d1 = h1 ? dom_order[j1] : INT_MAX;
+    {
+        const int px = 2 * lane;
+        const uint8_t *prow = img + (size_t)(ry + (px >> 3)) * g.pitch + rx + (px & 7);
+        sg.r[px] = prow[0];
+        sg.r[px + 1] = prow[1];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int e = lane + 32 * k, c = e >> 6, q = e & 63, y = q >> 3, x = q & 7;
+        const bool hk = c ? h1 : h0;
+        const uint16_t v = hk ? domS[(size_t)(c ? d1 : d0) * 64 + q] : (uint16_t)0;
+        sg.S[c][0][8 * y + x] = v;
+        sg.S[c][1][8 * x + y] = v;
+        sg.S[c][2][8 * y + 7 - x] = v;
+        sg.S[c][3][8 * x + 7 - y] = v;
+    }
+    __syncwarp();
     const int cidx = lane >> 4, t = (lane >> 1) & 7, hrow = (lane & 1) * 4;
-    const unsigned long long key = cidx == 0 ? b1 : b2;
-    const int jl = (int)(~(uint32_t)(key & 0xffffffffu)) - dom_off;  // position in this image
-    const bool has = key != 0 && jl >= 0 && jl < g.Dn;
+    const bool has = cidx ? h1 : h0;
     Gain gg{-1, 1};
-    int d = INT_MAX;
+    int d = cidx ? d1 : d0;
     long long P = 0, Q = 0, C = 0;
     int X = 0;
-    if (has) {
-        d = dom_order[jl];
-        const uint16_t *S = domS + (size_t)d * 64;
+    {
+        const int swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
+        const uint16_t *M = sg.S[cidx][swap + 2 * (swap ? fy : fx)];
+        const int flip = swap ? fx : fy;
+        unsigned acc = 0;
 #pragma unroll
         for (int y = hrow; y < hrow + 4; ++y) {
-            const uint8_t *row = img + (size_t)(ry + y) * g.pitch + rx;
-#pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                int sy, sx;
-                iso_src(8, t, y, x, sy, sx);
-                X += (int)row[x] * (int)S[sy * 8 + sx];
-            }
+            const uint4 m = *reinterpret_cast<const uint4 *>(M + 8 * (flip ? 7 - y : y));
+            const uint2 rr = *reinterpret_cast<const uint2 *>(sg.r + 8 * y);
+            acc = __dp2a_lo(m.x, rr.x, acc);
+            acc = __dp2a_hi(m.y, rr.x, acc);
+            acc = __dp2a_lo(m.z, rr.y, acc);
+            acc = __dp2a_hi(m.w, rr.y, acc);
         }
+        X = (int)acc;  // <= 32 * 255 * 1020 < 2^31
     }
     X += __shfl_xor_sync(0xffffffffu, X, 1);
     if (has) {
@@ -673,14 +712,15 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     if (lane != 0) return;
     bool certified = b1 != 0 && gg.num >= 0;
     if (certified && b2 != 0) {
-        // runner-up score (truncated key) * (1 + 2^-13) + 2^-8 bounds every other domain's exact
+        // runner-up score (truncated key) * (1 + 2^-13) + 2^-16 bounds every other domain's exact
         // gain / 512: the key drops < 2^-14 relatively (9 low bits hold the chunk offset), the
-        // FP32 score formula errs < 20 * 2^-24 relatively, and the accumulator's P / 64 errs
-        // < 2^-22 (|P / 64| + 16), which moves the score by < 2^-19 relatively plus < 2^-11
-        // absolutely (Q >= 63 when Q > 0)
+        // FP32 score formula errs < 20 * 2^-24 relatively, and the accumulator's P / 64 (an exact
+        // integer Y plus one rounded correction of magnitude <= 16) errs < 2^-22 (|P / 64| + 16);
+        // the score's slope in p is at most 1, so that moves it by < 2^-21 relatively plus
+        // < 2^-18 absolutely
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
         const double sc = (double)gg.num / (512.0 * (double)gg.den);  // exact gain / 512
-        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 256.0 < sc;
+        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0 < sc;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
@@ -794,7 +834,8 @@ cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
     if (attr_err) return attr_err;
     const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
     if (grid <= 0) return cudaSuccess;
-    k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.work_slot, tb.gcounters,
+    k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.work_slot, tb.tile_items,
+                                                   tb.gcounters,
                                                    tb.tile_win, tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
                                                    tb.gcounters + 2);
     ++g_launches;
@@ -804,7 +845,7 @@ cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
 cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, cudaStream_t st) {
     const long long threads = (long long)g.R * 32;
-    k_reeval<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+    k_reeval<<<(unsigned)((threads + kReevalThreads - 1) / kReevalThreads), kReevalThreads, 0, st>>>(
         g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, sort_buckets(g), b.rng_info,
         b.rng_off, b.dom_off, tb.tile_items, tb.cand, tb.gcounters, b.fallback, b.fb_best, b.counters, out);
     ++g_launches;

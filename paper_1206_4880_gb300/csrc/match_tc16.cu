@@ -185,6 +185,7 @@ __global__ void k_pack_domains16(Geo g, const uint16_t *__restrict__ domS, const
 __global__ void __launch_bounds__(kTc16Threads, 1)
     k_match_tc16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const int4 *__restrict__ work, const int32_t *__restrict__ work_slot,
+                 const int4 *__restrict__ tile_items,
                  const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
                  const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
                  unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *err) {
@@ -354,7 +355,10 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                 if (ok && valid) chunk_max[(size_t)(w.w + cabs - w.y / kChunkDom) * kTm16 + row] = t1 & 0xFFFFFE00u;
             }
             if (ok && valid) {
-                unsigned long long *dst = cand + ((size_t)work_slot[it] * kTm16 + row) * 2;
+                // the tile's keys are row-major (row, item, 2): a range reads its keys at once
+                const int4 ti = tile_items[w.x];
+                unsigned long long *dst =
+                    cand + (size_t)ti.x * kTm16 * 2 + ((size_t)row * ti.y + (work_slot[it] - ti.x)) * 2;
                 dst[0] = b1;
                 dst[1] = b2;
             }
@@ -385,10 +389,17 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
 // One warp per class-sorted range position i of one image, as the B = 8 re-evaluation: the two
 // best keys over the tile's work items are evaluated exactly under all 8 isometries (lane
 // (candidate, t, half) sums X over 8 of the 16 rows), the best is certified if the runner-up's
-// score * (1 + 2^-13) + 2^-8 < exact best gain / 2048 (the key truncation errs by less than 2^-14,
-// the score formula and the accumulator's single rounding by less than 2^-18 relatively, the
-// latter also by less than 2^-16 absolutely), else the range is queued for the exact re-search.
-__global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
+// score * (1 + 2^-13) + 2^-16 < exact best gain / 2048 (the key truncation errs by less than
+// 2^-14 relatively, the score formula and the epilogue's single rounding of the exact Y by less
+// than 2^-18 relatively; the absolute term only guards the degenerate scores near zero), else the
+// range is queued for the exact re-search.
+constexpr int kReeval16Threads = 256;
+struct __align__(16) Reeval16Stage {
+    uint16_t S[2][4][256];
+    uint8_t r[256];
+};
+
+__global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                            const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                            const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
                            const int32_t *__restrict__ bin_off, int nbuckets, const int4 *__restrict__ rng_info,
@@ -396,6 +407,7 @@ __global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_
                            const unsigned long long *__restrict__ cand, const int32_t *__restrict__ gcounters,
                            int32_t *__restrict__ fallback, FallbackBest *__restrict__ fb_best, int32_t *counters,
                            fic_codes out) {
+    __shared__ Reeval16Stage stage16[kReeval16Threads / 32];
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= g.R) return;
@@ -431,7 +443,8 @@ __global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_
     const int row = ig % kTm16;
     const int4 ti = tile_items[ig / kTm16];
     unsigned long long b1 = 0, b2 = 0;
-    for (int e = lane; e < 2 * ti.y; e += 32) top2(b1, b2, cand[((size_t)(ti.x + (e >> 1)) * kTm16 + row) * 2 + (e & 1)]);
+    const unsigned long long *ck = cand + (size_t)ti.x * kTm16 * 2 + (size_t)row * ti.y * 2;
+    for (int e = lane; e < 2 * ti.y; e += 32) top2(b1, b2, ck[e]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, off);
@@ -439,26 +452,66 @@ __global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_
         top2(b1, b2, o1);
         top2(b1, b2, o2);
     }
+    // exact evaluation, staged as in the 8x8 re-evaluation: the range and both candidates' blocks
+    // (four layouts each: as stored, transposed, rows reversed, transposed with rows reversed) in
+    // shared memory; lane (c, t, half) sums X over 8 of the 16 rows with packed dot products.
+    Reeval16Stage &sg = stage16[threadIdx.x >> 5];
+    const int j0 = (int)(~(uint32_t)(b1 & 0xffffffffu)) - dom_off;
+    const int j1 = (int)(~(uint32_t)(b2 & 0xffffffffu)) - dom_off;
+    const bool h0 = b1 != 0 && j0 >= 0 && j0 < g.Dn, h1 = b2 != 0 && j1 >= 0 && j1 < g.Dn;
+    const int d0 = h0 ? dom_order[j0] : INT_MAX, d1 = h1 ? dom_order[j1] : INT_MAX;
+    {
+        const int px = 8 * lane;  // 8 pixels of row px / 16
+        const uint8_t *prow = img + (size_t)(ry + (px >> 4)) * g.pitch + rx + (px & 15);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sg.r[px + k] = prow[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int e = 8 * (lane + 32 * k), c = e >> 8, q = e & 255, y = q >> 4, x = q & 15;  // x = 0 or 8
+        const bool hk = c ? h1 : h0;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (hk) v = *reinterpret_cast<const uint4 *>(domS + (size_t)(c ? d1 : d0) * 256 + q);
+        *reinterpret_cast<uint4 *>(&sg.S[c][0][16 * y + x]) = v;
+        // reversed: elements x..x+7 land at 15-x-7..15-x in reverse order
+        const uint4 rv = make_uint4(__byte_perm(v.w, 0, 0x1032), __byte_perm(v.z, 0, 0x1032),
+                                    __byte_perm(v.y, 0, 0x1032), __byte_perm(v.x, 0, 0x1032));
+        *reinterpret_cast<uint4 *>(&sg.S[c][2][16 * y + 8 - x]) = rv;
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const uint16_t u = (uint16_t)(w4[h >> 1] >> (16 * (h & 1)));
+            sg.S[c][1][16 * (x + h) + y] = u;
+            sg.S[c][3][16 * (x + h) + 15 - y] = u;
+        }
+    }
+    __syncwarp();
     const int cidx = lane >> 4, t = (lane >> 1) & 7, hrow = (lane & 1) * 8;
-    const unsigned long long key = cidx == 0 ? b1 : b2;
-    const int jl = (int)(~(uint32_t)(key & 0xffffffffu)) - dom_off;
-    const bool has = key != 0 && jl >= 0 && jl < g.Dn;
+    const bool has = cidx ? h1 : h0;
     GainW gg{-1, 1};
-    int d = INT_MAX;
+    int d = cidx ? d1 : d0;
     long long P = 0, Q = 0, C = 0;
     int X = 0;
-    if (has) {
-        d = dom_order[jl];
-        const uint16_t *S = domS + (size_t)d * 256;
-        for (int y = hrow; y < hrow + 8; ++y) {
-            const uint8_t *prow = img + (size_t)(ry + y) * g.pitch + rx;
+    {
+        const int swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
+        const uint16_t *M = sg.S[cidx][swap + 2 * (swap ? fy : fx)];
+        const int flip = swap ? fx : fy;
+        unsigned acc = 0;
 #pragma unroll
-            for (int x = 0; x < 16; ++x) {
-                int sy, sx;
-                iso_src(16, t, y, x, sy, sx);
-                X += (int)prow[x] * (int)S[sy * 16 + sx];
-            }
+        for (int y = hrow; y < hrow + 8; ++y) {
+            const uint4 *mrow = reinterpret_cast<const uint4 *>(M + 16 * (flip ? 15 - y : y));
+            const uint4 m0 = mrow[0], m1 = mrow[1];
+            const uint4 rr = *reinterpret_cast<const uint4 *>(sg.r + 16 * y);
+            acc = __dp2a_lo(m0.x, rr.x, acc);
+            acc = __dp2a_hi(m0.y, rr.x, acc);
+            acc = __dp2a_lo(m0.z, rr.y, acc);
+            acc = __dp2a_hi(m0.w, rr.y, acc);
+            acc = __dp2a_lo(m1.x, rr.z, acc);
+            acc = __dp2a_hi(m1.y, rr.z, acc);
+            acc = __dp2a_lo(m1.z, rr.w, acc);
+            acc = __dp2a_hi(m1.w, rr.w, acc);
         }
+        X = (int)acc;  // <= 128 * 255 * 1020 < 2^31
     }
     X += __shfl_xor_sync(0xffffffffu, X, 1);
     if (has) {
@@ -492,7 +545,7 @@ __global__ void k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_
     if (certified && b2 != 0) {
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
         const double sc = i128_to_double_rn(gg.num) / (2048.0 * (double)gg.den);
-        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 256.0 < sc;
+        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0 < sc;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
@@ -549,7 +602,8 @@ cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st) {
     if (attr_err) return attr_err;
     const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
     if (grid <= 0) return cudaSuccess;
-    k_match_tc16<<<grid, kTc16Threads, kTc16Smem, st>>>(tmA, tmB, tb.work, tb.work_slot, tb.gcounters, tb.tile_win,
+    k_match_tc16<<<grid, kTc16Threads, kTc16Smem, st>>>(tmA, tmB, tb.work, tb.work_slot, tb.tile_items, tb.gcounters,
+                                                         tb.tile_win,
                                                          tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
                                                          tb.gcounters + 2);
     ++g_launches;
@@ -559,7 +613,7 @@ cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st) {
 cudaError_t launch_reeval16(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                             const fic_codes &out, cudaStream_t st) {
     const long long threads = (long long)g.R * 32;
-    k_reeval16<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+    k_reeval16<<<(unsigned)((threads + kReeval16Threads - 1) / kReeval16Threads), kReeval16Threads, 0, st>>>(
         g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, sort_buckets(g), b.rng_info,
         b.rng_off, b.dom_off, tb.tile_items, tb.cand, tb.gcounters, b.fallback, b.fb_best, b.counters, out);
     ++g_launches;
