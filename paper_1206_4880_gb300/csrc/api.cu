@@ -9,7 +9,7 @@
 #include "fic_internal.cuh"
 
 namespace fic {
-cudaError_t launch_dom_csr(const Geo &g, const int32_t *dom, int32_t *cnt, int32_t *off,
+cudaError_t launch_dom_csr(const Geo &g, const int32_t *dom, const double *s, int32_t *cnt, int32_t *off,
                            int32_t *cursor, int32_t *list, cudaStream_t st);
 cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const int32_t *off,
                                   const int32_t *list, const float *lam, float *lam_prev,
@@ -602,7 +602,7 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
         FIC_TRY(launch_grads_out(g.R, g64, g64 + g.R, grad_s, grad_o, st), "grads_out");
         return FIC_OK;
     }
-    FIC_TRY(launch_dom_csr(g, codes->dom, cnt, off, cursor, list, st), "csr");
+    FIC_TRY(launch_dom_csr(g, codes->dom, codes->s, cnt, off, cursor, list, st), "csr");
     // forward: checkpoints x_0, x_ck, x_2ck, ...
     if (x0) FIC_TRY(cudaMemcpyAsync(ckpt, x0, img * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy");
     else FIC_TRY(launch_fill(ckpt, img, 128.f, st), "fill");

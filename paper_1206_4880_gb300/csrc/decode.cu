@@ -84,10 +84,12 @@ cudaError_t launch_decode_step_scaled(const fic_codes &c, const Geo &g, int z, c
 }
 
 // ---- adjoint -------------------------------------------------------------------------------
-// domain -> ranges CSR: cnt[d] = #ranges using d; off = exclusive scan; list sorted per segment.
-__global__ void k_dom_count(Geo g, const int32_t *__restrict__ dom, int32_t *cnt) {
+// domain -> ranges CSR: cnt[d] = #ranges using d with s != 0 (a range with s = 0 contributes
+// nothing to W^T l, and flat ranges, which all take the pool's smallest domain id, would otherwise
+// pile onto one domain); off = exclusive scan; list sorted per segment.
+__global__ void k_dom_count(Geo g, const int32_t *__restrict__ dom, const double *__restrict__ s, int32_t *cnt) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < g.R) atomicAdd(&cnt[dom[r]], 1);
+    if (r < g.R && s[r] != 0.0) atomicAdd(&cnt[dom[r]], 1);
 }
 
 // Single-block exclusive scan of cnt[0..n) into off[0..n], chunk by chunk.
@@ -120,10 +122,10 @@ __global__ void k_scan_single(const int32_t *__restrict__ cnt, int n, int32_t *_
     if (threadIdx.x == 0) off[n] = carry;
 }
 
-__global__ void k_dom_fill(Geo g, const int32_t *__restrict__ dom, int32_t *cursor,
+__global__ void k_dom_fill(Geo g, const int32_t *__restrict__ dom, const double *__restrict__ s, int32_t *cursor,
                            int32_t *__restrict__ list) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < g.R) list[atomicAdd(&cursor[dom[r]], 1)] = r;
+    if (r < g.R && s[r] != 0.0) list[atomicAdd(&cursor[dom[r]], 1)] = r;
 }
 
 // Insertion-sort each domain's segment so the gather order is fixed.
@@ -223,15 +225,15 @@ __global__ void k_grads_out(int R, const double *__restrict__ gs64, const double
     }
 }
 
-cudaError_t launch_dom_csr(const Geo &g, const int32_t *dom, int32_t *cnt, int32_t *off,
+cudaError_t launch_dom_csr(const Geo &g, const int32_t *dom, const double *s, int32_t *cnt, int32_t *off,
                            int32_t *cursor, int32_t *list, cudaStream_t st) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * g.Dn, st))) return e;
-    k_dom_count<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, cnt);
+    k_dom_count<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, s, cnt);
     ++g_launches;
     k_scan_single<<<1, 1024, 0, st>>>(cnt, g.Dn, off, cursor);
     ++g_launches;
-    k_dom_fill<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, cursor, list);
+    k_dom_fill<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, s, cursor, list);
     ++g_launches;
     k_dom_sortseg<<<(g.Dn + 255) / 256, 256, 0, st>>>(g.Dn, off, list);
     ++g_launches;
