@@ -51,6 +51,58 @@ fic_status fail(fic_status s, const char *fmt, ...) {
     return s;
 }
 
+// Internal streams on which the per-image stages of a batch run concurrently (fork/join through
+// events on the caller's stream; inside a CUDA graph capture they become parallel branches). One
+// set per host thread and device, created on first use outside a capture and kept.
+constexpr int kSideStreams = 4;
+struct SidePool {
+    cudaStream_t s[kSideStreams];
+    cudaEvent_t fork, join[kSideStreams];
+    bool ready = false;
+};
+constexpr int kMaxDevices = 64;
+thread_local SidePool g_side[kMaxDevices];
+
+// The pool for `dev`, or nullptr (run serially) when it does not exist yet and `st` is capturing.
+SidePool *side_pool(int dev, cudaStream_t st) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    SidePool &p = g_side[dev];
+    if (p.ready) return &p;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    for (int k = 0; k < kSideStreams; ++k) {
+        if (cudaStreamCreateWithFlags(&p.s[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p.join[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+    }
+    if (cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    p.ready = true;
+    return &p;
+}
+
+cudaError_t side_fork(cudaStream_t st, SidePool *p, int ns) {
+    cudaError_t e = cudaEventRecord(p->fork, st);
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->s[k], p->fork, 0);
+    return e;
+}
+
+cudaError_t side_join(cudaStream_t st, SidePool *p, int ns) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(p->join[k], p->s[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->join[k], 0);
+    }
+    return e;
+}
+
 fic_status cuda_fail(cudaError_t e, const char *where) {
     return fail(FIC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
@@ -381,33 +433,71 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
     auto mark = [&](int i) -> cudaError_t {
         return g_prof.on ? cudaEventRecord(g_prof.ev[i], st) : cudaSuccess;
     };
+    // a batch runs its per-image stages on internal streams, image k on stream k % ns, joined back
+    // before the batch-wide matcher and at the end; a single image stays on the caller's stream
+    SidePool *sp = n > 1 ? side_pool(dev, st) : nullptr;
+    const int ns = sp ? (n < kSideStreams ? n : kSideStreams) : 0;
+    auto on = [&](int k) -> cudaStream_t { return ns ? sp->s[k % ns] : st; };
+    const bool tensor = p->engine != FIC_ENGINE_SIMT;
+    const bool b16 = g[0].B == 16;
     FIC_TRY(mark(0), "event");
     FIC_TRY(cudaMemsetAsync(b[0].counters, 0, 8 * sizeof(int32_t) * n, st), "memset");
     FIC_TRY(cudaMemsetAsync(tb.gcounters, 0, 8 * sizeof(int32_t), st), "memset");
-    for (int k = 0; k < n; ++k) FIC_TRY(launch_classify(imgs[k], g[k], b[k], st), "classify");
-    FIC_TRY(mark(1), "event");
-    for (int k = 0; k < n; ++k) FIC_TRY(launch_pools(g[k], b[k], st), "pools");
-    FIC_TRY(mark(2), "event");
-    if (p->engine == FIC_ENGINE_SIMT) {
+    if (ns) {
+        // classification, pools and packing per image (stage marks 1 and 2 coincide with 0)
+        FIC_TRY(mark(1), "event");
+        FIC_TRY(mark(2), "event");
+        FIC_TRY(side_fork(st, sp, ns), "fork");
+        for (int k = 0; k < n; ++k) {
+            FIC_TRY(launch_classify(imgs[k], g[k], b[k], on(k)), "classify");
+            FIC_TRY(launch_pools(g[k], b[k], on(k)), "pools");
+            if (tensor)
+                FIC_TRY(b16 ? launch_pack16(imgs[k], g[k], b[k], on(k)) : launch_pack(imgs[k], g[k], b[k], on(k)),
+                        "pack");
+            else
+                FIC_TRY(launch_match_simt(imgs[k], g[k], b[k], outs[k], on(k)), "match_simt");
+        }
+        FIC_TRY(side_join(st, sp, ns), "join");
+    } else {
+        for (int k = 0; k < n; ++k) FIC_TRY(launch_classify(imgs[k], g[k], b[k], st), "classify");
+        FIC_TRY(mark(1), "event");
+        for (int k = 0; k < n; ++k) FIC_TRY(launch_pools(g[k], b[k], st), "pools");
+        FIC_TRY(mark(2), "event");
+        if (tensor)
+            for (int k = 0; k < n; ++k)
+                FIC_TRY(b16 ? launch_pack16(imgs[k], g[k], b[k], st) : launch_pack(imgs[k], g[k], b[k], st), "pack");
+        else
+            for (int k = 0; k < n; ++k) FIC_TRY(launch_match_simt(imgs[k], g[k], b[k], outs[k], st), "match_simt");
+    }
+    if (!tensor) {
         FIC_TRY(mark(3), "event");
-        for (int k = 0; k < n; ++k) FIC_TRY(launch_match_simt(imgs[k], g[k], b[k], outs[k], st), "match_simt");
         FIC_TRY(mark(4), "event");
         FIC_TRY(mark(5), "event");
     } else {
-        const bool b16 = g[0].B == 16;
-        for (int k = 0; k < n; ++k)
-            FIC_TRY(b16 ? launch_pack16(imgs[k], g[k], b[k], st) : launch_pack(imgs[k], g[k], b[k], st), "pack");
         FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), st),
                 "work_list");
         FIC_TRY(mark(3), "event");
         FIC_TRY(b16 ? launch_match_tc16(tb, sms, st) : launch_match_tc(tb, sms, st), "match_tc");
         FIC_TRY(mark(4), "event");
-        for (int k = 0; k < n; ++k)
-            FIC_TRY(b16 ? launch_reeval16(imgs[k], g[k], b[k], tb, outs[k], st)
-                        : launch_reeval(imgs[k], g[k], b[k], tb, outs[k], st),
-                    "reeval");
-        FIC_TRY(mark(5), "event");
-        for (int k = 0; k < n; ++k) FIC_TRY(launch_rescan(imgs[k], g[k], b[k], tb, outs[k], sms, st), "rescan");
+        if (ns) {
+            // re-evaluation and exact re-search per image (stage mark 5 coincides with 4)
+            FIC_TRY(mark(5), "event");
+            FIC_TRY(side_fork(st, sp, ns), "fork");
+            for (int k = 0; k < n; ++k) {
+                FIC_TRY(b16 ? launch_reeval16(imgs[k], g[k], b[k], tb, outs[k], on(k))
+                            : launch_reeval(imgs[k], g[k], b[k], tb, outs[k], on(k)),
+                        "reeval");
+                FIC_TRY(launch_rescan(imgs[k], g[k], b[k], tb, outs[k], sms, on(k)), "rescan");
+            }
+            FIC_TRY(side_join(st, sp, ns), "join");
+        } else {
+            for (int k = 0; k < n; ++k)
+                FIC_TRY(b16 ? launch_reeval16(imgs[k], g[k], b[k], tb, outs[k], st)
+                            : launch_reeval(imgs[k], g[k], b[k], tb, outs[k], st),
+                        "reeval");
+            FIC_TRY(mark(5), "event");
+            for (int k = 0; k < n; ++k) FIC_TRY(launch_rescan(imgs[k], g[k], b[k], tb, outs[k], sms, st), "rescan");
+        }
     }
     FIC_TRY(mark(6), "event");
     if (info) FIC_TRY(launch_info(b.data(), n, tb, info, st), "info");
