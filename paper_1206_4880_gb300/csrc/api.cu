@@ -209,8 +209,10 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->win_hi = c.take<int32_t>(g.R);
         b->dom_key = c.take<uint8_t>(g.Dn);
         b->range_key = c.take<uint8_t>(g.R);
-        b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 256);
-        b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 256);
+        // each holds per-block counts and bases for one sort when the domain and range sorts run
+        // concurrently (pools.cu), or counts / bases of both sorts in turn
+        b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 512);
+        b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 512);
         b->fallback = c.take<int32_t>(g.R);
         b->fb_best = c.take<FallbackBest>(g.R);
         b->counters = img_counters ? img_counters + 8 * k : nullptr;
@@ -443,7 +445,25 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
     FIC_TRY(mark(0), "event");
     FIC_TRY(cudaMemsetAsync(b[0].counters, 0, 8 * sizeof(int32_t) * n, st), "memset");
     FIC_TRY(cudaMemsetAsync(tb.gcounters, 0, 8 * sizeof(int32_t), st), "memset");
-    if (ns) {
+    // a single image in class mode on the tensor engine overlaps its independent stages: the range
+    // sort with the domain sort, and the domain packing with windows, range packing and the work
+    // list (which need the domain sort's class offsets)
+    SidePool *sp1 = (n == 1 && tensor && !g[0].literal) ? side_pool(dev, st) : nullptr;
+    if (sp1) {
+        FIC_TRY(launch_classify(imgs[0], g[0], b[0], st), "classify");
+        FIC_TRY(mark(1), "event");
+        FIC_TRY(side_fork(st, sp1, 1), "fork");
+        FIC_TRY(launch_pools_ranges_sort(g[0], b[0], sp1->s[0]), "pools");
+        FIC_TRY(launch_pools_domains(g[0], b[0], st), "pools");
+        FIC_TRY(cudaEventRecord(sp1->fork, st), "event");  // domain sort done
+        FIC_TRY(cudaStreamWaitEvent(sp1->s[0], sp1->fork, 0), "event");
+        FIC_TRY(mark(2), "event");
+        FIC_TRY(launch_pools_windows(g[0], b[0], sp1->s[0]), "pools");
+        FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], sp1->s[0], 1) : launch_pack(imgs[0], g[0], b[0], sp1->s[0], 1),
+                "pack");
+        FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], st, 2) : launch_pack(imgs[0], g[0], b[0], st, 2), "pack");
+        FIC_TRY(side_join(st, sp1, 1), "join");
+    } else if (ns) {
         // classification, pools and packing per image (stage marks 1 and 2 coincide with 0)
         FIC_TRY(mark(1), "event");
         FIC_TRY(mark(2), "event");

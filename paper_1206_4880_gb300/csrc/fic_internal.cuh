@@ -294,17 +294,23 @@ cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &
                             cudaStream_t st);
 cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st);
 int sort_buckets(const Geo &g);  // buckets of the pool sort: K, or distinct FD values
+// class-mode pools split for concurrent streams (see pools.cu); sort scratch sized by
+// sort_scratch_ints
+cudaError_t launch_pools_domains(const Geo &g, const EncodeBufs &b, cudaStream_t st);
+cudaError_t launch_pools_ranges_sort(const Geo &g, const EncodeBufs &b, cudaStream_t st);
+cudaError_t launch_pools_windows(const Geo &g, const EncodeBufs &b, cudaStream_t st);
 cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                               const fic_codes &out, cudaStream_t st);
 cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, int num_sms, cudaStream_t st);
-cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st);
+// operand packing: part 0 both, 1 ranges only, 2 domains only
+cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st, int part = 0);
 cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st);
 cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st);
 cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, cudaStream_t st);
 // B = 16 tensor engine (match_tc16.cu)
-cudaError_t launch_pack16(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st);
+cudaError_t launch_pack16(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st, int part = 0);
 cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st);
 cudaError_t launch_reeval16(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                             const fic_codes &out, cudaStream_t st);

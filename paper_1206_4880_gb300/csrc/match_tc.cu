@@ -787,15 +787,15 @@ cudaError_t make_map_f16(CUtensorMap *map, void *base, unsigned long long rows, 
 namespace {
 }  // namespace
 
-cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st) {
-    {
+cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st, int part) {
+    if (part != 2) {
         const long long n = (long long)b.R_pad * 8;
         k_pack_ranges<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, img, b.range_order, b.range_sum, b.win_lo,
                                                                   b.win_hi, b.R_pad, b.dom_off, b.A_mat,
                                                                   (uint4 *)b.A1_mat, b.rng_info);
         ++g_launches;
     }
-    {
+    if (part != 1) {
         const long long n = (long long)b.Dn_aux * 64;
         k_pack_domains<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, b.dom_S, b.dom_order, b.dom_sum,
                                                                    b.dom_sumsq, b.Dn_aux, b.B_mat, (uint4 *)b.B1_mat,

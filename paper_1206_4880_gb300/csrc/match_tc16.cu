@@ -572,15 +572,15 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
 }
 
 // ---- host side -------------------------------------------------------------------------------
-cudaError_t launch_pack16(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st) {
-    {
+cudaError_t launch_pack16(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st, int part) {
+    if (part != 2) {
         const long long n = (long long)b.R_pad * 16;
         k_pack_ranges16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, img, b.range_order, b.range_sum, b.win_lo,
                                                                     b.win_hi, b.R_pad, b.dom_off, b.A_mat,
                                                                     b.rng_info);
         ++g_launches;
     }
-    {
+    if (part != 1) {
         const long long n = (long long)b.Dn_aux * 128;
         k_pack_domains16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, b.dom_S, b.dom_order, b.dom_sum,
                                                                      b.dom_sumsq, b.Dn_aux, b.B_mat, b.dom_aux);

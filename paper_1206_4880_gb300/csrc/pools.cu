@@ -243,6 +243,30 @@ cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The class-mode pools in two halves that can run on different streams: the domain sort
+// (dom_order, bin_off), and the range sort plus the windows (which also need bin_off: the caller
+// orders the second half after the first's domain sort). The two halves use separate sort
+// scratch (sort_counts for domains, sort_offs for ranges), each holding counts and bases.
+cudaError_t launch_pools_domains(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
+    const int nd = (g.Dn + kSortChunk - 1) / kSortChunk;
+    return counting_sort(b.dom_bin, g.Dn, g.K, b.sort_counts, b.sort_counts + (size_t)nd * 256, b.dom_order,
+                         b.bin_off, st);
+}
+
+cudaError_t launch_pools_ranges_sort(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
+    const int nr = (g.R + kSortChunk - 1) / kSortChunk;
+    return counting_sort(b.range_bin, g.R, g.K, b.sort_offs, b.sort_offs + (size_t)nr * 256, b.range_order,
+                         b.rbin_off, st);
+}
+
+cudaError_t launch_pools_windows(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.matches, 0, sizeof(long long), st))) return e;
+    k_windows<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_bin, b.bin_off, b.win_lo, b.win_hi, b.matches);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
 int sort_buckets(const Geo &g) { return g.literal ? fd_ranks().n : g.K; }
 
 }  // namespace fic
