@@ -98,7 +98,9 @@ __device__ __forceinline__ void finalize_code(int n, long long A, long long Bs, 
         s = __ddiv_rn(__dmul_rn(4.0, (double)P), (double)Q);
     else
         s = P > 0 ? 1.0 : -1.0;
-    o = __ddiv_rn(__dsub_rn((double)A, __dmul_rn(s, __ddiv_rn((double)C, 4.0))), (double)n);
+    // C / 4 and the division by n (a power of two) are exact scalings: multiplications by the
+    // exact reciprocals give the same doubles as the divisions, without the FP64 divide sequence
+    o = __dmul_rn(__dsub_rn((double)A, __dmul_rn(s, __dmul_rn((double)C, 0.25))), 1.0 / (double)n);
     const long long base = 16 * ((long long)n * Bs - A * A);
     const long long num = base * g.den - g.num;  // < 2^62 for n = 64
     sse = __ddiv_rn((double)num, __dmul_rn(__dmul_rn(16.0, (double)n), (double)g.den));
@@ -169,7 +171,9 @@ __device__ __forceinline__ void finalize_code(int n, long long A, long long Bs, 
         s = __ddiv_rn(__dmul_rn(4.0, (double)P), (double)Q);
     else
         s = P > 0 ? 1.0 : -1.0;
-    o = __ddiv_rn(__dsub_rn((double)A, __dmul_rn(s, __ddiv_rn((double)C, 4.0))), (double)n);
+    // C / 4 and the division by n (a power of two) are exact scalings: multiplications by the
+    // exact reciprocals give the same doubles as the divisions, without the FP64 divide sequence
+    o = __dmul_rn(__dsub_rn((double)A, __dmul_rn(s, __dmul_rn((double)C, 0.25))), 1.0 / (double)n);
     const long long base = 16 * ((long long)n * Bs - A * A);  // < 2^37
     const __int128 num = (__int128)base * (__int128)g.den - g.num;
     sse = __ddiv_rn(i128_to_double_rn(num), __dmul_rn(__dmul_rn(16.0, (double)n), (double)g.den));

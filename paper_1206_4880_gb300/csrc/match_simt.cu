@@ -211,7 +211,10 @@ __global__ void __launch_bounds__(kSimtThreads)
         g0.num = fb.num;
         g0.den = fb.den;
         Best<B> b{g0, fb.d, fb.t, fb.C, fb.P, fb.Q};
-        const double thr = fb.num < 0 ? -1.0 : i128_to_double_rn(fb.num) / (8.0 * B * B * (double)fb.den);
+        // chunks are flagged when score * (1 + 2^-13) + 2^-16 >= best gain / (8 n), compared as
+        // (...) * 8 n den >= best gain numerator (no FP64 division)
+        const double thr_num = fb.num < 0 ? -1.0 : i128_to_double_rn(fb.num);
+        const double thr_den = 8.0 * B * B * (double)fb.den;
         const long long A = ri.x, Bs = rsumsq[r];
         const int ig = rng_off + i, row = ig % TM;
         const int4 tw = tile_win[ig / TM];
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kSimtThreads)
 #pragma unroll
                 for (int h = 1; h < H; ++h) key = max(key, chunk_max[e + h]);
                 const double s1 = (double)__uint_as_float(key);
-                if (key != 0 && s1 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0 >= thr)
+                if (key != 0 && (s1 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0) * thr_den >= thr_num)
                     sh.flagged[atomicAdd(&sh.n_flagged, 1)] = c;
             }
             __syncthreads();

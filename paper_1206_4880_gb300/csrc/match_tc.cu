@@ -292,6 +292,11 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
                             int4 *__restrict__ tile_items, int32_t *__restrict__ grp, int32_t *gcounters) {
     __shared__ int sc[1024];
     __shared__ int total_chunks_s;
+    // group counters and cursors: in shared memory when they fit (the atomics below are then
+    // cheap), else in the global array
+    constexpr int kSmemGroups = 8192;
+    __shared__ int sgrp[kSmemGroups];
+    int *grp_c = ng_max <= kSmemGroups ? sgrp : grp;
     int tot = 0;
     for (int m = threadIdx.x; m < n_mtiles; m += 1024) tot += n_chunks[m];
     int all = 0;
@@ -301,7 +306,7 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
     const int total = total_chunks_s;
     const int cpi = max(1, min(cpi_cap, (total + target - 1) / max(1, target)));
     const int gdom = cpi * kChunkDom;  // domains per group
-    for (int G = threadIdx.x; G < ng_max; G += 1024) grp[G] = 0;
+    for (int G = threadIdx.x; G < ng_max; G += 1024) grp_c[G] = 0;
     __syncthreads();
     // key slots and chunk ids per tile (tile-major); group counts
     int item_base = 0, chunk_base = 0;
@@ -319,7 +324,7 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
         const int c_off = chunk_base + block_scan_1024(c, sc, &c_all);
         if (m < n_mtiles) {
             tile_items[m] = make_int4(q_off, q, c_off, c);
-            for (int k = 0; k < q; ++k) atomicAdd(&grp[glo + k], 1);
+            for (int k = 0; k < q; ++k) atomicAdd(&grp_c[glo + k], 1);
         }
         item_base += q_all;
         chunk_base += c_all;
@@ -329,10 +334,10 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
     int carry = 0;
     for (int g0 = 0; g0 < ng_max; g0 += 1024) {
         const int G = g0 + threadIdx.x;
-        const int v = G < ng_max ? grp[G] : 0;
+        const int v = G < ng_max ? grp_c[G] : 0;
         int g_all = 0;
         const int off = carry + block_scan_1024(v, sc, &g_all);
-        if (G < ng_max) grp[G] = off;
+        if (G < ng_max) grp_c[G] = off;
         carry += g_all;
     }
     __syncthreads();
@@ -345,7 +350,7 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
             const int G = glo + k;
             const int d0 = max(t.x, G * gdom) / td * td;
             const int d1 = min(t.y, (G + 1) * gdom);
-            const int pos = atomicAdd(&grp[G], 1);
+            const int pos = atomicAdd(&grp_c[G], 1);
             work[pos] = make_int4(m, d0, d1, ti.z + d0 / kChunkDom - c_lo);
             work_slot[pos] = ti.x + k;
         }
@@ -687,19 +692,30 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
         X = (int)acc;  // <= 32 * 255 * 1020 < 2^31
     }
     X += __shfl_xor_sync(0xffffffffu, X, 1);
+    // best isometry of each candidate: with the domain (so Q and C) fixed, the clamped gain grows
+    // with |P|, so it is the largest |P|, ties to the smaller t (lanes 16 c .. 16 c + 15)
     if (has) {
         C = dsum[d];
         Q = 64LL * dsumsq[d] - C * C;
         P = 64LL * (long long)X - A * C;
-        gg = exact_gain(P, Q);
     }
     int bt = t;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const Gain og{__shfl_xor_sync(0xffffffffu, gg.num, off), __shfl_xor_sync(0xffffffffu, gg.den, off)};
-        const int od = __shfl_xor_sync(0xffffffffu, d, off), ot = __shfl_xor_sync(0xffffffffu, bt, off);
-        const long long oP = __shfl_xor_sync(0xffffffffu, P, off), oQ = __shfl_xor_sync(0xffffffffu, Q, off);
-        const long long oC = __shfl_xor_sync(0xffffffffu, C, off);
+    for (int off = 2; off < 16; off <<= 1) {
+        const long long oP = __shfl_xor_sync(0xffffffffu, P, off);
+        const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
+        const long long a0 = P < 0 ? -P : P, a1 = oP < 0 ? -oP : oP;
+        if (a1 > a0 || (a1 == a0 && ot < bt)) {
+            P = oP;
+            bt = ot;
+        }
+    }
+    if (has) gg = exact_gain(P, Q);
+    {  // the better of the two candidates
+        const Gain og{__shfl_xor_sync(0xffffffffu, gg.num, 16), __shfl_xor_sync(0xffffffffu, gg.den, 16)};
+        const int od = __shfl_xor_sync(0xffffffffu, d, 16), ot = __shfl_xor_sync(0xffffffffu, bt, 16);
+        const long long oP = __shfl_xor_sync(0xffffffffu, P, 16), oQ = __shfl_xor_sync(0xffffffffu, Q, 16);
+        const long long oC = __shfl_xor_sync(0xffffffffu, C, 16);
         if (cand_better(og, od, ot, gg, d, bt)) {
             gg = og;
             d = od;
@@ -719,8 +735,8 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
         // the score's slope in p is at most 1, so that moves it by < 2^-21 relatively plus
         // < 2^-18 absolutely
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
-        const double sc = (double)gg.num / (512.0 * (double)gg.den);  // exact gain / 512
-        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0 < sc;
+        // bound < exact gain / 512, compared as bound * 512 den < gain numerator (no division)
+        certified = (u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0) * (512.0 * (double)gg.den) < (double)gg.num;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);

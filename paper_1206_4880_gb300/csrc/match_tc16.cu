@@ -514,15 +514,27 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
         X = (int)acc;  // <= 128 * 255 * 1020 < 2^31
     }
     X += __shfl_xor_sync(0xffffffffu, X, 1);
+    // best isometry of each candidate (largest |P|, ties to the smaller t), then the better of the
+    // two candidates (as in the 8x8 re-evaluation)
     if (has) {
         C = dsum[d];
         Q = 256LL * dsumsq[d] - C * C;
         P = 256LL * (long long)X - A * C;
-        gg = exact_gain_w(P, Q);
     }
     int bt = t;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 2; off < 16; off <<= 1) {
+        const long long oP = __shfl_xor_sync(0xffffffffu, P, off);
+        const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
+        const long long a0 = P < 0 ? -P : P, a1 = oP < 0 ? -oP : oP;
+        if (a1 > a0 || (a1 == a0 && ot < bt)) {
+            P = oP;
+            bt = ot;
+        }
+    }
+    if (has) gg = exact_gain_w(P, Q);
+    {
+        const int off = 16;
         GainW og;
         const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)gg.num, off);
         const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(gg.num >> 64), off);
@@ -544,8 +556,7 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
     bool certified = b1 != 0 && gg.num >= 0;
     if (certified && b2 != 0) {
         const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
-        const double sc = i128_to_double_rn(gg.num) / (2048.0 * (double)gg.den);
-        certified = u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0 < sc;
+        certified = (u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0) * (2048.0 * (double)gg.den) < i128_to_double_rn(gg.num);
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
