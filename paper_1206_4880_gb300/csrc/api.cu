@@ -167,8 +167,9 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
     Carver c(ws, cap);
     long long R_pad_tot = 0, Dn_aux_tot = 0, mt_tot = 0, chunks_tot = 0;
     const int B = gs[0].B, TM = tile_rows(B), npx = B * B, H = B == 16 ? 1 : 2, NS = n_scales(B);
+    // per image 8 int32 zeroed together at the start of an encode: [0] re-search count, [2..3] the
+    // match count (int64), [4..7] the FD extent reduction words (2 x uint64)
     int32_t *img_counters = c.take<int32_t>(8 * (size_t)n);
-    long long *img_matches = c.take<long long>((size_t)n);
     for (int k = 0; k < n; ++k) {
         const Geo &g = gs[k];
         EncodeBufs *b = &bs[k];
@@ -199,7 +200,6 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->dom_fd = c.take<double>(g.Dn);
         b->dom_bin = c.take<uint8_t>(g.Dn);
         b->fd_extent = c.take<double>(2);
-        b->extent_bits = c.take<unsigned long long>(2);
         b->dom_S = c.take<uint16_t>((size_t)g.Dn * npx);
         b->dom_order = c.take<int32_t>(g.Dn);
         b->bin_off = c.take<int32_t>(kMaxClasses + 2);
@@ -216,7 +216,8 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->fallback = c.take<int32_t>(g.R);
         b->fb_best = c.take<FallbackBest>(g.R);
         b->counters = img_counters ? img_counters + 8 * k : nullptr;
-        b->matches = img_matches ? img_matches + k : nullptr;
+        b->matches = img_counters ? reinterpret_cast<long long *>(img_counters + 8 * k + 2) : nullptr;
+        b->extent_bits = img_counters ? reinterpret_cast<unsigned long long *>(img_counters + 8 * k + 4) : nullptr;
     }
     tb->B = B;
     tb->tm = TM;
@@ -263,12 +264,12 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
     return c.off + 256;
 }
 
-__global__ void k_write_info(const long long *matches, const int32_t *img_counters, int n,
-                             const int32_t *gcounters, fic_encode_info *info) {
+// img_counters: 8 int32 per image ([0] re-search count, [2..3] match count, see encode_workspace)
+__global__ void k_write_info(const int32_t *img_counters, int n, const int32_t *gcounters, fic_encode_info *info) {
     long long m = 0;
     int fb = 0;
     for (int k = 0; k < n; ++k) {
-        m += matches[k];
+        m += *reinterpret_cast<const long long *>(img_counters + 8 * k + 2);
         fb += img_counters[8 * k];
     }
     info->matches = m;
@@ -279,7 +280,7 @@ __global__ void k_write_info(const long long *matches, const int32_t *img_counte
 }
 
 cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encode_info *info, cudaStream_t st) {
-    k_write_info<<<1, 1, 0, st>>>(b[0].matches, b[0].counters, n, tb.gcounters, info);
+    k_write_info<<<1, 1, 0, st>>>(b[0].counters, n, tb.gcounters, info);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -373,6 +374,7 @@ fic_status fic_classify(const uint8_t *img, const fic_geom *gm, const fic_params
     b.dom_bin = out->dom_bin;
     b.fd_extent = out->fd_extent;
     g_launches = 0;
+    FIC_TRY(cudaMemsetAsync(b.counters, 0, 8 * sizeof(int32_t), (cudaStream_t)stream), "memset");
     FIC_TRY(launch_classify(img, g, b, (cudaStream_t)stream), "classify");
     return FIC_OK;
 }
@@ -406,6 +408,7 @@ fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *gm, const f
     b.win_lo = out->win_lo;
     b.win_hi = out->win_hi;
     g_launches = 0;
+    FIC_TRY(cudaMemsetAsync(b.counters, 0, 8 * sizeof(int32_t), (cudaStream_t)stream), "memset");
     FIC_TRY(launch_pools(g, b, (cudaStream_t)stream), "build_pools");
     return FIC_OK;
 }

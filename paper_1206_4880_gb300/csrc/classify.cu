@@ -149,8 +149,9 @@ __global__ void k_range_stats(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
 }
 
 // One thread per domain: contracted block of 2x2 sums S (kept for packing and exact search),
-// C = sum S, E = sum S^2, N_2, N_4, FD; the block's least/largest FD go to extent_bits by
-// atomic min/max on the bit patterns (FD > 0, so they order like the values).
+// C = sum S, E = sum S^2, N_2, N_4, FD; the block's largest FD and the complement of its least
+// FD go to extent_bits by atomicMax on the bit patterns (FD > 0, so they order like the values;
+// both words start at zero).
 __global__ void k_dom_stats(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
                             uint16_t *__restrict__ domS, int32_t *__restrict__ dsum,
                             int32_t *__restrict__ dsumsq, int32_t *__restrict__ dcounts,
@@ -221,7 +222,7 @@ __global__ void k_dom_stats(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
         fbits_max = max(fbits_max, __shfl_xor_sync(0xffffffffu, fbits_max, off));
     }
     if ((threadIdx.x & 31) == 0 && fbits_max != 0ull) {
-        atomicMin(&extent_bits[0], fbits_min);
+        atomicMax(&extent_bits[0], ~fbits_min);  // the least FD as the largest complement
         atomicMax(&extent_bits[1], fbits_max);
     }
 }
@@ -231,7 +232,7 @@ __global__ void k_bins(Geo g, const double *__restrict__ rfd, const double *__re
                        const unsigned long long *__restrict__ extent_bits, double *fd_extent,
                        uint8_t *__restrict__ rbin, uint8_t *__restrict__ dbin) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const double Fl = __longlong_as_double((long long)extent_bits[0]);
+    const double Fl = __longlong_as_double((long long)~extent_bits[0]);
     const double Fm = __longlong_as_double((long long)extent_bits[1]);
     if (i == 0) {
         fd_extent[0] = Fl;
@@ -386,7 +387,7 @@ __global__ void k_dom_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
         fbits_max = max(fbits_max, __shfl_xor_sync(0xffffffffu, fbits_max, off));
     }
     if ((threadIdx.x & 31) == 0 && fbits_max != 0ull) {
-        atomicMin(&extent_bits[0], fbits_min);
+        atomicMax(&extent_bits[0], ~fbits_min);  // the least FD as the largest complement
         atomicMax(&extent_bits[1], fbits_max);
     }
 }
@@ -394,10 +395,8 @@ __global__ void k_dom_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
 cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                             cudaStream_t st) {
     const Log2Tab &L = log2_table();
-    cudaError_t e;
-    // extent_bits[0] = all ones (min identity), extent_bits[1] = 0 (max identity)
-    if ((e = cudaMemsetAsync(b.extent_bits, 0xff, sizeof(unsigned long long), st))) return e;
-    if ((e = cudaMemsetAsync(b.extent_bits + 1, 0, sizeof(unsigned long long), st))) return e;
+    // extent_bits = {complement of the least FD's bits, the largest FD's bits}, both reduced by
+    // atomicMax from zero: the caller zeroes them with the image's counters
     if (g.B == 16) {
         k_range_stats16<<<(g.R + 127) / 128, 128, 0, st>>>(img, g, L, b.range_sum, b.range_sumsq,
                                                            b.range_counts, b.range_fd);

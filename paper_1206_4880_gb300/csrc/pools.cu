@@ -224,7 +224,6 @@ cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
         if ((e = counting_sort(b.range_key, g.R, fr.n, b.sort_counts, b.sort_offs, b.range_order, b.rbin_off,
                                st)))
             return e;
-        if ((e = cudaMemsetAsync(b.matches, 0, sizeof(long long), st))) return e;
         k_windows_literal<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_fd, b.fd_extent, vt, fr.n, b.bin_off,
                                                              b.win_lo, b.win_hi, b.matches);
         ++g_launches;
@@ -236,7 +235,6 @@ cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
     if ((e = counting_sort(b.range_bin, g.R, g.K, b.sort_counts, b.sort_offs, b.range_order,
                            b.rbin_off, st)))
         return e;
-    if ((e = cudaMemsetAsync(b.matches, 0, sizeof(long long), st))) return e;
     k_windows<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_bin, b.bin_off, b.win_lo, b.win_hi,
                                                  b.matches);
     ++g_launches;
@@ -260,8 +258,6 @@ cudaError_t launch_pools_ranges_sort(const Geo &g, const EncodeBufs &b, cudaStre
 }
 
 cudaError_t launch_pools_windows(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(b.matches, 0, sizeof(long long), st))) return e;
     k_windows<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_bin, b.bin_off, b.win_lo, b.win_hi, b.matches);
     ++g_launches;
     return cudaGetLastError();
