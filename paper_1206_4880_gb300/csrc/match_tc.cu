@@ -69,7 +69,7 @@ struct TcShared {
     uint8_t B[kStages][kBBytes];
     uint8_t A1[2][kA1Bytes];
     uint8_t B1[kStages][kB1Bytes];
-    float4 aux[2][kChunkDom];  // per-domain constants of the current and next work item
+    float4 aux[2][kChunkDom / 2];  // (Q / 256, 128 / Q) of two domains per entry: current, next chunk
     unsigned long long full_a[2], empty_a[2], full_b[kStages], empty_b[kStages], tfull[2],
         tempty[2], aux_ready[2], drain;
     uint32_t tmem_base;
@@ -91,9 +91,22 @@ __device__ __forceinline__ float absmax8(const uint32_t *v) {
     return fmaxf(fmaxf(a, b), fmaxf(c, d));
 }
 
+// Key of domain l (compile time, < 16) of a half tile whose first domain sits at offset jrel (a
+// multiple of 16) of its chunk: the score's bits with the low 9 replaced by 511 - jrel - l. base =
+// 511 - jrel has its low 4 bits set and nothing above bit 8, so 511 - jrel - l = base ^ l and the
+// whole key is one lop3 of (bits, base, 0xFFFFFE00 | l) with the truth table
+// (a & c & ~b) | (b & ~c) = 0x64.
+template <int L>
+__device__ __forceinline__ uint32_t chunk_key(float sc, uint32_t base) {
+    uint32_t key;
+    asm("lop3.b32 %0, %1, %2, %3, 0x64;" : "=r"(key) : "r"(__float_as_uint(sc)), "r"(base), "n"(0xFFFFFE00u | L));
+    return key;
+}
+
 template <bool MASK>
 __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int jh, int jrel, int lo_r, int hi_r,
                                          uint32_t &t1, uint32_t &t2) {
+    const uint32_t base = 511u - (uint32_t)jrel;
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
@@ -109,13 +122,23 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int l = 4 * c + q;
-            const float4 a = auxp[l];
+            // two domains' (Q / 256, 128 / Q) per 16-byte shared load
+            const float4 a2 = auxp[l >> 1];
+            const float qy = (l & 1) ? a2.z : a2.x, qz = (l & 1) ? a2.w : a2.y;
             // accumulator = P / 64 up to the FP32 accumulation error, which k_reeval's
             // certification margin covers
             const float p = absmax8(cur + 8 * q);
-            const float mm = fminf(p, a.y);
-            const float sc = fmaf(mm, mm * a.z, p - mm);
-            uint32_t key = (__float_as_uint(sc) & 0xFFFFFE00u) | (uint32_t)(511 - jrel - l);
+            const float mm = fminf(p, qy);
+            const float sc = fmaf(mm, mm * qz, p - mm);
+            uint32_t key;
+            switch (l) {
+#define FIC_KEY_CASE(L) \
+    case L: key = chunk_key<L>(sc, base); break;
+                FIC_KEY_CASE(0) FIC_KEY_CASE(1) FIC_KEY_CASE(2) FIC_KEY_CASE(3) FIC_KEY_CASE(4) FIC_KEY_CASE(5)
+                FIC_KEY_CASE(6) FIC_KEY_CASE(7) FIC_KEY_CASE(8) FIC_KEY_CASE(9) FIC_KEY_CASE(10) FIC_KEY_CASE(11)
+                FIC_KEY_CASE(12) FIC_KEY_CASE(13) FIC_KEY_CASE(14) default: key = chunk_key<15>(sc, base); break;
+#undef FIC_KEY_CASE
+            }
             if (MASK) {
                 const int j = jh + l;
                 key = (j >= lo_r && j < hi_r) ? key : 0u;
@@ -173,11 +196,11 @@ __global__ void k_pack_ranges(Geo g, const uint8_t *__restrict__ img, const int3
 }
 
 // One thread per (sorted domain j, isometry t, row y): B_mat row 8j+t = T_t(S_{dom_order[j]}) -
-// round(C / 64); dom_aux[j] = (|gamma|, Q / 256, 128 / Q or 0, 0) with gamma = C - 64 round(C/64).
+// round(C / 64); dom_aux2[j] = (Q / 256, 128 / Q or 0), the constants of the epilogue's clamped gain.
 // Entries j >= Dn are zero.
 __global__ void k_pack_domains(Geo g, const uint16_t *__restrict__ domS, const int32_t *__restrict__ dom_order,
                                const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq, int n_pad,
-                               __half *__restrict__ B_mat, uint4 *__restrict__ B1, float4 *__restrict__ dom_aux) {
+                               __half *__restrict__ B_mat, uint4 *__restrict__ B1, float2 *__restrict__ dom_aux2) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = (int)(gid >> 6), t = (int)(gid >> 3) & 7, y = (int)gid & 7;
     if (j >= n_pad) return;
@@ -206,16 +229,14 @@ __global__ void k_pack_domains(Geo g, const uint16_t *__restrict__ domS, const i
         if (t == 0 && y == 0) {
             const long long C = dsum[d];
             const long long Q = 64LL * dsumsq[d] - C * C;
-            const int gamma = (int)C - 64 * cbar;
-            dom_aux[j] = make_float4(0.f, (float)Q * (1.0f / 256.0f), Q > 0 ? 128.0f / (float)Q : 0.f, 0.f);
-            (void)gamma;
+            dom_aux2[j] = make_float2((float)Q * (1.0f / 256.0f), Q > 0 ? 128.0f / (float)Q : 0.f);
         }
     } else {
         if (y == 0) {
             B1[2 * ((size_t)j * 8 + t)] = make_uint4(0, 0, 0, 0);
             B1[2 * ((size_t)j * 8 + t) + 1] = make_uint4(0, 0, 0, 0);
         }
-        if (t == 0 && y == 0) dom_aux[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t == 0 && y == 0) dom_aux2[j] = make_float2(0.f, 0.f);
     }
     reinterpret_cast<uint4 *>(B_mat + ((size_t)j * 8 + t) * 64)[y] = pk;
 }
@@ -504,8 +525,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // per-domain constants of this chunk into shared memory (double-buffered by chunk
                 // parity; a thread reaches chunk lc + 2 only after every thread has left chunk lc)
                 const int ab = lc & 1;
-                for (int k = ew * 32 + lane; k < ntc * kTileDom; k += 32 * kEpiWarps)
-                    sh.aux[ab][k] = __ldg(&dom_aux[jc + k]);
+                for (int k = ew * 32 + lane; k < ntc * kTileDom / 2; k += 32 * kEpiWarps)
+                    sh.aux[ab][k] = __ldg(&dom_aux[jc / 2 + k]);  // dom_aux holds float2 pairs here
                 mbar_arrive(&sh.aux_ready[ab]);
                 ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (lc >> 1) & 1, abort_flag));
                 if (!ok) break;
@@ -518,7 +539,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (!ok) break;
                     tc_fence_after();
                     const int jh = jc + k * kTileDom + half * (kTileDom / 2);
-                    const float4 *auxp = &sh.aux[ab][k * kTileDom + half * (kTileDom / 2)];
+                    const float4 *auxp = &sh.aux[ab][(k * kTileDom + half * (kTileDom / 2)) / 2];
                     const uint32_t taddr = tbase + acc * kTileN;
                     const int jrel = jrel0 + k * kTileDom;
                     if (jh >= f_lo && jh + kTileDom / 2 <= f_hi)
@@ -815,7 +836,9 @@ cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, c
         const long long n = (long long)b.Dn_aux * 64;
         k_pack_domains<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, b.dom_S, b.dom_order, b.dom_sum,
                                                                    b.dom_sumsq, b.Dn_aux, b.B_mat, (uint4 *)b.B1_mat,
-                                                                   b.dom_aux);
+                                                                   // float2 pairs indexed by batch-wide domain position
+                                                                   reinterpret_cast<float2 *>(b.dom_aux - b.dom_off) +
+                                                                       b.dom_off);
         ++g_launches;
     }
     return cudaGetLastError();
