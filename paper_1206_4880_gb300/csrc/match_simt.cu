@@ -3,10 +3,9 @@
 // (restricted to the domain chunks that could still hold the winner).
 //
 // For a range r, a domain d of its pool (Section 3.1 Eq. 3) and an isometry t, the correlation
-// X_t = sum_p r[p] * (T_t S_d)[p] is formed exactly (integer products <= 255*1020; FP32 FMA sums
-// over at most 64 pixels stay below 2^24 and are exact, and B = 16 adds four such partial sums in
-// integers), then P = n X - A C and Q = n E - C^2 give the exact least-squares gain (Section 1's
-// intensity map with |s| <= 1); the best (gain, -d, -t) wins.
+// X_t = sum_p r[p] * (T_t S_d)[p] is formed exactly in 32-bit integers (packed byte x halfword
+// dot products), then P = n X - A C and Q = n E - C^2 give the exact least-squares gain
+// (Section 1's intensity map with |s| <= 1); the best (gain, -d, -t) wins.
 //
 // One CTA per range: the range's 8 inverse-permuted copies sit in shared memory, each thread
 // walks every 256th domain, and a shared-memory tree picks the block's best.
@@ -23,8 +22,8 @@ constexpr int kSimtThreads = 256;
 template <int B>
 struct ScanShared {
     using G = typename FitOf<B>::G;
-    // rp[t][q] = r[p] with src_t(p) = q, so that X_t = sum_q S[q] * rp[t][q]
-    float rp[8][B * B];
+    // rp[t][q] = r[p] with src_t(p) = q, so that X_t = sum_q S[q] * rp[t][q]; bytes, 16-aligned
+    alignas(16) uint8_t rp[8][B * B];
     G g[kSimtThreads];
     long long P[kSimtThreads], Q[kSimtThreads];
     int d[kSimtThreads], t[kSimtThreads], C[kSimtThreads];
@@ -44,7 +43,7 @@ __device__ __forceinline__ void load_range(ScanShared<B> &sh, const Geo &g, cons
     for (int p = threadIdx.x; p < B * B; p += kSimtThreads) {
         const int y = p / B, x = p % B;
         const int ry = (r / g.nRx) * B, rx = (r % g.nRx) * B;
-        const float v = (float)img[(size_t)(ry + y) * g.pitch + rx + x];
+        const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             int sy, sx;
@@ -54,57 +53,42 @@ __device__ __forceinline__ void load_range(ScanShared<B> &sh, const Geo &g, cons
     }
 }
 
-// X_t over source indices [q0, q0 + 64) of domain d (a 64-entry slice of S), exact in FP32.
-template <int B>
-__device__ __forceinline__ void slice_dot(const ScanShared<B> &sh, const uint16_t *__restrict__ Sd, int q0,
-                                          float (&acc)[8]) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(Sd + q0);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint4 u = __ldg(src + k);
-        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float s0 = (float)(w4[2 * h] & 0xffffu), s1 = (float)(w4[2 * h] >> 16);
-            const float s2 = (float)(w4[2 * h + 1] & 0xffffu), s3 = (float)(w4[2 * h + 1] >> 16);
-            const int q = q0 + 8 * k + 4 * h;
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const float4 rv = *reinterpret_cast<const float4 *>(&sh.rp[t][q]);
-                acc[t] = fmaf(s0, rv.x, acc[t]);
-                acc[t] = fmaf(s1, rv.y, acc[t]);
-                acc[t] = fmaf(s2, rv.z, acc[t]);
-                acc[t] = fmaf(s3, rv.w, acc[t]);
-            }
-        }
-    }
-}
-
-// Exact evaluation of domain d under all 8 isometries against the range in sh.rp.
+// Exact evaluation of domain d under all 8 isometries against the range in sh.rp: X_t = sum_q
+// S[q] rp[t][q] in unsigned integers (X <= B^2 * 255 * 1020 < 2^31), two products per __dp2a (a
+// pair of 16-bit sums against two of the range's bytes), 16 source indices per step.
 template <int B>
 __device__ __forceinline__ void scan_domain(const ScanShared<B> &sh, int d, long long A,
                                             const uint16_t *__restrict__ domS,
                                             const int32_t *__restrict__ dsum,
                                             const int32_t *__restrict__ dsumsq, Best<B> &b) {
     constexpr int n = B * B;
-    const uint16_t *Sd = domS + (size_t)d * n;
-    int X[8];
+    const uint4 *Sd = reinterpret_cast<const uint4 *>(domS + (size_t)d * n);
+    unsigned X[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) X[t] = 0;
-#pragma unroll 1
-    for (int q0 = 0; q0 < n; q0 += 64) {
-        float acc[8];
+#pragma unroll(B == 8 ? 4 : 2)
+    for (int q0 = 0; q0 < n; q0 += 16) {
+        const uint4 sa = __ldg(Sd + q0 / 8), sb = __ldg(Sd + q0 / 8 + 1);  // S[q0 .. q0 + 15]
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = 0.f;
-        slice_dot<B>(sh, Sd, q0, acc);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) X[t] += (int)acc[t];
+        for (int t = 0; t < 8; ++t) {
+            const uint4 r = *reinterpret_cast<const uint4 *>(&sh.rp[t][q0]);  // rp[t][q0 .. q0 + 15]
+            unsigned acc = X[t];
+            acc = __dp2a_lo(sa.x, r.x, acc);
+            acc = __dp2a_hi(sa.y, r.x, acc);
+            acc = __dp2a_lo(sa.z, r.y, acc);
+            acc = __dp2a_hi(sa.w, r.y, acc);
+            acc = __dp2a_lo(sb.x, r.z, acc);
+            acc = __dp2a_hi(sb.y, r.z, acc);
+            acc = __dp2a_lo(sb.z, r.w, acc);
+            acc = __dp2a_hi(sb.w, r.w, acc);
+            X[t] = acc;
+        }
     }
     const long long C = dsum[d];
     const long long Q = (long long)n * dsumsq[d] - C * C;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        const long long P = (long long)n * X[t] - A * C;
+        const long long P = (long long)n * (long long)X[t] - A * C;
         const auto gg = FitOf<B>::gain(P, Q);
         if (cand_better(gg, d, t, b.g, b.d, b.t)) {
             b.g = gg;
