@@ -464,6 +464,9 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(launch_pools_windows(g[0], b[0], sp1->s[0]), "pools");
         FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], sp1->s[0], 1) : launch_pack(imgs[0], g[0], b[0], sp1->s[0], 1),
                 "pack");
+        // the work list needs only the packed ranges' windows: it runs beside the domain packing
+        FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), sp1->s[0]),
+                "work_list");
         FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], st, 2) : launch_pack(imgs[0], g[0], b[0], st, 2), "pack");
         FIC_TRY(side_join(st, sp1, 1), "join");
     } else if (ns) {
@@ -497,8 +500,9 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(mark(4), "event");
         FIC_TRY(mark(5), "event");
     } else {
-        FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), st),
-                "work_list");
+        if (!sp1)
+            FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), st),
+                    "work_list");
         FIC_TRY(mark(3), "event");
         FIC_TRY(b16 ? launch_match_tc16(tb, sms, st) : launch_match_tc(tb, sms, st), "match_tc");
         FIC_TRY(mark(4), "event");
