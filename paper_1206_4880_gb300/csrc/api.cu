@@ -247,7 +247,7 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
     tb->work_slot = c.take<int32_t>((size_t)tb->max_items);
     tb->grp = c.take<int32_t>((size_t)tb->ng_max);
     tb->cand = c.take<unsigned long long>((size_t)tb->max_items * TM * H * 2);
-    tb->chunk_max = c.take<uint32_t>((size_t)chunks_tot * TM * H);
+    tb->chunk_max = c.take<uint32_t>((size_t)chunks_tot * TM * H * 2);
     tb->gcounters = c.take<int32_t>(8);
     for (int k = 0; k < n; ++k) {
         EncodeBufs *b = &bs[k];

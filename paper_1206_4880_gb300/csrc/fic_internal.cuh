@@ -45,6 +45,34 @@ __host__ __device__ __forceinline__ void iso_src(int B, int t, int y, int x, int
     sx = fx ? N - v : v;
 }
 
+// Four layouts of a block S (side B, N = B - 1) in shared memory: L0 as stored, L1 transposed,
+// L2 with each row reversed, L3[a][b] = S[N - b][a]. Row y of the isometry T_t(S) of iso_src is
+// then one contiguous row: row (swap ? fx : fy) ? N - y : y of layout swap + 2 (swap ? fy : fx).
+// stage_layouts places element e = B a + b of S in all four.
+template <int B>
+__device__ __forceinline__ void stage_layouts(uint16_t (*L)[B * B], int e, uint16_t v) {
+    const int a = e / B, b = e % B, N = B - 1;
+    L[0][a * B + b] = v;
+    L[1][b * B + a] = v;
+    L[2][a * B + N - b] = v;
+    L[3][b * B + N - a] = v;
+}
+template <int B>
+__device__ __forceinline__ const uint16_t *iso_row(const uint16_t (*L)[B * B], int t, int y) {
+    const int swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
+    const int row = (swap ? fx : fy) ? B - 1 - y : y;
+    return L[swap + 2 * (swap ? fy : fx)] + row * B;
+}
+
+// FP16 pair (v0 - c, v1 - c) from packed 16-bit integers v0, v1 in [0, 1023] (pair = v0 | v1 << 16)
+// and cpair = (0x6400 + c) * 0x10001, c in [0, 1023]: 0x6400 + v is the FP16 pattern of 1024 + v,
+// and the difference of two such values is an integer of magnitude < 1024, exact in FP16.
+__device__ __forceinline__ uint32_t centred_h2(uint32_t pair, uint32_t cpair) {
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(pair + 0x64006400u), "r"(cpair));
+    return r;
+}
+
 // ----------------------------------------------------------------------------------------
 // Exact least-squares gain of one candidate (B = 8, n = 64).
 // With P = n X - A C and Q = n E - C^2, 16 n SSE = 16 (n Bs - A^2) - gain where
@@ -272,7 +300,7 @@ struct TcBatch {
     int32_t *grp;          // [ng_max] per domain group: item count, then schedule cursor
     unsigned long long *cand;  // top-2 keys: range tile m owns [first slot, + items) x tm x halves x 2
                                // entries, ordered (row, item, half, key)
-    uint32_t *chunk_max;   // [max_chunks][tm rows][halves] best key per chunk
+    uint32_t *chunk_max;   // [max_chunks][tm rows][halves][2] best key, runner-up score per chunk
     int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks, [4] chunks per group
     int R_pad, Dn_aux, n_mtiles, max_items, max_chunks, ng_max, cpi_cap;
 };

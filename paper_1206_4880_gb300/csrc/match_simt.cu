@@ -28,7 +28,9 @@ struct ScanShared {
     long long P[kSimtThreads], Q[kSimtThreads];
     int d[kSimtThreads], t[kSimtThreads], C[kSimtThreads];
     int flagged[kSimtThreads];
-    int n_flagged;
+    int single[2 * kSimtThreads];
+    int n_flagged, n_single;
+    float thr;
 };
 
 template <int B>
@@ -138,6 +140,13 @@ __device__ __forceinline__ void reduce_and_write(ScanShared<B> &sh, const Best<B
     __syncthreads();
 }
 
+// A chunk key's bound reaches the re-search threshold: score * (1 + 2^-13) + 2^-16 >= thr,
+// evaluated rounded up (thr itself is rounded down), so no chunk that exact arithmetic would flag
+// is missed.
+__device__ __forceinline__ bool reaches(uint32_t score_bits, float thr) {
+    return __fmaf_ru(__uint_as_float(score_bits), 1.0f + 1.0f / 8192.0f, 1.0f / 65536.0f) >= thr;
+}
+
 template <class G>
 __device__ __forceinline__ G no_gain() {
     G g;
@@ -171,9 +180,9 @@ __global__ void __launch_bounds__(kSimtThreads)
 // the exact best of its evaluated candidates; the 512-domain chunks of the range's tile whose best
 // FP32 score could still reach that best (score * (1 + 2^-13) + 2^-16 >= best gain / (8 n), the
 // bound the re-evaluation certifies with) are scanned exactly. TM ranges per tile, H key columns
-// per row (chunk_max layout [chunk][TM][H]).
+// per row (chunk_max layout [chunk][TM][H] of (best key, runner-up score bits)).
 template <int B, int TM, int H>
-__global__ void __launch_bounds__(kSimtThreads)
+__global__ void __launch_bounds__(kSimtThreads, 2)
     k_rescan(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
              const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
              const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
@@ -195,33 +204,48 @@ __global__ void __launch_bounds__(kSimtThreads)
         g0.num = fb.num;
         g0.den = fb.den;
         Best<B> b{g0, fb.d, fb.t, fb.C, fb.P, fb.Q};
-        // chunks are flagged when score * (1 + 2^-13) + 2^-16 >= best gain / (8 n), compared as
-        // (...) * 8 n den >= best gain numerator (no FP64 division)
-        const double thr_num = fb.num < 0 ? -1.0 : i128_to_double_rn(fb.num);
-        const double thr_den = 8.0 * B * B * (double)fb.den;
+        // chunks are flagged when score * (1 + 2^-13) + 2^-16 >= best gain / (8 n), evaluated in
+        // FP32 with the left side rounded up and the threshold rounded down (so a superset of the
+        // exactly flagged chunks; the FP64 threshold's own rounding, 2^-52 relatively, lies well
+        // inside the margin's slack). One thread forms the threshold: FP64 throughput is low.
+        if (threadIdx.x == 0)
+            sh.thr = fb.num < 0 ? -1.0f
+                                : __double2float_rd(__ddiv_rn(i128_to_double_rn(fb.num), 8.0 * B * B * (double)fb.den));
         const long long A = ri.x, Bs = rsumsq[r];
         const int ig = rng_off + i, row = ig % TM;
         const int4 tw = tile_win[ig / TM];
         const int4 ti = tile_items[ig / TM];
         const int nch = ti.w;
-        // flag the chunks whose best score reaches the threshold (256 chunks at a time, in
-        // parallel), then scan the flagged chunks' domains with all threads
+        const int c_lo = tw.x / kChunkDom;  // the tile's first chunk of the absolute grid
+        // the chunks, 256 at a time in parallel: a half (key column) whose runner-up
+        // score reaches the threshold has its whole chunk scanned; one whose best score alone
+        // reaches it contributes only that best domain (every other domain of the half scores at
+        // most the runner-up); then all threads scan the flagged chunks' and single domains
         for (int base = 0; base < nch; base += kSimtThreads) {
-            if (threadIdx.x == 0) sh.n_flagged = 0;
+            if (threadIdx.x == 0) sh.n_flagged = sh.n_single = 0;
             __syncthreads();
+            const float thr = sh.thr;
             const int c = base + threadIdx.x;
             if (c < nch) {
-                const size_t e = ((size_t)(ti.z + c) * TM + row) * H;
-                uint32_t key = chunk_max[e];
+                const uint2 *e = reinterpret_cast<const uint2 *>(chunk_max) + ((size_t)(ti.z + c) * TM + row) * H;
+                uint2 k[H];  // (best key, runner-up score bits) per half
+                bool full = false;
 #pragma unroll
-                for (int h = 1; h < H; ++h) key = max(key, chunk_max[e + h]);
-                const double s1 = (double)__uint_as_float(key);
-                if (key != 0 && (s1 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0) * thr_den >= thr_num)
+                for (int h = 0; h < H; ++h) {
+                    k[h] = e[h];
+                    full = full || (k[h].y != 0 && reaches(k[h].y, thr));
+                }
+                if (full) {
                     sh.flagged[atomicAdd(&sh.n_flagged, 1)] = c;
+                } else {
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        if (k[h].x != 0 && reaches(k[h].x & 0xFFFFFE00u, thr))
+                            sh.single[atomicAdd(&sh.n_single, 1)] = (c + c_lo) * kChunkDom + 511 - (int)(k[h].x & 511u);
+                }
             }
             __syncthreads();
-            const int nf = sh.n_flagged;
-            const int c_lo = tw.x / kChunkDom;  // the tile's first chunk of the absolute grid
+            const int nf = sh.n_flagged, nsg = sh.n_single;
             for (int f = 0; f < nf; ++f) {
                 const int cc = sh.flagged[f] + c_lo;
                 const int j0 = max(ri.y, cc * kChunkDom);
@@ -229,6 +253,8 @@ __global__ void __launch_bounds__(kSimtThreads)
                 for (int j = j0 + threadIdx.x; j < j1; j += kSimtThreads)
                     scan_domain<B>(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
             }
+            for (int f = threadIdx.x; f < nsg; f += kSimtThreads)
+                scan_domain<B>(sh, dom_order[sh.single[f] - dom_off], A, domS, dsum, dsumsq, b);
             __syncthreads();
         }
         reduce_and_write<B>(sh, b, r, A, Bs, out);
@@ -250,11 +276,11 @@ cudaError_t launch_match_simt(const uint8_t *img, const Geo &g, const EncodeBufs
 cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, int num_sms, cudaStream_t st) {
     if (g.B == 16)
-        k_rescan<16, 2 * kTileM, 1><<<4 * num_sms, kSimtThreads, 0, st>>>(
+        k_rescan<16, 2 * kTileM, 1><<<8 * num_sms, kSimtThreads, 0, st>>>(
             g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.rng_info, b.rng_off, b.dom_off,
             tb.tile_win, tb.tile_items, tb.chunk_max, b.fallback, b.fb_best, b.counters, out);
     else
-        k_rescan<8, kTileM, 2><<<4 * num_sms, kSimtThreads, 0, st>>>(
+        k_rescan<8, kTileM, 2><<<8 * num_sms, kSimtThreads, 0, st>>>(
             g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.rng_info, b.rng_off, b.dom_off,
             tb.tile_win, tb.tile_items, tb.chunk_max, b.fallback, b.fb_best, b.counters, out);
     ++g_launches;

@@ -84,11 +84,10 @@ constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 // domain's offset in its 512-domain chunk, jrel + l); t1, t2 keep the two largest keys of the
 // chunk. MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
 __device__ __forceinline__ float absmax8(const uint32_t *v) {
-    const float a = fmaxf(fabsf(__uint_as_float(v[0])), fabsf(__uint_as_float(v[1])));
-    const float b = fmaxf(fabsf(__uint_as_float(v[2])), fabsf(__uint_as_float(v[3])));
-    const float c = fmaxf(fabsf(__uint_as_float(v[4])), fabsf(__uint_as_float(v[5])));
-    const float d = fmaxf(fabsf(__uint_as_float(v[6])), fabsf(__uint_as_float(v[7])));
-    return fmaxf(fmaxf(a, b), fmaxf(c, d));
+    const float a = max3_abs(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
+    const float b = max3_abs(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5]));
+    const float c = max3_abs(__uint_as_float(v[6]), __uint_as_float(v[7]), a);
+    return fmaxf(b, c);
 }
 
 // Key of domain l (compile time, < 16) of a half tile whose first domain sits at offset jrel (a
@@ -120,30 +119,35 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
         }
         const uint32_t *cur = (c & 1) ? vb : va;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int l = 4 * c + q;
+        for (int q2 = 0; q2 < 2; ++q2) {
             // two domains' (Q / 256, 128 / Q) per 16-byte shared load
-            const float4 a2 = auxp[l >> 1];
-            const float qy = (l & 1) ? a2.z : a2.x, qz = (l & 1) ? a2.w : a2.y;
-            // accumulator = P / 64 up to the FP32 accumulation error, which k_reeval's
-            // certification margin covers
-            const float p = absmax8(cur + 8 * q);
-            const float mm = fminf(p, qy);
-            const float sc = fmaf(mm, mm * qz, p - mm);
-            uint32_t key;
-            switch (l) {
+            const float4 a2 = auxp[2 * c + q2];
+            uint32_t k[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = 2 * q2 + h, l = 4 * c + q;
+                const float qy = h ? a2.z : a2.x, qz = h ? a2.w : a2.y;
+                // accumulator = P / 64 up to the FP32 accumulation error, which k_reeval's
+                // certification margin covers
+                const float p = absmax8(cur + 8 * q);
+                const float mm = fminf(p, qy);
+                const float sc = fmaf(mm, mm * qz, p - mm);
+                uint32_t key;
+                switch (l) {
 #define FIC_KEY_CASE(L) \
     case L: key = chunk_key<L>(sc, base); break;
-                FIC_KEY_CASE(0) FIC_KEY_CASE(1) FIC_KEY_CASE(2) FIC_KEY_CASE(3) FIC_KEY_CASE(4) FIC_KEY_CASE(5)
-                FIC_KEY_CASE(6) FIC_KEY_CASE(7) FIC_KEY_CASE(8) FIC_KEY_CASE(9) FIC_KEY_CASE(10) FIC_KEY_CASE(11)
-                FIC_KEY_CASE(12) FIC_KEY_CASE(13) FIC_KEY_CASE(14) default: key = chunk_key<15>(sc, base); break;
+                    FIC_KEY_CASE(0) FIC_KEY_CASE(1) FIC_KEY_CASE(2) FIC_KEY_CASE(3) FIC_KEY_CASE(4) FIC_KEY_CASE(5)
+                    FIC_KEY_CASE(6) FIC_KEY_CASE(7) FIC_KEY_CASE(8) FIC_KEY_CASE(9) FIC_KEY_CASE(10) FIC_KEY_CASE(11)
+                    FIC_KEY_CASE(12) FIC_KEY_CASE(13) FIC_KEY_CASE(14) default: key = chunk_key<15>(sc, base); break;
 #undef FIC_KEY_CASE
+                }
+                if (MASK) {
+                    const int j = jh + l;
+                    key = (j >= lo_r && j < hi_r) ? key : 0u;
+                }
+                k[h] = key;
             }
-            if (MASK) {
-                const int j = jh + l;
-                key = (j >= lo_r && j < hi_r) ? key : 0u;
-            }
-            top2u(t1, t2, key);
+            top2u_pair(t1, t2, k[0], k[1]);
         }
         if (c < 3) {
             if (c & 1)
@@ -195,31 +199,33 @@ __global__ void k_pack_ranges(Geo g, const uint8_t *__restrict__ img, const int3
     reinterpret_cast<uint4 *>(A_mat + (size_t)i * 64)[y] = pk;
 }
 
-// One thread per (sorted domain j, isometry t, row y): B_mat row 8j+t = T_t(S_{dom_order[j]}) -
-// round(C / 64); dom_aux2[j] = (Q / 256, 128 / Q or 0), the constants of the epilogue's clamped gain.
-// Entries j >= Dn are zero.
-__global__ void k_pack_domains(Geo g, const uint16_t *__restrict__ domS, const int32_t *__restrict__ dom_order,
-                               const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq, int n_pad,
-                               __half *__restrict__ B_mat, uint4 *__restrict__ B1, float2 *__restrict__ dom_aux2) {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = (int)(gid >> 6), t = (int)(gid >> 3) & 7, y = (int)gid & 7;
+// One thread per (sorted domain j, isometry t, row y), four domains per 256-thread block: B_mat
+// row 8j+t = T_t(S_{dom_order[j]}) - round(C / 64), each output row one 16-byte row of a staged
+// layout converted pairwise to FP16; dom_aux2[j] = (Q / 256, 128 / Q or 0), the constants of the
+// epilogue's clamped gain. Entries j >= Dn are zero.
+__global__ void __launch_bounds__(256) k_pack_domains(Geo g, const uint16_t *__restrict__ domS,
+                                                      const int32_t *__restrict__ dom_order,
+                                                      const int32_t *__restrict__ dsum,
+                                                      const int32_t *__restrict__ dsumsq, int n_pad,
+                                                      __half *__restrict__ B_mat, uint4 *__restrict__ B1,
+                                                      float2 *__restrict__ dom_aux2) {
+    __shared__ __align__(16) uint16_t L[4][4][64];
+    const int jl = threadIdx.x >> 6, e = threadIdx.x & 63;
+    const int j = blockIdx.x * 4 + jl, t = e >> 3, y = e & 7;
+    const bool live = j < g.Dn;
+    int d = 0, cbar = 0;
+    if (live) {
+        d = dom_order[j];
+        cbar = (dsum[d] + 32) >> 6;  // round(C / 64)
+        stage_layouts<8>(L[jl], e, domS[(size_t)d * 64 + e]);
+    }
+    __syncthreads();
     if (j >= n_pad) return;
     uint4 pk = make_uint4(0, 0, 0, 0);
-    if (j < g.Dn) {
-        const int d = dom_order[j];
-        const uint16_t *S = domS + (size_t)d * 64;
-        const int cbar = (dsum[d] + 32) >> 6;  // round(C / 64)
-        uint32_t w[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            int sy, sx;
-            iso_src(8, t, y, 2 * h, sy, sx);
-            const __half a = __int2half_rn((int)S[sy * 8 + sx] - cbar);
-            iso_src(8, t, y, 2 * h + 1, sy, sx);
-            const __half b = __int2half_rn((int)S[sy * 8 + sx] - cbar);
-            w[h] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-        }
-        pk = make_uint4(w[0], w[1], w[2], w[3]);
+    if (live) {
+        const uint4 m = *reinterpret_cast<const uint4 *>(iso_row<8>(L[jl], t, y));
+        const uint32_t c2 = (0x6400u + (uint32_t)cbar) * 0x10001u;
+        pk = make_uint4(centred_h2(m.x, c2), centred_h2(m.y, c2), centred_h2(m.z, c2), centred_h2(m.w, c2));
         if (y == 0) {
             const int gamma = dsum[d] - 64 * cbar;
             const __half cg = __float2half_rn(-(float)gamma * (1.0f / 64.0f));  // exact: |gamma| <= 32
@@ -553,7 +559,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 merge_chunk_key(b1, b2, t1, cabs * kChunkDom);
                 merge_chunk_key(b1, b2, t2, cabs * kChunkDom);
                 if (ok && valid)
-                    chunk_max[((size_t)(w.w + cabs - w.y / kChunkDom) * kTileM + row) * 2 + half] = t1 & 0xFFFFFE00u;
+                    reinterpret_cast<uint2 *>(chunk_max)[((size_t)(w.w + cabs - w.y / kChunkDom) * kTileM + row) * 2 + half] =
+                        make_uint2(t1, t2 & 0xFFFFFE00u);
             }
             if (ok && valid) {
                 // the tile's keys are row-major (row, item, half, 2): a range reads its keys at once
@@ -588,7 +595,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---- exact re-evaluation and certification ----------------------------------------------------
-constexpr int kReevalThreads = 256;
+constexpr int kReevalThreads = 512;
 // Per-warp staging of one range (8x8 pixels) and its two candidates' 8x8 blocks of 2x2 sums in
 // four layouts each.
 struct __align__(16) ReevalStage {
@@ -596,28 +603,25 @@ struct __align__(16) ReevalStage {
     uint8_t r[64];
 };
 
-// One warp per class-sorted range position i of one image. Merges the range's top-2 keys over its
-// tile's work items, evaluates both candidates under all 8 isometries exactly, keeps the best (gain, then
-// smaller domain id, then smaller isometry) and certifies it: every other domain's FP32 score is
-// at most the runner-up's, and an FP32 score is an upper bound of that domain's exact gain / 512
-// up to a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
-// of single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other
-// domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
-// (n Bs = A^2) have zero error
-// for every candidate; their code is the smallest domain id of the pool with t = 0.
-__global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
-                         const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
-                         const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
-                         const int32_t *__restrict__ bin_off, int nbuckets,
-                         const int4 *__restrict__ rng_info, int rng_off, int dom_off,
-                         const int4 *__restrict__ tile_items, const unsigned long long *__restrict__ cand,
-                         const int32_t *__restrict__ gcounters, int32_t *__restrict__ fallback,
-                         FallbackBest *__restrict__ fb_best, int32_t *counters, fic_codes out) {
-    __shared__ ReevalStage stage[kReevalThreads / 32];
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // sorted position in this image
-    const int lane = threadIdx.x & 31;
-    if (i >= g.R) return;
-    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+// One warp's exact best, left for the block's finishing lanes. kind 0: no range; 1: flat range
+// (its code as is); 2: ranked range (certify, then code or queue). u2: the runner-up key's score
+// bits.
+struct ReevalRes {
+    long long num, den, P, Q, A, Bs;
+    int C, d, t, r, i;
+    uint32_t u2;
+    int kind, has1, has2;
+};
+
+// Exact evaluation of class-sorted range position i by one warp (see k_reeval).
+__device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
+                                            const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
+                                            const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
+                                            const int32_t *__restrict__ bin_off, int nbuckets,
+                                            const int4 *__restrict__ rng_info, int rng_off, int dom_off,
+                                            const int4 *__restrict__ tile_items,
+                                            const unsigned long long *__restrict__ cand, int i, int lane,
+                                            ReevalStage &sg, ReevalRes &res) {
     const int4 ri = rng_info[i];
     const int r = ri.w;
     const long long A = ri.x, Bs = rsumsq[r];
@@ -637,13 +641,8 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
             const long long C = dsum[dmin];
             const long long Q = 64LL * dsumsq[dmin] - C * C;
             // X = (A / 64) C exactly for a constant block, so P = 64 X - A C = 0
-            double s, o, sse;
-            finalize_code(64, A, Bs, C, 0, Q, exact_gain(0, Q), s, o, sse);
-            out.dom[r] = dmin;
-            out.iso[r] = 0;
-            out.s[r] = s;
-            out.o[r] = o;
-            out.sse[r] = sse;
+            const Gain g0 = exact_gain(0, Q);
+            res = ReevalRes{g0.num, g0.den, 0, Q, A, Bs, (int)C, dmin, 0, r, i, 0u, 1, 1, 0};
         }
         return;
     }
@@ -668,7 +667,6 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     // layout: layout swap + 2 rev, row (swap ? fx : fy) ? 7 - y : y, with rev = swap ? fy : fx and
     // swap, fy, fx the isometry's flags. Lanes 2 (8 c + t) and 2 (8 c + t) + 1 then form X of
     // candidate c, isometry t over range rows 0-3 and 4-7 with packed byte x halfword dot products.
-    ReevalStage &sg = stage[threadIdx.x >> 5];
     const int j0 = (int)(~(uint32_t)(b1 & 0xffffffffu)) - dom_off;  // positions in this image
     const int j1 = (int)(~(uint32_t)(b2 & 0xffffffffu)) - dom_off;
     const bool h0 = b1 != 0 && j0 >= 0 && j0 < g.Dn, h1 = b2 != 0 && j1 >= 0 && j1 < g.Dn;
@@ -746,41 +744,84 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
             C = oC;
         }
     }
-    if (lane != 0) return;
-    bool certified = b1 != 0 && gg.num >= 0;
-    if (certified && b2 != 0) {
+    if (lane == 0)
+        res = ReevalRes{gg.num, gg.den, P, Q, A, Bs, (int)C, d, bt, r, i, (uint32_t)(b2 >> 32), 2, b1 != 0, b2 != 0};
+}
+
+// Certification, code or queueing of one evaluated range (one thread). The FP64 steps run here,
+// one lane per range, so that one warp's FP64 instructions serve all the block's ranges: FP64
+// throughput on sm_103 is a small fraction of FP32, and with each warp finishing its own range on
+// one lane the FP64 pipe was this kernel's limit.
+__device__ __forceinline__ void reeval_finish(const ReevalRes &e, int32_t *__restrict__ fallback,
+                                              FallbackBest *__restrict__ fb_best, int32_t *counters,
+                                              const fic_codes &out) {
+    if (e.kind == 0) return;
+    const Gain gg{e.num, e.den};
+    bool certified = e.kind == 1 || (e.has1 && gg.num >= 0);
+    if (e.kind == 2 && certified && e.has2) {
         // runner-up score (truncated key) * (1 + 2^-13) + 2^-16 bounds every other domain's exact
         // gain / 512: the key drops < 2^-14 relatively (9 low bits hold the chunk offset), the
         // FP32 score formula errs < 20 * 2^-24 relatively, and the accumulator's P / 64 (an exact
         // integer Y plus one rounded correction of magnitude <= 16) errs < 2^-22 (|P / 64| + 16);
         // the score's slope in p is at most 1, so that moves it by < 2^-21 relatively plus
         // < 2^-18 absolutely
-        const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
+        const double u2 = (double)__uint_as_float(e.u2);
         // bound < exact gain / 512, compared as bound * 512 den < gain numerator (no division)
         certified = (u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0) * (512.0 * (double)gg.den) < (double)gg.num;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
-        fallback[slot] = i;
+        fallback[slot] = e.i;
         FallbackBest fb;
         fb.num = gg.num;
         fb.den = gg.den;
-        fb.P = P;
-        fb.Q = Q;
-        fb.d = d;
-        fb.t = bt;
-        fb.C = (int)C;
+        fb.P = e.P;
+        fb.Q = e.Q;
+        fb.d = e.d;
+        fb.t = e.t;
+        fb.C = e.C;
         fb.pad = 0;
         fb_best[slot] = fb;
         return;
     }
     double s, o, sse;
-    finalize_code(64, A, Bs, C, P, Q, gg, s, o, sse);
-    out.dom[r] = d;
-    out.iso[r] = bt;
-    out.s[r] = s;
-    out.o[r] = o;
-    out.sse[r] = sse;
+    finalize_code(64, e.A, e.Bs, e.C, e.P, e.Q, gg, s, o, sse);
+    out.dom[e.r] = e.d;
+    out.iso[e.r] = e.t;
+    out.s[e.r] = s;
+    out.o[e.r] = o;
+    out.sse[e.r] = sse;
+}
+
+// One warp per class-sorted range position i of one image. Merges the range's top-2 keys over its
+// tile's work items, evaluates both candidates under all 8 isometries exactly, keeps the best (gain, then
+// smaller domain id, then smaller isometry) and certifies it: every other domain's FP32 score is
+// at most the runner-up's, and an FP32 score is an upper bound of that domain's exact gain / 512
+// up to a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
+// of single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other
+// domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
+// (n Bs = A^2) have zero error
+// for every candidate; their code is the smallest domain id of the pool with t = 0.
+__global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
+                         const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
+                         const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
+                         const int32_t *__restrict__ bin_off, int nbuckets,
+                         const int4 *__restrict__ rng_info, int rng_off, int dom_off,
+                         const int4 *__restrict__ tile_items, const unsigned long long *__restrict__ cand,
+                         const int32_t *__restrict__ gcounters, int32_t *__restrict__ fallback,
+                         FallbackBest *__restrict__ fb_best, int32_t *counters, fic_codes out) {
+    __shared__ ReevalStage stage[kReevalThreads / 32];
+    __shared__ ReevalRes res[kReevalThreads / 32];
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // sorted position in this image
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+    if (i < g.R)
+        reeval_rank(g, img, domS, dsum, dsumsq, rsumsq, dom_order, bin_off, nbuckets, rng_info, rng_off, dom_off,
+                    tile_items, cand, i, lane, stage[wib], res[wib]);
+    else if (lane == 0)
+        res[wib].kind = 0;
+    __syncthreads();
+    if (threadIdx.x < kReevalThreads / 32) reeval_finish(res[threadIdx.x], fallback, fb_best, counters, out);
 }
 
 // ---- host side -------------------------------------------------------------------------------

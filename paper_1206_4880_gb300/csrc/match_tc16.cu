@@ -80,20 +80,26 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
         }
         const uint32_t *cur = (c & 1) ? vb : va;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int l = 4 * c + q;
-            const float4 a = auxp[l];
-            float p = 0.f;
+        for (int q2 = 0; q2 < 2; ++q2) {
+            uint32_t k[2];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) p = fmaxf(p, fabsf(fmaf(alpha, a.x, __uint_as_float(cur[8 * q + t]))));
-            const float mm = fminf(p, a.y);
-            const float sc = fmaf(mm, mm * a.z, p - mm);
-            uint32_t key = (__float_as_uint(sc) & 0xFFFFFE00u) | (uint32_t)(511 - jrel - l);
-            if (MASK) {
-                const int j = jh + l;
-                key = (j >= lo_r && j < hi_r) ? key : 0u;
+            for (int h = 0; h < 2; ++h) {
+                const int q = 2 * q2 + h, l = 4 * c + q;
+                const float4 a = auxp[l];
+                float y[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) y[t] = fmaf(alpha, a.x, __uint_as_float(cur[8 * q + t]));
+                const float p = fmaxf(max3_abs(y[0], y[1], y[2]), max3_abs(y[3], y[4], max3_abs(y[5], y[6], y[7])));
+                const float mm = fminf(p, a.y);
+                const float sc = fmaf(mm, mm * a.z, p - mm);
+                uint32_t key = (__float_as_uint(sc) & 0xFFFFFE00u) | (uint32_t)(511 - jrel - l);
+                if (MASK) {
+                    const int j = jh + l;
+                    key = (j >= lo_r && j < hi_r) ? key : 0u;
+                }
+                k[h] = key;
             }
-            top2u(t1, t2, key);
+            top2u_pair(t1, t2, k[0], k[1]);
         }
         if (c < 3) {
             if (c & 1)
@@ -140,32 +146,37 @@ __global__ void k_pack_ranges16(Geo g, const uint8_t *__restrict__ img, const in
     dst[1] = pk[1];
 }
 
-// One thread per (sorted domain j, isometry t, row y): B_mat row 8j+t = T_t(S_{dom_order[j]}) -
-// round(C / 256); dom_aux[j] = (-gamma / 256, Q / 1024, 512 / Q or 0, 0), gamma = C - 256 round(C/256).
-// Entries j >= Dn are zero.
-__global__ void k_pack_domains16(Geo g, const uint16_t *__restrict__ domS, const int32_t *__restrict__ dom_order,
-                                 const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq, int n_pad,
-                                 __half *__restrict__ B_mat, float4 *__restrict__ dom_aux) {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = (int)(gid >> 7), t = (int)(gid >> 4) & 7, y = (int)gid & 15;
+// One thread per (sorted domain j, isometry t, row y), two domains per 256-thread block: B_mat
+// row 8j+t = T_t(S_{dom_order[j]}) - round(C / 256), each output row one 32-byte row of a staged
+// layout converted pairwise to FP16; dom_aux[j] = (-gamma / 256, Q / 1024, 512 / Q or 0, 0) with
+// gamma = C - 256 round(C / 256). Entries j >= Dn are zero.
+__global__ void __launch_bounds__(256) k_pack_domains16(Geo g, const uint16_t *__restrict__ domS,
+                                                        const int32_t *__restrict__ dom_order,
+                                                        const int32_t *__restrict__ dsum,
+                                                        const int32_t *__restrict__ dsumsq, int n_pad,
+                                                        __half *__restrict__ B_mat, float4 *__restrict__ dom_aux) {
+    __shared__ __align__(16) uint16_t L[2][4][256];
+    const int jl = threadIdx.x >> 7, e = threadIdx.x & 127;
+    const int j = blockIdx.x * 2 + jl, t = e >> 4, y = e & 15;
+    const bool live = j < g.Dn;
+    int d = 0, cbar = 0;
+    if (live) {
+        d = dom_order[j];
+        cbar = (dsum[d] + 128) >> 8;  // round(C / 256)
+        stage_layouts<16>(L[jl], e, domS[(size_t)d * 256 + e]);
+        stage_layouts<16>(L[jl], e + 128, domS[(size_t)d * 256 + e + 128]);
+    }
+    __syncthreads();
     if (j >= n_pad) return;
     uint4 pk[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-    if (j < g.Dn) {
-        const int d = dom_order[j];
-        const uint16_t *S = domS + (size_t)d * 256;
-        const int cbar = (dsum[d] + 128) >> 8;  // round(C / 256)
-        uint32_t w[8];
+    if (live) {
+        const uint4 *m = reinterpret_cast<const uint4 *>(iso_row<16>(L[jl], t, y));
+        const uint32_t c2 = (0x6400u + (uint32_t)cbar) * 0x10001u;
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            int sy, sx;
-            iso_src(16, t, y, 2 * h, sy, sx);
-            const __half a = __int2half_rn((int)S[sy * 16 + sx] - cbar);
-            iso_src(16, t, y, 2 * h + 1, sy, sx);
-            const __half b = __int2half_rn((int)S[sy * 16 + sx] - cbar);
-            w[h] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+        for (int k = 0; k < 2; ++k) {
+            const uint4 v = m[k];
+            pk[k] = make_uint4(centred_h2(v.x, c2), centred_h2(v.y, c2), centred_h2(v.z, c2), centred_h2(v.w, c2));
         }
-        pk[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        pk[1] = make_uint4(w[4], w[5], w[6], w[7]);
         if (t == 0 && y == 0) {
             const long long C = dsum[d];
             const long long Q = 256LL * dsumsq[d] - C * C;
@@ -352,7 +363,9 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                 }
                 merge_chunk_key(b1, b2, t1, cabs * kChunkDom);
                 merge_chunk_key(b1, b2, t2, cabs * kChunkDom);
-                if (ok && valid) chunk_max[(size_t)(w.w + cabs - w.y / kChunkDom) * kTm16 + row] = t1 & 0xFFFFFE00u;
+                if (ok && valid)
+                    reinterpret_cast<uint2 *>(chunk_max)[(size_t)(w.w + cabs - w.y / kChunkDom) * kTm16 + row] =
+                        make_uint2(t1, t2 & 0xFFFFFE00u);
             }
             if (ok && valid) {
                 // the tile's keys are row-major (row, item, 2): a range reads its keys at once
@@ -399,19 +412,24 @@ struct __align__(16) Reeval16Stage {
     uint8_t r[256];
 };
 
-__global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
-                           const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
-                           const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
-                           const int32_t *__restrict__ bin_off, int nbuckets, const int4 *__restrict__ rng_info,
-                           int rng_off, int dom_off, const int4 *__restrict__ tile_items,
-                           const unsigned long long *__restrict__ cand, const int32_t *__restrict__ gcounters,
-                           int32_t *__restrict__ fallback, FallbackBest *__restrict__ fb_best, int32_t *counters,
-                           fic_codes out) {
-    __shared__ Reeval16Stage stage16[kReeval16Threads / 32];
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= g.R) return;
-    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+// One warp's exact best, left for the block's finishing lanes (kinds as in the B = 8 kernel).
+struct Reeval16Res {
+    __int128 num;
+    long long den, P, Q, A, Bs;
+    int C, d, t, r, i;
+    uint32_t u2;
+    int kind, has1, has2;
+};
+
+// Exact evaluation of class-sorted range position i by one warp (see k_reeval16).
+__device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__restrict__ img,
+                                              const uint16_t *__restrict__ domS, const int32_t *__restrict__ dsum,
+                                              const int32_t *__restrict__ dsumsq, const int32_t *__restrict__ rsumsq,
+                                              const int32_t *__restrict__ dom_order, const int32_t *__restrict__ bin_off,
+                                              int nbuckets, const int4 *__restrict__ rng_info, int rng_off, int dom_off,
+                                              const int4 *__restrict__ tile_items,
+                                              const unsigned long long *__restrict__ cand, int i, int lane,
+                                              Reeval16Stage &sg16, Reeval16Res &res) {
     const int4 ri = rng_info[i];
     const int r = ri.w;
     const long long A = ri.x, Bs = rsumsq[r];
@@ -428,13 +446,8 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
         if (lane == 0) {
             const long long C = dsum[dmin];
             const long long Q = 256LL * dsumsq[dmin] - C * C;
-            double s, o, sse;
-            finalize_code(256, A, Bs, C, 0, Q, exact_gain_w(0, Q), s, o, sse);
-            out.dom[r] = dmin;
-            out.iso[r] = 0;
-            out.s[r] = s;
-            out.o[r] = o;
-            out.sse[r] = sse;
+            const GainW g0 = exact_gain_w(0, Q);
+            res = Reeval16Res{g0.num, g0.den, 0, Q, A, Bs, (int)C, dmin, 0, r, i, 0u, 1, 1, 0};
         }
         return;
     }
@@ -455,7 +468,7 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
     // exact evaluation, staged as in the 8x8 re-evaluation: the range and both candidates' blocks
     // (four layouts each: as stored, transposed, rows reversed, transposed with rows reversed) in
     // shared memory; lane (c, t, half) sums X over 8 of the 16 rows with packed dot products.
-    Reeval16Stage &sg = stage16[threadIdx.x >> 5];
+    Reeval16Stage &sg = sg16;
     const int j0 = (int)(~(uint32_t)(b1 & 0xffffffffu)) - dom_off;
     const int j1 = (int)(~(uint32_t)(b2 & 0xffffffffu)) - dom_off;
     const bool h0 = b1 != 0 && j0 >= 0 && j0 < g.Dn, h1 = b2 != 0 && j1 >= 0 && j1 < g.Dn;
@@ -552,34 +565,69 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
             C = oC;
         }
     }
-    if (lane != 0) return;
-    bool certified = b1 != 0 && gg.num >= 0;
-    if (certified && b2 != 0) {
-        const double u2 = (double)__uint_as_float((uint32_t)(b2 >> 32));
+    if (lane == 0)
+        res = Reeval16Res{gg.num, gg.den, P, Q, A, Bs, (int)C, d, bt, r, i, (uint32_t)(b2 >> 32), 2, b1 != 0, b2 != 0};
+}
+
+// Certification, code or queueing of one evaluated range, one lane per range (the FP64 steps
+// serve all the block's ranges with one warp's instructions, as in the B = 8 kernel).
+__device__ __forceinline__ void reeval16_finish(const Reeval16Res &e, int32_t *__restrict__ fallback,
+                                                FallbackBest *__restrict__ fb_best, int32_t *counters,
+                                                const fic_codes &out) {
+    if (e.kind == 0) return;
+    GainW gg;
+    gg.num = e.num;
+    gg.den = e.den;
+    bool certified = e.kind == 1 || (e.has1 && gg.num >= 0);
+    if (e.kind == 2 && certified && e.has2) {
+        const double u2 = (double)__uint_as_float(e.u2);
         certified = (u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0) * (2048.0 * (double)gg.den) < i128_to_double_rn(gg.num);
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
-        fallback[slot] = i;
+        fallback[slot] = e.i;
         FallbackBest fb;
         fb.num = gg.num;
         fb.den = gg.den;
-        fb.P = P;
-        fb.Q = Q;
-        fb.d = d;
-        fb.t = bt;
-        fb.C = (int)C;
+        fb.P = e.P;
+        fb.Q = e.Q;
+        fb.d = e.d;
+        fb.t = e.t;
+        fb.C = e.C;
         fb.pad = 0;
         fb_best[slot] = fb;
         return;
     }
     double s, o, sse;
-    finalize_code(256, A, Bs, C, P, Q, gg, s, o, sse);
-    out.dom[r] = d;
-    out.iso[r] = bt;
-    out.s[r] = s;
-    out.o[r] = o;
-    out.sse[r] = sse;
+    finalize_code(256, e.A, e.Bs, e.C, e.P, e.Q, gg, s, o, sse);
+    out.dom[e.r] = e.d;
+    out.iso[e.r] = e.t;
+    out.s[e.r] = s;
+    out.o[e.r] = o;
+    out.sse[e.r] = sse;
+}
+
+__global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
+                           const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
+                           const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
+                           const int32_t *__restrict__ bin_off, int nbuckets, const int4 *__restrict__ rng_info,
+                           int rng_off, int dom_off, const int4 *__restrict__ tile_items,
+                           const unsigned long long *__restrict__ cand, const int32_t *__restrict__ gcounters,
+                           int32_t *__restrict__ fallback, FallbackBest *__restrict__ fb_best, int32_t *counters,
+                           fic_codes out) {
+    __shared__ Reeval16Stage stage16[kReeval16Threads / 32];
+    __shared__ Reeval16Res res[kReeval16Threads / 32];
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+    if (i < g.R)
+        reeval16_rank(g, img, domS, dsum, dsumsq, rsumsq, dom_order, bin_off, nbuckets, rng_info, rng_off, dom_off,
+                      tile_items, cand, i, lane, stage16[wib], res[wib]);
+    else if (lane == 0)
+        res[wib].kind = 0;
+    __syncthreads();
+    if (threadIdx.x < kReeval16Threads / 32)
+        reeval16_finish(res[threadIdx.x], fallback, fb_best, counters, out);
 }
 
 // ---- host side -------------------------------------------------------------------------------
