@@ -53,9 +53,8 @@ WORKLOADS = {
 }
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one matcher launch from an ncu capture of the current kernel on the
-# workload (profiles/match_tc_encode1024.md); set to None whenever the kernel changes until it is
-# captured again.
-MEASURED_TRAFFIC = {("encode-1024", "tensor"): 85.948672e6 + 12.945664e6}
+# workload (profiles/); emptied whenever the kernel changes until it is captured again.
+MEASURED_TRAFFIC = {}
 
 
 def flops_per_match(block: int) -> int:

@@ -45,6 +45,43 @@ __host__ __device__ __forceinline__ void iso_src(int B, int t, int y, int x, int
     sx = fx ? N - v : v;
 }
 
+// Exact correlations of one domain block with a range under all 8 isometries: X_t = sum_q S[q]
+// rp[t][q], where rp[t][q] = r[p] with iso_src(t, p) = q (the range's 8 inverse-permuted byte
+// copies, 16-byte aligned rows) and S is the domain's block of B*B 16-bit 2x2 sums (16-byte
+// aligned). Two products per __dp2a (a pair of sums against two bytes), 16 source indices per
+// step, unsigned: X < B^2 * 255 * 1020 < 2^31.
+// corr<B, NT>(rp, S, X) forms X_t of isometries t = 0 .. NT - 1 of the rows it is given (rp + t0
+// for isometries t0 .. t0 + NT - 1); corr8 is all eight.
+template <int B, int NT>
+__device__ __forceinline__ void corr(const uint8_t (*rp)[B * B], const uint16_t *__restrict__ S, unsigned (&X)[NT]) {
+    constexpr int n = B * B;
+    const uint4 *Sd = reinterpret_cast<const uint4 *>(S);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) X[t] = 0;
+#pragma unroll(B == 8 ? 4 : 2)
+    for (int q0 = 0; q0 < n; q0 += 16) {
+        const uint4 sa = __ldg(Sd + q0 / 8), sb = __ldg(Sd + q0 / 8 + 1);  // S[q0 .. q0 + 15]
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const uint4 r = *reinterpret_cast<const uint4 *>(&rp[t][q0]);  // rp[t][q0 .. q0 + 15]
+            unsigned acc = X[t];
+            acc = __dp2a_lo(sa.x, r.x, acc);
+            acc = __dp2a_hi(sa.y, r.x, acc);
+            acc = __dp2a_lo(sa.z, r.y, acc);
+            acc = __dp2a_hi(sa.w, r.y, acc);
+            acc = __dp2a_lo(sb.x, r.z, acc);
+            acc = __dp2a_hi(sb.y, r.z, acc);
+            acc = __dp2a_lo(sb.z, r.w, acc);
+            acc = __dp2a_hi(sb.w, r.w, acc);
+            X[t] = acc;
+        }
+    }
+}
+template <int B>
+__device__ __forceinline__ void corr8(const uint8_t (*rp)[B * B], const uint16_t *__restrict__ S, unsigned (&X)[8]) {
+    corr<B, 8>(rp, S, X);
+}
+
 // Four layouts of a block S (side B, N = B - 1) in shared memory: L0 as stored, L1 transposed,
 // L2 with each row reversed, L3[a][b] = S[N - b][a]. Row y of the isometry T_t(S) of iso_src is
 // then one contiguous row: row (swap ? fx : fy) ? N - y : y of layout swap + 2 (swap ? fy : fx).

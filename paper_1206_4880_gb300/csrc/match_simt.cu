@@ -28,7 +28,7 @@ struct ScanShared {
     long long P[kSimtThreads], Q[kSimtThreads];
     int d[kSimtThreads], t[kSimtThreads], C[kSimtThreads];
     int flagged[kSimtThreads];
-    int single[2 * kSimtThreads];
+    int single[2 * kSimtThreads];  // first positions of flagged 16-domain groups
     int n_flagged, n_single;
     float thr;
 };
@@ -55,37 +55,16 @@ __device__ __forceinline__ void load_range(ScanShared<B> &sh, const Geo &g, cons
     }
 }
 
-// Exact evaluation of domain d under all 8 isometries against the range in sh.rp: X_t = sum_q
-// S[q] rp[t][q] in unsigned integers (X <= B^2 * 255 * 1020 < 2^31), two products per __dp2a (a
-// pair of 16-bit sums against two of the range's bytes), 16 source indices per step.
+// Exact evaluation of domain d under all 8 isometries against the range in sh.rp (corr8), kept
+// in b if it is better (gain, then smaller domain id, then smaller isometry).
 template <int B>
 __device__ __forceinline__ void scan_domain(const ScanShared<B> &sh, int d, long long A,
                                             const uint16_t *__restrict__ domS,
                                             const int32_t *__restrict__ dsum,
                                             const int32_t *__restrict__ dsumsq, Best<B> &b) {
     constexpr int n = B * B;
-    const uint4 *Sd = reinterpret_cast<const uint4 *>(domS + (size_t)d * n);
     unsigned X[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) X[t] = 0;
-#pragma unroll(B == 8 ? 4 : 2)
-    for (int q0 = 0; q0 < n; q0 += 16) {
-        const uint4 sa = __ldg(Sd + q0 / 8), sb = __ldg(Sd + q0 / 8 + 1);  // S[q0 .. q0 + 15]
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const uint4 r = *reinterpret_cast<const uint4 *>(&sh.rp[t][q0]);  // rp[t][q0 .. q0 + 15]
-            unsigned acc = X[t];
-            acc = __dp2a_lo(sa.x, r.x, acc);
-            acc = __dp2a_hi(sa.y, r.x, acc);
-            acc = __dp2a_lo(sa.z, r.y, acc);
-            acc = __dp2a_hi(sa.w, r.y, acc);
-            acc = __dp2a_lo(sb.x, r.z, acc);
-            acc = __dp2a_hi(sb.y, r.z, acc);
-            acc = __dp2a_lo(sb.z, r.w, acc);
-            acc = __dp2a_hi(sb.w, r.w, acc);
-            X[t] = acc;
-        }
-    }
+    corr8<B>(sh.rp, domS + (size_t)d * n, X);
     const long long C = dsum[d];
     const long long Q = (long long)n * dsumsq[d] - C * C;
 #pragma unroll
@@ -217,10 +196,10 @@ __global__ void __launch_bounds__(kSimtThreads, 2)
         const int4 ti = tile_items[ig / TM];
         const int nch = ti.w;
         const int c_lo = tw.x / kChunkDom;  // the tile's first chunk of the absolute grid
-        // the chunks, 256 at a time in parallel: a half (key column) whose runner-up
-        // score reaches the threshold has its whole chunk scanned; one whose best score alone
-        // reaches it contributes only that best domain (every other domain of the half scores at
-        // most the runner-up); then all threads scan the flagged chunks' and single domains
+        // the chunks, 256 at a time in parallel: a key column whose runner-up group score reaches
+        // the threshold has its whole chunk scanned; one whose best group score alone reaches it
+        // contributes only that 16-domain group (every domain outside it scores at most the
+        // runner-up); then all threads scan the flagged chunks' and groups' domains
         for (int base = 0; base < nch; base += kSimtThreads) {
             if (threadIdx.x == 0) sh.n_flagged = sh.n_single = 0;
             __syncthreads();
@@ -241,7 +220,8 @@ __global__ void __launch_bounds__(kSimtThreads, 2)
 #pragma unroll
                     for (int h = 0; h < H; ++h)
                         if (k[h].x != 0 && reaches(k[h].x & 0xFFFFFE00u, thr))
-                            sh.single[atomicAdd(&sh.n_single, 1)] = (c + c_lo) * kChunkDom + 511 - (int)(k[h].x & 511u);
+                            sh.single[atomicAdd(&sh.n_single, 1)] =
+                                ((c + c_lo) * kChunkDom + 511 - (int)(k[h].x & 511u)) & ~15;
                 }
             }
             __syncthreads();
@@ -253,8 +233,10 @@ __global__ void __launch_bounds__(kSimtThreads, 2)
                 for (int j = j0 + threadIdx.x; j < j1; j += kSimtThreads)
                     scan_domain<B>(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
             }
-            for (int f = threadIdx.x; f < nsg; f += kSimtThreads)
-                scan_domain<B>(sh, dom_order[sh.single[f] - dom_off], A, domS, dsum, dsumsq, b);
+            for (int f = threadIdx.x; f < 16 * nsg; f += kSimtThreads) {
+                const int j = sh.single[f >> 4] + (f & 15);
+                if (j >= ri.y && j < ri.z) scan_domain<B>(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
+            }
             __syncthreads();
         }
         reduce_and_write<B>(sh, b, r, A, Bs, out);

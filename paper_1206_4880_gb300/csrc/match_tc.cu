@@ -81,8 +81,10 @@ constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 // range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
 // s = 128 m^2 / Q + (p - m), m = min(p, Q / 256) (the exact gain / 512 up to the accumulator's
 // and this formula's rounding), and a 32-bit key (s's bits with the low 9 replaced by 511 - the
-// domain's offset in its 512-domain chunk, jrel + l); t1, t2 keep the two largest keys of the
-// chunk. MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
+// domain's offset in its 512-domain chunk, jrel + l). The 16 domains form one group (positions
+// jh .. jh + 15, jh a multiple of 16): only the group's largest key goes on, into t1, t2, the two
+// largest group keys of the chunk; the exact re-evaluation evaluates the best group whole.
+// MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
 __device__ __forceinline__ float absmax8(const uint32_t *v) {
     const float a = max3_abs(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
     const float b = max3_abs(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5]));
@@ -106,6 +108,7 @@ template <bool MASK>
 __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int jh, int jrel, int lo_r, int hi_r,
                                          uint32_t &t1, uint32_t &t2) {
     const uint32_t base = 511u - (uint32_t)jrel;
+    float gmax = 0.f;  // keys are the bits of non-negative floats: their float order is their order
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
@@ -147,7 +150,7 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 }
                 k[h] = key;
             }
-            top2u_pair(t1, t2, k[0], k[1]);
+            gmax = max3f(gmax, __uint_as_float(k[0]), __uint_as_float(k[1]));
         }
         if (c < 3) {
             if (c & 1)
@@ -156,6 +159,7 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 tmem_ld_wait(vb);
         }
     }
+    top2u(t1, t2, __float_as_uint(gmax));
 }
 
 }  // namespace
@@ -596,11 +600,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---- exact re-evaluation and certification ----------------------------------------------------
 constexpr int kReevalThreads = 512;
-// Per-warp staging of one range (8x8 pixels) and its two candidates' 8x8 blocks of 2x2 sums in
-// four layouts each.
+// Per-warp staging of one range: its 8 inverse-permuted copies rp[t][src_t(p)] = r[p].
 struct __align__(16) ReevalStage {
-    uint16_t S[2][4][64];
-    uint8_t r[64];
+    uint8_t rp[8][64];
 };
 
 // One warp's exact best, left for the block's finishing lanes. kind 0: no range; 1: flat range
@@ -661,80 +663,56 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
         top2(b1, b2, o1);
         top2(b1, b2, o2);
     }
-    // exact evaluation. The warp stages the range's pixels and both candidates' blocks of 2x2
-    // sums in shared memory, each block in four layouts (as stored, transposed, rows reversed,
-    // transposed with rows reversed), so that row y of T_t(S) is one contiguous 16-byte row of one
-    // layout: layout swap + 2 rev, row (swap ? fx : fy) ? 7 - y : y, with rev = swap ? fy : fx and
-    // swap, fy, fx the isometry's flags. Lanes 2 (8 c + t) and 2 (8 c + t) + 1 then form X of
-    // candidate c, isometry t over range rows 0-3 and 4-7 with packed byte x halfword dot products.
-    const int j0 = (int)(~(uint32_t)(b1 & 0xffffffffu)) - dom_off;  // positions in this image
-    const int j1 = (int)(~(uint32_t)(b2 & 0xffffffffu)) - dom_off;
-    const bool h0 = b1 != 0 && j0 >= 0 && j0 < g.Dn, h1 = b2 != 0 && j1 >= 0 && j1 < g.Dn;
-    const int d0 = h0 ? dom_order[j0] : INT_MAX, d1 = h1 ? dom_order[j1] : INT_MAX;
-    {
-        const int px = 2 * lane;
-        const uint8_t *prow = img + (size_t)(ry + (px >> 3)) * g.pitch + rx + (px & 7);
-        sg.r[px] = prow[0];
-        sg.r[px + 1] = prow[1];
-    }
+    // exact evaluation of the best key's group: the epilogue ranks 16-domain groups by their best
+    // key, so every domain outside that group scores at most the runner-up key, and only the
+    // group's domains inside the pool window can be certified (the runner-up's own domain is
+    // bounded by its key, so it can never pass the test below). The warp stages the range's
+    // inverse-permuted copies; lane l forms X_t of domain (l mod 16) of the group for isometries
+    // 4 (l / 16) .. 4 (l / 16) + 3 exactly (corr) and keeps its best (gain, then smaller t); a
+    // warp reduction keeps the best (gain, then smaller domain id, then smaller t).
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int e = lane + 32 * k, c = e >> 6, q = e & 63, y = q >> 3, x = q & 7;
-        const bool hk = c ? h1 : h0;
-        const uint16_t v = hk ? domS[(size_t)(c ? d1 : d0) * 64 + q] : (uint16_t)0;
-        sg.S[c][0][8 * y + x] = v;
-        sg.S[c][1][8 * x + y] = v;
-        sg.S[c][2][8 * y + 7 - x] = v;
-        sg.S[c][3][8 * x + 7 - y] = v;
+    for (int k = 0; k < 2; ++k) {
+        const int px = 2 * lane + k, y = px >> 3, x = px & 7;
+        const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int sy, sx;
+            iso_src(8, t, y, x, sy, sx);
+            sg.rp[t][sy * 8 + sx] = v;
+        }
     }
     __syncwarp();
-    const int cidx = lane >> 4, t = (lane >> 1) & 7, hrow = (lane & 1) * 4;
-    const bool has = cidx ? h1 : h0;
+    const int p1 = (int)(~(uint32_t)(b1 & 0xffffffffu));  // batch-wide positions
+    int pos = b1 != 0 ? (p1 & ~15) + (lane & 15) : -1;
+    if (pos < ri.y || pos >= ri.z) pos = -1;
+    const int t0 = (lane >> 4) * 4;  // lanes 0-15: isometries 0-3 of their domain, lanes 16-31: 4-7
     Gain gg{-1, 1};
-    int d = cidx ? d1 : d0;
+    int d = INT_MAX, bt = 0;
     long long P = 0, Q = 0, C = 0;
-    int X = 0;
-    {
-        const int swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
-        const uint16_t *M = sg.S[cidx][swap + 2 * (swap ? fy : fx)];
-        const int flip = swap ? fx : fy;
-        unsigned acc = 0;
-#pragma unroll
-        for (int y = hrow; y < hrow + 4; ++y) {
-            const uint4 m = *reinterpret_cast<const uint4 *>(M + 8 * (flip ? 7 - y : y));
-            const uint2 rr = *reinterpret_cast<const uint2 *>(sg.r + 8 * y);
-            acc = __dp2a_lo(m.x, rr.x, acc);
-            acc = __dp2a_hi(m.y, rr.x, acc);
-            acc = __dp2a_lo(m.z, rr.y, acc);
-            acc = __dp2a_hi(m.w, rr.y, acc);
-        }
-        X = (int)acc;  // <= 32 * 255 * 1020 < 2^31
-    }
-    X += __shfl_xor_sync(0xffffffffu, X, 1);
-    // best isometry of each candidate: with the domain (so Q and C) fixed, the clamped gain grows
-    // with |P|, so it is the largest |P|, ties to the smaller t (lanes 16 c .. 16 c + 15)
-    if (has) {
+    if (pos >= 0) {
+        d = dom_order[pos - dom_off];
+        unsigned X[4];
+        corr<8, 4>(sg.rp + t0, domS + (size_t)d * 64, X);
         C = dsum[d];
         Q = 64LL * dsumsq[d] - C * C;
-        P = 64LL * (long long)X - A * C;
-    }
-    int bt = t;
 #pragma unroll
-    for (int off = 2; off < 16; off <<= 1) {
-        const long long oP = __shfl_xor_sync(0xffffffffu, P, off);
-        const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
-        const long long a0 = P < 0 ? -P : P, a1 = oP < 0 ? -oP : oP;
-        if (a1 > a0 || (a1 == a0 && ot < bt)) {
-            P = oP;
-            bt = ot;
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + k;
+            const long long Pt = 64LL * (long long)X[k] - A * C;
+            const Gain gt = exact_gain(Pt, Q);
+            if (cand_better(gt, d, t, gg, d, bt)) {
+                gg = gt;
+                bt = t;
+                P = Pt;
+            }
         }
     }
-    if (has) gg = exact_gain(P, Q);
-    {  // the better of the two candidates
-        const Gain og{__shfl_xor_sync(0xffffffffu, gg.num, 16), __shfl_xor_sync(0xffffffffu, gg.den, 16)};
-        const int od = __shfl_xor_sync(0xffffffffu, d, 16), ot = __shfl_xor_sync(0xffffffffu, bt, 16);
-        const long long oP = __shfl_xor_sync(0xffffffffu, P, 16), oQ = __shfl_xor_sync(0xffffffffu, Q, 16);
-        const long long oC = __shfl_xor_sync(0xffffffffu, C, 16);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Gain og{__shfl_xor_sync(0xffffffffu, gg.num, off), __shfl_xor_sync(0xffffffffu, gg.den, off)};
+        const int od = __shfl_xor_sync(0xffffffffu, d, off), ot = __shfl_xor_sync(0xffffffffu, bt, off);
+        const long long oP = __shfl_xor_sync(0xffffffffu, P, off), oQ = __shfl_xor_sync(0xffffffffu, Q, off);
+        const long long oC = __shfl_xor_sync(0xffffffffu, C, off);
         if (cand_better(og, od, ot, gg, d, bt)) {
             gg = og;
             d = od;
@@ -793,15 +771,15 @@ __device__ __forceinline__ void reeval_finish(const ReevalRes &e, int32_t *__res
     out.sse[e.r] = sse;
 }
 
-// One warp per class-sorted range position i of one image. Merges the range's top-2 keys over its
-// tile's work items, evaluates both candidates under all 8 isometries exactly, keeps the best (gain, then
-// smaller domain id, then smaller isometry) and certifies it: every other domain's FP32 score is
-// at most the runner-up's, and an FP32 score is an upper bound of that domain's exact gain / 512
-// up to a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful
-// of single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other
-// domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
-// (n Bs = A^2) have zero error
-// for every candidate; their code is the smallest domain id of the pool with t = 0.
+// One warp per class-sorted range position i of one image. Merges the range's top-2 group keys
+// over its tile's work items, evaluates the best key's 16-domain group under all 8 isometries
+// exactly, keeps the best (gain, then smaller domain id, then smaller isometry) and certifies it: every domain outside the evaluated group has an FP32 score at most
+// the runner-up key's, and an FP32 score is an upper bound of that domain's exact gain / 512 up to
+// a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful of
+// single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other
+// domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat
+// ranges (n Bs = A^2) have zero error for every candidate; their code is the smallest domain id of
+// the pool with t = 0.
 __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                          const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                          const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,

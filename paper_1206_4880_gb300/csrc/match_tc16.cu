@@ -63,10 +63,13 @@ struct Tc16Shared {
 constexpr size_t kTc16Smem = sizeof(Tc16Shared) + 1024;
 static_assert(kTc16Smem <= 232448, "shared memory per CTA");
 
-// Scores of one accumulator tile for this thread's range row: 16 domains x 8 isometries.
+// Scores of one accumulator tile for this thread's range row: 16 domains x 8 isometries. The 16
+// domains (positions jh .. jh + 15, jh a multiple of 16) form one group, whose largest key goes on
+// into t1, t2 (the two largest group keys of the chunk), as in the B = 8 kernel.
 template <bool MASK>
 __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float alpha, int jh, int jrel, int lo_r,
                                       int hi_r, uint32_t &t1, uint32_t &t2) {
+    float gmax = 0.f;
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
@@ -99,7 +102,7 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                 }
                 k[h] = key;
             }
-            top2u_pair(t1, t2, k[0], k[1]);
+            gmax = max3f(gmax, __uint_as_float(k[0]), __uint_as_float(k[1]));
         }
         if (c < 3) {
             if (c & 1)
@@ -108,6 +111,7 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                 tmem_ld_wait(vb);
         }
     }
+    top2u(t1, t2, __float_as_uint(gmax));
 }
 
 }  // namespace
@@ -399,17 +403,16 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
 }
 
 // ---- exact re-evaluation and certification ----------------------------------------------------
-// One warp per class-sorted range position i of one image, as the B = 8 re-evaluation: the two
-// best keys over the tile's work items are evaluated exactly under all 8 isometries (lane
-// (candidate, t, half) sums X over 8 of the 16 rows), the best is certified if the runner-up's
+// One warp per class-sorted range position i of one image, as the B = 8 re-evaluation: the best
+// group key's 16 domains are evaluated exactly under all 8 isometries (two lanes per domain), the
+// best is certified if the runner-up's
 // score * (1 + 2^-13) + 2^-16 < exact best gain / 2048 (the key truncation errs by less than
 // 2^-14 relatively, the score formula and the epilogue's single rounding of the exact Y by less
 // than 2^-18 relatively; the absolute term only guards the degenerate scores near zero), else the
 // range is queued for the exact re-search.
 constexpr int kReeval16Threads = 256;
 struct __align__(16) Reeval16Stage {
-    uint16_t S[2][4][256];
-    uint8_t r[256];
+    uint8_t rp[8][256];  // the range's inverse-permuted copies rp[t][src_t(p)] = r[p]
 };
 
 // One warp's exact best, left for the block's finishing lanes (kinds as in the B = 8 kernel).
@@ -465,89 +468,50 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
         top2(b1, b2, o1);
         top2(b1, b2, o2);
     }
-    // exact evaluation, staged as in the 8x8 re-evaluation: the range and both candidates' blocks
-    // (four layouts each: as stored, transposed, rows reversed, transposed with rows reversed) in
-    // shared memory; lane (c, t, half) sums X over 8 of the 16 rows with packed dot products.
+    // exact evaluation of the best key's 16-domain group inside the pool window, as in the 8x8
+    // re-evaluation (lane l: domain l mod 16, isometries 4 (l / 16) .. 4 (l / 16) + 3)
     Reeval16Stage &sg = sg16;
-    const int j0 = (int)(~(uint32_t)(b1 & 0xffffffffu)) - dom_off;
-    const int j1 = (int)(~(uint32_t)(b2 & 0xffffffffu)) - dom_off;
-    const bool h0 = b1 != 0 && j0 >= 0 && j0 < g.Dn, h1 = b2 != 0 && j1 >= 0 && j1 < g.Dn;
-    const int d0 = h0 ? dom_order[j0] : INT_MAX, d1 = h1 ? dom_order[j1] : INT_MAX;
-    {
-        const int px = 8 * lane;  // 8 pixels of row px / 16
-        const uint8_t *prow = img + (size_t)(ry + (px >> 4)) * g.pitch + rx + (px & 15);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sg.r[px + k] = prow[k];
-    }
+    for (int k = 0; k < 8; ++k) {
+        const int px = 8 * lane + k, y = px >> 4, x = px & 15;
+        const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int e = 8 * (lane + 32 * k), c = e >> 8, q = e & 255, y = q >> 4, x = q & 15;  // x = 0 or 8
-        const bool hk = c ? h1 : h0;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (hk) v = *reinterpret_cast<const uint4 *>(domS + (size_t)(c ? d1 : d0) * 256 + q);
-        *reinterpret_cast<uint4 *>(&sg.S[c][0][16 * y + x]) = v;
-        // reversed: elements x..x+7 land at 15-x-7..15-x in reverse order
-        const uint4 rv = make_uint4(__byte_perm(v.w, 0, 0x1032), __byte_perm(v.z, 0, 0x1032),
-                                    __byte_perm(v.y, 0, 0x1032), __byte_perm(v.x, 0, 0x1032));
-        *reinterpret_cast<uint4 *>(&sg.S[c][2][16 * y + 8 - x]) = rv;
-        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            const uint16_t u = (uint16_t)(w4[h >> 1] >> (16 * (h & 1)));
-            sg.S[c][1][16 * (x + h) + y] = u;
-            sg.S[c][3][16 * (x + h) + 15 - y] = u;
+        for (int t = 0; t < 8; ++t) {
+            int sy, sx;
+            iso_src(16, t, y, x, sy, sx);
+            sg.rp[t][sy * 16 + sx] = v;
         }
     }
     __syncwarp();
-    const int cidx = lane >> 4, t = (lane >> 1) & 7, hrow = (lane & 1) * 8;
-    const bool has = cidx ? h1 : h0;
-    GainW gg{-1, 1};
-    int d = cidx ? d1 : d0;
+    const int p1 = (int)(~(uint32_t)(b1 & 0xffffffffu));  // batch-wide positions
+    int pos = b1 != 0 ? (p1 & ~15) + (lane & 15) : -1;
+    if (pos < ri.y || pos >= ri.z) pos = -1;
+    const int t0 = (lane >> 4) * 4;  // lanes 0-15: isometries 0-3 of their domain, lanes 16-31: 4-7
+    GainW gg;
+    gg.num = -1;
+    gg.den = 1;
+    int d = INT_MAX, bt = 0;
     long long P = 0, Q = 0, C = 0;
-    int X = 0;
-    {
-        const int swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
-        const uint16_t *M = sg.S[cidx][swap + 2 * (swap ? fy : fx)];
-        const int flip = swap ? fx : fy;
-        unsigned acc = 0;
-#pragma unroll
-        for (int y = hrow; y < hrow + 8; ++y) {
-            const uint4 *mrow = reinterpret_cast<const uint4 *>(M + 16 * (flip ? 15 - y : y));
-            const uint4 m0 = mrow[0], m1 = mrow[1];
-            const uint4 rr = *reinterpret_cast<const uint4 *>(sg.r + 16 * y);
-            acc = __dp2a_lo(m0.x, rr.x, acc);
-            acc = __dp2a_hi(m0.y, rr.x, acc);
-            acc = __dp2a_lo(m0.z, rr.y, acc);
-            acc = __dp2a_hi(m0.w, rr.y, acc);
-            acc = __dp2a_lo(m1.x, rr.z, acc);
-            acc = __dp2a_hi(m1.y, rr.z, acc);
-            acc = __dp2a_lo(m1.z, rr.w, acc);
-            acc = __dp2a_hi(m1.w, rr.w, acc);
-        }
-        X = (int)acc;  // <= 128 * 255 * 1020 < 2^31
-    }
-    X += __shfl_xor_sync(0xffffffffu, X, 1);
-    // best isometry of each candidate (largest |P|, ties to the smaller t), then the better of the
-    // two candidates (as in the 8x8 re-evaluation)
-    if (has) {
+    if (pos >= 0) {
+        d = dom_order[pos - dom_off];
+        unsigned X[4];
+        corr<16, 4>(sg.rp + t0, domS + (size_t)d * 256, X);
         C = dsum[d];
         Q = 256LL * dsumsq[d] - C * C;
-        P = 256LL * (long long)X - A * C;
-    }
-    int bt = t;
 #pragma unroll
-    for (int off = 2; off < 16; off <<= 1) {
-        const long long oP = __shfl_xor_sync(0xffffffffu, P, off);
-        const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
-        const long long a0 = P < 0 ? -P : P, a1 = oP < 0 ? -oP : oP;
-        if (a1 > a0 || (a1 == a0 && ot < bt)) {
-            P = oP;
-            bt = ot;
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + k;
+            const long long Pt = 256LL * (long long)X[k] - A * C;
+            const GainW gt = exact_gain_w(Pt, Q);
+            if (cand_better(gt, d, t, gg, d, bt)) {
+                gg = gt;
+                bt = t;
+                P = Pt;
+            }
         }
     }
-    if (has) gg = exact_gain_w(P, Q);
-    {
-        const int off = 16;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
         GainW og;
         const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)gg.num, off);
         const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(gg.num >> 64), off);

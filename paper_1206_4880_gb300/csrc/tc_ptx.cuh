@@ -166,17 +166,6 @@ __device__ __forceinline__ float max3_abs(float a, float b, float c) {
     return d;
 }
 
-// Top-2 (b1 >= b2) of the running pair and two new 32-bit keys. Keys are the bits of non-negative
-// finite floats (or 0), whose order as floats is their order as unsigned integers, so the
-// floating-point min/max pipes rank them; the second largest of {b1, b2, hi, lo} is
-// max(b2, min(b1, hi), lo).
-__device__ __forceinline__ void top2u_pair(uint32_t &b1, uint32_t &b2, uint32_t k1, uint32_t k2) {
-    const float f1 = __uint_as_float(k1), f2 = __uint_as_float(k2), t1 = __uint_as_float(b1);
-    const float hi = fmaxf(f1, f2), lo = fminf(f1, f2);
-    b2 = __float_as_uint(max3f(__uint_as_float(b2), fminf(t1, hi), lo));
-    b1 = __float_as_uint(fmaxf(t1, hi));
-}
-
 // Folds a chunk's 32-bit key (score bits, low 9 bits = 511 - domain offset in the chunk starting
 // at batch-wide position cbase) into the running 64-bit keys (score bits << 32 | ~position).
 __device__ __forceinline__ void merge_chunk_key(unsigned long long &b1, unsigned long long &b2, uint32_t t,
