@@ -599,13 +599,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---- exact re-evaluation and certification ----------------------------------------------------
-constexpr int kReevalThreads = 512;
+constexpr int kReevalThreads = 256;
 // Per-warp staging of one range: its 8 inverse-permuted copies rp[t][src_t(p)] = r[p].
 struct __align__(16) ReevalStage {
     uint8_t rp[8][64];
 };
 
-// One warp's exact best, left for the block's finishing lanes. kind 0: no range; 1: flat range
+// One half-warp's exact best, left for the block's finishing lanes. kind 0: no range; 1: flat range
 // (its code as is); 2: ranked range (certify, then code or queue). u2: the runner-up key's score
 // bits.
 struct ReevalRes {
@@ -615,14 +615,15 @@ struct ReevalRes {
     int kind, has1, has2;
 };
 
-// Exact evaluation of class-sorted range position i by one warp (see k_reeval).
+// Exact evaluation of class-sorted range position i by one half-warp (lanes hmask, hl = lane
+// mod 16; see k_reeval).
 __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                                             const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                                             const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
                                             const int32_t *__restrict__ bin_off, int nbuckets,
                                             const int4 *__restrict__ rng_info, int rng_off, int dom_off,
                                             const int4 *__restrict__ tile_items,
-                                            const unsigned long long *__restrict__ cand, int i, int lane,
+                                            const unsigned long long *__restrict__ cand, int i, int hl, unsigned hmask,
                                             ReevalStage &sg, ReevalRes &res) {
     const int4 ri = rng_info[i];
     const int r = ri.w;
@@ -634,12 +635,12 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
         // smallest id of the pool is the smallest first entry of a bucket inside the window
         int dmin = INT_MAX;
         const int wlo = ri.y - dom_off, whi = ri.z - dom_off;
-        for (int bb = lane; bb < nbuckets; bb += 32)
+        for (int bb = hl; bb < nbuckets; bb += 16)
             if (bin_off[bb] < bin_off[bb + 1] && bin_off[bb] >= wlo && bin_off[bb] < whi)
                 dmin = min(dmin, dom_order[bin_off[bb]]);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
-        if (lane == 0) {
+        for (int off = 8; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(hmask, dmin, off));
+        if (hl == 0) {
             const long long C = dsum[dmin];
             const long long Q = 64LL * dsumsq[dmin] - C * C;
             // X = (A / 64) C exactly for a constant block, so P = 64 X - A C = 0
@@ -655,11 +656,11 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
     const int4 ti = tile_items[ig / kTileM];
     unsigned long long b1 = 0, b2 = 0;
     const unsigned long long *ck = cand + (size_t)ti.x * kTileM * 4 + (size_t)row * ti.y * 4;
-    for (int e = lane; e < 4 * ti.y; e += 32) top2(b1, b2, ck[e]);
+    for (int e = hl; e < 4 * ti.y; e += 16) top2(b1, b2, ck[e]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, off);
-        const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, b2, off);
+    for (int off = 8; off > 0; off >>= 1) {
+        const unsigned long long o1 = __shfl_xor_sync(hmask, b1, off);
+        const unsigned long long o2 = __shfl_xor_sync(hmask, b2, off);
         top2(b1, b2, o1);
         top2(b1, b2, o2);
     }
@@ -667,12 +668,12 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
     // key, so every domain outside that group scores at most the runner-up key, and only the
     // group's domains inside the pool window can be certified (the runner-up's own domain is
     // bounded by its key, so it can never pass the test below). The warp stages the range's
-    // inverse-permuted copies; lane l forms X_t of domain (l mod 16) of the group for isometries
-    // 4 (l / 16) .. 4 (l / 16) + 3 exactly (corr) and keeps its best (gain, then smaller t); a
-    // warp reduction keeps the best (gain, then smaller domain id, then smaller t).
+    // inverse-permuted copies; lane hl forms X_t of the group's domain hl for all 8 isometries
+    // exactly (corr8) and keeps its best (gain, then smaller t); a half-warp reduction keeps the
+    // best (gain, then smaller domain id, then smaller t).
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int px = 2 * lane + k, y = px >> 3, x = px & 7;
+    for (int k = 0; k < 4; ++k) {
+        const int px = 4 * hl + k, y = px >> 3, x = px & 7;
         const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -681,24 +682,22 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
             sg.rp[t][sy * 8 + sx] = v;
         }
     }
-    __syncwarp();
+    __syncwarp(hmask);
     const int p1 = (int)(~(uint32_t)(b1 & 0xffffffffu));  // batch-wide positions
-    int pos = b1 != 0 ? (p1 & ~15) + (lane & 15) : -1;
+    int pos = b1 != 0 ? (p1 & ~15) + hl : -1;
     if (pos < ri.y || pos >= ri.z) pos = -1;
-    const int t0 = (lane >> 4) * 4;  // lanes 0-15: isometries 0-3 of their domain, lanes 16-31: 4-7
     Gain gg{-1, 1};
     int d = INT_MAX, bt = 0;
     long long P = 0, Q = 0, C = 0;
     if (pos >= 0) {
         d = dom_order[pos - dom_off];
-        unsigned X[4];
-        corr<8, 4>(sg.rp + t0, domS + (size_t)d * 64, X);
+        unsigned X[8];
+        corr8<8>(sg.rp, domS + (size_t)d * 64, X);
         C = dsum[d];
         Q = 64LL * dsumsq[d] - C * C;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = t0 + k;
-            const long long Pt = 64LL * (long long)X[k] - A * C;
+        for (int t = 0; t < 8; ++t) {
+            const long long Pt = 64LL * (long long)X[t] - A * C;
             const Gain gt = exact_gain(Pt, Q);
             if (cand_better(gt, d, t, gg, d, bt)) {
                 gg = gt;
@@ -708,11 +707,11 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
         }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const Gain og{__shfl_xor_sync(0xffffffffu, gg.num, off), __shfl_xor_sync(0xffffffffu, gg.den, off)};
-        const int od = __shfl_xor_sync(0xffffffffu, d, off), ot = __shfl_xor_sync(0xffffffffu, bt, off);
-        const long long oP = __shfl_xor_sync(0xffffffffu, P, off), oQ = __shfl_xor_sync(0xffffffffu, Q, off);
-        const long long oC = __shfl_xor_sync(0xffffffffu, C, off);
+    for (int off = 8; off > 0; off >>= 1) {
+        const Gain og{__shfl_xor_sync(hmask, gg.num, off), __shfl_xor_sync(hmask, gg.den, off)};
+        const int od = __shfl_xor_sync(hmask, d, off), ot = __shfl_xor_sync(hmask, bt, off);
+        const long long oP = __shfl_xor_sync(hmask, P, off), oQ = __shfl_xor_sync(hmask, Q, off);
+        const long long oC = __shfl_xor_sync(hmask, C, off);
         if (cand_better(og, od, ot, gg, d, bt)) {
             gg = og;
             d = od;
@@ -722,7 +721,7 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
             C = oC;
         }
     }
-    if (lane == 0)
+    if (hl == 0)
         res = ReevalRes{gg.num, gg.den, P, Q, A, Bs, (int)C, d, bt, r, i, (uint32_t)(b2 >> 32), 2, b1 != 0, b2 != 0};
 }
 
@@ -771,15 +770,16 @@ __device__ __forceinline__ void reeval_finish(const ReevalRes &e, int32_t *__res
     out.sse[e.r] = sse;
 }
 
-// One warp per class-sorted range position i of one image. Merges the range's top-2 group keys
-// over its tile's work items, evaluates the best key's 16-domain group under all 8 isometries
-// exactly, keeps the best (gain, then smaller domain id, then smaller isometry) and certifies it: every domain outside the evaluated group has an FP32 score at most
-// the runner-up key's, and an FP32 score is an upper bound of that domain's exact gain / 512 up to
-// a relative 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful of
-// single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other
-// domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat
-// ranges (n Bs = A^2) have zero error for every candidate; their code is the smallest domain id of
-// the pool with t = 0.
+// One half-warp per class-sorted range position i of one image. Merges the range's top-2 group
+// keys over its tile's work items, evaluates the best key's 16-domain group under all 8
+// isometries exactly, keeps the best (gain, then smaller domain id, then smaller isometry) and
+// certifies it: every domain outside the evaluated group has an FP32 score at most the runner-up
+// key's, and an FP32 score is an upper bound of that domain's exact gain / 512 up to a relative
+// 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful of
+// single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other domain
+// can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
+// (n Bs = A^2) have zero error for every candidate; their code is the smallest domain id of the
+// pool with t = 0.
 __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
                          const int32_t *__restrict__ dsum, const int32_t *__restrict__ dsumsq,
                          const int32_t *__restrict__ rsumsq, const int32_t *__restrict__ dom_order,
@@ -788,18 +788,19 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
                          const int4 *__restrict__ tile_items, const unsigned long long *__restrict__ cand,
                          const int32_t *__restrict__ gcounters, int32_t *__restrict__ fallback,
                          FallbackBest *__restrict__ fb_best, int32_t *counters, fic_codes out) {
-    __shared__ ReevalStage stage[kReevalThreads / 32];
-    __shared__ ReevalRes res[kReevalThreads / 32];
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // sorted position in this image
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ ReevalStage stage[kReevalThreads / 16];
+    __shared__ ReevalRes res[kReevalThreads / 16];
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;  // sorted position in this image
+    const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
+    const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
     if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
     if (i < g.R)
         reeval_rank(g, img, domS, dsum, dsumsq, rsumsq, dom_order, bin_off, nbuckets, rng_info, rng_off, dom_off,
-                    tile_items, cand, i, lane, stage[wib], res[wib]);
-    else if (lane == 0)
-        res[wib].kind = 0;
+                    tile_items, cand, i, hl, hmask, stage[slot], res[slot]);
+    else if (hl == 0)
+        res[slot].kind = 0;
     __syncthreads();
-    if (threadIdx.x < kReevalThreads / 32) reeval_finish(res[threadIdx.x], fallback, fb_best, counters, out);
+    if (threadIdx.x < kReevalThreads / 16) reeval_finish(res[threadIdx.x], fallback, fb_best, counters, out);
 }
 
 // ---- host side -------------------------------------------------------------------------------
@@ -902,7 +903,7 @@ cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
 
 cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, cudaStream_t st) {
-    const long long threads = (long long)g.R * 32;
+    const long long threads = (long long)g.R * 16;
     k_reeval<<<(unsigned)((threads + kReevalThreads - 1) / kReevalThreads), kReevalThreads, 0, st>>>(
         g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, sort_buckets(g), b.rng_info,
         b.rng_off, b.dom_off, tb.tile_items, tb.cand, tb.gcounters, b.fallback, b.fb_best, b.counters, out);

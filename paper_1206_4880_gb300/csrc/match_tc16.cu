@@ -403,9 +403,9 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
 }
 
 // ---- exact re-evaluation and certification ----------------------------------------------------
-// One warp per class-sorted range position i of one image, as the B = 8 re-evaluation: the best
-// group key's 16 domains are evaluated exactly under all 8 isometries (two lanes per domain), the
-// best is certified if the runner-up's
+// One half-warp per class-sorted range position i of one image, as the B = 8 re-evaluation: the
+// best group key's 16 domains are evaluated exactly under all 8 isometries (one lane per domain),
+// the best is certified if the runner-up's
 // score * (1 + 2^-13) + 2^-16 < exact best gain / 2048 (the key truncation errs by less than
 // 2^-14 relatively, the score formula and the epilogue's single rounding of the exact Y by less
 // than 2^-18 relatively; the absolute term only guards the degenerate scores near zero), else the
@@ -415,7 +415,7 @@ struct __align__(16) Reeval16Stage {
     uint8_t rp[8][256];  // the range's inverse-permuted copies rp[t][src_t(p)] = r[p]
 };
 
-// One warp's exact best, left for the block's finishing lanes (kinds as in the B = 8 kernel).
+// One half-warp's exact best, left for the block's finishing lanes (kinds as in the B = 8 kernel).
 struct Reeval16Res {
     __int128 num;
     long long den, P, Q, A, Bs;
@@ -424,14 +424,15 @@ struct Reeval16Res {
     int kind, has1, has2;
 };
 
-// Exact evaluation of class-sorted range position i by one warp (see k_reeval16).
+// Exact evaluation of class-sorted range position i by one half-warp (lanes hmask, hl = lane
+// mod 16; see k_reeval16).
 __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__restrict__ img,
                                               const uint16_t *__restrict__ domS, const int32_t *__restrict__ dsum,
                                               const int32_t *__restrict__ dsumsq, const int32_t *__restrict__ rsumsq,
                                               const int32_t *__restrict__ dom_order, const int32_t *__restrict__ bin_off,
                                               int nbuckets, const int4 *__restrict__ rng_info, int rng_off, int dom_off,
                                               const int4 *__restrict__ tile_items,
-                                              const unsigned long long *__restrict__ cand, int i, int lane,
+                                              const unsigned long long *__restrict__ cand, int i, int hl, unsigned hmask,
                                               Reeval16Stage &sg16, Reeval16Res &res) {
     const int4 ri = rng_info[i];
     const int r = ri.w;
@@ -441,12 +442,12 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
     if (256LL * Bs - A * A == 0) {  // flat range: every candidate has P = 0
         int dmin = INT_MAX;
         const int wlo = ri.y - dom_off, whi = ri.z - dom_off;
-        for (int bb = lane; bb < nbuckets; bb += 32)
+        for (int bb = hl; bb < nbuckets; bb += 16)
             if (bin_off[bb] < bin_off[bb + 1] && bin_off[bb] >= wlo && bin_off[bb] < whi)
                 dmin = min(dmin, dom_order[bin_off[bb]]);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
-        if (lane == 0) {
+        for (int off = 8; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(hmask, dmin, off));
+        if (hl == 0) {
             const long long C = dsum[dmin];
             const long long Q = 256LL * dsumsq[dmin] - C * C;
             const GainW g0 = exact_gain_w(0, Q);
@@ -460,20 +461,20 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
     const int4 ti = tile_items[ig / kTm16];
     unsigned long long b1 = 0, b2 = 0;
     const unsigned long long *ck = cand + (size_t)ti.x * kTm16 * 2 + (size_t)row * ti.y * 2;
-    for (int e = lane; e < 2 * ti.y; e += 32) top2(b1, b2, ck[e]);
+    for (int e = hl; e < 2 * ti.y; e += 16) top2(b1, b2, ck[e]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, b1, off);
-        const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, b2, off);
+    for (int off = 8; off > 0; off >>= 1) {
+        const unsigned long long o1 = __shfl_xor_sync(hmask, b1, off);
+        const unsigned long long o2 = __shfl_xor_sync(hmask, b2, off);
         top2(b1, b2, o1);
         top2(b1, b2, o2);
     }
     // exact evaluation of the best key's 16-domain group inside the pool window, as in the 8x8
-    // re-evaluation (lane l: domain l mod 16, isometries 4 (l / 16) .. 4 (l / 16) + 3)
+    // re-evaluation (lane hl: the group's domain hl, all 8 isometries)
     Reeval16Stage &sg = sg16;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int px = 8 * lane + k, y = px >> 4, x = px & 15;
+    for (int k = 0; k < 16; ++k) {
+        const int px = 16 * hl + k, y = px >> 4, x = px & 15;
         const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -482,11 +483,10 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
             sg.rp[t][sy * 16 + sx] = v;
         }
     }
-    __syncwarp();
+    __syncwarp(hmask);
     const int p1 = (int)(~(uint32_t)(b1 & 0xffffffffu));  // batch-wide positions
-    int pos = b1 != 0 ? (p1 & ~15) + (lane & 15) : -1;
+    int pos = b1 != 0 ? (p1 & ~15) + hl : -1;
     if (pos < ri.y || pos >= ri.z) pos = -1;
-    const int t0 = (lane >> 4) * 4;  // lanes 0-15: isometries 0-3 of their domain, lanes 16-31: 4-7
     GainW gg;
     gg.num = -1;
     gg.den = 1;
@@ -494,14 +494,13 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
     long long P = 0, Q = 0, C = 0;
     if (pos >= 0) {
         d = dom_order[pos - dom_off];
-        unsigned X[4];
-        corr<16, 4>(sg.rp + t0, domS + (size_t)d * 256, X);
+        unsigned X[8];
+        corr8<16>(sg.rp, domS + (size_t)d * 256, X);
         C = dsum[d];
         Q = 256LL * dsumsq[d] - C * C;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = t0 + k;
-            const long long Pt = 256LL * (long long)X[k] - A * C;
+        for (int t = 0; t < 8; ++t) {
+            const long long Pt = 256LL * (long long)X[t] - A * C;
             const GainW gt = exact_gain_w(Pt, Q);
             if (cand_better(gt, d, t, gg, d, bt)) {
                 gg = gt;
@@ -511,15 +510,15 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
         }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 8; off > 0; off >>= 1) {
         GainW og;
-        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)gg.num, off);
-        const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(gg.num >> 64), off);
+        const unsigned long long lo = __shfl_xor_sync(hmask, (unsigned long long)gg.num, off);
+        const long long hi = __shfl_xor_sync(hmask, (long long)(gg.num >> 64), off);
         og.num = (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned __int128)lo);
-        og.den = __shfl_xor_sync(0xffffffffu, gg.den, off);
-        const int od = __shfl_xor_sync(0xffffffffu, d, off), ot = __shfl_xor_sync(0xffffffffu, bt, off);
-        const long long oP = __shfl_xor_sync(0xffffffffu, P, off), oQ = __shfl_xor_sync(0xffffffffu, Q, off);
-        const long long oC = __shfl_xor_sync(0xffffffffu, C, off);
+        og.den = __shfl_xor_sync(hmask, gg.den, off);
+        const int od = __shfl_xor_sync(hmask, d, off), ot = __shfl_xor_sync(hmask, bt, off);
+        const long long oP = __shfl_xor_sync(hmask, P, off), oQ = __shfl_xor_sync(hmask, Q, off);
+        const long long oC = __shfl_xor_sync(hmask, C, off);
         if (cand_better(og, od, ot, gg, d, bt)) {
             gg = og;
             d = od;
@@ -529,7 +528,7 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
             C = oC;
         }
     }
-    if (lane == 0)
+    if (hl == 0)
         res = Reeval16Res{gg.num, gg.den, P, Q, A, Bs, (int)C, d, bt, r, i, (uint32_t)(b2 >> 32), 2, b1 != 0, b2 != 0};
 }
 
@@ -579,18 +578,19 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
                            const unsigned long long *__restrict__ cand, const int32_t *__restrict__ gcounters,
                            int32_t *__restrict__ fallback, FallbackBest *__restrict__ fb_best, int32_t *counters,
                            fic_codes out) {
-    __shared__ Reeval16Stage stage16[kReeval16Threads / 32];
-    __shared__ Reeval16Res res[kReeval16Threads / 32];
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ Reeval16Stage stage16[kReeval16Threads / 16];
+    __shared__ Reeval16Res res[kReeval16Threads / 16];
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
+    const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
     if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
     if (i < g.R)
         reeval16_rank(g, img, domS, dsum, dsumsq, rsumsq, dom_order, bin_off, nbuckets, rng_info, rng_off, dom_off,
-                      tile_items, cand, i, lane, stage16[wib], res[wib]);
-    else if (lane == 0)
-        res[wib].kind = 0;
+                      tile_items, cand, i, hl, hmask, stage16[slot], res[slot]);
+    else if (hl == 0)
+        res[slot].kind = 0;
     __syncthreads();
-    if (threadIdx.x < kReeval16Threads / 32)
+    if (threadIdx.x < kReeval16Threads / 16)
         reeval16_finish(res[threadIdx.x], fallback, fb_best, counters, out);
 }
 
@@ -635,7 +635,7 @@ cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st) {
 
 cudaError_t launch_reeval16(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                             const fic_codes &out, cudaStream_t st) {
-    const long long threads = (long long)g.R * 32;
+    const long long threads = (long long)g.R * 16;
     k_reeval16<<<(unsigned)((threads + kReeval16Threads - 1) / kReeval16Threads), kReeval16Threads, 0, st>>>(
         g, img, b.dom_S, b.dom_sum, b.dom_sumsq, b.range_sumsq, b.dom_order, b.bin_off, sort_buckets(g), b.rng_info,
         b.rng_off, b.dom_off, tb.tile_items, tb.cand, tb.gcounters, b.fallback, b.fb_best, b.counters, out);
