@@ -85,11 +85,11 @@ typedef struct {
     int32_t engine;        /* FIC_ENGINE_TENSOR or FIC_ENGINE_SIMT */
     int32_t flags;         /* 0, or FIC_FLAG_LITERAL_WINDOW */
     int32_t items_per_sm;  /* tensor engine scheduling: work items per SM the range tiles' domain
-                              chunks are split into, 1..64; 0 selects 16 */
+                              chunks are split into, 1..64; 0 selects 24 */
 } fic_params;
 
-/* Per-block statistics (Section 3.1: "the fractal dimension of the range blocks are calculated
- * and listed in a linear array", then the FD values of the overlapping domains). Device
+/* Per-block statistics (Section 3.1: the fractal dimensions of the range blocks are computed and
+ * kept in an array, then those of the overlapping domains). Device
  * arrays, R = (H/B)(W/B) entries for ranges and Dn = nDy*nDx for domains.
  *  range_sum = sum r, range_sumsq = sum r^2 over the B x B pixels;
  *  dom_sum = sum S, dom_sumsq = sum S^2 over the B x B integer 2x2 sums S of the domain;
@@ -191,7 +191,7 @@ fic_status fic_quality(const float *x, const uint8_t *ref, const fic_geom *g, do
 /* Doubles `header` must hold for fic_quantize. */
 #define FIC_QUANT_HEADER_DOUBLES 514
 
-/* A code format for Section 1's "transformation coefficients" (the paper fixes none): contrast
+/* A code format for the per-range map coefficients of Section 1 (the paper fixes none): contrast
  * s in [-1, 1] quantised uniformly to 2^bits_s levels including both endpoints, brightness o
  * quantised uniformly to 2^bits_o levels over the codes' own [min o, max o]; 1 <= bits <= 16.
  * With Ls = 2^bits_s - 1 and Lo = 2^bits_o - 1, each a separate binary64 operation:
@@ -219,7 +219,8 @@ fic_status fic_decode(const fic_codes *codes, const fic_geom *g, const fic_param
 /* Bytes of workspace fic_decode_scaled needs at this scale. */
 size_t fic_decode_scaled_workspace_size(const fic_geom *g, const fic_params *p, int32_t scale);
 
-/* Section 1, resolution independence ("the initial image can be of any size"): decodes the codes
+/* Section 1, resolution independence (decoding may start from an initial image of any size and
+ * reconstruct at any size): decodes the codes
  * of the H x W encoding g on the (scale*H) x (scale*W) grid, 1 <= scale <= 16: range r covers the
  * (B scale)^2 block at scale times its position, domain d the (2B scale)^2 block at scale times
  * its position, contracted by 2x2 averaging, under the isometries of the larger square. x0 and out

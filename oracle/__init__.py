@@ -13,7 +13,7 @@ Modules (each function cites the passage of the paper it follows):
             index derived from the fractal distance (Section 3.1, Eq. 2-3)
   pools     the per-range dynamic domain pool (Section 3, Section 3.1 Eq. 3)
   fit       least-squares contrast/brightness and the exact collage error of one candidate
-            (Section 1: "transformations in pixel intensity")
+            (Section 1: the intensity part of each map)
   match     exact best-match search over each range's pool (plain C, exact integers)
   decode    iterated application of the stored maps from an initial image (Section 1), its
             adjoint with respect to the per-range contrast and brightness, and PSNR (Table 4)

@@ -2,7 +2,7 @@
 
 Test infrastructure only (see the package docstring).
 
-Section 1: decoding applies the stored maps to an initial image ("mostly a background image")
+Section 1: decoding applies the stored maps to an initial image (typically a plain background)
 repeatedly; the maps are contractive, so the iterates are attracted to a fixed point. The paper
 gives no schedule; this oracle reads it as the Jacobi iteration
 
@@ -16,8 +16,8 @@ The adjoint: with W the linear part of one step (x -> s * T(D(x))), lambda_K = d
 lambda_k = W^T lambda_{k+1}, the gradients are
     dL/ds_r = sum_k sum_{p in r} lambda_{k+1}[p] * T_{t_r}(D(x_k, d_r))[p]
     dL/do_r = sum_k sum_{p in r} lambda_{k+1}[p].
-Resolution independence (Section 1: the initial image "can be of any size", decoding
-reconstructs "to any size"): decode_scaled applies the same codes on a z-times larger grid:
+Resolution independence (Section 1: the initial image may have any size, and decoding can
+reconstruct at any size): decode_scaled applies the same codes on a z-times larger grid:
 range r covers the (8z) x (8z) block at z times its position, domain d the (16z) x (16z) block at
 z times its position, contracted by 2x2 averaging, with the isometries of the larger square.
 

@@ -3,7 +3,7 @@
 Test infrastructure only (see the package docstring).
 
 Section 1: each range is approximated by a contracted, isometrically transformed domain under
-an affine "transformation in pixel intensity". Here that map is r ~ s * T_t(D) + o with D the
+an affine map of the pixel intensities. Here that map is r ~ s * T_t(D) + o with D the
 2x2-averaged domain (D = S / 4 for the integer 2x2 sums S), fitted by least squares, with the
 contrast clamped to |s| <= s_max for contractivity; when the clamp is active the brightness is
 re-solved for the clamped s. The paper prints none of these formulas; they are the textbook

@@ -4,7 +4,7 @@ Test infrastructure only (see the package docstring).
 
 * Ranges: the image is cut into non-overlapping B x B blocks (Section 1; Section 2 uses B = 8
   on a 1024 x 1024 image, giving 2^14 ranges).
-* Domains: 2B x 2B blocks, "scale size double that of range block", allowed to overlap
+* Domains: 2B x 2B blocks (twice the range side), allowed to overlap
   (Section 2). Their top-left corners lie on a grid of stride sigma; sigma = 1 gives the
   (n - 15)^2 domains per image of Table 1.
 * Contraction ("resizing", Section 1): a domain is reduced to B x B by summing each 2 x 2 pixel

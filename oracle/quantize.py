@@ -1,7 +1,7 @@
 """Oracle: a code format for the fractal codes (test infrastructure only, see the package
 docstring).
 
-Section 1 says the domain information and "the transformation coefficients" of every range are
+Section 1 says the domain information and the map coefficients of every range are
 stored in the compressed file, but the paper fixes no format, no bit allocation and no
 quantiser. This module reads that as: the domain index and the isometry are stored as
 integers; the contrast s in [-1, 1] is quantised uniformly to 2^bits_s levels including both

@@ -20,7 +20,7 @@ import torch
 
 from . import fic
 
-CANDIDATES = (4, 8, 16, 32)
+CANDIDATES = (4, 8, 16, 24, 32)
 
 
 def cache_path() -> str:

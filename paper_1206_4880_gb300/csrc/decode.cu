@@ -1,6 +1,6 @@
-// Fractal decoding and its adjoint (Revathy & Jayamohan, Section 1: "the transformations are
-// applied on an initial image"; the adjoint differentiates a fixed number of iterations with
-// respect to the per-range contrast s and brightness o).
+// Fractal decoding and its adjoint (Revathy & Jayamohan, Section 1: decoding iterates the stored
+// maps starting from an initial image; the adjoint differentiates a fixed number of iterations
+// with respect to the per-range contrast s and brightness o).
 //
 // One Jacobi step: x_{k+1}[p] = s_r * D(x_k, d_r)[src_{t_r}(p)] + o_r for every pixel p of range
 // r, with D the 2x2 average of the 2B x 2B domain. Adjoint of the linear part W:

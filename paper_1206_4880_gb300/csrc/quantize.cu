@@ -1,5 +1,5 @@
-// Code format and quantiser for the fractal codes. Section 1 stores "the domain information and
-// the transformation coefficients" of every range but the paper fixes no format; the library
+// Code format and quantiser for the fractal codes. Section 1 stores each range's domain and map
+// coefficients but the paper fixes no format; the library
 // quantises the contrast s uniformly to 2^bits_s levels on [-1, 1] (both endpoints included) and
 // the brightness o uniformly to 2^bits_o levels on the image's observed [min o, max o], rounding
 // half to even, with the binary64 operations in the order the header documents.
