@@ -85,7 +85,8 @@ typedef struct {
     int32_t engine;        /* FIC_ENGINE_TENSOR or FIC_ENGINE_SIMT */
     int32_t flags;         /* 0, or FIC_FLAG_LITERAL_WINDOW */
     int32_t items_per_sm;  /* tensor engine scheduling: work items per SM the range tiles' domain
-                              chunks are split into, 1..64; 0 selects 24 */
+                              chunks are split into, 1..64; 0 selects 24 (block 8) or 64
+                              (block 16) */
 } fic_params;
 
 /* Per-block statistics (Section 3.1: the fractal dimensions of the range blocks are computed and

@@ -445,6 +445,7 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
     auto on = [&](int k) -> cudaStream_t { return ns ? sp->s[k % ns] : st; };
     const bool tensor = p->engine != FIC_ENGINE_SIMT;
     const bool b16 = g[0].B == 16;
+    const int ipsm = p->items_per_sm > 0 ? p->items_per_sm : (b16 ? kItemsPerSm16 : kItemsPerSm);
     FIC_TRY(mark(0), "event");
     FIC_TRY(cudaMemsetAsync(b[0].counters, 0, 8 * sizeof(int32_t) * n, st), "memset");
     FIC_TRY(cudaMemsetAsync(tb.gcounters, 0, 8 * sizeof(int32_t), st), "memset");
@@ -465,7 +466,7 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], sp1->s[0], 1) : launch_pack(imgs[0], g[0], b[0], sp1->s[0], 1),
                 "pack");
         // the work list needs only the packed ranges' windows: it runs beside the domain packing
-        FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), sp1->s[0]),
+        FIC_TRY(launch_work_list(tb, sms * ipsm, sp1->s[0]),
                 "work_list");
         FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], st, 2) : launch_pack(imgs[0], g[0], b[0], st, 2), "pack");
         FIC_TRY(side_join(st, sp1, 1), "join");
@@ -501,7 +502,7 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(mark(5), "event");
     } else {
         if (!sp1)
-            FIC_TRY(launch_work_list(tb, sms * (p->items_per_sm > 0 ? p->items_per_sm : kItemsPerSm), st),
+            FIC_TRY(launch_work_list(tb, sms * ipsm, st),
                     "work_list");
         FIC_TRY(mark(3), "event");
         FIC_TRY(b16 ? launch_match_tc16(tb, sms, st) : launch_match_tc(tb, sms, st), "match_tc");

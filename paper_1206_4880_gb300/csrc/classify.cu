@@ -98,10 +98,9 @@ __device__ __forceinline__ double fd_of(const Log2Tab &L, int n2, int n4) {
 }
 
 // One thread per range: moments, N_2, N_4 and FD of the 8x8 pixel block.
-__global__ void k_range_stats(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
-                              int32_t *__restrict__ rsum, int32_t *__restrict__ rsumsq,
-                              int32_t *__restrict__ rcounts, double *__restrict__ rfd) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void range_stats(int r, const uint8_t *__restrict__ img, const Geo &g, const Log2Tab &L,
+                                            int32_t *__restrict__ rsum, int32_t *__restrict__ rsumsq,
+                                            int32_t *__restrict__ rcounts, double *__restrict__ rfd) {
     if (r >= g.R) return;
     const int y0 = (r / g.nRx) * 8, x0 = (r % g.nRx) * 8;
     int v[8][8];
@@ -152,11 +151,10 @@ __global__ void k_range_stats(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
 // C = sum S, E = sum S^2, N_2, N_4, FD; the block's largest FD and the complement of its least
 // FD go to extent_bits by atomicMax on the bit patterns (FD > 0, so they order like the values;
 // both words start at zero).
-__global__ void k_dom_stats(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
-                            uint16_t *__restrict__ domS, int32_t *__restrict__ dsum,
-                            int32_t *__restrict__ dsumsq, int32_t *__restrict__ dcounts,
-                            double *__restrict__ dfd, unsigned long long *extent_bits) {
-    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void dom_stats(int d, const uint8_t *__restrict__ img, const Geo &g, const Log2Tab &L,
+                                          uint16_t *__restrict__ domS, int32_t *__restrict__ dsum,
+                                          int32_t *__restrict__ dsumsq, int32_t *__restrict__ dcounts,
+                                          double *__restrict__ dfd, unsigned long long *extent_bits) {
     unsigned long long fbits_min = ~0ull, fbits_max = 0ull;
     if (d < g.Dn) {
         const int y0 = (d / g.nDx) * g.sigma, x0 = (d % g.nDx) * g.sigma;
@@ -304,10 +302,10 @@ struct Dbc16 {
 };
 
 // One thread per 16x16 range.
-__global__ void k_range_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
-                                int32_t *__restrict__ rsum, int32_t *__restrict__ rsumsq,
-                                int32_t *__restrict__ rcounts, double *__restrict__ rfd) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void range_stats16(int r, const uint8_t *__restrict__ img, const Geo &g,
+                                              const Log2Tab &L, int32_t *__restrict__ rsum,
+                                              int32_t *__restrict__ rsumsq, int32_t *__restrict__ rcounts,
+                                              double *__restrict__ rfd) {
     if (r >= g.R) return;
     const int y0 = (r / g.nRx) * 16, x0 = (r % g.nRx) * 16;
     Dbc16<5> dbc;
@@ -334,12 +332,12 @@ __global__ void k_range_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab 
 }
 
 // One thread per 32x32 domain: its 16x16 block of 2x2 sums S (stored), C, E, counts and FD; the
-// FD extent as in k_dom_stats.
-__global__ void k_dom_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
-                              uint16_t *__restrict__ domS, int32_t *__restrict__ dsum,
-                              int32_t *__restrict__ dsumsq, int32_t *__restrict__ dcounts,
-                              double *__restrict__ dfd, unsigned long long *extent_bits) {
-    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+// FD extent as in dom_stats.
+__device__ __forceinline__ void dom_stats16(int d, const uint8_t *__restrict__ img, const Geo &g,
+                                            const Log2Tab &L, uint16_t *__restrict__ domS,
+                                            int32_t *__restrict__ dsum, int32_t *__restrict__ dsumsq,
+                                            int32_t *__restrict__ dcounts, double *__restrict__ dfd,
+                                            unsigned long long *extent_bits) {
     unsigned long long fbits_min = ~0ull, fbits_max = 0ull;
     if (d < g.Dn) {
         const int y0 = (d / g.nDx) * g.sigma, x0 = (d % g.nDx) * g.sigma;
@@ -392,26 +390,45 @@ __global__ void k_dom_stats16(const uint8_t *__restrict__ img, Geo g, Log2Tab L,
     }
 }
 
+// Range and domain statistics in one launch: blocks [0, nbr) take 128 ranges each, the rest 128
+// domains each (whole blocks, so the domain blocks' warp reductions see full warps).
+template <int B>
+__global__ void __launch_bounds__(128) k_block_stats(const uint8_t *__restrict__ img, Geo g, Log2Tab L, int nbr,
+                                                     int32_t *__restrict__ rsum, int32_t *__restrict__ rsumsq,
+                                                     int32_t *__restrict__ rcounts, double *__restrict__ rfd,
+                                                     uint16_t *__restrict__ domS, int32_t *__restrict__ dsum,
+                                                     int32_t *__restrict__ dsumsq, int32_t *__restrict__ dcounts,
+                                                     double *__restrict__ dfd, unsigned long long *extent_bits) {
+    if ((int)blockIdx.x < nbr) {
+        const int r = blockIdx.x * 128 + threadIdx.x;
+        if (B == 16)
+            range_stats16(r, img, g, L, rsum, rsumsq, rcounts, rfd);
+        else
+            range_stats(r, img, g, L, rsum, rsumsq, rcounts, rfd);
+    } else {
+        const int d = (blockIdx.x - nbr) * 128 + threadIdx.x;
+        if (B == 16)
+            dom_stats16(d, img, g, L, domS, dsum, dsumsq, dcounts, dfd, extent_bits);
+        else
+            dom_stats(d, img, g, L, domS, dsum, dsumsq, dcounts, dfd, extent_bits);
+    }
+}
+
 cudaError_t launch_classify(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                             cudaStream_t st) {
     const Log2Tab &L = log2_table();
     // extent_bits = {complement of the least FD's bits, the largest FD's bits}, both reduced by
     // atomicMax from zero: the caller zeroes them with the image's counters
-    if (g.B == 16) {
-        k_range_stats16<<<(g.R + 127) / 128, 128, 0, st>>>(img, g, L, b.range_sum, b.range_sumsq,
-                                                           b.range_counts, b.range_fd);
-        ++g_launches;
-        k_dom_stats16<<<(g.Dn + 127) / 128, 128, 0, st>>>(img, g, L, b.dom_S, b.dom_sum, b.dom_sumsq,
-                                                          b.dom_counts, b.dom_fd, b.extent_bits);
-        ++g_launches;
-    } else {
-        k_range_stats<<<(g.R + 127) / 128, 128, 0, st>>>(img, g, L, b.range_sum, b.range_sumsq,
-                                                         b.range_counts, b.range_fd);
-        ++g_launches;
-        k_dom_stats<<<(g.Dn + 127) / 128, 128, 0, st>>>(img, g, L, b.dom_S, b.dom_sum, b.dom_sumsq,
-                                                        b.dom_counts, b.dom_fd, b.extent_bits);
-        ++g_launches;
-    }
+    const int nbr = (g.R + 127) / 128, nbd = (g.Dn + 127) / 128;
+    if (g.B == 16)
+        k_block_stats<16><<<nbr + nbd, 128, 0, st>>>(img, g, L, nbr, b.range_sum, b.range_sumsq, b.range_counts,
+                                                     b.range_fd, b.dom_S, b.dom_sum, b.dom_sumsq, b.dom_counts,
+                                                     b.dom_fd, b.extent_bits);
+    else
+        k_block_stats<8><<<nbr + nbd, 128, 0, st>>>(img, g, L, nbr, b.range_sum, b.range_sumsq, b.range_counts,
+                                                    b.range_fd, b.dom_S, b.dom_sum, b.dom_sumsq, b.dom_counts,
+                                                    b.dom_fd, b.extent_bits);
+    ++g_launches;
     const int n = g.R + g.Dn;
     k_bins<<<(n + 255) / 256, 256, 0, st>>>(g, b.range_fd, b.dom_fd, b.extent_bits, b.fd_extent,
                                             b.range_bin, b.dom_bin);

@@ -352,6 +352,9 @@ constexpr int kChunkDom = kTileDom * kChunkTiles;
 // slots) dominate; measured on GB300, 1024x1024 stride 4: 16 -> 0.944 ms, 24 -> 0.918 ms,
 // 32 -> 0.926 ms, 64 -> 0.944 ms (4096x4096 within 0.3% from 8 to 64)
 constexpr int kItemsPerSm = 24;
+// the same for 16x16 ranges (256-range tiles, 16-chunk groups): 2048x2048 stride 4:
+// 16 -> 10.53 ms, 32 -> 10.35, 64 -> 10.35; 4096x4096 stride 8: 16 -> 47.82, 64 -> 47.17
+constexpr int kItemsPerSm16 = 64;
 constexpr int kMaxItemTarget = 64 * 256;  // items_per_sm <= 64, SMs <= 256
 
 // Ranges per range tile of the tensor engine and box-count scales of a B x B block.
