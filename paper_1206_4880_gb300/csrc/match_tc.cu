@@ -86,10 +86,11 @@ constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 // largest group keys of the chunk; the exact re-evaluation evaluates the best group whole.
 // MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
 __device__ __forceinline__ float absmax8(const uint32_t *v) {
+    // a tree of depth two: three independent maxima of magnitudes, then their maximum
     const float a = max3_abs(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
     const float b = max3_abs(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5]));
-    const float c = max3_abs(__uint_as_float(v[6]), __uint_as_float(v[7]), a);
-    return fmaxf(b, c);
+    const float c = fmaxf(fabsf(__uint_as_float(v[6])), fabsf(__uint_as_float(v[7])));
+    return max3f(a, b, c);
 }
 
 // Key of domain l (compile time, < 16) of a half tile whose first domain sits at offset jrel (a
@@ -121,11 +122,11 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 tmem_ld32(taddr + (c + 1) * 32, vb);
         }
         const uint32_t *cur = (c & 1) ? vb : va;
+        uint32_t k[4];
 #pragma unroll
         for (int q2 = 0; q2 < 2; ++q2) {
             // two domains' (Q / 256, 128 / Q) per 16-byte shared load
             const float4 a2 = auxp[2 * c + q2];
-            uint32_t k[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q = 2 * q2 + h, l = 4 * c + q;
@@ -148,10 +149,12 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                     const int j = jh + l;
                     key = (j >= lo_r && j < hi_r) ? key : 0u;
                 }
-                k[h] = key;
+                k[2 * q2 + h] = key;
             }
-            gmax = max3f(gmax, __uint_as_float(k[0]), __uint_as_float(k[1]));
         }
+        // one link of the running group maximum per stage
+        gmax = max3f(gmax, max3f(__uint_as_float(k[0]), __uint_as_float(k[1]), __uint_as_float(k[2])),
+                     __uint_as_float(k[3]));
         if (c < 3) {
             if (c & 1)
                 tmem_ld_wait(va);

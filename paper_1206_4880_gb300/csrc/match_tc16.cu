@@ -82,9 +82,9 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                 tmem_ld32(taddr + (c + 1) * 32, vb);
         }
         const uint32_t *cur = (c & 1) ? vb : va;
+        uint32_t k[4];
 #pragma unroll
         for (int q2 = 0; q2 < 2; ++q2) {
-            uint32_t k[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q = 2 * q2 + h, l = 4 * c + q;
@@ -92,7 +92,8 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                 float y[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) y[t] = fmaf(alpha, a.x, __uint_as_float(cur[8 * q + t]));
-                const float p = fmaxf(max3_abs(y[0], y[1], y[2]), max3_abs(y[3], y[4], max3_abs(y[5], y[6], y[7])));
+                const float p = max3f(max3_abs(y[0], y[1], y[2]), max3_abs(y[3], y[4], y[5]),
+                                      fmaxf(fabsf(y[6]), fabsf(y[7])));
                 const float mm = fminf(p, a.y);
                 const float sc = fmaf(mm, mm * a.z, p - mm);
                 uint32_t key = (__float_as_uint(sc) & 0xFFFFFE00u) | (uint32_t)(511 - jrel - l);
@@ -100,10 +101,11 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                     const int j = jh + l;
                     key = (j >= lo_r && j < hi_r) ? key : 0u;
                 }
-                k[h] = key;
+                k[2 * q2 + h] = key;
             }
-            gmax = max3f(gmax, __uint_as_float(k[0]), __uint_as_float(k[1]));
         }
+        gmax = max3f(gmax, max3f(__uint_as_float(k[0]), __uint_as_float(k[1]), __uint_as_float(k[2])),
+                     __uint_as_float(k[3]));
         if (c < 3) {
             if (c & 1)
                 tmem_ld_wait(va);
