@@ -14,7 +14,7 @@
  * Conventions for every entry point:
  *  - Image, code, statistics and workspace pointers are DEVICE pointers owned by the caller.
  *    The library allocates no device memory and frees none; it keeps no state between calls
- *    except a per-device cache of its own kernel attributes and, for fic_encode_batched, four
+ *    except a per-device cache of its own kernel attributes and, for fic_encode_batched, eight
  *    internal CUDA streams and events per host thread and device (created on the first batched
  *    call that is not inside a stream capture; the images' per-image stages run on them,
  *    joined back into `stream` by events).

@@ -54,7 +54,7 @@ fic_status fail(fic_status s, const char *fmt, ...) {
 // Internal streams on which the per-image stages of a batch run concurrently (fork/join through
 // events on the caller's stream; inside a CUDA graph capture they become parallel branches). One
 // set per host thread and device, created on first use outside a capture and kept.
-constexpr int kSideStreams = 4;
+constexpr int kSideStreams = 8;
 struct SidePool {
     cudaStream_t s[kSideStreams];
     cudaEvent_t fork, join[kSideStreams];

@@ -206,52 +206,62 @@ __global__ void k_pack_ranges(Geo g, const uint8_t *__restrict__ img, const int3
     reinterpret_cast<uint4 *>(A_mat + (size_t)i * 64)[y] = pk;
 }
 
-// One thread per (sorted domain j, isometry t, row y), four domains per 256-thread block: B_mat
-// row 8j+t = T_t(S_{dom_order[j]}) - round(C / 64), each output row one 16-byte row of a staged
-// layout converted pairwise to FP16; dom_aux2[j] = (Q / 256, 128 / Q or 0), the constants of the
-// epilogue's clamped gain. Entries j >= Dn are zero.
+// Sixteen threads per sorted domain j, sixteen domains per 256-thread block: B_mat row 8j+t =
+// T_t(S_{dom_order[j]}) - round(C / 64). Each thread stages four elements of the domain's block
+// (one 8-byte load) into four layouts in shared memory, then writes four consecutive rows y of
+// one isometry t, each one 16-byte row of a layout converted pairwise to FP16; dom_aux2[j] =
+// (Q / 256, 128 / Q or 0), the constants of the epilogue's clamped gain. Entries j >= Dn are zero.
 __global__ void __launch_bounds__(256) k_pack_domains(Geo g, const uint16_t *__restrict__ domS,
                                                       const int32_t *__restrict__ dom_order,
                                                       const int32_t *__restrict__ dsum,
                                                       const int32_t *__restrict__ dsumsq, int n_pad,
                                                       __half *__restrict__ B_mat, uint4 *__restrict__ B1,
                                                       float2 *__restrict__ dom_aux2) {
-    __shared__ __align__(16) uint16_t L[4][4][64];
-    const int jl = threadIdx.x >> 6, e = threadIdx.x & 63;
-    const int j = blockIdx.x * 4 + jl, t = e >> 3, y = e & 7;
+    __shared__ __align__(16) uint16_t L[16][4][64];
+    const int jl = threadIdx.x >> 4, e = threadIdx.x & 15;
+    const int j = blockIdx.x * 16 + jl, t = e >> 1, y0 = (e & 1) * 4;
     const bool live = j < g.Dn;
     int d = 0, cbar = 0;
     if (live) {
         d = dom_order[j];
-        cbar = (dsum[d] + 32) >> 6;  // round(C / 64)
-        stage_layouts<8>(L[jl], e, domS[(size_t)d * 64 + e]);
+        const int C = dsum[d];
+        cbar = (C + 32) >> 6;  // round(C / 64)
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(domS + (size_t)d * 64) + e);  // elements 4e .. 4e + 3
+        stage_layouts<8>(L[jl], 4 * e, (uint16_t)(v.x & 0xFFFFu));
+        stage_layouts<8>(L[jl], 4 * e + 1, (uint16_t)(v.x >> 16));
+        stage_layouts<8>(L[jl], 4 * e + 2, (uint16_t)(v.y & 0xFFFFu));
+        stage_layouts<8>(L[jl], 4 * e + 3, (uint16_t)(v.y >> 16));
     }
     __syncthreads();
     if (j >= n_pad) return;
-    uint4 pk = make_uint4(0, 0, 0, 0);
+    uint4 *dst = reinterpret_cast<uint4 *>(B_mat + ((size_t)j * 8 + t) * 64) + y0;
     if (live) {
-        const uint4 m = *reinterpret_cast<const uint4 *>(iso_row<8>(L[jl], t, y));
         const uint32_t c2 = (0x6400u + (uint32_t)cbar) * 0x10001u;
-        pk = make_uint4(centred_h2(m.x, c2), centred_h2(m.y, c2), centred_h2(m.z, c2), centred_h2(m.w, c2));
-        if (y == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint4 m = *reinterpret_cast<const uint4 *>(iso_row<8>(L[jl], t, y0 + k));
+            dst[k] = make_uint4(centred_h2(m.x, c2), centred_h2(m.y, c2), centred_h2(m.z, c2), centred_h2(m.w, c2));
+        }
+        if (y0 == 0) {
             const int gamma = dsum[d] - 64 * cbar;
             const __half cg = __float2half_rn(-(float)gamma * (1.0f / 64.0f));  // exact: |gamma| <= 32
             B1[2 * ((size_t)j * 8 + t)] = make_uint4((uint32_t)__half_as_ushort(cg), 0, 0, 0);
             B1[2 * ((size_t)j * 8 + t) + 1] = make_uint4(0, 0, 0, 0);
         }
-        if (t == 0 && y == 0) {
+        if (e == 0) {
             const long long C = dsum[d];
             const long long Q = 64LL * dsumsq[d] - C * C;
             dom_aux2[j] = make_float2((float)Q * (1.0f / 256.0f), Q > 0 ? 128.0f / (float)Q : 0.f);
         }
     } else {
-        if (y == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(0, 0, 0, 0);
+        if (y0 == 0) {
             B1[2 * ((size_t)j * 8 + t)] = make_uint4(0, 0, 0, 0);
             B1[2 * ((size_t)j * 8 + t) + 1] = make_uint4(0, 0, 0, 0);
         }
-        if (t == 0 && y == 0) dom_aux2[j] = make_float2(0.f, 0.f);
+        if (e == 0) dom_aux2[j] = make_float2(0.f, 0.f);
     }
-    reinterpret_cast<uint4 *>(B_mat + ((size_t)j * 8 + t) * 64)[y] = pk;
 }
 
 // One block (TM threads) per range tile of the batch: the union [lo_u, hi_u) of its rows' pool
@@ -856,7 +866,7 @@ cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, c
         ++g_launches;
     }
     if (part != 1) {
-        const long long n = (long long)b.Dn_aux * 64;
+        const long long n = (long long)b.Dn_aux * 16;
         k_pack_domains<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, b.dom_S, b.dom_order, b.dom_sum,
                                                                    b.dom_sumsq, b.Dn_aux, b.B_mat, (uint4 *)b.B1_mat,
                                                                    // float2 pairs indexed by batch-wide domain position
