@@ -446,6 +446,8 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
     const bool tensor = p->engine != FIC_ENGINE_SIMT;
     const bool b16 = g[0].B == 16;
     const int ipsm = p->items_per_sm > 0 ? p->items_per_sm : (b16 ? kItemsPerSm16 : kItemsPerSm);
+    // 8x8 ranges in class mode on internal streams: windows, range packing and tile windows fused
+    const bool fused_tiles = ns && tensor && !b16 && !g[0].literal;
     FIC_TRY(mark(0), "event");
     FIC_TRY(cudaMemsetAsync(b[0].counters, 0, 8 * sizeof(int32_t) * n, st), "memset");
     FIC_TRY(cudaMemsetAsync(tb.gcounters, 0, 8 * sizeof(int32_t), st), "memset");
@@ -462,12 +464,15 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(cudaEventRecord(sp1->fork, st), "event");  // domain sort done
         FIC_TRY(cudaStreamWaitEvent(sp1->s[0], sp1->fork, 0), "event");
         FIC_TRY(mark(2), "event");
-        FIC_TRY(launch_pools_windows(g[0], b[0], sp1->s[0]), "pools");
-        FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], sp1->s[0], 1) : launch_pack(imgs[0], g[0], b[0], sp1->s[0], 1),
-                "pack");
+        if (b16) {
+            FIC_TRY(launch_pools_windows(g[0], b[0], sp1->s[0]), "pools");
+            FIC_TRY(launch_pack16(imgs[0], g[0], b[0], sp1->s[0], 1), "pack");
+        } else {
+            // windows, range packing and tile windows in one launch
+            FIC_TRY(launch_pack_ranges_tiles(imgs[0], g[0], b[0], tb, sp1->s[0]), "pack");
+        }
         // the work list needs only the packed ranges' windows: it runs beside the domain packing
-        FIC_TRY(launch_work_list(tb, sms * ipsm, sp1->s[0]),
-                "work_list");
+        FIC_TRY(launch_work_list(tb, sms * ipsm, sp1->s[0], !b16), "work_list");
         FIC_TRY(b16 ? launch_pack16(imgs[0], g[0], b[0], st, 2) : launch_pack(imgs[0], g[0], b[0], st, 2), "pack");
         FIC_TRY(side_join(st, sp1, 1), "join");
     } else if (ns) {
@@ -477,6 +482,14 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(side_fork(st, sp, ns), "fork");
         for (int k = 0; k < n; ++k) {
             FIC_TRY(launch_classify(imgs[k], g[k], b[k], on(k)), "classify");
+            if (fused_tiles) {
+                // both sorts, then windows, range packing and tile windows in one launch
+                FIC_TRY(launch_pools_domains(g[k], b[k], on(k)), "pools");
+                FIC_TRY(launch_pools_ranges_sort(g[k], b[k], on(k)), "pools");
+                FIC_TRY(launch_pack_ranges_tiles(imgs[k], g[k], b[k], tb, on(k)), "pack");
+                FIC_TRY(launch_pack(imgs[k], g[k], b[k], on(k), 2), "pack");
+                continue;
+            }
             FIC_TRY(launch_pools(g[k], b[k], on(k)), "pools");
             if (tensor)
                 FIC_TRY(b16 ? launch_pack16(imgs[k], g[k], b[k], on(k)) : launch_pack(imgs[k], g[k], b[k], on(k)),
@@ -501,9 +514,7 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         FIC_TRY(mark(4), "event");
         FIC_TRY(mark(5), "event");
     } else {
-        if (!sp1)
-            FIC_TRY(launch_work_list(tb, sms * ipsm, st),
-                    "work_list");
+        if (!sp1) FIC_TRY(launch_work_list(tb, sms * ipsm, st, fused_tiles), "work_list");
         FIC_TRY(mark(3), "event");
         FIC_TRY(b16 ? launch_match_tc16(tb, sms, st) : launch_match_tc(tb, sms, st), "match_tc");
         FIC_TRY(mark(4), "event");

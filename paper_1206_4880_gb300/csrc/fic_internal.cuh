@@ -381,7 +381,12 @@ cudaError_t launch_rescan(const uint8_t *img, const Geo &g, const EncodeBufs &b,
                           const fic_codes &out, int num_sms, cudaStream_t st);
 // operand packing: part 0 both, 1 ranges only, 2 domains only
 cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, cudaStream_t st, int part = 0);
-cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st);
+// range packing, pool windows, match count and tile windows of one image in one launch (8x8
+// ranges, class mode)
+cudaError_t launch_pack_ranges_tiles(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
+                                     cudaStream_t st);
+// tiles_done: the tile windows are already formed (launch_pack_ranges_tiles)
+cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st, bool tiles_done = false);
 cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st);
 cudaError_t launch_reeval(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
                           const fic_codes &out, cudaStream_t st);

@@ -67,18 +67,28 @@ __device__ __forceinline__ void scan_domain(const ScanShared<B> &sh, int d, long
     corr8<B>(sh.rp, domS + (size_t)d * n, X);
     const long long C = dsum[d];
     const long long Q = (long long)n * dsumsq[d] - C * C;
+    // with the domain fixed the clamped gain grows with |P|: its best isometry is the largest
+    // |P|, ties to the smaller t; one exact gain and one comparison per domain
+    long long P = (long long)n * (long long)X[0] - A * C, aP = P < 0 ? -P : P;
+    int bt = 0;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const long long P = (long long)n * (long long)X[t] - A * C;
-        const auto gg = FitOf<B>::gain(P, Q);
-        if (cand_better(gg, d, t, b.g, b.d, b.t)) {
-            b.g = gg;
-            b.d = d;
-            b.t = t;
-            b.P = P;
-            b.Q = Q;
-            b.C = (int)C;
+    for (int t = 1; t < 8; ++t) {
+        const long long Pt = (long long)n * (long long)X[t] - A * C;
+        const long long at = Pt < 0 ? -Pt : Pt;
+        if (at > aP) {
+            aP = at;
+            bt = t;
+            P = Pt;
         }
+    }
+    const auto gg = FitOf<B>::gain(P, Q);
+    if (cand_better(gg, d, bt, b.g, b.d, b.t)) {
+        b.g = gg;
+        b.d = d;
+        b.t = bt;
+        b.P = P;
+        b.Q = Q;
+        b.C = (int)C;
     }
 }
 

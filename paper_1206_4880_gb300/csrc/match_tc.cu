@@ -206,6 +206,90 @@ __global__ void k_pack_ranges(Geo g, const uint8_t *__restrict__ img, const int3
     reinterpret_cast<uint4 *>(A_mat + (size_t)i * 64)[y] = pk;
 }
 
+// k_pack_ranges for one range tile per 1024-thread block, in class mode, with the work the
+// separate window kernels would do: each range's pool window is read off the class offsets
+// (classes within w of its own; every domain if that is empty), the image's match count gains
+// 8 |window| per range, and the tile's union and intersection of windows and its chunk count
+// (as k_tile_windows) are formed by a block reduction. m0: the image's first tile in the batch.
+__global__ void __launch_bounds__(1024) k_pack_ranges_tile(Geo g, const uint8_t *__restrict__ img,
+                                                           const int32_t *__restrict__ range_order,
+                                                           const int32_t *__restrict__ rsum,
+                                                           const uint8_t *__restrict__ rbin,
+                                                           const int32_t *__restrict__ bin_off, int dom_off, int m0,
+                                                           __half *__restrict__ A_mat, uint4 *__restrict__ A1,
+                                                           int4 *__restrict__ rng_info, int4 *__restrict__ tile_win,
+                                                           int32_t *__restrict__ n_chunks, long long *matches) {
+    __shared__ int4 wred[32];
+    __shared__ long long mred[32];
+    const int i = blockIdx.x * kTileM + (threadIdx.x >> 3), y = threadIdx.x & 7;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 pk = make_uint4(0, 0, 0, 0);
+    int lo = 0, hi = 0;
+    const bool valid = i < g.R;
+    if (valid) {
+        const int r = range_order[i];
+        const int b = rbin[r];
+        lo = bin_off[max(0, b - g.w)];
+        hi = bin_off[min(g.K - 1, b + g.w) + 1];
+        if (lo == hi) {  // no domain in the window: search every domain
+            lo = 0;
+            hi = g.Dn;
+        }
+        const uint8_t *row = img + (size_t)((r / g.nRx) * 8 + y) * g.pitch + (r % g.nRx) * 8;
+        const int abar = (rsum[r] + 32) >> 6;  // round(A / 64)
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const __half a = __int2half_rn((int)row[2 * h] - abar);
+            const __half bb = __int2half_rn((int)row[2 * h + 1] - abar);
+            w[h] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(bb) << 16);
+        }
+        pk = make_uint4(w[0], w[1], w[2], w[3]);
+        if (y == 0) {
+            rng_info[i] = make_int4(rsum[r], lo + dom_off, hi + dom_off, r);
+            const int alpha = rsum[r] - 64 * abar;
+            A1[2 * i] = make_uint4((uint32_t)__half_as_ushort(__int2half_rn(alpha)), 0, 0, 0);
+            A1[2 * i + 1] = make_uint4(0, 0, 0, 0);
+        }
+    } else if (y == 0) {
+        rng_info[i] = make_int4(0, 0, 0, -1);
+        A1[2 * i] = make_uint4(0, 0, 0, 0);
+        A1[2 * i + 1] = make_uint4(0, 0, 0, 0);
+    }
+    reinterpret_cast<uint4 *>(A_mat + (size_t)i * 64)[y] = pk;
+    // tile windows (batch-wide positions) and the match count
+    int lo_u = valid ? lo + dom_off : INT_MAX, hi_u = valid ? hi + dom_off : INT_MIN;
+    int lo_i = valid ? lo + dom_off : INT_MIN, hi_i = valid ? hi + dom_off : INT_MAX;
+    long long mc = (valid && y == 0) ? 8LL * (hi - lo) : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo_u = min(lo_u, __shfl_xor_sync(0xffffffffu, lo_u, off));
+        hi_u = max(hi_u, __shfl_xor_sync(0xffffffffu, hi_u, off));
+        lo_i = max(lo_i, __shfl_xor_sync(0xffffffffu, lo_i, off));
+        hi_i = min(hi_i, __shfl_xor_sync(0xffffffffu, hi_i, off));
+        mc += __shfl_xor_sync(0xffffffffu, mc, off);
+    }
+    if (lane == 0) {
+        wred[warp] = make_int4(lo_u, hi_u, lo_i, hi_i);
+        mred[warp] = mc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int4 t = wred[0];
+        long long m = mred[0];
+        for (int k = 1; k < 32; ++k) {
+            t.x = min(t.x, wred[k].x);
+            t.y = max(t.y, wred[k].y);
+            t.z = max(t.z, wred[k].z);
+            t.w = min(t.w, wred[k].w);
+            m += mred[k];
+        }
+        tile_win[m0 + blockIdx.x] = t;
+        n_chunks[m0 + blockIdx.x] = t.y > t.x ? (t.y - 1) / kChunkDom - t.x / kChunkDom + 1 : 0;
+        if (m) atomicAdd(reinterpret_cast<unsigned long long *>(matches), (unsigned long long)m);
+    }
+}
+
 // Sixteen threads per sorted domain j, sixteen domains per 256-thread block: B_mat row 8j+t =
 // T_t(S_{dom_order[j]}) - round(C / 64). Each thread stages four elements of the domain's block
 // (one 8-byte load) into four layouts in shared memory, then writes four consecutive rows y of
@@ -709,15 +793,21 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
         C = dsum[d];
         Q = 64LL * dsumsq[d] - C * C;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
+        // with the domain (so Q and C) fixed the clamped gain grows with |P|: the best isometry
+        // is the largest |P|, ties to the smaller t (a flat domain has P = 0 for every t)
+        P = 64LL * (long long)X[0] - A * C;
+        long long aP = P < 0 ? -P : P;
+#pragma unroll
+        for (int t = 1; t < 8; ++t) {
             const long long Pt = 64LL * (long long)X[t] - A * C;
-            const Gain gt = exact_gain(Pt, Q);
-            if (cand_better(gt, d, t, gg, d, bt)) {
-                gg = gt;
+            const long long at = Pt < 0 ? -Pt : Pt;
+            if (at > aP) {
+                aP = at;
                 bt = t;
                 P = Pt;
             }
         }
+        gg = exact_gain(P, Q);
     }
 #pragma unroll
     for (int off = 8; off > 0; off >>= 1) {
@@ -877,12 +967,23 @@ cudaError_t launch_pack(const uint8_t *img, const Geo &g, const EncodeBufs &b, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st) {
-    if (tb.tm == 2 * kTileM)
-        k_tile_windows<2 * kTileM><<<tb.n_mtiles, 2 * kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
-    else
-        k_tile_windows<kTileM><<<tb.n_mtiles, kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
+cudaError_t launch_pack_ranges_tiles(const uint8_t *img, const Geo &g, const EncodeBufs &b, const TcBatch &tb,
+                                     cudaStream_t st) {
+    k_pack_ranges_tile<<<b.R_pad / kTileM, 1024, 0, st>>>(g, img, b.range_order, b.range_sum, b.range_bin, b.bin_off,
+                                                         b.dom_off, b.mt_off, b.A_mat, (uint4 *)b.A1_mat,
+                                                         b.rng_info, tb.tile_win, tb.n_chunks, b.matches);
     ++g_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t st, bool tiles_done) {
+    if (!tiles_done) {
+        if (tb.tm == 2 * kTileM)
+            k_tile_windows<2 * kTileM><<<tb.n_mtiles, 2 * kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
+        else
+            k_tile_windows<kTileM><<<tb.n_mtiles, kTileM, 0, st>>>(tb.rng_info, tb.tile_win, tb.n_chunks);
+        ++g_launches;
+    }
     const int target = max(1, min(target_items, kMaxItemTarget));
     k_work_list<<<1, 1024, 0, st>>>(tb.n_mtiles, target, tb.cpi_cap, tb.B == 16 ? 16 : kTileDom, tb.ng_max,
                                     tb.tile_win, tb.n_chunks, tb.work, tb.work_slot, tb.tile_items, tb.grp,

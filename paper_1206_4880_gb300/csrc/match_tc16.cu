@@ -501,15 +501,21 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
         C = dsum[d];
         Q = 256LL * dsumsq[d] - C * C;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
+        // with the domain (so Q and C) fixed the clamped gain grows with |P|: the best isometry
+        // is the largest |P|, ties to the smaller t (a flat domain has P = 0 for every t)
+        P = 256LL * (long long)X[0] - A * C;
+        long long aP = P < 0 ? -P : P;
+#pragma unroll
+        for (int t = 1; t < 8; ++t) {
             const long long Pt = 256LL * (long long)X[t] - A * C;
-            const GainW gt = exact_gain_w(Pt, Q);
-            if (cand_better(gt, d, t, gg, d, bt)) {
-                gg = gt;
+            const long long at = Pt < 0 ? -Pt : Pt;
+            if (at > aP) {
+                aP = at;
                 bt = t;
                 P = Pt;
             }
         }
+        gg = exact_gain_w(P, Q);
     }
 #pragma unroll
     for (int off = 8; off > 0; off >>= 1) {
