@@ -246,8 +246,10 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *g, const 
  *   ms[0] classification, ms[1] pool build, ms[2] operand packing, ms[3] matching,
  *   ms[4] exact re-evaluation, ms[5] exact re-search of uncertified ranges
  * (0 for stages the engine does not run), and the number of kernels the last fic_encode on
- * this thread launched to *launches (nullable). Enabling creates the events on the current
- * device; fic_profile_read returns FIC_ERR_INVALID_ARG if profiling is off. */
+ * this thread launched to *launches (nullable). The first enable creates the events on the
+ * current device; they are kept for the thread's lifetime (an encode captured in a CUDA graph
+ * with profiling on records into them at every replay, as event-record nodes). fic_profile_read
+ * returns FIC_ERR_INVALID_ARG if profiling is off. */
 fic_status fic_profile_enable(int32_t on);
 fic_status fic_profile_read(float *ms, int32_t n, int32_t *launches);
 

@@ -38,6 +38,8 @@ thread_local char g_err[512] = "";
 // re-search.
 struct Prof {
     bool on = false;
+    bool made = false;  // events exist (created on the first enable, kept: a captured graph may
+                        // record into them after profiling is switched off and on again)
     cudaEvent_t ev[7] = {};
     int launches = 0;
 };
@@ -435,8 +437,15 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
     int sms = 0;
     FIC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
     g_launches = 0;
+    // stage marks; inside a stream capture they become event-record nodes of the graph (external
+    // records), so a replayed encode still reports its stage times
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    if (g_prof.on) FIC_TRY(cudaStreamIsCapturing(st, &capturing), "capture status");
     auto mark = [&](int i) -> cudaError_t {
-        return g_prof.on ? cudaEventRecord(g_prof.ev[i], st) : cudaSuccess;
+        if (!g_prof.on) return cudaSuccess;
+        return capturing == cudaStreamCaptureStatusActive
+                   ? cudaEventRecordWithFlags(g_prof.ev[i], st, cudaEventRecordExternal)
+                   : cudaEventRecord(g_prof.ev[i], st);
     };
     // a batch runs its per-image stages on internal streams, image k on stream k % ns, joined back
     // before the batch-wide matcher and at the end; a single image stays on the caller's stream
@@ -579,13 +588,11 @@ fic_status fic_quantize(const fic_codes *in, int32_t n, int32_t bits_s, int32_t 
 }
 
 fic_status fic_profile_enable(int32_t on) {
-    if (on && !g_prof.on) {
+    if (on && !g_prof.made) {
         for (auto &e : g_prof.ev) FIC_TRY(cudaEventCreate(&e), "cudaEventCreate");
-        g_prof.on = true;
-    } else if (!on && g_prof.on) {
-        for (auto &e : g_prof.ev) cudaEventDestroy(e);
-        g_prof.on = false;
+        g_prof.made = true;
     }
+    g_prof.on = on != 0;
     return FIC_OK;
 }
 
