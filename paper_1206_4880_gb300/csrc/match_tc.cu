@@ -792,7 +792,6 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
         corr8<8>(sg.rp, domS + (size_t)d * 64, X);
         C = dsum[d];
         Q = 64LL * dsumsq[d] - C * C;
-#pragma unroll
         // with the domain (so Q and C) fixed the clamped gain grows with |P|: the best isometry
         // is the largest |P|, ties to the smaller t (a flat domain has P = 0 for every t)
         P = 64LL * (long long)X[0] - A * C;
