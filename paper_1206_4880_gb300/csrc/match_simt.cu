@@ -24,9 +24,10 @@ struct ScanShared {
     using G = typename FitOf<B>::G;
     // rp[t][q] = r[p] with src_t(p) = q, so that X_t = sum_q S[q] * rp[t][q]; bytes, 16-aligned
     alignas(16) uint8_t rp[8][B * B];
-    G g[kSimtThreads];
-    long long P[kSimtThreads], Q[kSimtThreads];
-    int d[kSimtThreads], t[kSimtThreads], C[kSimtThreads];
+    // per warp: its best candidate (the block reduction's second level)
+    G g[kSimtThreads / 32];
+    long long P[kSimtThreads / 32], Q[kSimtThreads / 32];
+    int d[kSimtThreads / 32], t[kSimtThreads / 32], C[kSimtThreads / 32];
     int flagged[kSimtThreads];
     int single[2 * kSimtThreads];  // first positions of flagged 16-domain groups
     int n_flagged, n_single;
@@ -92,39 +93,72 @@ __device__ __forceinline__ void scan_domain(const ScanShared<B> &sh, int d, long
     }
 }
 
-// Block-wide best and the code of range r (thread 0 writes it).
+// A warp's lane-wise best values exchanged over xor lane offsets.
+__device__ __forceinline__ Gain shfl_xor_gain(const Gain &g, int off) {
+    return Gain{__shfl_xor_sync(0xffffffffu, g.num, off), __shfl_xor_sync(0xffffffffu, g.den, off)};
+}
+__device__ __forceinline__ GainW shfl_xor_gain(const GainW &g, int off) {
+    GainW o;
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)g.num, off);
+    const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(g.num >> 64), off);
+    o.num = (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned __int128)lo);
+    o.den = __shfl_xor_sync(0xffffffffu, g.den, off);
+    return o;
+}
+// The best of a warp's 32 candidates (gain, then smaller domain id, then smaller isometry), in
+// every lane.
+template <int B>
+__device__ __forceinline__ void warp_best(Best<B> &b) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        Best<B> o;
+        o.g = shfl_xor_gain(b.g, off);
+        o.d = __shfl_xor_sync(0xffffffffu, b.d, off);
+        o.t = __shfl_xor_sync(0xffffffffu, b.t, off);
+        o.C = __shfl_xor_sync(0xffffffffu, b.C, off);
+        o.P = __shfl_xor_sync(0xffffffffu, b.P, off);
+        o.Q = __shfl_xor_sync(0xffffffffu, b.Q, off);
+        if (cand_better(o.g, o.d, o.t, b.g, b.d, b.t)) b = o;
+    }
+}
+
+// Block-wide best and the code of range r (thread 0 writes it): each warp's best by shuffles,
+// then the warps' bests by the first warp.
 template <int B>
 __device__ __forceinline__ void reduce_and_write(ScanShared<B> &sh, const Best<B> &b, int r, long long A,
                                                  long long Bs, const fic_codes &out) {
-    const int tid = threadIdx.x;
-    sh.g[tid] = b.g;
-    sh.d[tid] = b.d;
-    sh.t[tid] = b.t;
-    sh.P[tid] = b.P;
-    sh.Q[tid] = b.Q;
-    sh.C[tid] = b.C;
-    __syncthreads();
-    for (int s = kSimtThreads / 2; s > 0; s >>= 1) {
-        if (tid < s) {
-            if (cand_better(sh.g[tid + s], sh.d[tid + s], sh.t[tid + s], sh.g[tid], sh.d[tid], sh.t[tid])) {
-                sh.g[tid] = sh.g[tid + s];
-                sh.d[tid] = sh.d[tid + s];
-                sh.t[tid] = sh.t[tid + s];
-                sh.P[tid] = sh.P[tid + s];
-                sh.Q[tid] = sh.Q[tid + s];
-                sh.C[tid] = sh.C[tid + s];
-            }
-        }
-        __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Best<B> m = b;
+    warp_best<B>(m);
+    if (lane == 0) {
+        sh.g[warp] = m.g;
+        sh.d[warp] = m.d;
+        sh.t[warp] = m.t;
+        sh.P[warp] = m.P;
+        sh.Q[warp] = m.Q;
+        sh.C[warp] = m.C;
     }
-    if (tid == 0) {
-        double s, o, sse;
-        finalize_code(B * B, A, Bs, sh.C[0], sh.P[0], sh.Q[0], sh.g[0], s, o, sse);
-        out.dom[r] = sh.d[0];
-        out.iso[r] = sh.t[0];
-        out.s[r] = s;
-        out.o[r] = o;
-        out.sse[r] = sse;
+    __syncthreads();
+    if (warp == 0) {
+        Best<B> x = m;
+        if (lane < kSimtThreads / 32) {
+            x = Best<B>{sh.g[lane], sh.d[lane], sh.t[lane], sh.C[lane], sh.P[lane], sh.Q[lane]};
+        } else {
+            x.g.num = -1;  // no candidate
+            x.g.den = 1;
+            x.d = INT_MAX;
+            x.t = 0;
+        }
+        warp_best<B>(x);
+        if (lane == 0) {
+            double s, o, sse;
+            finalize_code(B * B, A, Bs, x.C, x.P, x.Q, x.g, s, o, sse);
+            out.dom[r] = x.d;
+            out.iso[r] = x.t;
+            out.s[r] = s;
+            out.o[r] = o;
+            out.sse[r] = sse;
+        }
     }
     __syncthreads();
 }

@@ -270,3 +270,47 @@ def test_conci_two_groups(engine):
     torch.cuda.synchronize()
     ref = omatch.encode(img, B=8, sigma=4, K=2, w=0, n_threads=8)
     _compare_codes(codes, ref)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("prof", [False, True])
+def test_encode_graph_replay(engine, prof):
+    """One fic_encode call captured in a CUDA graph (internal streams, and with `prof` the stage
+    events as graph nodes) replays to the same codes as a direct call, on a changed image too, and
+    the stage times read back after a replay; profiling switched off and on again between capture
+    and replay keeps the captured events valid."""
+    _need_tensor(engine)
+    a_np, b_np = synth.fbm_image(21, 200, 136), synth.fbm_image(22, 200, 136)
+    img = _t(a_np)
+    p = _params(4, 8, -1, engine)
+    R, _ = fic.counts(200, 136, p)
+    ws = torch.empty(fic.encode_workspace_size(200, 136, p), dtype=torch.uint8, device="cuda")
+    out = fic.alloc_codes(R, img.device)
+    fic.profile_enable(prof)
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fic.encode(img, p, out=out, workspace=ws)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            fic.encode(img, p, out=out, workspace=ws)
+        fic.profile_enable(False)
+        fic.profile_enable(prof)
+        for src in (a_np, b_np):
+            img.copy_(_t(src))
+            for k in out:
+                out[k].zero_()
+            graph.replay()
+            torch.cuda.synchronize()
+            if prof:
+                stages, _ = fic.profile_read()
+                assert set(stages) == set(fic.STAGES) and all(v >= 0 for v in stages.values())
+            ref = fic.encode(_t(src), p)
+            torch.cuda.synchronize()
+            for k in out:
+                assert torch.equal(out[k], ref[k]), k
+    finally:
+        fic.profile_enable(False)
