@@ -30,8 +30,8 @@ def test_table1_counts():
         if comps > 0:
             assert prod == comps
         else:
-            # the printed "> 35000000000" for n = 1024 is not met by the product; Section 2's
-            # own statement of the same case ("around 2^34") is.
+            # the lower bound printed for n = 1024 (more than 3.5e10) is not met by the product;
+            # Section 2's own estimate of the same case (about 2^34) is.
             assert prod == 16384 * 1009 * 1009 == 16_680_239_104
             assert prod < -comps
             assert 0.95 < prod / 2 ** 34 < 1.0
