@@ -54,8 +54,7 @@ WORKLOADS = {
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one matcher launch from an ncu capture of the current kernel on the
 # workload (profiles/); emptied whenever the kernel changes until it is captured again.
-MEASURED_TRAFFIC = {("encode-1024", "tensor"): 85.477632e6 + 22.183424e6,
-                    ("encode-2048-s4-b16", "tensor"): 1.067006e9 + 82.904576e6}
+MEASURED_TRAFFIC = {}
 
 
 def flops_per_match(block: int) -> int:

@@ -80,11 +80,12 @@ constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 // Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
 // range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
 // s = 128 m^2 / Q + (p - m), m = min(p, Q / 256) (the exact gain / 512 up to the accumulator's
-// and this formula's rounding), and a 32-bit key (s's bits with the low 9 replaced by 511 - the
-// domain's offset in its 512-domain chunk, jrel + l). The 16 domains form one group (positions
-// jh .. jh + 15, jh a multiple of 16): only the group's largest key goes on, into t1, t2, the two
-// largest group keys of the chunk; the exact re-evaluation evaluates the best group whole.
-// MASK: keys of domains outside this row's pool window [lo_r, hi_r) are 0.
+// and this formula's rounding). The 16 domains form one ranking group (positions jh .. jh + 15,
+// jh a multiple of 16): only the group's largest score goes on, as one 32-bit key (its bits with
+// the low 9 replaced by 511 - the group's offset jrel in its 512-domain chunk), into t1, t2, the
+// two largest group keys of the chunk; the exact re-evaluation evaluates the best group whole, so
+// no domain position within a group is kept. MASK: domains outside this row's pool window
+// [lo_r, hi_r) score -1, and a group with none inside gives key 0.
 __device__ __forceinline__ float absmax8(const uint32_t *v) {
     // a tree of depth two: three independent maxima of magnitudes, then their maximum
     const float a = max3_abs(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
@@ -93,23 +94,19 @@ __device__ __forceinline__ float absmax8(const uint32_t *v) {
     return max3f(a, b, c);
 }
 
-// Key of domain l (compile time, < 16) of a half tile whose first domain sits at offset jrel (a
-// multiple of 16) of its chunk: the score's bits with the low 9 replaced by 511 - jrel - l. base =
-// 511 - jrel has its low 4 bits set and nothing above bit 8, so 511 - jrel - l = base ^ l and the
-// whole key is one lop3 of (bits, base, 0xFFFFFE00 | l) with the truth table
-// (a & c & ~b) | (b & ~c) = 0x64.
-template <int L>
+// Key of a group whose first domain sits at offset jrel of its chunk: the score's bits with the
+// low 9 replaced by base = 511 - jrel (nothing above bit 8), one lop3 of (bits, base, 0xFFFFFE00)
+// with the truth table (a & c & ~b) | (b & ~c) = 0x64.
 __device__ __forceinline__ uint32_t chunk_key(float sc, uint32_t base) {
     uint32_t key;
-    asm("lop3.b32 %0, %1, %2, %3, 0x64;" : "=r"(key) : "r"(__float_as_uint(sc)), "r"(base), "n"(0xFFFFFE00u | L));
+    asm("lop3.b32 %0, %1, %2, %3, 0x64;" : "=r"(key) : "r"(__float_as_uint(sc)), "r"(base), "n"(0xFFFFFE00u));
     return key;
 }
 
 template <bool MASK>
 __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int jh, int jrel, int lo_r, int hi_r,
                                          uint32_t &t1, uint32_t &t2) {
-    const uint32_t base = 511u - (uint32_t)jrel;
-    float gmax = 0.f;  // keys are the bits of non-negative floats: their float order is their order
+    float gmax = MASK ? -1.f : 0.f;  // the group's largest score
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
@@ -122,7 +119,7 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 tmem_ld32(taddr + (c + 1) * 32, vb);
         }
         const uint32_t *cur = (c & 1) ? vb : va;
-        uint32_t k[4];
+        float sv[4];
 #pragma unroll
         for (int q2 = 0; q2 < 2; ++q2) {
             // two domains' (Q / 256, 128 / Q) per 16-byte shared load
@@ -135,26 +132,16 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 // certification margin covers
                 const float p = absmax8(cur + 8 * q);
                 const float mm = fminf(p, qy);
-                const float sc = fmaf(mm, mm * qz, p - mm);
-                uint32_t key;
-                switch (l) {
-#define FIC_KEY_CASE(L) \
-    case L: key = chunk_key<L>(sc, base); break;
-                    FIC_KEY_CASE(0) FIC_KEY_CASE(1) FIC_KEY_CASE(2) FIC_KEY_CASE(3) FIC_KEY_CASE(4) FIC_KEY_CASE(5)
-                    FIC_KEY_CASE(6) FIC_KEY_CASE(7) FIC_KEY_CASE(8) FIC_KEY_CASE(9) FIC_KEY_CASE(10) FIC_KEY_CASE(11)
-                    FIC_KEY_CASE(12) FIC_KEY_CASE(13) FIC_KEY_CASE(14) default: key = chunk_key<15>(sc, base); break;
-#undef FIC_KEY_CASE
-                }
+                float sc = fmaf(mm, mm * qz, p - mm);
                 if (MASK) {
                     const int j = jh + l;
-                    key = (j >= lo_r && j < hi_r) ? key : 0u;
+                    sc = (j >= lo_r && j < hi_r) ? sc : -1.f;
                 }
-                k[2 * q2 + h] = key;
+                sv[q] = sc;
             }
         }
         // one link of the running group maximum per stage
-        gmax = max3f(gmax, max3f(__uint_as_float(k[0]), __uint_as_float(k[1]), __uint_as_float(k[2])),
-                     __uint_as_float(k[3]));
+        gmax = max3f(gmax, max3f(sv[0], sv[1], sv[2]), sv[3]);
         if (c < 3) {
             if (c & 1)
                 tmem_ld_wait(va);
@@ -162,7 +149,9 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 tmem_ld_wait(vb);
         }
     }
-    top2u(t1, t2, __float_as_uint(gmax));
+    uint32_t key = chunk_key(gmax, 511u - (uint32_t)jrel);
+    if (MASK && gmax < 0.f) key = 0u;  // no domain of the group in the window
+    top2u(t1, t2, key);
 }
 
 }  // namespace

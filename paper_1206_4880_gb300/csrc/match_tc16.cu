@@ -64,12 +64,12 @@ constexpr size_t kTc16Smem = sizeof(Tc16Shared) + 1024;
 static_assert(kTc16Smem <= 232448, "shared memory per CTA");
 
 // Scores of one accumulator tile for this thread's range row: 16 domains x 8 isometries. The 16
-// domains (positions jh .. jh + 15, jh a multiple of 16) form one group, whose largest key goes on
-// into t1, t2 (the two largest group keys of the chunk), as in the B = 8 kernel.
+// domains (positions jh .. jh + 15, jh a multiple of 16) form one group, whose largest score goes
+// on as one key into t1, t2 (the two largest group keys of the chunk), as in the B = 8 kernel.
 template <bool MASK>
 __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float alpha, int jh, int jrel, int lo_r,
                                       int hi_r, uint32_t &t1, uint32_t &t2) {
-    float gmax = 0.f;
+    float gmax = MASK ? -1.f : 0.f;  // the group's largest score
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
@@ -82,7 +82,7 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                 tmem_ld32(taddr + (c + 1) * 32, vb);
         }
         const uint32_t *cur = (c & 1) ? vb : va;
-        uint32_t k[4];
+        float sv[4];
 #pragma unroll
         for (int q2 = 0; q2 < 2; ++q2) {
 #pragma unroll
@@ -95,17 +95,15 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                 const float p = max3f(max3_abs(y[0], y[1], y[2]), max3_abs(y[3], y[4], y[5]),
                                       fmaxf(fabsf(y[6]), fabsf(y[7])));
                 const float mm = fminf(p, a.y);
-                const float sc = fmaf(mm, mm * a.z, p - mm);
-                uint32_t key = (__float_as_uint(sc) & 0xFFFFFE00u) | (uint32_t)(511 - jrel - l);
+                float sc = fmaf(mm, mm * a.z, p - mm);
                 if (MASK) {
                     const int j = jh + l;
-                    key = (j >= lo_r && j < hi_r) ? key : 0u;
+                    sc = (j >= lo_r && j < hi_r) ? sc : -1.f;
                 }
-                k[2 * q2 + h] = key;
+                sv[2 * q2 + h] = sc;
             }
         }
-        gmax = max3f(gmax, max3f(__uint_as_float(k[0]), __uint_as_float(k[1]), __uint_as_float(k[2])),
-                     __uint_as_float(k[3]));
+        gmax = max3f(gmax, max3f(sv[0], sv[1], sv[2]), sv[3]);
         if (c < 3) {
             if (c & 1)
                 tmem_ld_wait(va);
@@ -113,7 +111,11 @@ __device__ __forceinline__ void epi16(uint32_t taddr, const float4 *auxp, float 
                 tmem_ld_wait(vb);
         }
     }
-    top2u(t1, t2, __float_as_uint(gmax));
+    // the group's key: its largest score's bits with the low 9 replaced by 511 - its offset in
+    // the chunk (key 0 when no domain of the group is in the window)
+    uint32_t key = (__float_as_uint(gmax) & 0xFFFFFE00u) | (uint32_t)(511 - jrel);
+    if (MASK && gmax < 0.f) key = 0u;
+    top2u(t1, t2, key);
 }
 
 }  // namespace
