@@ -14,7 +14,8 @@
  * Conventions for every entry point:
  *  - Image, code, statistics and workspace pointers are DEVICE pointers owned by the caller.
  *    The library allocates no device memory and frees none; it keeps no state between calls
- *    except a per-device cache of its own kernel attributes and, for fic_encode_batched, eight
+ *    except a per-device cache of its own kernel attributes, fic_encode's per-thread cache of
+ *    captured graphs (see fic_encode) and, for fic_encode_batched and single encodes, eight
  *    internal CUDA streams and events per host thread and device (created on the first batched
  *    call that is not inside a stream capture; the images' per-image stages run on them,
  *    joined back into `stream` by events).
@@ -162,7 +163,11 @@ fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *g, const fi
 
 /* Sections 1 and 3: the whole encoder, image -> codes. Equal to the exact least-error search
  * over each range's pool (ties as in fic_codes). `info` (device, nullable) receives the
- * report. */
+ * report. The first call with a given argument set (pointers, geometry, parameters, device) on a
+ * host thread captures its work into a CUDA graph on a private stream; later calls with the same
+ * arguments replay that graph on `stream` (up to 4 argument sets per thread, least recently used
+ * replaced). Calls with profiling on, or on a stream the caller is capturing, run the stages
+ * directly. */
 fic_status fic_encode(const uint8_t *img, const fic_geom *g, const fic_params *p,
                       const fic_codes *out, fic_encode_info *info, void *workspace,
                       size_t workspace_bytes, void *stream);

@@ -314,3 +314,32 @@ def test_encode_graph_replay(engine, prof):
                 assert torch.equal(out[k], ref[k]), k
     finally:
         fic.profile_enable(False)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_encode_repeated_calls_replay(engine):
+    """Repeated fic_encode calls with the same arguments replay the library's cached graph of the
+    call: codes follow the image content, different parameters on the same buffers give their own
+    codes, and both equal the direct path (profiling on bypasses the cache)."""
+    _need_tensor(engine)
+    H, W = 152, 200
+    img = torch.empty(H, W, dtype=torch.uint8, device="cuda")
+    params = [_params(4, 8, -1, engine), _params(4, 5, 1, engine)]
+    R, _ = fic.counts(H, W, params[0])
+    ws = torch.empty(max(fic.encode_workspace_size(H, W, q) for q in params), dtype=torch.uint8, device="cuda")
+    out = fic.alloc_codes(R, img.device)
+    for rep in range(3):
+        for q in params:
+            src = synth.fbm_image(30 + rep, H, W)
+            img.copy_(_t(src))
+            fic.encode(img, q, out=out, workspace=ws)
+            torch.cuda.synchronize()
+            got = {k: v.clone() for k, v in out.items()}
+            fic.profile_enable(True)
+            try:
+                ref = fic.encode(_t(src), q)
+                torch.cuda.synchronize()
+            finally:
+                fic.profile_enable(False)
+            for k in got:
+                assert torch.equal(got[k], ref[k]), (rep, k)
