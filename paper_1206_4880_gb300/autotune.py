@@ -21,6 +21,9 @@ import torch
 from . import fic
 
 CANDIDATES = (4, 8, 16, 24, 32)
+# bumped when the matchers' scheduling changes, so that timings cached under another schedule are
+# not reused (2: persistent CTAs fetch work items from a global counter)
+SCHEDULE = 2
 
 
 def cache_path() -> str:
@@ -30,7 +33,8 @@ def cache_path() -> str:
 
 def signature(shapes, p: fic.EncodeParams) -> str:
     desc = {"shapes": sorted([list(s) for s in shapes]), "sigma": p.domain_stride,
-            "K": p.num_classes, "w": p.half_width, "engine": p.engine, "block": p.block}
+            "K": p.num_classes, "w": p.half_width, "engine": p.engine, "block": p.block,
+            "schedule": SCHEDULE}
     return hashlib.sha1(json.dumps(desc, sort_keys=True).encode()).hexdigest()[:16]
 
 

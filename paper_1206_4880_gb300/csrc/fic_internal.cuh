@@ -338,7 +338,8 @@ struct TcBatch {
     unsigned long long *cand;  // top-2 keys: range tile m owns [first slot, + items) x tm x halves x 2
                                // entries, ordered (row, item, half, key)
     uint32_t *chunk_max;   // [max_chunks][tm rows][halves][2] best key, runner-up score per chunk
-    int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks, [4] chunks per group
+    int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks, [4] chunks per group,
+                           // [5] next work item to hand out (zero before the matcher)
     int R_pad, Dn_aux, n_mtiles, max_items, max_chunks, ng_max, cpi_cap;
 };
 
@@ -347,15 +348,20 @@ constexpr int kTileM = 128;       // rows of one MMA (ranges per B = 8 range til
 constexpr int kTileDom = 32;      // domains per accumulator tile (8 isometries -> N = 256)
 constexpr int kChunkTiles = 16;   // accumulator tiles per chunk (the re-search granule)
 constexpr int kChunkDom = kTileDom * kChunkTiles;
-// default work items per SM the work list aims for: the items are dealt round-robin to the
-// persistent CTAs, so more, smaller items balance better until per-item costs (A tile loads, key
-// slots) dominate; measured on GB300, 1024x1024 stride 4: 16 -> 0.944 ms, 24 -> 0.918 ms,
-// 32 -> 0.926 ms, 64 -> 0.944 ms (4096x4096 within 0.3% from 8 to 64)
-constexpr int kItemsPerSm = 24;
-// the same for 16x16 ranges (256-range tiles, 16-chunk groups): 2048x2048 stride 4:
-// 16 -> 10.53 ms, 32 -> 10.35, 64 -> 10.35; 4096x4096 stride 8: 16 -> 47.82, 64 -> 47.17
-constexpr int kItemsPerSm16 = 64;
+// default work items per SM the work list aims for: smaller items shorten the tail of the
+// persistent CTAs (each CTA holds about one item beyond the one it is scoring, its next A tile)
+// until per-item costs (A tile loads, key slots) dominate; matcher on GB300, 1024x1024 stride 4:
+// 8 -> 0.914 ms, 16 -> 0.900, 24 -> 0.899, 32 -> 0.893, 48 -> 0.895, 64 -> 0.911 (4096x4096
+// within 0.2% from 8 to 64)
+constexpr int kItemsPerSm = 32;
+// the same for 16x16 ranges (256-range tiles, 16-chunk groups), 4096x4096 stride 8: 8 -> 46.14 ms,
+// 16 -> 46.13, 24 -> 46.10, 32 -> 46.23, 48 -> 46.10, 64 -> 46.32
+constexpr int kItemsPerSm16 = 48;
 constexpr int kMaxItemTarget = 64 * 256;  // items_per_sm <= 64, SMs <= 256
+// The persistent matchers take work items in list order from a global counter (gcounters[5]): the
+// producer thread of a CTA fetches one and hands it to the MMA and epilogue warps through a ring
+// of this many shared-memory slots, so a CTA that finishes early takes the next item.
+constexpr int kItemRing = 4;
 
 // Ranges per range tile of the tensor engine and box-count scales of a B x B block.
 __host__ __device__ constexpr int tile_rows(int B) { return B == 16 ? 2 * kTileM : kTileM; }

@@ -71,7 +71,8 @@ struct TcShared {
     uint8_t B1[kStages][kB1Bytes];
     float4 aux[2][kChunkDom / 2];  // (Q / 256, 128 / Q) of two domains per entry: current, next chunk
     unsigned long long full_a[2], empty_a[2], full_b[kStages], empty_b[kStages], tfull[2],
-        tempty[2], aux_ready[2], drain;
+        tempty[2], aux_ready[2], drain, item_full[kItemRing], item_empty[kItemRing];
+    int item_id[kItemRing];  // work items fetched by the producer, in this CTA's order (-1: none left)
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -487,7 +488,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                const int4 *__restrict__ tile_items,
                const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
                const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
-               unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *err) {
+               unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *next_item,
+               int32_t *err) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
     TcShared &sh = *reinterpret_cast<TcShared *>(smem_raw + pad);
@@ -506,6 +508,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sh.full_b[s], 1);
             mbar_init(&sh.empty_b[s], 1);
+        }
+        for (int s = 0; s < kItemRing; ++s) {
+            mbar_init(&sh.item_full[s], 1);
+            mbar_init(&sh.item_empty[s], 1 + kEpiWarps);
         }
         mbar_init(&sh.drain, 1);
         sh.abort_flag = 0;
@@ -526,9 +532,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // ---- TMA producer
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
-            uint32_t gt = 0, li = 0;
+            uint32_t gt = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+            for (uint32_t li = 0; ok; ++li) {
+                // the next item of the whole grid, handed to the MMA and epilogue warps
+                const int s = li % kItemRing;
+                ok = mbar_wait(&sh.item_empty[s], ((li / kItemRing) & 1) ^ 1, abort_flag);
+                if (!ok) break;
+                int it = atomicAdd(next_item, 1);
+                if (it >= n_items) it = -1;
+                sh.item_id[s] = it;
+                mbar_arrive(&sh.item_full[s]);
+                if (it < 0) break;
                 const int4 w = work[it];
                 const int ab = li & 1;
                 ok = mbar_wait(&sh.empty_a[ab], ((li >> 1) & 1) ^ 1, abort_flag);
@@ -554,9 +569,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            uint32_t gt = 0, li = 0;
+            uint32_t gt = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+            for (uint32_t li = 0; ok; ++li) {
+                const int s = li % kItemRing;
+                ok = mbar_wait(&sh.item_full[s], (li / kItemRing) & 1, abort_flag);
+                if (!ok) break;
+                const int it = sh.item_id[s];
+                mbar_arrive(&sh.item_empty[s]);
+                if (it < 0) break;
                 const int4 w = work[it];
                 const int ab = li & 1;
                 ok = mbar_wait(&sh.full_a[ab], (li >> 1) & 1, abort_flag);
@@ -602,7 +623,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(half * (kTileN / 2));
         uint32_t gt = 0, lc = 0;  // accumulator tiles and chunks this CTA has processed
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        for (uint32_t li = 0; ok; ++li) {
+            const int s = li % kItemRing;
+            ok = __all_sync(0xffffffffu, mbar_wait(&sh.item_full[s], (li / kItemRing) & 1, abort_flag));
+            if (!ok) break;
+            const int it = sh.item_id[s];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.item_empty[s]);
+            if (it < 0) break;
             const int4 w = work[it];
             const int nt = (w.z - w.y + kTileDom - 1) / kTileDom;
             const int i = w.x * kTileM + row;
@@ -998,7 +1026,7 @@ cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
     k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.work_slot, tb.tile_items,
                                                    tb.gcounters,
                                                    tb.tile_win, tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
-                                                   tb.gcounters + 2);
+                                                   tb.gcounters + 5, tb.gcounters + 2);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -56,7 +56,8 @@ struct Tc16Shared {
     uint8_t B[kStages16][kQB];     // ring of K-quarters
     float4 aux[2][kChunkDom];      // per-domain constants of the current and next chunk
     unsigned long long full_a, empty_a, full_b[kStages16], empty_b[kStages16], tfull[2], tempty[2], aux_ready[2],
-        drain;
+        drain, item_full[kItemRing], item_empty[kItemRing];
+    int item_id[kItemRing];  // work items fetched by the producer, in this CTA's order (-1: none left)
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -207,7 +208,8 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                  const int4 *__restrict__ tile_items,
                  const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
                  const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
-                 unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *err) {
+                 unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *next_item,
+                 int32_t *err) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
     Tc16Shared &sh = *reinterpret_cast<Tc16Shared *>(smem_raw + pad);
@@ -226,6 +228,10 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
         for (int s = 0; s < kStages16; ++s) {
             mbar_init(&sh.full_b[s], 1);
             mbar_init(&sh.empty_b[s], 1);
+        }
+        for (int s = 0; s < kItemRing; ++s) {
+            mbar_init(&sh.item_full[s], 1);
+            mbar_init(&sh.item_empty[s], 1 + kEpi16);
         }
         mbar_init(&sh.drain, 1);
         sh.abort_flag = 0;
@@ -246,9 +252,18 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
             // ---- TMA producer
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
-            uint32_t gs = 0, li = 0;
+            uint32_t gs = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+            for (uint32_t li = 0; ok; ++li) {
+                // the next item of the whole grid, handed to the MMA and epilogue warps
+                const int s = li % kItemRing;
+                ok = mbar_wait(&sh.item_empty[s], ((li / kItemRing) & 1) ^ 1, abort_flag);
+                if (!ok) break;
+                int it = atomicAdd(next_item, 1);
+                if (it >= n_items) it = -1;
+                sh.item_id[s] = it;
+                mbar_arrive(&sh.item_full[s]);
+                if (it < 0) break;
                 const int4 w = work[it];
                 ok = mbar_wait(&sh.empty_a, (li & 1) ^ 1, abort_flag);
                 if (!ok) break;
@@ -277,9 +292,15 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            uint32_t gs = 0, gt = 0, li = 0;
+            uint32_t gs = 0, gt = 0;
             bool ok = true;
-            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+            for (uint32_t li = 0; ok; ++li) {
+                const int s = li % kItemRing;
+                ok = mbar_wait(&sh.item_full[s], (li / kItemRing) & 1, abort_flag);
+                if (!ok) break;
+                const int it = sh.item_id[s];
+                mbar_arrive(&sh.item_empty[s]);
+                if (it < 0) break;
                 const int4 w = work[it];
                 ok = mbar_wait(&sh.full_a, li & 1, abort_flag);
                 if (!ok) break;
@@ -330,7 +351,14 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
         const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(m * kN16);
         uint32_t gt = 0, lc = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        for (uint32_t li = 0; ok; ++li) {
+            const int s = li % kItemRing;
+            ok = __all_sync(0xffffffffu, mbar_wait(&sh.item_full[s], (li / kItemRing) & 1, abort_flag));
+            if (!ok) break;
+            const int it = sh.item_id[s];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.item_empty[s]);
+            if (it < 0) break;
             const int4 w = work[it];
             const int nt = (w.z - w.y + kDom16 - 1) / kDom16;
             const int i = w.x * kTm16 + row;
@@ -637,7 +665,7 @@ cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st) {
     k_match_tc16<<<grid, kTc16Threads, kTc16Smem, st>>>(tmA, tmB, tb.work, tb.work_slot, tb.tile_items, tb.gcounters,
                                                          tb.tile_win,
                                                          tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
-                                                         tb.gcounters + 2);
+                                                         tb.gcounters + 5, tb.gcounters + 2);
     ++g_launches;
     return cudaGetLastError();
 }
