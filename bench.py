@@ -54,8 +54,8 @@ WORKLOADS = {
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one matcher launch from an ncu capture of the current kernel on the
 # workload (profiles/); emptied whenever the kernel changes until it is captured again.
-MEASURED_TRAFFIC = {("encode-1024", "tensor"): 85.4848e6 + 23.601664e6,
-                    ("encode-2048-s4-b16", "tensor"): 1.075636e9 + 75.012608e6}
+MEASURED_TRAFFIC = {("encode-1024", "tensor"): 85.47328e6 + 22.088448e6,
+                    ("encode-2048-s4-b16", "tensor"): 1.073587e9 + 74.92992e6}
 
 
 def flops_per_match(block: int) -> int:

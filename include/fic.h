@@ -86,7 +86,7 @@ typedef struct {
     int32_t engine;        /* FIC_ENGINE_TENSOR or FIC_ENGINE_SIMT */
     int32_t flags;         /* 0, or FIC_FLAG_LITERAL_WINDOW */
     int32_t items_per_sm;  /* tensor engine scheduling: work items per SM the range tiles' domain
-                              chunks are split into, 1..64; 0 selects 32 (block 8) or 48
+                              chunks are split into, 1..64; 0 selects 24 (block 8) or 48
                               (block 16) */
 } fic_params;
 

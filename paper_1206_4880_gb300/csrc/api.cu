@@ -229,12 +229,14 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
     tb->n_mtiles = (int)mt_tot;
     // cpi_cap chunks per domain group: about 32 MB of B rows (512 KB per chunk for B = 8, 2 MB
     // for B = 16). A tile meets at most chunks / cpi + 2 groups, and cpi >= min(cap, total /
-    // target), so items <= 2 tiles + max(target, chunks / cap).
+    // target), so items <= 2 tiles + max(target, chunks / cap); cutting the last two groups in
+    // four adds at most 6 items per tile.
     tb->cpi_cap = B == 16 ? 16 : 64;
-    tb->max_items = (int)(2 * mt_tot + (chunks_tot / tb->cpi_cap + 1 > kMaxItemTarget ? chunks_tot / tb->cpi_cap + 1
+    tb->max_items = (int)(8 * mt_tot + (chunks_tot / tb->cpi_cap + 1 > kMaxItemTarget ? chunks_tot / tb->cpi_cap + 1
                                                                                         : kMaxItemTarget));
     tb->max_chunks = (int)chunks_tot;
-    tb->ng_max = (int)(Dn_aux_tot / kChunkDom + 2);
+    // groups: at most ceil(chunks / cpi) + 6 (the last two cut in four) <= chunks + 6
+    tb->ng_max = (int)(Dn_aux_tot / kChunkDom + 8);
     const size_t slice = B == 8 ? 16 : 0;  // correction slice columns (B = 16 corrects in the epilogue)
     tb->A_mat = c.take<__half>((size_t)R_pad_tot * npx, 1024);
     tb->B_mat = c.take<__half>((size_t)8 * Dn_aux_tot * npx, 1024);

@@ -349,13 +349,15 @@ constexpr int kTileDom = 32;      // domains per accumulator tile (8 isometries 
 constexpr int kChunkTiles = 16;   // accumulator tiles per chunk (the re-search granule)
 constexpr int kChunkDom = kTileDom * kChunkTiles;
 // default work items per SM the work list aims for: smaller items shorten the tail of the
-// persistent CTAs (each CTA holds about one item beyond the one it is scoring, its next A tile)
-// until per-item costs (A tile loads, key slots) dominate; matcher on GB300, 1024x1024 stride 4:
-// 8 -> 0.914 ms, 16 -> 0.900, 24 -> 0.899, 32 -> 0.893, 48 -> 0.895, 64 -> 0.911 (4096x4096
-// within 0.2% from 8 to 64)
-constexpr int kItemsPerSm = 32;
-// the same for 16x16 ranges (256-range tiles, 16-chunk groups), 4096x4096 stride 8: 8 -> 46.14 ms,
-// 16 -> 46.13, 24 -> 46.10, 32 -> 46.23, 48 -> 46.10, 64 -> 46.32
+// persistent CTAs until per-item costs (A tile loads, key slots) dominate; the work list also cuts
+// the last two domain groups in four, so the items taken last are short whatever this is. Matcher
+// on GB300, 1024x1024 stride 4: 8 -> 0.884 ms, 16 -> 0.881, 24 -> 0.881, 32 -> 0.887, 48 -> 0.901,
+// 64 -> 0.909 (4096x4096 within 0.2% from 8 to 64)
+constexpr int kItemsPerSm = 24;
+// the same for 16x16 ranges (256-range tiles, 16-chunk groups), 4096x4096 stride 8: 8 -> 46.05 ms,
+// 16 -> 46.02, 24 -> 46.02, 32 -> 46.04, 48 -> 46.07, 64 -> 46.07; at 2048x2048 stride 4, 16 items
+// per SM made the groups large enough that their B rows were re-read from DRAM (3.45 GB a launch
+// against 1.15 GB at 48-64)
 constexpr int kItemsPerSm16 = 48;
 constexpr int kMaxItemTarget = 64 * 256;  // items_per_sm <= 64, SMs <= 256
 // The persistent matchers take work items in list order from a global counter (gcounters[5]): the

@@ -393,7 +393,8 @@ __device__ __forceinline__ int block_scan_1024(int v, int *sc, int *total) {
 // One block of 1024 threads: the work list and its schedule. Chunks of the absolute grid are
 // grouped cpi at a time (domain group G = positions [512 cpi G, 512 cpi (G + 1))), cpi chosen so
 // the batch has about `target` items but at most cpi_cap (so one group's B rows stay L2-resident
-// while every range tile meeting the group streams them). A work item is (range tile m, group G):
+// while every range tile meeting the group streams them); the last two groups are cut in up to
+// four. A work item is (range tile m, group G):
 // the part of m's union window inside G, its first domain rounded down to the accumulator tile
 // width td (the extra columns lie below every row's window and are masked). tile_items[m] =
 // (first key slot, items, first chunk id, chunks): m's items own consecutive key slots in group
@@ -404,7 +405,7 @@ __device__ __forceinline__ int block_scan_1024(int v, int *sc, int *total) {
 __device__ __forceinline__ int tile_chunk_lo(int4 t) { return t.x / kChunkDom; }
 __device__ __forceinline__ int tile_chunk_hi(int4 t) { return (t.y - 1) / kChunkDom + 1; }  // exclusive
 
-__global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int ng_max,
+__global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int ng_max, int nc,
                             const int4 *__restrict__ tile_win, const int32_t *__restrict__ n_chunks,
                             int4 *__restrict__ work, int32_t *__restrict__ work_slot,
                             int4 *__restrict__ tile_items, int32_t *__restrict__ grp, int32_t *gcounters) {
@@ -423,7 +424,13 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
     __syncthreads();
     const int total = total_chunks_s;
     const int cpi = max(1, min(cpi_cap, (total + target - 1) / max(1, target)));
-    const int gdom = cpi * kChunkDom;  // domains per group
+    // the last two groups of the grid (nc chunks) are cut into groups of sub = ceil(cpi / 4)
+    // chunks: the items taken last are then short, and the persistent CTAs finish closer together
+    const int sub = (cpi + 3) / 4;
+    const int g1 = sub < cpi ? max(0, (nc + cpi - 1) / cpi - 2) : ng_max;  // full groups before the tail
+    const int c1 = g1 * cpi;                                                 // first chunk of the tail
+    auto group_of = [=](int ch) { return ch < c1 ? ch / cpi : g1 + (ch - c1) / sub; };
+    auto group_lo = [=](int G) { return G < g1 ? G * cpi : c1 + (G - g1) * sub; };  // first chunk
     for (int G = threadIdx.x; G < ng_max; G += 1024) grp_c[G] = 0;
     __syncthreads();
     // key slots and chunk ids per tile (tile-major); group counts
@@ -434,8 +441,8 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
         int q = 0, glo = 0;
         if (c > 0) {
             const int4 t = tile_win[m];
-            glo = tile_chunk_lo(t) / cpi;
-            q = (tile_chunk_hi(t) - 1) / cpi - glo + 1;
+            glo = group_of(tile_chunk_lo(t));
+            q = group_of(tile_chunk_hi(t) - 1) - glo + 1;
         }
         int q_all = 0, c_all = 0;
         const int q_off = item_base + block_scan_1024(q, sc, &q_all);
@@ -463,11 +470,11 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
         const int4 ti = tile_items[m];
         if (ti.y == 0) continue;
         const int4 t = tile_win[m];
-        const int c_lo = tile_chunk_lo(t), glo = c_lo / cpi;
+        const int c_lo = tile_chunk_lo(t), glo = group_of(c_lo);
         for (int k = 0; k < ti.y; ++k) {
             const int G = glo + k;
-            const int d0 = max(t.x, G * gdom) / td * td;
-            const int d1 = min(t.y, (G + 1) * gdom);
+            const int d0 = max(t.x, group_lo(G) * kChunkDom) / td * td;
+            const int d1 = min(t.y, group_lo(G + 1) * kChunkDom);
             const int pos = atomicAdd(&grp_c[G], 1);
             work[pos] = make_int4(m, d0, d1, ti.z + d0 / kChunkDom - c_lo);
             work_slot[pos] = ti.x + k;
@@ -1002,7 +1009,7 @@ cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t s
     }
     const int target = max(1, min(target_items, kMaxItemTarget));
     k_work_list<<<1, 1024, 0, st>>>(tb.n_mtiles, target, tb.cpi_cap, tb.B == 16 ? 16 : kTileDom, tb.ng_max,
-                                    tb.tile_win, tb.n_chunks, tb.work, tb.work_slot, tb.tile_items, tb.grp,
+                                    (tb.Dn_aux + kChunkDom - 1) / kChunkDom, tb.tile_win, tb.n_chunks, tb.work, tb.work_slot, tb.tile_items, tb.grp,
                                     tb.gcounters);
     ++g_launches;
     return cudaGetLastError();

@@ -165,6 +165,32 @@ def test_encode_deterministic(engine):
         assert torch.equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("block", [8, 16])
+def test_encode_schedule_independent(block):
+    """The persistent tensor matchers hand out work items from a global counter, so which CTA
+    scores which item changes from run to run, and items_per_sm changes how the chunks are cut
+    into items: the codes must not change with either."""
+    _need_tensor("tensor")
+    img = _t(synth.fbm_image(41, 1024, 768))
+    sigma, K = 4, (16 if block == 8 else 12)
+    base, items = None, []
+    for ipsm in (1, 5, 32, 64, 32):
+        p = fic.EncodeParams(domain_stride=sigma, num_classes=K, engine="tensor", block=block,
+                             items_per_sm=ipsm)
+        info = fic.new_info("cuda")
+        codes = fic.encode(img, p, info=info)
+        torch.cuda.synchronize()
+        rep = fic.read_info(info)
+        assert rep["device_error"] == 0
+        items.append(rep["work_items"])
+        if base is None:
+            base = codes
+            continue
+        for k in base:
+            assert torch.equal(base[k], codes[k]), (ipsm, k)
+    assert items[0] < items[3], items  # the item counts really differ
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 def test_encode_1024_sampled(engine):
     """The 1024x1024, stride-4, K=16 workload at full size, in the bench's launch
