@@ -97,19 +97,61 @@ __device__ __forceinline__ double fd_of(const Log2Tab &L, int n2, int n4) {
     return __dsub_rn(L.v[n2], L.v[n4]);
 }
 
+// Rows read as 32-bit words when the image base, its pitch and the block's first column are all
+// multiples of 4 (strides 4, 8, ... on an aligned image); otherwise byte by byte.
+__device__ __forceinline__ bool word_rows(const uint8_t *img, int pitch, int x0) {
+    return ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch | (uintptr_t)x0) & 3u) == 0;
+}
+// Two 2x2 sums from one word of each of two rows (pixels 4k .. 4k + 3), packed as
+// (p0 + p1 + q0 + q1) | (p2 + p3 + q2 + q3) << 16; each sum is at most 1020, so no half carries.
+__device__ __forceinline__ uint32_t pair_sums(uint32_t a, uint32_t b) {
+    return (a & 0x00FF00FFu) + ((a >> 8) & 0x00FF00FFu) + (b & 0x00FF00FFu) + ((b >> 8) & 0x00FF00FFu);
+}
+// The same two sums from bytes.
+__device__ __forceinline__ uint32_t pair_sums_bytes(const uint8_t *r0, const uint8_t *r1) {
+    const uint32_t s0 = (uint32_t)__ldg(r0) + __ldg(r0 + 1) + __ldg(r1) + __ldg(r1 + 1);
+    const uint32_t s1 = (uint32_t)__ldg(r0 + 2) + __ldg(r0 + 3) + __ldg(r1 + 2) + __ldg(r1 + 3);
+    return s0 | (s1 << 16);
+}
+// n consecutive pixels of one row into v[0 .. n), n a multiple of 4.
+template <int N>
+__device__ __forceinline__ void load_row(const uint8_t *row, bool words, int *v) {
+    if (words) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(row);
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) {
+            const uint32_t x = __ldg(w + k);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[4 * k + i] = (int)((x >> (8 * i)) & 0xFFu);
+        }
+    } else {
+#pragma unroll
+        for (int x = 0; x < N; ++x) v[x] = __ldg(row + x);
+    }
+}
+// The 2x2 sums of rows r0, r1 over 4 M pixels, as M packed pairs.
+template <int M>
+__device__ __forceinline__ void load_pair_sums(const uint8_t *r0, const uint8_t *r1, bool words, uint32_t *pk) {
+    if (words) {
+        const uint32_t *w0 = reinterpret_cast<const uint32_t *>(r0), *w1 = reinterpret_cast<const uint32_t *>(r1);
+#pragma unroll
+        for (int k = 0; k < M; ++k) pk[k] = pair_sums(__ldg(w0 + k), __ldg(w1 + k));
+    } else {
+#pragma unroll
+        for (int k = 0; k < M; ++k) pk[k] = pair_sums_bytes(r0 + 4 * k, r1 + 4 * k);
+    }
+}
+
 // One thread per range: moments, N_2, N_4 and FD of the 8x8 pixel block.
 __device__ __forceinline__ void range_stats(int r, const uint8_t *__restrict__ img, const Geo &g, const Log2Tab &L,
                                             int32_t *__restrict__ rsum, int32_t *__restrict__ rsumsq,
                                             int32_t *__restrict__ rcounts, double *__restrict__ rfd) {
     if (r >= g.R) return;
     const int y0 = (r / g.nRx) * 8, x0 = (r % g.nRx) * 8;
+    const bool words = word_rows(img, g.pitch, x0);
     int v[8][8];
 #pragma unroll
-    for (int y = 0; y < 8; ++y) {
-        const uint8_t *row = img + (size_t)(y0 + y) * g.pitch + x0;
-#pragma unroll
-        for (int x = 0; x < 8; ++x) v[y][x] = __ldg(row + x);
-    }
+    for (int y = 0; y < 8; ++y) load_row<8>(img + (size_t)(y0 + y) * g.pitch + x0, words, v[y]);
     int A = 0, Bs = 0, n2 = 0, n4 = 0;
 #pragma unroll
     for (int y = 0; y < 8; ++y)
@@ -158,26 +200,21 @@ __device__ __forceinline__ void dom_stats(int d, const uint8_t *__restrict__ img
     unsigned long long fbits_min = ~0ull, fbits_max = 0ull;
     if (d < g.Dn) {
         const int y0 = (d / g.nDx) * g.sigma, x0 = (d % g.nDx) * g.sigma;
+        const bool words = word_rows(img, g.pitch, x0);
         int S[8][8];
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-            const uint8_t *r0 = img + (size_t)(y0 + 2 * y) * g.pitch + x0;
-            const uint8_t *r1 = r0 + g.pitch;
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-                S[y][x] = (int)__ldg(r0 + 2 * x) + __ldg(r0 + 2 * x + 1) + __ldg(r1 + 2 * x) +
-                          __ldg(r1 + 2 * x + 1);
-        }
         int C = 0, E = 0, n2 = 0, n4 = 0;
         uint4 *dst = reinterpret_cast<uint4 *>(domS + (size_t)d * 64);
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
-            uint4 pk;
-            pk.x = (uint32_t)S[y][0] | ((uint32_t)S[y][1] << 16);
-            pk.y = (uint32_t)S[y][2] | ((uint32_t)S[y][3] << 16);
-            pk.z = (uint32_t)S[y][4] | ((uint32_t)S[y][5] << 16);
-            pk.w = (uint32_t)S[y][6] | ((uint32_t)S[y][7] << 16);
-            dst[y] = pk;
+            const uint8_t *r0 = img + (size_t)(y0 + 2 * y) * g.pitch + x0;
+            uint32_t pk[4];
+            load_pair_sums<4>(r0, r0 + g.pitch, words, pk);
+            dst[y] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                S[y][2 * k] = (int)(pk[k] & 0xFFFFu);
+                S[y][2 * k + 1] = (int)(pk[k] >> 16);
+            }
 #pragma unroll
             for (int x = 0; x < 8; ++x) {
                 C += S[y][x];
@@ -308,16 +345,16 @@ __device__ __forceinline__ void range_stats16(int r, const uint8_t *__restrict__
                                               double *__restrict__ rfd) {
     if (r >= g.R) return;
     const int y0 = (r / g.nRx) * 16, x0 = (r % g.nRx) * 16;
+    const bool words = word_rows(img, g.pitch, x0);
     Dbc16<5> dbc;
     int A = 0, Bs = 0;
     for (int p = 0; p < 8; ++p) {
         int a[16], b[16];
         const uint8_t *r0 = img + (size_t)(y0 + 2 * p) * g.pitch + x0;
-        const uint8_t *r1 = r0 + g.pitch;
+        load_row<16>(r0, words, a);
+        load_row<16>(r0 + g.pitch, words, b);
 #pragma unroll
         for (int x = 0; x < 16; ++x) {
-            a[x] = __ldg(r0 + x);
-            b[x] = __ldg(r1 + x);
             A += a[x] + b[x];
             Bs += a[x] * a[x] + b[x] * b[x];
         }
@@ -341,6 +378,7 @@ __device__ __forceinline__ void dom_stats16(int d, const uint8_t *__restrict__ i
     unsigned long long fbits_min = ~0ull, fbits_max = 0ull;
     if (d < g.Dn) {
         const int y0 = (d / g.nDx) * g.sigma, x0 = (d % g.nDx) * g.sigma;
+        const bool words = word_rows(img, g.pitch, x0);
         Dbc16<7> dbc;
         int C = 0, E = 0;
         uint4 *dst = reinterpret_cast<uint4 *>(domS + (size_t)d * 256);
@@ -350,22 +388,19 @@ __device__ __forceinline__ void dom_stats16(int d, const uint8_t *__restrict__ i
             for (int h = 0; h < 2; ++h) {
                 int *S = h ? b : a;
                 const uint8_t *q0 = img + (size_t)(y0 + 4 * p + 2 * h) * g.pitch + x0;
-                const uint8_t *q1 = q0 + g.pitch;
+                uint32_t pk[8];
+                load_pair_sums<8>(q0, q0 + g.pitch, words, pk);
+                dst[(2 * p + h) * 2] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                dst[(2 * p + h) * 2 + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 #pragma unroll
-                for (int x = 0; x < 16; ++x) {
-                    S[x] = (int)__ldg(q0 + 2 * x) + __ldg(q0 + 2 * x + 1) + __ldg(q1 + 2 * x) +
-                           __ldg(q1 + 2 * x + 1);
-                    C += S[x];
-                    E += S[x] * S[x];
+                for (int k = 0; k < 8; ++k) {
+                    S[2 * k] = (int)(pk[k] & 0xFFFFu);
+                    S[2 * k + 1] = (int)(pk[k] >> 16);
                 }
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    uint4 pk;
-                    pk.x = (uint32_t)S[8 * k + 0] | ((uint32_t)S[8 * k + 1] << 16);
-                    pk.y = (uint32_t)S[8 * k + 2] | ((uint32_t)S[8 * k + 3] << 16);
-                    pk.z = (uint32_t)S[8 * k + 4] | ((uint32_t)S[8 * k + 5] << 16);
-                    pk.w = (uint32_t)S[8 * k + 6] | ((uint32_t)S[8 * k + 7] << 16);
-                    dst[(2 * p + h) * 2 + k] = pk;
+                for (int x = 0; x < 16; ++x) {
+                    C += S[x];
+                    E += S[x] * S[x];
                 }
             }
             dbc.row_pair(p, a, b);

@@ -280,11 +280,13 @@ __global__ void __launch_bounds__(1024) k_pack_ranges_tile(Geo g, const uint8_t 
     }
 }
 
-// Sixteen threads per sorted domain j, sixteen domains per 256-thread block: B_mat row 8j+t =
-// T_t(S_{dom_order[j]}) - round(C / 64). Each thread stages four elements of the domain's block
-// (one 8-byte load) into four layouts in shared memory, then writes four consecutive rows y of
-// one isometry t, each one 16-byte row of a layout converted pairwise to FP16; dom_aux2[j] =
-// (Q / 256, 128 / Q or 0), the constants of the epilogue's clamped gain. Entries j >= Dn are zero.
+// Sixteen domains per 256-thread block: B_mat row 8j+t = T_t(S_{dom_order[j]}) - round(C / 64).
+// Sixteen threads per sorted domain j stage its block (one 8-byte load of four elements each) into
+// four layouts in shared memory; then each warp writes the rows of two domains, 2 x 8 rows x 128 B,
+// lane l of store k taking 16-byte piece 32 k + l (one row y of one isometry t, from one layout row,
+// converted pairwise to FP16), so that every store instruction covers 512 contiguous bytes. B1 rows
+// are (-gamma / 64, 0, ...) and dom_aux2[j] = (Q / 256, 128 / Q or 0), the constants of the
+// epilogue's clamped gain. Entries Dn <= j < n_pad are zero.
 __global__ void __launch_bounds__(256) k_pack_domains(Geo g, const uint16_t *__restrict__ domS,
                                                       const int32_t *__restrict__ dom_order,
                                                       const int32_t *__restrict__ dsum,
@@ -292,49 +294,53 @@ __global__ void __launch_bounds__(256) k_pack_domains(Geo g, const uint16_t *__r
                                                       __half *__restrict__ B_mat, uint4 *__restrict__ B1,
                                                       float2 *__restrict__ dom_aux2) {
     __shared__ __align__(16) uint16_t L[16][4][64];
+    __shared__ uint32_t c2s[16], cgs[16];  // per domain: centring pair, -gamma / 64 as FP16 bits
     const int jl = threadIdx.x >> 4, e = threadIdx.x & 15;
-    const int j = blockIdx.x * 16 + jl, t = e >> 1, y0 = (e & 1) * 4;
-    const bool live = j < g.Dn;
-    int d = 0, cbar = 0;
-    if (live) {
-        d = dom_order[j];
+    const int j0 = blockIdx.x * 16;
+    const int j = j0 + jl;
+    if (j < g.Dn) {
+        const int d = dom_order[j];
         const int C = dsum[d];
-        cbar = (C + 32) >> 6;  // round(C / 64)
+        const int cbar = (C + 32) >> 6;  // round(C / 64)
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(domS + (size_t)d * 64) + e);  // elements 4e .. 4e + 3
         stage_layouts<8>(L[jl], 4 * e, (uint16_t)(v.x & 0xFFFFu));
         stage_layouts<8>(L[jl], 4 * e + 1, (uint16_t)(v.x >> 16));
         stage_layouts<8>(L[jl], 4 * e + 2, (uint16_t)(v.y & 0xFFFFu));
         stage_layouts<8>(L[jl], 4 * e + 3, (uint16_t)(v.y >> 16));
-    }
-    __syncthreads();
-    if (j >= n_pad) return;
-    uint4 *dst = reinterpret_cast<uint4 *>(B_mat + ((size_t)j * 8 + t) * 64) + y0;
-    if (live) {
-        const uint32_t c2 = (0x6400u + (uint32_t)cbar) * 0x10001u;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint4 m = *reinterpret_cast<const uint4 *>(iso_row<8>(L[jl], t, y0 + k));
-            dst[k] = make_uint4(centred_h2(m.x, c2), centred_h2(m.y, c2), centred_h2(m.z, c2), centred_h2(m.w, c2));
-        }
-        if (y0 == 0) {
-            const int gamma = dsum[d] - 64 * cbar;
-            const __half cg = __float2half_rn(-(float)gamma * (1.0f / 64.0f));  // exact: |gamma| <= 32
-            B1[2 * ((size_t)j * 8 + t)] = make_uint4((uint32_t)__half_as_ushort(cg), 0, 0, 0);
-            B1[2 * ((size_t)j * 8 + t) + 1] = make_uint4(0, 0, 0, 0);
-        }
         if (e == 0) {
-            const long long C = dsum[d];
-            const long long Q = 64LL * dsumsq[d] - C * C;
+            c2s[jl] = (0x6400u + (uint32_t)cbar) * 0x10001u;
+            const int gamma = C - 64 * cbar;
+            cgs[jl] = __half_as_ushort(__float2half_rn(-(float)gamma * (1.0f / 64.0f)));  // exact: |gamma| <= 32
+            const long long Q = 64LL * dsumsq[d] - (long long)C * C;
             dom_aux2[j] = make_float2((float)Q * (1.0f / 256.0f), Q > 0 ? 128.0f / (float)Q : 0.f);
         }
-    } else {
+    } else if (j < n_pad && e == 0) {
+        dom_aux2[j] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(0, 0, 0, 0);
-        if (y0 == 0) {
-            B1[2 * ((size_t)j * 8 + t)] = make_uint4(0, 0, 0, 0);
-            B1[2 * ((size_t)j * 8 + t) + 1] = make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < 4; ++k) {
+        const int u = 32 * k + lane;  // 16-byte piece of the warp's two domains
+        const int dl = 2 * warp + (u >> 6), t = (u >> 3) & 7, y = u & 7;
+        const int jj = j0 + dl;
+        if (jj >= n_pad) continue;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (jj < g.Dn) {
+            const uint4 m = *reinterpret_cast<const uint4 *>(iso_row<8>(L[dl], t, y));
+            const uint32_t c2 = c2s[dl];
+            val = make_uint4(centred_h2(m.x, c2), centred_h2(m.y, c2), centred_h2(m.z, c2), centred_h2(m.w, c2));
         }
-        if (e == 0) dom_aux2[j] = make_float2(0.f, 0.f);
+        reinterpret_cast<uint4 *>(B_mat)[(size_t)jj * 64 + (u & 63)] = val;
+    }
+    {
+        // B1: 8 rows x 32 bytes per domain, 16-byte piece lane of the warp's two domains
+        const int dl = 2 * warp + (lane >> 4);
+        const int jj = j0 + dl;
+        if (jj < n_pad) {
+            const bool lead = (lane & 1) == 0 && jj < g.Dn;  // first 16 bytes of a row hold the value
+            B1[(size_t)jj * 16 + (lane & 15)] = make_uint4(lead ? cgs[dl] : 0u, 0, 0, 0);
+        }
     }
 }
 
