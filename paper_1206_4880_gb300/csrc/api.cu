@@ -211,10 +211,9 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->win_hi = c.take<int32_t>(g.R);
         b->dom_key = c.take<uint8_t>(g.Dn);
         b->range_key = c.take<uint8_t>(g.R);
-        // each holds per-block counts and bases for one sort when the domain and range sorts run
-        // concurrently (pools.cu), or counts / bases of both sorts in turn
-        b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 512);
-        b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 512);
+        // per-block class histograms: of the domain sort and of the range sort
+        b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 256);
+        b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 256);
         b->fallback = c.take<int32_t>(g.R);
         b->fb_best = c.take<FallbackBest>(g.R);
         b->counters = img_counters ? img_counters + 8 * k : nullptr;

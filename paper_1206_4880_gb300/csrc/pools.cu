@@ -28,43 +28,45 @@ __global__ void k_sort_hist(const uint8_t *__restrict__ keys, int n, int32_t *__
     for (int k = threadIdx.x; k < 256; k += blockDim.x) counts[blockIdx.x * 256 + k] = h[k];
 }
 
-// One block of 256 threads: class totals, class starts (bin_off) and per-block scatter bases.
-__global__ void k_sort_scan(const int32_t *__restrict__ counts, int nblk, int K,
-                            int32_t *__restrict__ offs, int32_t *__restrict__ bin_off) {
-    __shared__ int tot[256];
-    const int k = threadIdx.x;
-    int t = 0;
-    for (int b = 0; b < nblk; ++b) t += counts[b * 256 + k];
-    tot[k] = t;
-    __syncthreads();
-    if (k == 0) {
-        int run = 0;
-        for (int i = 0; i < 256; ++i) {
-            const int c = tot[i];
-            tot[i] = run;
-            run += c;
-        }
-        bin_off[K] = run;
-    }
-    __syncthreads();
-    int run = tot[k];
-    if (k < K) bin_off[k] = run;
-    for (int b = 0; b < nblk; ++b) {
-        offs[b * 256 + k] = run;
-        run += counts[b * 256 + k];
-    }
-}
-
-// Stable scatter: block b places its kSortChunk keys, in index order, after the elements of
-// the same class from blocks < b. Within a 256-element step, a thread's rank among equal keys
-// is (earlier warps' counts) + (earlier lanes with the same key).
-__global__ void __launch_bounds__(256) k_sort_scatter(const uint8_t *__restrict__ keys, int n,
-                                                      const int32_t *__restrict__ offs,
-                                                      int32_t *__restrict__ order) {
+// Stable scatter: block b places its kSortChunk keys, in index order, after the elements of the
+// same class from blocks < b. Each block first forms its own bases from every block's histogram:
+// thread k sums class k over the blocks before b and over all blocks, an exclusive scan of the
+// totals gives the class starts (block 0 also stores them as bin_off[0 .. K], bin_off[K] = n).
+// Within a 256-element step, a thread's rank among equal keys is (earlier warps' counts) +
+// (earlier lanes with the same key).
+__global__ void __launch_bounds__(256) k_sort_scatter(const uint8_t *__restrict__ keys, int n, int nblk, int K,
+                                                      const int32_t *__restrict__ counts,
+                                                      int32_t *__restrict__ order, int32_t *__restrict__ bin_off) {
     __shared__ int run[256];
     __shared__ int wc[8][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    run[tid] = offs[blockIdx.x * 256 + tid];
+    {
+        int tot = 0, before = 0;
+#pragma unroll 4
+        for (int b = 0; b < nblk; ++b) {
+            const int c = counts[b * 256 + tid];
+            tot += c;
+            before += b < (int)blockIdx.x ? c : 0;
+        }
+        // exclusive scan of the class totals over the 256 classes
+        int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) wc[0][warp] = incl;
+        __syncthreads();
+        int wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += wc[0][w];
+        const int start = wbase + incl - tot;
+        run[tid] = start + before;
+        if (blockIdx.x == 0) {
+            if (tid < K) bin_off[tid] = start;
+            if (tid == 0) bin_off[K] = n;
+        }
+        __syncthreads();
+    }
     const int base = blockIdx.x * kSortChunk;
     const unsigned lt = (1u << lane) - 1u;
     for (int sub = 0; sub < kSortChunk; sub += 256) {
@@ -195,14 +197,12 @@ __global__ void k_windows_literal(Geo g, const double *__restrict__ rfd, const d
     if ((threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long *)matches, (unsigned long long)m);
 }
 
-static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *counts, int32_t *offs,
-                                 int32_t *order, int32_t *bin_off, cudaStream_t st) {
+static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *counts, int32_t *order,
+                                 int32_t *bin_off, cudaStream_t st) {
     const int nblk = (n + kSortChunk - 1) / kSortChunk;
     k_sort_hist<<<nblk, 256, 0, st>>>(keys, n, counts);
     ++g_launches;
-    k_sort_scan<<<1, 256, 0, st>>>(counts, nblk, K, offs, bin_off);
-    ++g_launches;
-    k_sort_scatter<<<nblk, 256, 0, st>>>(keys, n, offs, order);
+    k_sort_scatter<<<nblk, 256, 0, st>>>(keys, n, nblk, K, counts, order, bin_off);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -219,22 +219,15 @@ cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
         ++g_launches;
         k_fd_keys<<<(g.R + 255) / 256, 256, 0, st>>>(g.R, b.range_counts, rt, b.range_key);
         ++g_launches;
-        if ((e = counting_sort(b.dom_key, g.Dn, fr.n, b.sort_counts, b.sort_offs, b.dom_order, b.bin_off, st)))
-            return e;
-        if ((e = counting_sort(b.range_key, g.R, fr.n, b.sort_counts, b.sort_offs, b.range_order, b.rbin_off,
-                               st)))
-            return e;
+        if ((e = counting_sort(b.dom_key, g.Dn, fr.n, b.sort_counts, b.dom_order, b.bin_off, st))) return e;
+        if ((e = counting_sort(b.range_key, g.R, fr.n, b.sort_offs, b.range_order, b.rbin_off, st))) return e;
         k_windows_literal<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_fd, b.fd_extent, vt, fr.n, b.bin_off,
                                                              b.win_lo, b.win_hi, b.matches);
         ++g_launches;
         return cudaGetLastError();
     }
-    if ((e = counting_sort(b.dom_bin, g.Dn, g.K, b.sort_counts, b.sort_offs, b.dom_order,
-                           b.bin_off, st)))
-        return e;
-    if ((e = counting_sort(b.range_bin, g.R, g.K, b.sort_counts, b.sort_offs, b.range_order,
-                           b.rbin_off, st)))
-        return e;
+    if ((e = counting_sort(b.dom_bin, g.Dn, g.K, b.sort_counts, b.dom_order, b.bin_off, st))) return e;
+    if ((e = counting_sort(b.range_bin, g.R, g.K, b.sort_offs, b.range_order, b.rbin_off, st))) return e;
     k_windows<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_bin, b.bin_off, b.win_lo, b.win_hi,
                                                  b.matches);
     ++g_launches;
@@ -244,17 +237,13 @@ cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
 // The class-mode pools in two halves that can run on different streams: the domain sort
 // (dom_order, bin_off), and the range sort plus the windows (which also need bin_off: the caller
 // orders the second half after the first's domain sort). The two halves use separate sort
-// scratch (sort_counts for domains, sort_offs for ranges), each holding counts and bases.
+// scratch (sort_counts for domains, sort_offs for ranges).
 cudaError_t launch_pools_domains(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
-    const int nd = (g.Dn + kSortChunk - 1) / kSortChunk;
-    return counting_sort(b.dom_bin, g.Dn, g.K, b.sort_counts, b.sort_counts + (size_t)nd * 256, b.dom_order,
-                         b.bin_off, st);
+    return counting_sort(b.dom_bin, g.Dn, g.K, b.sort_counts, b.dom_order, b.bin_off, st);
 }
 
 cudaError_t launch_pools_ranges_sort(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
-    const int nr = (g.R + kSortChunk - 1) / kSortChunk;
-    return counting_sort(b.range_bin, g.R, g.K, b.sort_offs, b.sort_offs + (size_t)nr * 256, b.range_order,
-                         b.rbin_off, st);
+    return counting_sort(b.range_bin, g.R, g.K, b.sort_offs, b.range_order, b.rbin_off, st);
 }
 
 cudaError_t launch_pools_windows(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
