@@ -756,6 +756,19 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
     const int r = ri.w;
     const long long A = ri.x, Bs = rsumsq[r];
     const int ry = (r / g.nRx) * 8, rx = (r % g.nRx) * 8;
+    // the range's 8 inverse-permuted copies, staged before the key merge so that the pixel loads
+    // overlap the key loads (a flat range does not use them)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int px = 4 * hl + k, y = px >> 3, x = px & 7;
+        const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int sy, sx;
+            iso_src(8, t, y, x, sy, sx);
+            sg.rp[t][sy * 8 + sx] = v;
+        }
+    }
 
     if (64LL * Bs - A * A == 0) {  // flat range
         // the pool is a union of whole sort buckets, each holding ascending domain ids: the
@@ -794,21 +807,10 @@ __device__ __forceinline__ void reeval_rank(const Geo &g, const uint8_t *__restr
     // exact evaluation of the best key's group: the epilogue ranks 16-domain groups by their best
     // key, so every domain outside that group scores at most the runner-up key, and only the
     // group's domains inside the pool window can be certified (the runner-up's own domain is
-    // bounded by its key, so it can never pass the test below). The warp stages the range's
-    // inverse-permuted copies; lane hl forms X_t of the group's domain hl for all 8 isometries
+    // bounded by its key, so it can never pass the test below). With the range's inverse-permuted
+    // copies staged above, lane hl forms X_t of the group's domain hl for all 8 isometries
     // exactly (corr8) and keeps its best (gain, then smaller t); a half-warp reduction keeps the
     // best (gain, then smaller domain id, then smaller t).
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int px = 4 * hl + k, y = px >> 3, x = px & 7;
-        const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int sy, sx;
-            iso_src(8, t, y, x, sy, sx);
-            sg.rp[t][sy * 8 + sx] = v;
-        }
-    }
     __syncwarp(hmask);
     const int p1 = (int)(~(uint32_t)(b1 & 0xffffffffu));  // batch-wide positions
     int pos = b1 != 0 ? (p1 & ~15) + hl : -1;

@@ -470,6 +470,20 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
     const int r = ri.w;
     const long long A = ri.x, Bs = rsumsq[r];
     const int ry = (r / g.nRx) * 16, rx = (r % g.nRx) * 16;
+    // the range's 8 inverse-permuted copies, staged before the key merge so that the pixel loads
+    // overlap the key loads (a flat range does not use them)
+    Reeval16Stage &sg = sg16;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int px = 16 * hl + k, y = px >> 4, x = px & 15;
+        const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int sy, sx;
+            iso_src(16, t, y, x, sy, sx);
+            sg.rp[t][sy * 16 + sx] = v;
+        }
+    }
 
     if (256LL * Bs - A * A == 0) {  // flat range: every candidate has P = 0
         int dmin = INT_MAX;
@@ -503,18 +517,6 @@ __device__ __forceinline__ void reeval16_rank(const Geo &g, const uint8_t *__res
     }
     // exact evaluation of the best key's 16-domain group inside the pool window, as in the 8x8
     // re-evaluation (lane hl: the group's domain hl, all 8 isometries)
-    Reeval16Stage &sg = sg16;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int px = 16 * hl + k, y = px >> 4, x = px & 15;
-        const uint8_t v = img[(size_t)(ry + y) * g.pitch + rx + x];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int sy, sx;
-            iso_src(16, t, y, x, sy, sx);
-            sg.rp[t][sy * 16 + sx] = v;
-        }
-    }
     __syncwarp(hmask);
     const int p1 = (int)(~(uint32_t)(b1 & 0xffffffffu));  // batch-wide positions
     int pos = b1 != 0 ? (p1 & ~15) + hl : -1;
