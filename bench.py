@@ -289,6 +289,8 @@ def run_ours(args, wl, world, rank, local):
     fic.encode(img, p, out=out, workspace=ws, info=info)
     rep = fic.read_info(info)
     matches = rep["matches"]
+    # kernels of one encode as the timed graph runs it (no info record, so no k_write_info)
+    fic.encode(img, p, out=out, workspace=ws)
     launches = fic.profile_read()[1]
     torch.cuda.synchronize()
 
