@@ -693,7 +693,7 @@ fic_status fic_profile_read(float *ms, int32_t n, int32_t *launches) {
 
 size_t fic_decode_workspace_size(const fic_geom *gm, const fic_params *p, int32_t iters,
                                  int32_t ckpt_every) {
-    Geo g;
+    Geo g{};
     if (make_geo(gm, p, &g) != FIC_OK || iters < 0) return 0;
     const size_t img = (size_t)g.H * g.W;
     const int ck = ckpt_every < 1 ? 1 : ckpt_every;
@@ -718,7 +718,7 @@ static fic_status check_codes(const fic_codes *c) {
 fic_status fic_decode(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
                       int32_t iters, const float *x0, float *out, void *ws, size_t bytes,
                       void *stream) {
-    Geo g;
+    Geo g{};
     fic_status s = make_geo(gm, p, &g);
     if (s != FIC_OK) return s;
     if ((s = check_codes(codes)) != FIC_OK) return s;
@@ -751,14 +751,14 @@ fic_status fic_decode(const fic_codes *codes, const fic_geom *gm, const fic_para
 }
 
 size_t fic_decode_scaled_workspace_size(const fic_geom *gm, const fic_params *p, int32_t scale) {
-    Geo g;
+    Geo g{};
     if (make_geo(gm, p, &g) != FIC_OK || scale < 1 || scale > 16) return 0;
     return (size_t)g.H * g.W * scale * scale * sizeof(float) + 256;
 }
 
 fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *gm, const fic_params *p, int32_t scale,
                              int32_t iters, const float *x0, float *out, void *ws, size_t bytes, void *stream) {
-    Geo g;
+    Geo g{};
     fic_status s = make_geo(gm, p, &g);
     if (s != FIC_OK) return s;
     if ((s = check_codes(codes)) != FIC_OK) return s;
@@ -793,7 +793,7 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
                                int32_t iters, int32_t ckpt_every, const float *x0,
                                const float *grad_out, float *grad_s, float *grad_o, void *ws,
                                size_t bytes, void *stream) {
-    Geo g;
+    Geo g{};
     fic_status s = make_geo(gm, p, &g);
     if (s != FIC_OK) return s;
     if ((s = check_codes(codes)) != FIC_OK) return s;
