@@ -10,6 +10,7 @@ matches = sum over ranges of |Pool(r)| * 8.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--engine tensor|simt]
   python bench.py --impl reference ...   (the CPU oracle, timed on the host cores)
+  python bench.py --case decode|backward|classify --workload W   (one stage alone, for profiling)
 
 Under torchrun each rank encodes its own image (seed + rank) on its own GPU: independent
 problems, no data exchange, weak scaling; the timed region is the max over ranks.
@@ -52,10 +53,42 @@ WORKLOADS = {
                                  "domains at stride 8 (259081) x 8 isometries; K=32 LFD classes, w=10"),
 }
 FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one matcher launch from an ncu capture of the current kernel on the
-# workload (profiles/); emptied whenever the kernel changes until it is captured again.
-MEASURED_TRAFFIC = {("encode-1024", "tensor"): 85.47328e6 + 22.088448e6,
-                    ("encode-2048-s4-b16", "tensor"): 1.073587e9 + 74.92992e6}
+CSRC = os.path.join(ROOT, "paper_1206_4880_gb300", "csrc")
+PROFILES = os.path.join(ROOT, "profiles")
+# the source files each profiled kernel is compiled from: a capture's DRAM traffic is used only
+# while their contents hash to what the capture recorded
+KERNEL_SOURCES = {
+    "k_match_tc": ("match_tc.cu", "tc_ptx.cuh", "fic_internal.cuh"),
+    "k_match_tc16": ("match_tc16.cu", "tc_ptx.cuh", "fic_internal.cuh"),
+    "k_decode_step": ("decode.cu", "fic_internal.cuh"),
+    "k_block_stats": ("classify.cu", "fic_internal.cuh"),
+}
+
+
+def source_hash(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the ncu summaries under
+    profiles/ (a line "traffic: <kernel> <workload> dram_bytes_per_launch=<n> source=<hash>"), or
+    None when no capture exists or the kernel's sources changed since it was taken."""
+    import glob
+    import re
+    pat = re.compile(r"^traffic: (\S+) (\S+) dram_bytes_per_launch=(\d+) source=(\w+)")
+    cur = source_hash(kernel)
+    for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        with open(path) as f:
+            for line in f:
+                m = pat.match(line.strip())
+                if m and m.group(1) == kernel and m.group(2) == workload and m.group(4) == cur:
+                    return float(m.group(3))
+    return None
 
 
 def flops_per_match(block: int) -> int:
@@ -407,7 +440,9 @@ def run_ours(args, wl, world, rank, local):
         "stages_ms": {k: statistics.median(st[k] for st in stage_ms) for k in fic.STAGES},
         "roofline": {"kernel": "match", "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
-                     "traffic": MEASURED_TRAFFIC.get((args.workload, args.engine)), "traffic_unit": "bytes per launch",
+                     "traffic": measured_traffic("k_match_tc16" if wl["block"] == 16 else "k_match_tc", args.workload)
+                     if args.engine == "tensor" else None,
+                     "traffic_unit": "bytes per launch (ncu, profiles/; null once the kernel's sources changed)",
                      "per_launch_ms": mean_match_ms, "peak_source": peak_note},
         "e2e": {"value": e2e_value, "unit": "matches/s", "h2d_bytes_per_step": H * W,
                 "d2h_bytes_per_step": d2h},
@@ -431,8 +466,9 @@ def run_ours(args, wl, world, rank, local):
 def batched(args, dev):
     """The batched workload: 64 seeded images with sides drawn from {256, ..., 2048} and mixed
     Hurst exponents, stride-8 domains, K = 16, encoded by one fic_encode_batched call per step (one
-    tensor-engine launch for all images), captured once in a CUDA graph and replayed; the work
-    item granularity comes from the autotuner."""
+    tensor-engine launch for all images), captured once in a CUDA graph and replayed; the
+    matcher's pipeline depth, domain-group size and work-item granularity come from the
+    autotuner, whose per-candidate times are reported."""
     import dataclasses
 
     import torch
@@ -442,9 +478,9 @@ def batched(args, dev):
     imgs = [torch.from_numpy(a).to(dev) for a in imgs_np]
     p = fic.EncodeParams(domain_stride=8, num_classes=16, half_width=-1, engine=args.engine)
     t0 = time.perf_counter()
-    best, tune_ms = autotune.tune(imgs, p, use_cache=False)
+    best, tune_ms, tune_noise = autotune.tune(imgs, p, use_cache=False)
     tune_s = time.perf_counter() - t0
-    p = dataclasses.replace(p, items_per_sm=best)
+    p = dataclasses.replace(p, **best)
     shapes = [tuple(t.shape) for t in imgs]
     ws = torch.empty(fic.encode_batched_workspace_size(shapes, p), dtype=torch.uint8, device=dev)
     info = fic.new_info(dev)
@@ -477,8 +513,9 @@ def batched(args, dev):
                         "fic_encode_batched per step replayed from a CUDA graph" % sides,
             "matches_per_step": rep["matches"], "ms_per_step": med, "steps": steps,
             "matches_per_s": rep["matches"] / (med / 1e3), "fallback_ranges": rep["fallback_ranges"],
-            "work_items": rep["work_items"], "items_per_sm": best,
-            "autotune_ms": tune_ms, "autotune_s": tune_s}
+            "work_items": rep["work_items"], "variant": best,
+            "autotune_ms": tune_ms, "autotune_noise_ms": tune_noise,
+            "autotune_spread_ms": max(tune_ms.values()) - min(tune_ms.values()), "autotune_s": tune_s}
 
 
 def large(args, dev):
@@ -504,7 +541,7 @@ def large(args, dev):
         rep = fic.read_info(info)
         for _ in range(2):
             fic.encode(img, p, out=out, workspace=ws)
-        ms, mm = [], []
+        ms, mm, mc = [], [], []
         for k in range(3):
             flush.fill_(k & 255)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -513,20 +550,75 @@ def large(args, dev):
             b.record()
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
-            mm.append(fic.profile_read()[0]["match"])
+            st = fic.profile_read()[0]
+            mm.append(st["match"])
+            mc.append(st["classify"])
         x = fic.decode(out, H, W, p, 8)
         psnr = fic.quality(x, img)[1]
-        med, mmatch = statistics.median(ms), statistics.median(mm)
+        med, mmatch, mcls = statistics.median(ms), statistics.median(mm), statistics.median(mc)
         tf = rep["matches"] * flops_per_match(B) / (mmatch / 1e3) / 1e12
+        cls_bytes = classify_bytes(H, W, B, R, Dn)
         res[f"b{B}"] = {"ranges": R, "domains": Dn, "matches_per_step": rep["matches"],
                         "pool_fraction": rep["matches"] / (R * Dn * 8), "encode_ms": med,
                         "matches_per_s": rep["matches"] / (med / 1e3), "match_ms": mmatch,
                         "match_tflops": tf, "match_frac_of_peak": tf / peak,
+                        "classify_ms": mcls, "classify_bytes": cls_bytes,
+                        "classify_gbs": cls_bytes / (mcls / 1e3) / 1e9,
+                        "classify_frac_of_hbm": cls_bytes / (mcls / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
                         "fallback_ranges": rep["fallback_ranges"], "work_items": rep["work_items"],
-                        "device_error": rep["device_error"], "psnr_db": psnr}
+                        "device_error": rep["device_error"], "psnr_db": psnr,
+                        **decode_rates(out, H, W, p, flush, float(peaks["hbm_gbs"]))}
         del ws, out
     res["peak_source"] = f"{peak_src} bf16 dense burst x nominal fp16/bf16 ratio 1.0"
     return res
+
+
+def classify_bytes(H, W, B, R, Dn):
+    """Algorithmic bytes of the classification stage: every pixel read once; per range its sum,
+    sum of squares, box counts, FD and class written; per domain the same plus its B x B block of
+    16-bit 2x2 sums (which the operand packing reads)."""
+    ns = 3 if B == 16 else 2
+    per_range = 4 + 4 + 4 * ns + 8 + 1
+    per_dom = per_range + 2 * B * B
+    return H * W + R * per_range + Dn * per_dom
+
+
+def decode_rates(codes, H, W, p, flush, hbm_gbs, iters=8, ckpt=2, reps=5):
+    """fic_decode (iters Jacobi steps from mid-grey, one cached graph per call) and
+    fic_decode_backward (the adjoint of those steps, a checkpoint every `ckpt`), L2 flushed before
+    every call. Algorithmic bytes: 8 per pixel per decode step (read and write one FP32 image);
+    the adjoint recomputes the forward steps between checkpoints and per step gathers W^T l and
+    forms the gradient terms: about 16 per pixel per step besides the recomputation."""
+    import torch
+
+    from paper_1206_4880_gb300 import fic
+    dev = codes["dom"].device
+    ws = torch.empty(fic.decode_workspace_size(H, W, p, iters, ckpt), dtype=torch.uint8, device=dev)
+    out = torch.empty(H, W, dtype=torch.float32, device=dev)
+    g = torch.randn(H, W, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ms = []
+        for k in range(reps):
+            flush.fill_(k & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    dec_ms = timed(lambda: fic.decode(codes, H, W, p, iters, out=out, workspace=ws))
+    bwd_ms = timed(lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, g, workspace=ws))
+    dec_b = iters * H * W * 8
+    bwd_b = iters * H * W * 16
+    return {"decode_iters": iters, "decode_ms": dec_ms, "decode_gbs": dec_b / (dec_ms / 1e3) / 1e9,
+            "decode_frac_of_hbm": dec_b / (dec_ms / 1e3) / 1e9 / hbm_gbs,
+            "backward_ms": bwd_ms, "backward_gbs": bwd_b / (bwd_ms / 1e3) / 1e9,
+            "backward_frac_of_hbm": bwd_b / (bwd_ms / 1e3) / 1e9 / hbm_gbs}
 
 
 def diff(args, dev):
@@ -613,7 +705,94 @@ def comparators(img, img_np, wl, args, dev):
             res[f"{eng}_{name}_ms"] = ms
             res[f"{eng}_{name}_psnr_db"] = ps
     res["plain_gpu_full_over_classified"] = res["simt_full_ms"] / res[f"{args.engine}_classified_ms"]
+
+    # the method's own leverage on one engine: other readings of the pool window against the
+    # same engine's full search, each with its pool fraction and decoded PSNR
+    eng = args.engine
+    R, Dn = fic.counts(H, W, fic.EncodeParams(domain_stride=wl["sigma"], block=wl["block"]))
+    full_ms, full_psnr = res[f"{eng}_full_ms"], res[f"{eng}_full_psnr_db"]
+    K = wl["K"]
+    variants = {"default": (K, wl["w"]), "w_k6": (K, K // 6), "conci_k2_w0": (2, 0)}
+    method = {}
+    for name, (k, w) in variants.items():
+        p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=k, half_width=w, engine=eng,
+                             block=wl["block"])
+        info = fic.new_info(dev)
+        fic.encode(img, p, info=info)
+        frac = fic.read_info(info)["matches"] / (R * Dn * 8)
+        ms, ps = timed(p, 10 if eng == "tensor" else 3)
+        method[name] = {"K": k, "w": (k // 3 if w < 0 else w), "pool_fraction": frac, "encode_ms": ms,
+                        "psnr_db": ps, "delta_psnr_db": ps - full_psnr, "speedup_vs_full": full_ms / ms}
+    # "at equal PSNR": where a reading loses more than 0.1 dB against full search, full search at a
+    # coarser domain stride is the cheaper alternative of equal quality; time it at the strides
+    # 2, 3 and 4 times the workload's and compare with the fastest whose PSNR is not lower
+    coarse = {}
+    if any(abs(v["delta_psnr_db"]) > 0.1 for v in method.values()):
+        for mult in (2, 3, 4):
+            p = fic.EncodeParams(domain_stride=wl["sigma"] * mult, num_classes=1, engine=eng, block=wl["block"])
+            ms, ps = timed(p, 10 if eng == "tensor" else 3)
+            coarse[str(wl["sigma"] * mult)] = {"encode_ms": ms, "psnr_db": ps}
+        res["full_search_coarser_strides"] = coarse
+    for v in method.values():
+        ok = [c["encode_ms"] for c in coarse.values() if c["psnr_db"] >= v["psnr_db"]]
+        v["equal_psnr_full_ms"] = full_ms if abs(v["delta_psnr_db"]) <= 0.1 else min(ok + [full_ms])
+        v["speedup_at_equal_psnr"] = v["equal_psnr_full_ms"] / v["encode_ms"]
+    res["method"] = method
     return res
+
+
+def run_case(args, wl, local):
+    """One stage alone on the workload, for profiling: `decode` runs fic_decode (8 iterations from
+    mid-grey) on the workload's codes, `backward` its adjoint (fic_decode_backward, a checkpoint
+    every 2 iterations), `classify` runs fic_classify; `steps` timed calls after
+    `warmup`, L2 flushed before each; one JSON line with the median time and algorithmic GB/s."""
+    import torch
+
+    from paper_1206_4880_gb300 import fic
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    img_np = _image(wl, 0)
+    H, W = img_np.shape
+    img = torch.from_numpy(img_np).to(dev)
+    p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=wl["K"], half_width=wl["w"],
+                         engine=args.engine, block=wl["block"])
+    R, Dn = fic.counts(H, W, p)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.case in ("decode", "backward"):
+        codes = fic.encode(img, p)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()  # the encode's workspace is not needed by the decode
+        iters, ckpt = 8, 2
+        ws = torch.empty(fic.decode_workspace_size(H, W, p, iters, ckpt), dtype=torch.uint8, device=dev)
+        out = torch.empty(H, W, dtype=torch.float32, device=dev)
+        if args.case == "decode":
+            fn = lambda: fic.decode(codes, H, W, p, iters, out=out, workspace=ws)  # noqa: E731
+            nbytes = iters * H * W * 8
+        else:
+            gout = torch.randn(H, W, dtype=torch.float32, device=dev)
+            fn = lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, gout, workspace=ws)  # noqa: E731
+            nbytes = iters * H * W * 16
+    else:
+        ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)
+        stats = fic.classify(img, p, workspace=ws)
+        fn = lambda: fic.classify(img, p, workspace=ws)  # noqa: E731
+        nbytes = classify_bytes(H, W, wl["block"], R, Dn)
+        del stats
+    for _ in range(args.warmup):
+        fn()
+    ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    med = statistics.median(ms)
+    print(json.dumps({"case": args.case, "workload": args.workload, "ms": med, "algorithmic_bytes": nbytes,
+                      "gbs": nbytes / (med / 1e3) / 1e9}))
+    return 0
 
 
 def main():
@@ -627,12 +806,16 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--case", choices=("decode", "backward", "classify"), default=None,
+                    help="time one stage alone on the workload (for profiling) instead of the encode")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, wl, world, rank)
+    if args.case:
+        return run_case(args, wl, local)
     return run_ours(args, wl, world, rank, local)
 
 

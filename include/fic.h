@@ -55,7 +55,7 @@ typedef enum {
     FIC_ERR_INVALID_ARG = 1,  /* bad geometry, parameters or null pointer */
     FIC_ERR_WORKSPACE = 2,    /* workspace missing, too small or (decode) not 256-byte aligned */
     FIC_ERR_CUDA = 3,         /* a CUDA runtime/driver call or launch failed */
-    FIC_ERR_DEVICE_TIMEOUT = 4, /* a bounded device-side wait gave up (see fic_check) */
+    FIC_ERR_DEVICE_TIMEOUT = 4, /* a bounded device-side wait gave up (reported by fic_check) */
     FIC_ERR_UNSUPPORTED = 5   /* device or build lacks a required feature (sm_103a) */
 } fic_status;
 
@@ -88,6 +88,14 @@ typedef struct {
     int32_t items_per_sm;  /* tensor engine scheduling: work items per SM the range tiles' domain
                               chunks are split into, 1..64; 0 selects 24 (block 8) or 48
                               (block 16) */
+    int32_t group_chunks;  /* tensor engine scheduling: at most this many 512-domain chunks form one
+                              domain group, the band of domain operand rows the SMs running together
+                              stream (kept L2-resident), 1..1024; 0 selects 64 (block 8) or 16
+                              (block 16). Smaller groups need a larger workspace (size queries take
+                              it into account). */
+    int32_t pipeline_stages; /* tensor engine: shared-memory stages of the streamed domain operand,
+                                3 or 4 (block 8), 4 or 5 (block 16); 0 selects 4 (block 8) or 5
+                                (block 16). Results do not depend on it. */
 } fic_params;
 
 /* Per-block statistics (Section 3.1: the fractal dimensions of the range blocks are computed and
@@ -142,7 +150,8 @@ typedef struct {
     int64_t matches;          /* sum over ranges of |Pool(r)| * 8: range-domain-isometry fits */
     int32_t fallback_ranges;  /* ranges re-searched exactly because ranking could not certify */
     int32_t work_items;       /* tensor engine: (range tile, domain chunk) items */
-    int32_t device_error;     /* 0, or FIC_ERR_DEVICE_TIMEOUT if a bounded wait gave up */
+    int32_t device_error;     /* 0, or FIC_ERR_DEVICE_TIMEOUT if a bounded wait gave up (the
+                                 codes are then marked invalid, see fic_encode) */
     int32_t reserved;
 } fic_encode_info;
 
@@ -163,7 +172,11 @@ fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *g, const fi
 
 /* Sections 1 and 3: the whole encoder, image -> codes. Equal to the exact least-error search
  * over each range's pool (ties as in fic_codes). `info` (device, nullable) receives the
- * report. The first call with a given argument set (pointers, geometry, parameters, device) on a
+ * report. Device-side failure: every wait of the tensor matcher on another role of its CTA is
+ * bounded (2 s); if one gives up, the kernel stops without leaving work in flight, every code of
+ * the call is written as invalid (dom = iso = -1, s = o = sse = NaN), info->device_error (when
+ * `info` is given) is FIC_ERR_DEVICE_TIMEOUT, and the next fic_check on the device returns
+ * FIC_ERR_DEVICE_TIMEOUT. The call itself returns before the GPU runs, so it cannot report this. The first call with a given argument set (pointers, geometry, parameters, device) on a
  * host thread captures its work into a CUDA graph on a private stream; later calls with the same
  * arguments replay that graph on `stream` (up to 4 argument sets per thread, least recently used
  * replaced). Calls with profiling on, or on a stream the caller is capturing, run the stages
@@ -172,6 +185,16 @@ fic_status fic_encode(const uint8_t *img, const fic_geom *g, const fic_params *p
                       const fic_codes *out, fic_encode_info *info, void *workspace,
                       size_t workspace_bytes, void *stream);
 
+/* Instrumentation (not part of the method): after a fic_encode with this workspace, geometry and
+ * parameters has run on `stream`, writes the ids of the ranges whose best code the tensor engine's
+ * ranking could not certify and that were therefore re-searched exactly (Section 1's exhaustive
+ * least squares over the uncertified part of the pool), in no particular order, to ids[0 ..
+ * min(count, max_ids)) and their number to *count. ids and count are device pointers; 0 ranges
+ * for the SIMT engine. Enqueued on `stream`. */
+fic_status fic_encode_fallback_ranges(const fic_geom *g, const fic_params *p, void *workspace,
+                                      size_t workspace_bytes, int32_t *ids, int32_t max_ids,
+                                      int32_t *count, void *stream);
+
 /* Bytes of workspace fic_encode_batched needs for these n images (1 <= n <= 4096). */
 size_t fic_encode_batched_workspace_size(const fic_geom *geoms, int32_t n, const fic_params *p);
 
@@ -179,7 +202,8 @@ size_t fic_encode_batched_workspace_size(const fic_geom *geoms, int32_t n, const
  * image has its own classes, F_l/F_m and pools). imgs, geoms and outs are HOST arrays of n
  * entries (device image pointers, geometries, code structs of device arrays). The tensor engine
  * matches all images' pools in one persistent launch. `info` (device, nullable) receives the
- * totals over the batch. */
+ * totals over the batch. A device-side timeout marks every image's codes invalid, as in
+ * fic_encode. */
 fic_status fic_encode_batched(const uint8_t *const *imgs, const fic_geom *geoms, int32_t n,
                               const fic_params *p, const fic_codes *outs, fic_encode_info *info,
                               void *workspace, size_t workspace_bytes, void *stream);
@@ -217,7 +241,11 @@ size_t fic_decode_workspace_size(const fic_geom *g, const fic_params *p, int32_t
 /* Section 1: decoding. x_0 = x0 (H*W float, row-major, dense) or 128 everywhere when x0 is
  * NULL; x_{k+1}[range r] = s_r T_{t_r}(D(x_k, dom_r)) + o_r for all ranges from x_k (Jacobi),
  * D the 2x2 average of the 2B x 2B domain; `out` (H*W float) receives x_iters, unclamped.
- * iters >= 0. Workspace: fic_decode_workspace_size. */
+ * iters >= 0. Workspace: fic_decode_workspace_size. Codes whose domain or isometry is out of range
+ * (such as the invalid codes of an encode whose matcher gave up) give NaN pixels for their range.
+ * Like fic_encode, the first call with a given argument set on a host thread captures its
+ * iterations into a CUDA graph; later calls with the same arguments replay it (4 argument sets per
+ * thread; calls on a stream the caller is capturing run the steps directly). */
 fic_status fic_decode(const fic_codes *codes, const fic_geom *g, const fic_params *p,
                       int32_t iters, const float *x0, float *out, void *workspace,
                       size_t workspace_bytes, void *stream);
@@ -269,12 +297,27 @@ fic_status fic_profile_read(float *ms, int32_t n, int32_t *launches);
  * a fixed scratch image of FIC_DECODE_STATIC_MAX_PIXELS floats (4 MiB) kept in the library's
  * device memory, which every GPU that loads the library holds until the process exits. Images
  * with more pixels return FIC_ERR_INVALID_ARG. The first call made with a given device current
- * looks up the scratch's device address (cudaGetSymbolAddress) and caches it; make that first
- * call before any stream capture. All calls share the one scratch image: calls whose GPU work
+ * looks up the scratch's device address (cudaGetSymbolAddress) and caches it for that device and
+ * its current CUDA context (a call after the context was destroyed and re-created, e.g. after
+ * cudaDeviceReset, looks it up again); make that first call before any stream capture. All calls share the one scratch image: calls whose GPU work
  * overlaps (different streams, concurrent host threads) race on it and must be ordered by the
  * caller. x0 and out must not alias each other. */
 fic_status fic_decode_static(const fic_codes *codes, const fic_geom *g, const fic_params *p,
                              int32_t iters, const float *x0, float *out, void *stream);
+
+/* Waits for the work enqueued on `stream` (cudaStreamSynchronize), then reads and clears the
+ * library's device error word on the current device: FIC_ERR_DEVICE_TIMEOUT if a bounded
+ * device-side wait of any encode on this device gave up since the last fic_check (the codes of that
+ * encode are marked invalid, see fic_encode), FIC_ERR_CUDA if the stream reported an error, else
+ * FIC_OK. Synchronises the host; not for use on a stream that is being captured. */
+fic_status fic_check(void *stream);
+
+/* Testing hook for the device-side error path (not needed to use the library). With ns > 0, the
+ * tensor matchers launched by this host thread's later fic_encode / fic_encode_batched calls first
+ * wait up to ns nanoseconds (ns <= 1e9) on a barrier that nothing completes, before they issue any
+ * copy or MMA, so the wait gives up and the call ends as a device timeout (see fic_encode) with no
+ * work in flight. ns = 0 turns it off. While it is on, fic_encode does not use its graph cache. */
+fic_status fic_debug_stall_matcher(int64_t ns);
 
 /* 1 if `engine` (FIC_ENGINE_*) can run on the current device with this build, else 0. */
 int32_t fic_engine_available(int32_t engine);

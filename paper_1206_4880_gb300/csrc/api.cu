@@ -1,5 +1,7 @@
 // C ABI of the fic library (include/fic.h): argument validation, workspace carving and the
 // order of launches. All device work is enqueued on the caller's stream.
+#include <cuda.h>
+
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +35,10 @@ using namespace fic;
 namespace {
 
 thread_local char g_err[512] = "";
+
+// Testing hook of fic_debug_stall_matcher: the forced wait (ns) of the tensor matchers launched by
+// this thread's encodes; 0 = off.
+thread_local unsigned long long g_stall_ns = 0;
 
 // Stage timing for fic_profile_*: events 0..6 bracket classify, pools, pack, match, re-evaluate,
 // re-search.
@@ -138,6 +144,12 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
         return fail(FIC_ERR_INVALID_ARG, "the literal FD window is implemented for block 8 only");
     if (p->items_per_sm < 0 || p->items_per_sm > 64)
         return fail(FIC_ERR_INVALID_ARG, "items_per_sm must be in [0, 64]");
+    if (p->group_chunks < 0 || p->group_chunks > 1024)
+        return fail(FIC_ERR_INVALID_ARG, "group_chunks must be in [0, 1024]");
+    if (p->pipeline_stages != 0 && (B == 8 ? (p->pipeline_stages < 3 || p->pipeline_stages > 4)
+                                           : (p->pipeline_stages < 4 || p->pipeline_stages > 5)))
+        return fail(FIC_ERR_INVALID_ARG, "pipeline_stages must be 0 or in [%d, %d] for block %d", B == 8 ? 3 : 4,
+                    B == 8 ? 4 : 5, B);
     g->H = gm->H;
     g->W = gm->W;
     g->pitch = gm->pitch;
@@ -153,6 +165,10 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
     g->K = p->num_classes;
     g->w = p->half_width < 0 ? p->num_classes / 3 : p->half_width;
     g->literal = (p->flags & FIC_FLAG_LITERAL_WINDOW) ? 1 : 0;
+    g->fRx = make_fastdiv((uint32_t)g->nRx);
+    g->fDx = make_fastdiv((uint32_t)g->nDx);
+    g->group_chunks = p->group_chunks > 0 ? p->group_chunks : (B == 16 ? 16 : 64);
+    g->stages = p->pipeline_stages;
     return FIC_OK;
 }
 
@@ -162,8 +178,69 @@ namespace fic {
 
 thread_local int g_launches = 0;
 
-// Sets the message fic_last_error() returns on this thread.
+// The library's device error word on every GPU that loads it: a matcher whose bounded wait gave up
+// writes FIC_ERR_DEVICE_TIMEOUT here (besides the encode's own report); fic_check reads and clears
+// it. Its address is looked up with the device current at each encode that launches a matcher.
+__device__ int32_t g_device_error = 0;
+
 void set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+fic_status make_geometry(const fic_geom *gm, const fic_params *p, Geo *g) { return make_geo(gm, p, g); }
+
+namespace {
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+std::mutex g_errword_mu;
+struct SymbolEntry {
+    void *ctx = nullptr;
+    int32_t *ptr = nullptr;
+};
+SymbolEntry g_errword[kMaxDevices];
+}  // namespace
+
+bool current_context(void **ctx) {
+    CtxGetCurrentFn get = ctx_get_current();
+    CUcontext c = nullptr;
+    if (!get || get(&c) != CUDA_SUCCESS) return false;
+    *ctx = (void *)c;
+    return true;
+}
+
+// Device address of g_device_error in the current device's current context, looked up once per
+// (device, context); the encode paths look it up before they begin any stream capture.
+cudaError_t device_error_word(int32_t **ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    void *ctx = nullptr;
+    if (!current_context(&ctx)) return cudaErrorDeviceUninitialized;
+    std::lock_guard<std::mutex> lock(g_errword_mu);
+    SymbolEntry &ent = g_errword[dev];
+    if (!ctx || !ent.ptr || ent.ctx != ctx) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_device_error);  // makes the primary context current if none is
+        if (e != cudaSuccess) return e;
+        if (!current_context(&ctx) || !ctx) return cudaErrorDeviceUninitialized;
+        ent.ptr = static_cast<int32_t *>(p);
+        ent.ctx = ctx;
+    }
+    *ptr = ent.ptr;
+    return cudaSuccess;
+}
 
 size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void *ws, size_t cap, bool *ok) {
     Carver c(ws, cap);
@@ -230,7 +307,8 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
     // for B = 16). A tile meets at most chunks / cpi + 2 groups, and cpi >= min(cap, total /
     // target), so items <= 2 tiles + max(target, chunks / cap); cutting the last two groups in
     // four adds at most 6 items per tile.
-    tb->cpi_cap = B == 16 ? 16 : 64;
+    tb->cpi_cap = gs[0].group_chunks;
+    tb->stages = gs[0].stages;
     tb->max_items = (int)(8 * mt_tot + (chunks_tot / tb->cpi_cap + 1 > kMaxItemTarget ? chunks_tot / tb->cpi_cap + 1
                                                                                         : kMaxItemTarget));
     tb->max_chunks = (int)chunks_tot;
@@ -280,6 +358,16 @@ __global__ void k_write_info(const int32_t *img_counters, int n, const int32_t *
     info->work_items = gcounters[1];
     info->device_error = gcounters[2];
     info->reserved = 0;
+}
+
+// Range ids of the re-searched ranges: fallback[] holds class-sorted positions.
+__global__ void k_fallback_ids(const int32_t *__restrict__ fallback, const int32_t *__restrict__ counters,
+                               const int32_t *__restrict__ range_order, int max_ids, int32_t *__restrict__ ids,
+                               int32_t *__restrict__ count) {
+    const int n = counters[0];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n && k < max_ids; k += gridDim.x * blockDim.x)
+        ids[k] = range_order[fallback[k]];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = n;
 }
 
 cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encode_info *info, cudaStream_t st) {
@@ -437,6 +525,10 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
         return fail(FIC_ERR_UNSUPPORTED, "tensor engine needs an sm_103 device");
     int sms = 0;
     FIC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+    if (p->engine == FIC_ENGINE_TENSOR) {
+        FIC_TRY(device_error_word(&tb.lib_error), "device error word");
+        tb.stall_ns = g_stall_ns;
+    }
     g_launches = 0;
     // stage marks; inside a stream capture they become event-record nodes of the graph (external
     // records), so a replayed encode still reports its stage times
@@ -554,61 +646,37 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
     return FIC_OK;
 }
 
-// ---- repeated single-image encodes: one cached CUDA graph per argument set -------------------
-// A call whose arguments (pointers, geometry, parameters, device) equal an earlier call's on this
-// host thread replays that call's captured graph: one launch instead of the stage kernels,
-// memsets and stream forks. The graph embeds every pointer and parameter, so equal arguments mean
-// the same work on whatever the buffers hold now.
-namespace {
-struct EncodeKey {
-    const void *img, *ws, *info;
-    size_t bytes;
-    fic_geom g;
-    fic_params p;
-    fic_codes out;
-    int dev;
-};
-struct GraphEntry {
-    EncodeKey key;
-    cudaGraphExec_t exec = nullptr;
-    int launches = 0;
-    unsigned long long used = 0;
-};
-constexpr int kGraphCache = 4;
-struct GraphCache {
-    GraphEntry e[kGraphCache];
-    unsigned long long tick = 0;
-    cudaStream_t cap[kMaxDevices] = {};  // private capture streams
-};
-thread_local GraphCache g_graphs;
-}  // namespace
+}  // extern "C"
 
-fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *p,
-                      const fic_codes *out, fic_encode_info *info, void *ws, size_t bytes,
-                      void *stream) {
-    const uint8_t *imgs[1] = {img};
-    if (!out) return fail(FIC_ERR_INVALID_ARG, "null code pointer");
-    cudaStream_t st = (cudaStream_t)stream;
-    // profiling (stage events), a caller's own capture and bad arguments take the direct path
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    int dev = -1;
-    if (g_prof.on || !gm || !p || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
-        cs != cudaStreamCaptureStatusNone || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return encode_batch(imgs, gm, 1, p, out, info, ws, bytes, stream);
-    }
-    EncodeKey k;
-    memset(&k, 0, sizeof k);  // padding included: keys compare as bytes
-    k.img = img;
-    k.ws = ws;
-    k.info = info;
-    k.bytes = bytes;
-    k.g = *gm;
-    k.p = *p;
-    k.out = *out;
-    k.dev = dev;
-    GraphEntry *hit = nullptr, *victim = nullptr;
-    for (auto &e : g_graphs.e) {
+// ---- repeated calls: one cached CUDA graph per argument set ----------------------------------
+// A fic_encode or fic_decode call whose arguments (pointers, geometry, parameters, device) equal an
+// earlier call's on this host thread replays that call's captured graph: one launch instead of the
+// stage kernels, memsets and stream forks (encode) or of the iterations (decode). The graph embeds
+// every pointer and parameter, so equal arguments mean the same work on whatever the buffers hold
+// now.
+namespace {
+constexpr int kGraphCache = 4;
+template <class Key>
+struct GraphCacheT {
+    struct Entry {
+        Key key;
+        cudaGraphExec_t exec = nullptr;
+        int launches = 0;
+        unsigned long long used = 0;
+    };
+    Entry e[kGraphCache];
+    unsigned long long tick = 0;
+};
+thread_local cudaStream_t g_capture_stream[kMaxDevices] = {};  // private capture streams
+
+// Replays the graph cached for `k`, or captures enqueue(capture stream) into a new one (after
+// prepare(), which creates whatever must exist before a capture begins) and replays that. Keys
+// compare as bytes, padding included, so callers zero them before filling them in.
+template <class Key, class Prepare, class Enqueue>
+fic_status replay_or_capture(GraphCacheT<Key> &cache, const Key &k, int dev, cudaStream_t st, Prepare prepare,
+                             Enqueue enqueue) {
+    typename GraphCacheT<Key>::Entry *hit = nullptr, *victim = nullptr;
+    for (auto &e : cache.e) {
         if (e.exec && memcmp(&e.key, &k, sizeof k) == 0) {
             hit = &e;
             break;
@@ -616,12 +684,12 @@ fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *
         if (!victim || !e.exec || (victim->exec && e.used < victim->used)) victim = &e;
     }
     if (!hit) {
-        // the internal streams and the capture stream exist before the capture starts
-        side_pool(dev, st);
-        cudaStream_t &cap = g_graphs.cap[dev];
+        const fic_status ps = prepare();
+        if (ps != FIC_OK) return ps;
+        cudaStream_t &cap = g_capture_stream[dev];
         if (!cap) FIC_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
         FIC_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-        const fic_status s = encode_batch(imgs, gm, 1, p, out, info, ws, bytes, cap);
+        const fic_status s = enqueue(cap);
         cudaGraph_t graph = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
         if (s != FIC_OK) {
@@ -640,9 +708,84 @@ fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *
         victim->launches = g_launches;
         hit = victim;
     }
-    hit->used = ++g_graphs.tick;
+    hit->used = ++cache.tick;
     FIC_TRY(cudaGraphLaunch(hit->exec, st), "cudaGraphLaunch");
-    g_prof.launches = hit->launches;
+    g_launches = hit->launches;
+    return FIC_OK;
+}
+
+// The current device, when a call on `st` may use the graph cache (not while `st` is capturing).
+bool cacheable(cudaStream_t st, int *dev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+        cudaGetDevice(dev) != cudaSuccess || *dev < 0 || *dev >= kMaxDevices) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+struct EncodeKey {
+    const void *img, *ws, *info;
+    size_t bytes;
+    fic_geom g;
+    fic_params p;
+    fic_codes out;
+    int dev;
+};
+thread_local GraphCacheT<EncodeKey> g_encode_graphs;
+}  // namespace
+
+extern "C" {
+
+fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *p,
+                      const fic_codes *out, fic_encode_info *info, void *ws, size_t bytes,
+                      void *stream) {
+    const uint8_t *imgs[1] = {img};
+    if (!out) return fail(FIC_ERR_INVALID_ARG, "null code pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    // profiling (stage events), the stall hook, a caller's own capture and bad arguments take the
+    // direct path
+    int dev = -1;
+    if (g_prof.on || g_stall_ns || !gm || !p || !cacheable(st, &dev))
+        return encode_batch(imgs, gm, 1, p, out, info, ws, bytes, stream);
+    EncodeKey k;
+    memset(&k, 0, sizeof k);  // padding included: keys compare as bytes
+    k.img = img;
+    k.ws = ws;
+    k.info = info;
+    k.bytes = bytes;
+    k.g = *gm;
+    k.p = *p;
+    k.out = *out;
+    k.dev = dev;
+    const fic_status s = replay_or_capture(
+        g_encode_graphs, k, dev, st,
+        [&]() -> fic_status {
+            // the internal streams and the error word's address exist before the capture starts
+            side_pool(dev, st);
+            int32_t *ew = nullptr;
+            FIC_TRY(device_error_word(&ew), "device error word");
+            return FIC_OK;
+        },
+        [&](cudaStream_t cap) { return encode_batch(imgs, gm, 1, p, out, info, ws, bytes, cap); });
+    g_prof.launches = g_launches;
+    return s;
+}
+
+fic_status fic_encode_fallback_ranges(const fic_geom *gm, const fic_params *p, void *ws, size_t bytes,
+                                      int32_t *ids, int32_t max_ids, int32_t *count, void *stream) {
+    std::vector<Geo> gv;
+    std::vector<EncodeBufs> bv;
+    TcBatch tb;
+    fic_status s = carve_batch(gm, 1, p, ws, bytes, gv, bv, &tb);
+    if (s != FIC_OK) return s;
+    if (!count || max_ids < 0 || (max_ids > 0 && !ids)) return fail(FIC_ERR_INVALID_ARG, "null output or max_ids < 0");
+    g_launches = 0;
+    k_fallback_ids<<<64, 256, 0, (cudaStream_t)stream>>>(bv[0].fallback, bv[0].counters, bv[0].range_order, max_ids,
+                                                        ids, count);
+    ++g_launches;
+    FIC_TRY(cudaGetLastError(), "fallback_ranges");
     return FIC_OK;
 }
 
@@ -691,6 +834,24 @@ fic_status fic_profile_read(float *ms, int32_t n, int32_t *launches) {
     return FIC_OK;
 }
 
+fic_status fic_check(void *stream) {
+    FIC_TRY(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    int32_t v = 0;
+    FIC_TRY(cudaMemcpyFromSymbol(&v, g_device_error, sizeof v), "reading the device error word");
+    if (v == 0) return FIC_OK;
+    const int32_t zero = 0;
+    FIC_TRY(cudaMemcpyToSymbol(g_device_error, &zero, sizeof zero), "clearing the device error word");
+    return fail(FIC_ERR_DEVICE_TIMEOUT,
+                "a bounded wait of the tensor matcher gave up; that encode's codes are marked invalid "
+                "(dom = iso = -1, s = o = sse = NaN)");
+}
+
+fic_status fic_debug_stall_matcher(int64_t ns) {
+    if (ns < 0 || ns > 1000000000LL) return fail(FIC_ERR_INVALID_ARG, "stall must be in [0, 1e9] ns");
+    g_stall_ns = (unsigned long long)ns;
+    return FIC_OK;
+}
+
 size_t fic_decode_workspace_size(const fic_geom *gm, const fic_params *p, int32_t iters,
                                  int32_t ckpt_every) {
     Geo g{};
@@ -715,21 +876,14 @@ static fic_status check_codes(const fic_codes *c) {
     return FIC_OK;
 }
 
-fic_status fic_decode(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
-                      int32_t iters, const float *x0, float *out, void *ws, size_t bytes,
-                      void *stream) {
-    Geo g{};
-    fic_status s = make_geo(gm, p, &g);
-    if (s != FIC_OK) return s;
-    if ((s = check_codes(codes)) != FIC_OK) return s;
-    if (!out || iters < 0) return fail(FIC_ERR_INVALID_ARG, "null output or negative iters");
-    if (!ws || (uintptr_t)ws % 256) return fail(FIC_ERR_WORKSPACE, "workspace null or misaligned");
-    const size_t need = fic_decode_workspace_size(gm, p, iters, 1);
+}  // extern "C"
+
+namespace {
+// Enqueues x_iters = W^iters(x_0) (ping-pong between `out` and `tmp`, landing in `out`).
+fic_status decode_enqueue(const fic_codes &codes, const Geo &g, int iters, const float *x0, float *out, float *tmp,
+                          cudaStream_t st) {
     const size_t img = (size_t)g.H * g.W;
-    if (bytes < img * sizeof(float)) return fail(FIC_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", bytes, need);
-    (void)need;
-    cudaStream_t st = (cudaStream_t)stream;
-    float *tmp = (float *)ws;
+    g_launches = 0;
     if (iters == 0) {
         if (x0) FIC_TRY(cudaMemcpyAsync(out, x0, img * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy");
         else FIC_TRY(launch_fill(out, img, 128.f, st), "fill");
@@ -744,10 +898,55 @@ fic_status fic_decode(const fic_codes *codes, const fic_geom *gm, const fic_para
     }
     for (int k = 0; k < iters; ++k) {
         float *dst = ((iters - 1 - k) % 2 == 0) ? out : tmp;
-        FIC_TRY(launch_decode_step(*codes, g, cur, dst, st), "decode_step");
+        FIC_TRY(launch_decode_step(codes, g, cur, dst, st), "decode_step");
         cur = dst;
     }
     return FIC_OK;
+}
+
+struct DecodeKey {
+    fic_codes codes;
+    fic_geom g;
+    fic_params p;
+    const void *x0, *out, *ws;
+    size_t bytes;
+    int iters, dev;
+};
+thread_local GraphCacheT<DecodeKey> g_decode_graphs;
+}  // namespace
+
+extern "C" {
+
+fic_status fic_decode(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
+                      int32_t iters, const float *x0, float *out, void *ws, size_t bytes,
+                      void *stream) {
+    Geo g{};
+    fic_status s = make_geo(gm, p, &g);
+    if (s != FIC_OK) return s;
+    if ((s = check_codes(codes)) != FIC_OK) return s;
+    if (!out || iters < 0) return fail(FIC_ERR_INVALID_ARG, "null output or negative iters");
+    if (!ws || (uintptr_t)ws % 256) return fail(FIC_ERR_WORKSPACE, "workspace null or misaligned");
+    const size_t need = fic_decode_workspace_size(gm, p, iters, 1);
+    const size_t img = (size_t)g.H * g.W;
+    if (bytes < img * sizeof(float)) return fail(FIC_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    float *tmp = (float *)ws;
+    int dev = -1;
+    if (!cacheable(st, &dev)) return decode_enqueue(*codes, g, iters, x0, out, tmp, st);
+    DecodeKey k;
+    memset(&k, 0, sizeof k);  // padding included: keys compare as bytes
+    k.codes = *codes;
+    k.g = *gm;
+    k.p = *p;
+    k.x0 = x0;
+    k.out = out;
+    k.ws = ws;
+    k.bytes = bytes;
+    k.iters = iters;
+    k.dev = dev;
+    return replay_or_capture(
+        g_decode_graphs, k, dev, st, []() { return FIC_OK; },
+        [&](cudaStream_t cap) { return decode_enqueue(*codes, g, iters, x0, out, tmp, cap); });
 }
 
 size_t fic_decode_scaled_workspace_size(const fic_geom *gm, const fic_params *p, int32_t scale) {

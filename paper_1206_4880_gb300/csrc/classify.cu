@@ -147,7 +147,8 @@ __device__ __forceinline__ void range_stats(int r, const uint8_t *__restrict__ i
                                             int32_t *__restrict__ rsum, int32_t *__restrict__ rsumsq,
                                             int32_t *__restrict__ rcounts, double *__restrict__ rfd) {
     if (r >= g.R) return;
-    const int y0 = (r / g.nRx) * 8, x0 = (r % g.nRx) * 8;
+    const int rq = fdiv(r, g.fRx);
+    const int y0 = rq * 8, x0 = (r - rq * g.nRx) * 8;
     const bool words = word_rows(img, g.pitch, x0);
     int v[8][8];
 #pragma unroll
@@ -199,7 +200,8 @@ __device__ __forceinline__ void dom_stats(int d, const uint8_t *__restrict__ img
                                           double *__restrict__ dfd, unsigned long long *extent_bits) {
     unsigned long long fbits_min = ~0ull, fbits_max = 0ull;
     if (d < g.Dn) {
-        const int y0 = (d / g.nDx) * g.sigma, x0 = (d % g.nDx) * g.sigma;
+        const int dq = fdiv(d, g.fDx);
+        const int y0 = dq * g.sigma, x0 = (d - dq * g.nDx) * g.sigma;
         const bool words = word_rows(img, g.pitch, x0);
         int S[8][8];
         int C = 0, E = 0, n2 = 0, n4 = 0;
@@ -344,7 +346,8 @@ __device__ __forceinline__ void range_stats16(int r, const uint8_t *__restrict__
                                               int32_t *__restrict__ rsumsq, int32_t *__restrict__ rcounts,
                                               double *__restrict__ rfd) {
     if (r >= g.R) return;
-    const int y0 = (r / g.nRx) * 16, x0 = (r % g.nRx) * 16;
+    const int rq = fdiv(r, g.fRx);
+    const int y0 = rq * 16, x0 = (r - rq * g.nRx) * 16;
     const bool words = word_rows(img, g.pitch, x0);
     Dbc16<5> dbc;
     int A = 0, Bs = 0;
@@ -377,7 +380,8 @@ __device__ __forceinline__ void dom_stats16(int d, const uint8_t *__restrict__ i
                                             unsigned long long *extent_bits) {
     unsigned long long fbits_min = ~0ull, fbits_max = 0ull;
     if (d < g.Dn) {
-        const int y0 = (d / g.nDx) * g.sigma, x0 = (d % g.nDx) * g.sigma;
+        const int dq = fdiv(d, g.fDx);
+        const int y0 = dq * g.sigma, x0 = (d - dq * g.nDx) * g.sigma;
         const bool words = word_rows(img, g.pitch, x0);
         Dbc16<7> dbc;
         int C = 0, E = 0;

@@ -25,31 +25,126 @@ cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// One thread per output pixel.
+// One warp per range r: the warp reads the 2B x 2B source domain of x_k, forms the B x B averages
+// D(x_k, d_r) in shared memory, and writes the range's B x B pixels of x_{k+1},
+// y[p] = s_r * D[src_t(p)] + o_r, two (B = 8) or four (B = 16) adjacent pixels per store.
+// LD selects the source loads: 4 = 16-byte loads, each the top or bottom row of two adjacent 2x2
+// cells (every domain starts at a column that is a multiple of 4 and the image is 16-byte
+// aligned); 2 = aligned pairs, one row of one cell; 1 = single floats. VS: the output is aligned for
+// the vector stores (else single stores). The isometry is affine in the pixel coordinates, so a
+// warp forms src_t(py, px) = c0 + ky py + kx px from three warp-uniform constants. The sum order
+// ((x00 + x01) + x10) + x11, the scaling by 1/4 and the fma are those of the per-pixel definition,
+// so every variant gives the same bits.
+constexpr int kDecodeWarps = 8;
+
+template <int B, int LD, bool VS>
+__global__ void __launch_bounds__(32 * kDecodeWarps)
+    k_decode_step(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                  const double *__restrict__ s, const double *__restrict__ o, const float *__restrict__ x,
+                  float *__restrict__ y) {
+    constexpr int NC = B * B / 32;     // cells (and output pixels) per lane
+    constexpr int PV = B == 8 ? 2 : 4;  // pixels per vector store
+    __shared__ __align__(16) float cell[kDecodeWarps][B * B];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * kDecodeWarps + warp;
+    if (r >= g.R) return;  // whole warps leave together; the block has no block-wide barrier
+    const int d = __ldg(dom + r), t = __ldg(iso + r);
+    const int rq = fdiv(r, g.fRx), dq = fdiv(d, g.fDx);
+    float *dst = y + (size_t)(rq * B) * g.W + (r - rq * g.nRx) * B;
+    if (!valid_code(g, d, t)) {  // an invalid code (an encode that gave up): NaN pixels, no read
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            dst[(size_t)((lane + 32 * k) / B) * g.W + (lane + 32 * k) % B] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const float sr = (float)__ldg(s + r), orr = (float)__ldg(o + r);
+    const float *src = x + (size_t)(dq * g.sigma) * g.W + (d - dq * g.nDx) * g.sigma;
+    float *cw = cell[warp];
+    if constexpr (LD == 4) {
+#pragma unroll
+        for (int k = 0; k < NC / 2; ++k) {
+            const int q = lane + 32 * k, cy = q / (B / 2), cp = q % (B / 2);  // cells (cy, 2cp), (cy, 2cp + 1)
+            const float4 *p = reinterpret_cast<const float4 *>(src + (size_t)(2 * cy) * g.W + 4 * cp);
+            const float4 a = __ldg(p), b = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(p) + g.W));
+            *reinterpret_cast<float2 *>(&cw[cy * B + 2 * cp]) =
+                make_float2((((a.x + a.y) + b.x) + b.y) * 0.25f, (((a.z + a.w) + b.z) + b.w) * 0.25f);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const int c = lane + 32 * k, cy = c / B, cx = c % B;
+            const float *p = src + (size_t)(2 * cy) * g.W + 2 * cx;
+            float v;
+            if (LD == 2) {
+                const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+                const float2 b = __ldg(reinterpret_cast<const float2 *>(p + g.W));
+                v = (((a.x + a.y) + b.x) + b.y) * 0.25f;
+            } else {
+                v = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + g.W)) + __ldg(p + g.W + 1)) * 0.25f;
+            }
+            cw[c] = v;
+        }
+    }
+    __syncwarp();
+    // src_t(py, px) = sy B + sx with (sy, sx) from iso_src: affine in (py, px)
+    constexpr int N = B - 1;
+    const bool swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
+    const int sgy = fy ? -1 : 1, sgx = fx ? -1 : 1;
+    const int c0 = (fy ? N * B : 0) + (fx ? N : 0);
+    const int ky = swap ? sgx : sgy * B, kx = swap ? sgy * B : sgx;
+#pragma unroll
+    for (int k = 0; k < NC / PV; ++k) {
+        const int p0 = PV * (lane + 32 * k), py = p0 / B, px = p0 % B;
+        const int s0 = c0 + ky * py + kx * px;
+        float v[PV];
+#pragma unroll
+        for (int i = 0; i < PV; ++i) v[i] = fmaf(sr, cw[s0 + i * kx], orr);
+        float *q = dst + (size_t)py * g.W + px;
+        if constexpr (VS && PV == 2) {
+            *reinterpret_cast<float2 *>(q) = make_float2(v[0], v[1]);
+        } else if constexpr (VS && PV == 4) {
+            *reinterpret_cast<float4 *>(q) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < PV; ++i) q[i] = v[i];
+        }
+    }
+}
+
+template <int B, int LD>
+void decode_step_vs(bool vs, unsigned blocks, const Geo &g, const fic_codes &c, const float *x, float *y,
+                    cudaStream_t st) {
+    if (vs)
+        k_decode_step<B, LD, true><<<blocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+    else
+        k_decode_step<B, LD, false><<<blocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+}
+
 template <int B>
-__global__ void k_decode_step(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
-                              const double *__restrict__ s, const double *__restrict__ o,
-                              const float *__restrict__ x, float *__restrict__ y) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= g.H * g.W) return;
-    const int py = idx / g.W, px = idx - py * g.W;
-    const int r = (py / B) * g.nRx + (px / B);
-    const int d = dom[r], t = iso[r];
-    int sy, sx;
-    iso_src(B, t, py % B, px % B, sy, sx);
-    const int qy = (d / g.nDx) * g.sigma + 2 * sy, qx = (d % g.nDx) * g.sigma + 2 * sx;
-    const float *p = x + (size_t)qy * g.W + qx;
-    const float v = (((p[0] + p[1]) + p[g.W]) + p[g.W + 1]) * 0.25f;
-    y[idx] = fmaf((float)s[r], v, (float)o[r]);
+void decode_step_b(int ld, bool vs, unsigned blocks, const Geo &g, const fic_codes &c, const float *x, float *y,
+                   cudaStream_t st) {
+    if (ld == 4)
+        decode_step_vs<B, 4>(vs, blocks, g, c, x, y, st);
+    else if (ld == 2)
+        decode_step_vs<B, 2>(vs, blocks, g, c, x, y, st);
+    else
+        decode_step_vs<B, 1>(vs, blocks, g, c, x, y, st);
 }
 
 cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,
                                cudaStream_t st) {
-    const int n = g.H * g.W;
+    const unsigned blocks = (unsigned)((g.R + kDecodeWarps - 1) / kDecodeWarps);
+    // W is a multiple of B, so every row starts at a multiple of 8 floats: domain columns that are
+    // multiples of 4 (2) and a 16-byte (8-byte) aligned base keep every source vector aligned, and
+    // range blocks start at multiples of B floats, so an output aligned to the store width keeps
+    // every store aligned
+    const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
+    const int ld = (g.sigma % 4 == 0 && xa % 16 == 0) ? 4 : (g.sigma % 2 == 0 && xa % 8 == 0) ? 2 : 1;
+    const bool vs = ya % (g.B == 16 ? 16 : 8) == 0;
     if (g.B == 16)
-        k_decode_step<16><<<(n + 255) / 256, 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+        decode_step_b<16>(ld, vs, blocks, g, c, x, y, st);
     else
-        k_decode_step<8><<<(n + 255) / 256, 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+        decode_step_b<8>(ld, vs, blocks, g, c, x, y, st);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -67,6 +162,10 @@ __global__ void k_decode_step_scaled(Geo g, int z, const int32_t *__restrict__ d
     const int py = (int)(idx / Wz), px = (int)(idx - (long long)py * Wz);
     const int r = (py / Bz) * g.nRx + px / Bz;
     const int d = dom[r], t = iso[r];
+    if (!valid_code(g, d, t)) {  // an invalid code: NaN, no read
+        y[idx] = __int_as_float(0x7fc00000);
+        return;
+    }
     int sy, sx;
     iso_src(Bz, t, py % Bz, px % Bz, sy, sx);
     const int qy = (d / g.nDx) * g.sigma * z + 2 * sy, qx = (d % g.nDx) * g.sigma * z + 2 * sx;
@@ -89,7 +188,7 @@ cudaError_t launch_decode_step_scaled(const fic_codes &c, const Geo &g, int z, c
 // pile onto one domain); off = exclusive scan; list sorted per segment.
 __global__ void k_dom_count(Geo g, const int32_t *__restrict__ dom, const double *__restrict__ s, int32_t *cnt) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < g.R && s[r] != 0.0) atomicAdd(&cnt[dom[r]], 1);
+    if (r < g.R && s[r] != 0.0 && valid_code(g, dom[r], 0)) atomicAdd(&cnt[dom[r]], 1);
 }
 
 // Single-block exclusive scan of cnt[0..n) into off[0..n], chunk by chunk.
@@ -125,7 +224,7 @@ __global__ void k_scan_single(const int32_t *__restrict__ cnt, int n, int32_t *_
 __global__ void k_dom_fill(Geo g, const int32_t *__restrict__ dom, const double *__restrict__ s, int32_t *cursor,
                            int32_t *__restrict__ list) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < g.R && s[r] != 0.0) list[atomicAdd(&cursor[dom[r]], 1)] = r;
+    if (r < g.R && s[r] != 0.0 && valid_code(g, dom[r], 0)) list[atomicAdd(&cursor[dom[r]], 1)] = r;
 }
 
 // Insertion-sort each domain's segment so the gather order is fixed.
@@ -166,12 +265,14 @@ __global__ void k_adjoint_gather(Geo g, const int32_t *__restrict__ iso, const d
             const int d = jy * g.nDx + jx;
             for (int k = off[d]; k < off[d + 1]; ++k) {
                 const int r = list[k];
-                const int t = iso[r];
+                const int t = iso[r] & 7;  // listed ranges have a valid domain; a bad isometry
+                                           // makes the range's own gradients NaN (k_adjoint_grads)
                 // range pixel p with src_t(p) = (cy, cx): p = src_{t^-1}(cy, cx)
                 const int tinv = (t == 1) ? 3 : (t == 3 ? 1 : t);
                 int py, px;
                 iso_src(B, tinv, cy, cx, py, px);
-                const int ry = (r / g.nRx) * B, rx = (r % g.nRx) * B;
+                const int rq = fdiv(r, g.fRx);
+                const int ry = rq * B, rx = (r - rq * g.nRx) * B;
                 acc = fmaf((float)s[r] * 0.25f, lam[(size_t)(ry + py) * g.W + rx + px], acc);
             }
         }
@@ -190,8 +291,13 @@ __global__ void k_adjoint_grads(Geo g, const int32_t *__restrict__ dom, const in
     const int lane = threadIdx.x & 31;
     if (r >= g.R) return;
     const int d = dom[r], t = iso[r];
-    const int ry = (r / g.nRx) * B, rx = (r % g.nRx) * B;
-    const int dy = (d / g.nDx) * g.sigma, dx = (d % g.nDx) * g.sigma;
+    if (!valid_code(g, d, t)) {  // an invalid code: NaN gradients, no read
+        if (lane == 0) gs[r] = go[r] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    const int rq = fdiv(r, g.fRx), dq = fdiv(d, g.fDx);
+    const int ry = rq * B, rx = (r - rq * g.nRx) * B;
+    const int dy = dq * g.sigma, dx = (d - dq * g.nDx) * g.sigma;
     double a_s = 0.0, a_o = 0.0;
 #pragma unroll
     for (int h = 0; h < B * B / 32; ++h) {

@@ -8,9 +8,9 @@
 // scratch in a fixed array in the library's device memory instead: every GPU that loads the
 // library holds the array (kStaticDecodeMaxPixels floats, 4 MiB) until the process exits.
 //
-// The array's device address is looked up once per device (cudaGetSymbolAddress, with that
-// device current) on the first call made with that device current; host code must not use the
-// array's name directly, which on the host only names a stand-in, not device memory. Every call
+// The array's device address is looked up (cudaGetSymbolAddress, with the device current) on the
+// first call made with a device current, and again after that device's context was re-created;
+// host code must not use the array's name directly, which on the host only names a stand-in, not device memory. Every call
 // shares the one array and leaves its last contents behind: nothing here reads scratch that the
 // same call has not written first, and calls whose GPU work overlaps (other streams, other host
 // threads) race on it.
@@ -21,8 +21,6 @@
 
 namespace fic {
 
-void set_error(const char *msg);
-
 constexpr size_t kStaticDecodeMaxPixels = (size_t)FIC_DECODE_STATIC_MAX_PIXELS;
 
 static __device__ __align__(256) float g_decode_scratch[kStaticDecodeMaxPixels];
@@ -30,22 +28,33 @@ static __device__ __align__(256) float g_decode_scratch[kStaticDecodeMaxPixels];
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-float *g_scratch_ptr[kMaxDevices] = {};
+struct ScratchEntry {
+    void *ctx = nullptr;  // the context (CUcontext) the address belongs to
+    float *ptr = nullptr;
+};
+ScratchEntry g_scratch[kMaxDevices];
 
-// Device address of g_decode_scratch on the current device (looked up once per device).
+// Device address of g_decode_scratch in the current device's current context, looked up once per
+// (device, context): the module, and with it the array, is loaded again when a context is
+// re-created, so an address cached for an earlier context is not reused.
 cudaError_t scratch_for_current_device(float **ptr) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    void *ctx = nullptr;
+    if (!current_context(&ctx)) return cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchEntry &ent = g_scratch[dev];
+    if (!ctx || !ent.ptr || ent.ctx != ctx) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_decode_scratch);
+        e = cudaGetSymbolAddress(&p, g_decode_scratch);  // makes the primary context current if none is
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<float *>(p);
+        if (!current_context(&ctx) || !ctx) return cudaErrorDeviceUninitialized;
+        ent.ptr = static_cast<float *>(p);
+        ent.ctx = ctx;
     }
-    *ptr = g_scratch_ptr[dev];
+    *ptr = ent.ptr;
     return cudaSuccess;
 }
 }  // namespace
@@ -55,8 +64,10 @@ cudaError_t scratch_for_current_device(float **ptr) {
 extern "C" fic_status fic_decode_static(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
                                         int32_t iters, const float *x0, float *out, void *stream) {
     using namespace fic;
-    // geometry and parameters are validated by the same checks as fic_decode's workspace query
-    if (fic_decode_workspace_size(gm, p, iters < 0 ? 0 : iters, 1) == 0) return FIC_ERR_INVALID_ARG;
+    // geometry and parameters pass the same checks, and give the same grids, as in fic_decode
+    Geo g{};
+    const fic_status gs = make_geometry(gm, p, &g);
+    if (gs != FIC_OK) return gs;
     if (!codes || !codes->dom || !codes->iso || !codes->s || !codes->o || !out || iters < 0) {
         set_error("fic_decode_static: null code or output pointer, or negative iters");
         return FIC_ERR_INVALID_ARG;
@@ -71,22 +82,6 @@ extern "C" fic_status fic_decode_static(const fic_codes *codes, const fic_geom *
         set_error(msg);
         return FIC_ERR_INVALID_ARG;
     }
-    Geo g;
-    g.H = gm->H;
-    g.W = gm->W;
-    g.pitch = gm->pitch;
-    g.B = p->block;
-    g.n = g.B * g.B;
-    g.sigma = p->domain_stride;
-    g.nRy = g.H / g.B;
-    g.nRx = g.W / g.B;
-    g.R = g.nRy * g.nRx;
-    g.nDy = (g.H - 2 * g.B) / g.sigma + 1;
-    g.nDx = (g.W - 2 * g.B) / g.sigma + 1;
-    g.Dn = g.nDy * g.nDx;
-    g.K = p->num_classes;
-    g.w = p->half_width < 0 ? p->num_classes / 3 : p->half_width;
-
     float *tmp = nullptr;
     cudaError_t e = scratch_for_current_device(&tmp);
     if (e != cudaSuccess) {

@@ -14,6 +14,25 @@ constexpr int kMaxClasses = 255;
 // Kernels launched by the current fic_* call on this thread (reset at each entry point).
 extern thread_local int g_launches;
 
+// Division by an invariant divisor 1 <= d < 2^31 of dividends 0 <= x < 2^31 with one multiply-high,
+// one add and one shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, q = (mulhi(x, m) + x) >> s.
+// The kernels index ranges and domains by row-major ids, and a division by a value known only at
+// run time costs tens of instructions.
+struct FastDiv {
+    uint32_t d = 1, m = 1, s = 0;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    while ((1u << f.s) < d) ++f.s;
+    f.m = (uint32_t)((((unsigned long long)1 << 32) * (((unsigned long long)1 << f.s) - d)) / d + 1);
+    return f;
+}
+__device__ __forceinline__ int fdiv(int x, const FastDiv &f) {
+    return (int)((__umulhi((uint32_t)x, f.m) + (uint32_t)x) >> f.s);
+}
+
 // Derived geometry of one image (Section 1 range partition, Section 2 domain grid).
 struct Geo {
     int H, W, pitch;
@@ -22,6 +41,9 @@ struct Geo {
     int nDy, nDx, Dn;    // domain grid
     int K, w;            // classes and pool half-width (Section 3.1 Eq. 2-3)
     int literal;         // 1: Eq. 3 window on FD values (FIC_FLAG_LITERAL_WINDOW)
+    FastDiv fRx, fDx;    // division by nRx and by nDx
+    int group_chunks;    // tensor engine: chunk cap of a domain group
+    int stages;          // tensor engine: B-operand ring stages (0: the kernel's default)
 };
 
 // Correctly rounded log2(n) for n = 0..512 (entry 0 unused; box counts of 16x16 blocks reach
@@ -43,6 +65,13 @@ __host__ __device__ __forceinline__ void iso_src(int B, int t, int y, int x, int
     const int u = swap ? x : y, v = swap ? y : x;
     sy = fy ? N - u : u;
     sx = fx ? N - v : v;
+}
+
+// Whether a code's domain and isometry can be used to index the image: decoding kernels skip
+// invalid codes (such as those an encode writes when its matcher gave up) instead of reading
+// outside the image.
+__host__ __device__ __forceinline__ bool valid_code(const Geo &g, int d, int t) {
+    return (unsigned)d < (unsigned)g.Dn && (unsigned)t < 8u;
 }
 
 // Exact correlations of one domain block with a range under all 8 isometries: X_t = sum_q S[q]
@@ -340,8 +369,23 @@ struct TcBatch {
     uint32_t *chunk_max;   // [max_chunks][tm rows][halves][2] best key, runner-up score per chunk
     int32_t *gcounters;    // [8]: [1] work items, [2] device error, [3] chunks, [4] chunks per group,
                            // [5] next work item to hand out (zero before the matcher)
+    int32_t *lib_error = nullptr;  // the library's per-device error word (fic_check), or nullptr
+    unsigned long long stall_ns = 0;  // testing hook (fic_debug_stall_matcher): > 0 makes every
+                                      // matcher CTA wait this long on a barrier nothing completes
     int R_pad, Dn_aux, n_mtiles, max_items, max_chunks, ng_max, cpi_cap;
+    int stages = 0;        // matcher B-operand ring stages (0: the kernel's default)
 };
+
+// Marks the code of range r invalid (dom = iso = -1, s = o = sse = NaN): written when the matching
+// kernel gave up, so that stale or uninitialised codes are never mistaken for results.
+__device__ __forceinline__ void poison_code(const fic_codes &out, int r) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    out.dom[r] = -1;
+    out.iso[r] = -1;
+    out.s[r] = nan;
+    out.o[r] = nan;
+    out.sse[r] = nan;
+}
 
 constexpr int kSortChunk = 1024;  // elements per counting-sort block
 constexpr int kTileM = 128;       // rows of one MMA (ranges per B = 8 range tile)
@@ -409,5 +453,13 @@ cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encod
 cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,
                                cudaStream_t st);
 cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st);
+// Validates the geometry and parameters of one image and derives its grids (the checks every entry
+// point applies); sets the thread's error message on failure.
+fic_status make_geometry(const fic_geom *gm, const fic_params *p, Geo *g);
+// Sets the message fic_last_error() returns on this thread.
+void set_error(const char *msg);
+// The calling thread's current CUDA context (a CUcontext, nullptr if none); false if the driver
+// cannot be asked.
+bool current_context(void **ctx);
 
 }  // namespace fic

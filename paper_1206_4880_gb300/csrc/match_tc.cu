@@ -51,7 +51,7 @@ bool tensor_engine_available(int device) {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStagesDefault = 4;  // B-operand ring stages (3 or 4: fic_params.pipeline_stages)
 constexpr int kTileN = 8 * kTileDom;     // 256 accumulator columns
 constexpr int kABytes = kTileM * 128;    // 128 rows x 64 fp16
 constexpr int kBBytes = kTileN * 128;    // 256 rows x 64 fp16
@@ -64,19 +64,23 @@ constexpr int kTmemCols = 2 * kTileN;    // two accumulators
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 
+template <int S>
 struct TcShared {
     uint8_t A[2][kABytes];
-    uint8_t B[kStages][kBBytes];
+    uint8_t B[S][kBBytes];
     uint8_t A1[2][kA1Bytes];
-    uint8_t B1[kStages][kB1Bytes];
+    uint8_t B1[S][kB1Bytes];
     float4 aux[2][kChunkDom / 2];  // (Q / 256, 128 / Q) of two domains per entry: current, next chunk
-    unsigned long long full_a[2], empty_a[2], full_b[kStages], empty_b[kStages], tfull[2],
-        tempty[2], aux_ready[2], drain, item_full[kItemRing], item_empty[kItemRing];
+    unsigned long long full_a[2], empty_a[2], full_b[S], empty_b[S], tfull[2],
+        tempty[2], aux_ready[2], drain, item_full[kItemRing], item_empty[kItemRing],
+        never;  // completed by nothing: the forced wait of the testing hook (fic_debug_stall_matcher)
     int item_id[kItemRing];  // work items fetched by the producer, in this CTA's order (-1: none left)
     uint32_t tmem_base;
     int abort_flag;
 };
-constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
+template <int S>
+constexpr size_t tc_smem() { return sizeof(TcShared<S>) + 1024; }
+static_assert(sizeof(TcShared<4>) + 1024 <= 232448, "shared memory per CTA");
 
 // Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
 // range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
@@ -494,6 +498,7 @@ __global__ void k_work_list(int n_mtiles, int target, int cpi_cap, int td, int n
 }
 
 // ---- the matching kernel ----------------------------------------------------------------------
+template <int S>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
@@ -502,10 +507,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
                const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
                unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *next_item,
-               int32_t *err) {
+               int32_t *err, int32_t *lib_err, unsigned long long stall_ns) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
-    TcShared &sh = *reinterpret_cast<TcShared *>(smem_raw + pad);
+    TcShared<S> &sh = *reinterpret_cast<TcShared<S> *>(smem_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_items = counters_in[1];
     volatile int *abort_flag = &sh.abort_flag;
@@ -518,7 +523,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&sh.tempty[s], kEpiWarps);
             mbar_init(&sh.aux_ready[s], 32 * kEpiWarps);
         }
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&sh.full_b[s], 1);
             mbar_init(&sh.empty_b[s], 1);
         }
@@ -527,6 +532,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&sh.item_empty[s], 1 + kEpiWarps);
         }
         mbar_init(&sh.drain, 1);
+        mbar_init(&sh.never, 1);
         sh.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -547,6 +553,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
             uint32_t gt = 0;
             bool ok = true;
+            // testing hook: a wait that nothing completes, before any copy or MMA is issued, so the
+            // bounded-wait error path runs with nothing in flight
+            if (stall_ns && !mbar_wait_for(&sh.never, 0, abort_flag, stall_ns)) ok = false;
             for (uint32_t li = 0; ok; ++li) {
                 // the next item of the whole grid, handed to the MMA and epilogue warps
                 const int s = li % kItemRing;
@@ -566,8 +575,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tma_load_2d(sh.A1[ab], &tmA1, &sh.full_a[ab], 0, w.x * kTileM);
                 const int nt = (w.z - w.y + kTileDom - 1) / kTileDom;
                 for (int k = 0; k < nt; ++k, ++gt) {
-                    const int s = gt % kStages;
-                    ok = mbar_wait(&sh.empty_b[s], ((gt / kStages) & 1) ^ 1, abort_flag);
+                    const int s = gt % S;
+                    ok = mbar_wait(&sh.empty_b[s], ((gt / S) & 1) ^ 1, abort_flag);
                     if (!ok) break;
                     mbar_expect_tx(&sh.full_b[s], kBBytes + kB1Bytes);
                     tma_load_2d(sh.B[s], &tmB, &sh.full_b[s], 0, 8 * (w.y + k * kTileDom));
@@ -575,8 +584,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
             if (!ok) {
-                atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
-                *abort_flag = 1;
+                report_timeout(err, lib_err, abort_flag);
             }
         }
     } else if (warp == 1) {
@@ -599,10 +607,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const uint32_t a0 = su32(sh.A[ab]);
                 const int nt = (w.z - w.y + kTileDom - 1) / kTileDom;
                 for (int k = 0; k < nt; ++k, ++gt) {
-                    const int s = gt % kStages, acc = gt & 1;
+                    const int s = gt % S, acc = gt & 1;
                     ok = mbar_wait(&sh.tempty[acc], ((gt >> 1) & 1) ^ 1, abort_flag);
                     if (!ok) break;
-                    ok = mbar_wait(&sh.full_b[s], (gt / kStages) & 1, abort_flag);
+                    ok = mbar_wait(&sh.full_b[s], (gt / S) & 1, abort_flag);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t b0 = su32(sh.B[s]);
@@ -622,8 +630,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             umma_commit(&sh.drain);
             if (!mbar_wait(&sh.drain, 0, abort_flag) && !*abort_flag) ok = false;
             if (!ok) {
-                atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
-                *abort_flag = 1;
+                report_timeout(err, lib_err, abort_flag);
             }
         }
     } else {
@@ -703,8 +710,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
         if (!ok) {
-            atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
-            *abort_flag = 1;
+            report_timeout(err, lib_err, abort_flag);
         }
     }
 
@@ -927,7 +933,11 @@ __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t 
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;  // sorted position in this image
     const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
     const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
-    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+    if (gcounters[2] != 0) {
+        // the matching kernel gave up: its keys are not trusted, so every code is marked invalid
+        if (hl == 0 && i < g.R) poison_code(out, i);
+        return;
+    }
     if (i < g.R)
         reeval_rank(g, img, domS, dsum, dsumsq, rsumsq, dom_order, bin_off, nbuckets, rng_info, rng_off, dom_off,
                     tile_items, cand, i, hl, hmask, stage[slot], res[slot]);
@@ -1023,6 +1033,22 @@ cudaError_t launch_work_list(const TcBatch &tb, int target_items, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t launch_tc_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const CUtensorMap &tmA1,
+                              const CUtensorMap &tmB1, const TcBatch &tb, int grid, cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(k_match_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<S>());
+    });
+    if (attr_err) return attr_err;
+    k_match_tc<S><<<grid, kTcThreads, tc_smem<S>(), st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.work_slot, tb.tile_items,
+                                                         tb.gcounters, tb.tile_win, tb.rng_info, tb.dom_aux, tb.cand,
+                                                         tb.chunk_max, tb.gcounters + 5, tb.gcounters + 2,
+                                                         tb.lib_error, tb.stall_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
     CUtensorMap tmA, tmB, tmA1, tmB1;
     cudaError_t e;
@@ -1030,18 +1056,13 @@ cudaError_t launch_match_tc(const TcBatch &tb, int num_sms, cudaStream_t st) {
     if ((e = make_map_f16(&tmB, tb.B_mat, (unsigned long long)tb.Dn_aux * 8, 64, kTileN, 64))) return e;
     if ((e = make_map_f16(&tmA1, tb.A1_mat, (unsigned long long)tb.R_pad, 16, kTileM, 16))) return e;
     if ((e = make_map_f16(&tmB1, tb.B1_mat, (unsigned long long)tb.Dn_aux * 8, 16, kTileN, 16))) return e;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-    });
-    if (attr_err) return attr_err;
     const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
     if (grid <= 0) return cudaSuccess;
-    k_match_tc<<<grid, kTcThreads, kTcSmem, st>>>(tmA, tmB, tmA1, tmB1, tb.work, tb.work_slot, tb.tile_items,
-                                                   tb.gcounters,
-                                                   tb.tile_win, tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
-                                                   tb.gcounters + 5, tb.gcounters + 2);
+    if (tb.stages == 3)
+        e = launch_tc_variant<3>(tmA, tmB, tmA1, tmB1, tb, grid, st);
+    else
+        e = launch_tc_variant<4>(tmA, tmB, tmA1, tmB1, tb, grid, st);
+    if (e) return e;
     ++g_launches;
     return cudaGetLastError();
 }

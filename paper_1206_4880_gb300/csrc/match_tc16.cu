@@ -43,7 +43,7 @@ namespace {
 constexpr int kTm16 = 2 * kTileM;                   // 256 ranges per range tile
 constexpr int kDom16 = 16;                          // domains per accumulator tile
 constexpr int kN16 = 8 * kDom16;                    // 128 accumulator columns
-constexpr int kStages16 = 5;
+constexpr int kStages16Default = 5;  // B-operand ring stages (4 or 5: fic_params.pipeline_stages)
 constexpr int kQA = kTileM * 128;                   // one K-quarter of one MMA row tile: 16 KB
 constexpr int kQB = kN16 * 128;                     // one K-quarter of one domain tile: 16 KB
 constexpr int kEpi16 = 8;
@@ -51,18 +51,21 @@ constexpr int kTc16Threads = 32 * (2 + kEpi16);
 constexpr int kTmem16 = 4 * kN16;                   // 512 columns
 constexpr uint32_t kIdesc16 = (1u << 4) | ((uint32_t)(kN16 >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 
+template <int S>
 struct Tc16Shared {
     uint8_t A[2][4][kQA];          // [MMA row tile][K-quarter]
-    uint8_t B[kStages16][kQB];     // ring of K-quarters
+    uint8_t B[S][kQB];             // ring of K-quarters
     float4 aux[2][kChunkDom];      // per-domain constants of the current and next chunk
-    unsigned long long full_a, empty_a, full_b[kStages16], empty_b[kStages16], tfull[2], tempty[2], aux_ready[2],
-        drain, item_full[kItemRing], item_empty[kItemRing];
+    unsigned long long full_a, empty_a, full_b[S], empty_b[S], tfull[2], tempty[2], aux_ready[2],
+        drain, item_full[kItemRing], item_empty[kItemRing],
+        never;  // completed by nothing: the forced wait of the testing hook (fic_debug_stall_matcher)
     int item_id[kItemRing];  // work items fetched by the producer, in this CTA's order (-1: none left)
     uint32_t tmem_base;
     int abort_flag;
 };
-constexpr size_t kTc16Smem = sizeof(Tc16Shared) + 1024;
-static_assert(kTc16Smem <= 232448, "shared memory per CTA");
+template <int S>
+constexpr size_t tc16_smem() { return sizeof(Tc16Shared<S>) + 1024; }
+static_assert(sizeof(Tc16Shared<5>) + 1024 <= 232448, "shared memory per CTA");
 
 // Scores of one accumulator tile for this thread's range row: 16 domains x 8 isometries. The 16
 // domains (positions jh .. jh + 15, jh a multiple of 16) form one group, whose largest score goes
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(256) k_pack_domains16(Geo g, const uint16_t *_
 }
 
 // ---- the matching kernel ----------------------------------------------------------------------
+template <int S>
 __global__ void __launch_bounds__(kTc16Threads, 1)
     k_match_tc16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const int4 *__restrict__ work, const int32_t *__restrict__ work_slot,
@@ -209,10 +213,10 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                  const int32_t *__restrict__ counters_in, const int4 *__restrict__ tile_win,
                  const int4 *__restrict__ rng_info, const float4 *__restrict__ dom_aux,
                  unsigned long long *__restrict__ cand, uint32_t *__restrict__ chunk_max, int32_t *next_item,
-                 int32_t *err) {
+                 int32_t *err, int32_t *lib_err, unsigned long long stall_ns) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
-    Tc16Shared &sh = *reinterpret_cast<Tc16Shared *>(smem_raw + pad);
+    Tc16Shared<S> &sh = *reinterpret_cast<Tc16Shared<S> *>(smem_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_items = counters_in[1];
     volatile int *abort_flag = &sh.abort_flag;
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
             mbar_init(&sh.tempty[s], kEpi16);
             mbar_init(&sh.aux_ready[s], 32 * kEpi16);
         }
-        for (int s = 0; s < kStages16; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&sh.full_b[s], 1);
             mbar_init(&sh.empty_b[s], 1);
         }
@@ -234,6 +238,7 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
             mbar_init(&sh.item_empty[s], 1 + kEpi16);
         }
         mbar_init(&sh.drain, 1);
+        mbar_init(&sh.never, 1);
         sh.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -254,6 +259,9 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
             uint32_t gs = 0;
             bool ok = true;
+            // testing hook: a wait that nothing completes, before any copy or MMA is issued, so the
+            // bounded-wait error path runs with nothing in flight
+            if (stall_ns && !mbar_wait_for(&sh.never, 0, abort_flag, stall_ns)) ok = false;
             for (uint32_t li = 0; ok; ++li) {
                 // the next item of the whole grid, handed to the MMA and epilogue warps
                 const int s = li % kItemRing;
@@ -276,8 +284,8 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                 const int nt = (w.z - w.y + kDom16 - 1) / kDom16;
                 for (int k = 0; k < nt && ok; ++k) {
                     for (int q = 0; q < 4; ++q, ++gs) {
-                        const int s = gs % kStages16;
-                        ok = mbar_wait(&sh.empty_b[s], ((gs / kStages16) & 1) ^ 1, abort_flag);
+                        const int s = gs % S;
+                        ok = mbar_wait(&sh.empty_b[s], ((gs / S) & 1) ^ 1, abort_flag);
                         if (!ok) break;
                         mbar_expect_tx(&sh.full_b[s], kQB);
                         tma_load_2d(sh.B[s], &tmB, &sh.full_b[s], 64 * q, 8 * (w.y + k * kDom16));
@@ -285,8 +293,7 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                 }
             }
             if (!ok) {
-                atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
-                *abort_flag = 1;
+                report_timeout(err, lib_err, abort_flag);
             }
         }
     } else if (warp == 1) {
@@ -312,8 +319,8 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
                     if (!ok) break;
                     tc_fence_after();
                     for (int q = 0; q < 4; ++q, ++gs) {
-                        const int s = gs % kStages16;
-                        ok = mbar_wait(&sh.full_b[s], (gs / kStages16) & 1, abort_flag);
+                        const int s = gs % S;
+                        ok = mbar_wait(&sh.full_b[s], (gs / S) & 1, abort_flag);
                         if (!ok) break;
                         tc_fence_after();
                         const uint32_t b0 = su32(sh.B[s]);
@@ -337,8 +344,7 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
             umma_commit(&sh.drain);
             if (!mbar_wait(&sh.drain, 0, abort_flag) && !*abort_flag) ok = false;
             if (!ok) {
-                atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
-                *abort_flag = 1;
+                report_timeout(err, lib_err, abort_flag);
             }
         }
     } else {
@@ -413,8 +419,7 @@ __global__ void __launch_bounds__(kTc16Threads, 1)
             }
         }
         if (!ok) {
-            atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
-            *abort_flag = 1;
+            report_timeout(err, lib_err, abort_flag);
         }
     }
 
@@ -622,7 +627,11 @@ __global__ void __launch_bounds__(kReeval16Threads) k_reeval16(Geo g, const uint
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
     const int hl = threadIdx.x & 15, slot = threadIdx.x >> 4;
     const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
-    if (gcounters[2] != 0) return;  // the matching kernel gave up: its keys are not trusted
+    if (gcounters[2] != 0) {
+        // the matching kernel gave up: its keys are not trusted, so every code is marked invalid
+        if (hl == 0 && i < g.R) poison_code(out, i);
+        return;
+    }
     if (i < g.R)
         reeval16_rank(g, img, domS, dsum, dsumsq, rsumsq, dom_order, bin_off, nbuckets, rng_info, rng_off, dom_off,
                       tile_items, cand, i, hl, hmask, stage16[slot], res[slot]);
@@ -651,23 +660,35 @@ cudaError_t launch_pack16(const uint8_t *img, const Geo &g, const EncodeBufs &b,
     return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t launch_tc16_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const TcBatch &tb, int grid,
+                                cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err =
+            cudaFuncSetAttribute(k_match_tc16<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc16_smem<S>());
+    });
+    if (attr_err) return attr_err;
+    k_match_tc16<S><<<grid, kTc16Threads, tc16_smem<S>(), st>>>(tmA, tmB, tb.work, tb.work_slot, tb.tile_items,
+                                                               tb.gcounters, tb.tile_win, tb.rng_info, tb.dom_aux,
+                                                               tb.cand, tb.chunk_max, tb.gcounters + 5,
+                                                               tb.gcounters + 2, tb.lib_error, tb.stall_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_match_tc16(const TcBatch &tb, int num_sms, cudaStream_t st) {
     CUtensorMap tmA, tmB;
     cudaError_t e;
     if ((e = make_map_f16(&tmA, tb.A_mat, (unsigned long long)tb.R_pad, 256, kTileM, 64))) return e;
     if ((e = make_map_f16(&tmB, tb.B_mat, (unsigned long long)tb.Dn_aux * 8, 256, kN16, 64))) return e;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(k_match_tc16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc16Smem);
-    });
-    if (attr_err) return attr_err;
     const int grid = num_sms < tb.max_items ? num_sms : tb.max_items;
     if (grid <= 0) return cudaSuccess;
-    k_match_tc16<<<grid, kTc16Threads, kTc16Smem, st>>>(tmA, tmB, tb.work, tb.work_slot, tb.tile_items, tb.gcounters,
-                                                         tb.tile_win,
-                                                         tb.rng_info, tb.dom_aux, tb.cand, tb.chunk_max,
-                                                         tb.gcounters + 5, tb.gcounters + 2);
+    if (tb.stages == 4)
+        e = launch_tc16_variant<4>(tmA, tmB, tb, grid, st);
+    else
+        e = launch_tc16_variant<5>(tmA, tmB, tb, grid, st);
+    if (e) return e;
     ++g_launches;
     return cudaGetLastError();
 }

@@ -43,17 +43,30 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *b, uint32_t parity
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of parity `parity`; false on timeout or when another role gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, volatile int *abort_flag) {
+// Wait of at most limit_ns for the phase of parity `parity`; false on timeout or when another
+// role gave up.
+__device__ __forceinline__ bool mbar_wait_for(unsigned long long *b, uint32_t parity, volatile int *abort_flag,
+                                              unsigned long long limit_ns) {
     if (mbar_test(b, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
         if (mbar_test(b, parity)) return true;
         if ((i & 63) == 0) {
             if (*abort_flag) return false;
-            if (gtimer() - t0 > kTimeoutNs) return false;
+            if (gtimer() - t0 > limit_ns) return false;
         }
     }
+}
+// Bounded wait (kTimeoutNs) for the phase of parity `parity`.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, volatile int *abort_flag) {
+    return mbar_wait_for(b, parity, abort_flag, kTimeoutNs);
+}
+// A role that gave up: records the timeout in the encode's error word and in the library's
+// per-device word (read by fic_check), and tells the CTA's other roles to stop.
+__device__ __forceinline__ void report_timeout(int32_t *err, int32_t *lib_err, volatile int *abort_flag) {
+    atomicExch(err, (int)FIC_ERR_DEVICE_TIMEOUT);
+    if (lib_err) atomicExch(lib_err, (int)FIC_ERR_DEVICE_TIMEOUT);
+    *abort_flag = 1;
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, unsigned long long *bar,
                                             int x, int y) {

@@ -29,7 +29,7 @@ class Geom(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("block", c_i32), ("domain_stride", c_i32), ("num_classes", c_i32),
                 ("half_width", c_i32), ("s_max", c_dbl), ("engine", c_i32), ("flags", c_i32),
-                ("items_per_sm", c_i32)]
+                ("items_per_sm", c_i32), ("group_chunks", c_i32), ("pipeline_stages", c_i32)]
 
 
 class BlockStats(ctypes.Structure):
@@ -58,6 +58,7 @@ SIGNATURES = {
     "fic_classify": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_build_pools": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_encode": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
+    "fic_encode_fallback_ranges": (c_i32, [c_vp, c_vp, c_vp, c_size, c_vp, c_i32, c_vp, c_vp]),
     "fic_encode_batched_workspace_size": (c_size, [c_vp, c_i32, c_vp]),
     "fic_encode_batched": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "fic_decode_workspace_size": (c_size, [c_vp, c_vp, c_i32, c_i32]),
@@ -71,6 +72,8 @@ SIGNATURES = {
     "fic_quantize": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "fic_decode_scaled_workspace_size": (c_size, [c_vp, c_vp, c_i32]),
     "fic_decode_scaled": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_size, c_vp]),
+    "fic_check": (c_i32, [c_vp]),
+    "fic_debug_stall_matcher": (c_i32, [c_i64]),
     "fic_engine_available": (c_i32, [c_i32]),
     "fic_last_error": (ctypes.c_char_p, []),
     "fic_version": (c_i32, []),
@@ -124,11 +127,13 @@ class EncodeParams:
     s_max: float = 1.0
     items_per_sm: int = 0
     literal: bool = False   # Eq. 3's window on FD values instead of the class window
+    group_chunks: int = 0   # tensor engine: chunk cap of a domain group (0: library default)
+    pipeline_stages: int = 0  # tensor engine: domain-operand ring stages (0: library default)
 
     def c(self) -> Params:
         return Params(self.block, self.domain_stride, self.num_classes, self.half_width,
                       self.s_max, ENGINES[self.engine], FLAG_LITERAL_WINDOW if self.literal else 0,
-                      self.items_per_sm)
+                      self.items_per_sm, self.group_chunks, self.pipeline_stages)
 
 
 def geom(H: int, W: int, pitch: int | None = None) -> Geom:
@@ -199,6 +204,30 @@ def encode(img: torch.Tensor, p: EncodeParams, out: dict | None = None,
     _check(load().fic_encode(_p(img), ctypes.byref(g), ctypes.byref(pc), ctypes.byref(cs),
                              _p(info), _p(workspace), workspace.numel(), _stream(stream)))
     return out
+
+
+def check(stream=None):
+    """fic_check: wait for `stream` and raise FicError (status FIC_ERR_DEVICE_TIMEOUT) if a bounded
+    device-side wait of an encode on this device gave up since the last check."""
+    _check(load().fic_check(_stream(stream)))
+
+
+def debug_stall_matcher(ns: int):
+    """fic_debug_stall_matcher: testing hook that makes this thread's tensor matchers time out
+    (ns > 0) before they issue any work; 0 turns it off."""
+    _check(load().fic_debug_stall_matcher(int(ns)))
+
+
+def fallback_ranges(H: int, W: int, p: EncodeParams, workspace: torch.Tensor, stream=None) -> torch.Tensor:
+    """fic_encode_fallback_ranges: ids of the ranges the last encode with `workspace` re-searched
+    exactly because the tensor engine's ranking could not certify them (sorted)."""
+    R, _ = counts(H, W, p)
+    ids = torch.empty(R, dtype=torch.int32, device=workspace.device)
+    n = torch.zeros(1, dtype=torch.int32, device=workspace.device)
+    g, pc = geom(H, W), p.c()
+    _check(load().fic_encode_fallback_ranges(ctypes.byref(g), ctypes.byref(pc), _p(workspace),
+                                             workspace.numel(), _p(ids), R, _p(n), _stream(stream)))
+    return torch.sort(ids[:int(n.item())]).values
 
 
 def engine_available(engine: str) -> bool:

@@ -34,6 +34,13 @@ def test_log2_table_is_correctly_rounded():
         assert lib.fic_debug_log2(n) == dbc.log2_cr(n), n
 
 
+def test_debug_stall_hook_validates_on_the_host():
+    lib = fic.load()
+    assert lib.fic_debug_stall_matcher(-1) == fic.FIC_ERR_INVALID_ARG
+    assert lib.fic_debug_stall_matcher(2_000_000_000) == fic.FIC_ERR_INVALID_ARG
+    assert lib.fic_debug_stall_matcher(0) == fic.FIC_OK
+
+
 def _ws_size(H, W, **kw):
     p = fic.EncodeParams(**kw).c()
     g = fic.geom(H, W)
@@ -45,13 +52,20 @@ def test_workspace_size_and_validation():
     assert _ws_size(1024, 1024, domain_stride=4, num_classes=16) > _ws_size(256, 256)
     for kw in ({"domain_stride": 0}, {"num_classes": 0}, {"num_classes": 256},
                {"block": 12}, {"s_max": 0.5}, {"half_width": -2},
-               {"block": 16, "literal": True}):
+               {"block": 16, "literal": True}, {"group_chunks": -1}, {"group_chunks": 1025},
+               {"pipeline_stages": 2}, {"pipeline_stages": 5}, {"block": 16, "pipeline_stages": 3},
+               {"block": 16, "pipeline_stages": 6}):
         assert _ws_size(64, 64, **kw) == 0, kw
     assert _ws_size(12, 64) == 0 and _ws_size(64, 60) == 0 and _ws_size(8, 64) == 0
     # 16x16 ranges: sides multiples of 16 and at least 32
     assert _ws_size(64, 64, block=16) > 0
     assert _ws_size(24, 64, block=16) == 0 and _ws_size(64, 48, block=16) > 0 and _ws_size(16, 64, block=16) == 0
     assert _ws_size(1024, 1024, block=16) > _ws_size(512, 512, block=16)
+    for kw in ({"pipeline_stages": 3}, {"pipeline_stages": 4}, {"block": 16, "pipeline_stages": 4},
+               {"block": 16, "pipeline_stages": 5}, {"group_chunks": 1}, {"group_chunks": 1024}):
+        assert _ws_size(64, 64, **kw) > 0, kw
+    # smaller domain groups need more work-item slots
+    assert _ws_size(4096, 4096, domain_stride=8, group_chunks=4) > _ws_size(4096, 4096, domain_stride=8)
 
 
 def test_encode_rejects_before_any_launch():

@@ -6,6 +6,8 @@ Bars as for 8x8 ranges: moments, box counts, FD bit patterns and classes bit-exa
 (domain, isometry) identical; s and o within 1e-6; sse within 1e-9 relative; decoded iterates
 within 2e-3 of the FP64 oracle; gradients within 1e-4 relative.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -17,6 +19,8 @@ from oracle import pools as opools
 from paper_1206_4880_gb300 import fic, synth
 
 pytestmark = pytest.mark.gpu
+
+NT = os.cpu_count() or 1  # oracle threads: every host core
 
 ENGINES = ["simt", "tensor"]
 
@@ -108,7 +112,7 @@ def test_encode16_parity_small(case, engine):
     info = fic.new_info("cuda")
     codes = fic.encode(_t(img), _params(sigma, K, w, engine), info=info)
     torch.cuda.synchronize()
-    ref = omatch.encode(img, B=16, sigma=sigma, K=K, w=None if w < 0 else w, n_threads=8)
+    ref = omatch.encode(img, B=16, sigma=sigma, K=K, w=None if w < 0 else w, n_threads=NT)
     _compare_codes(codes, ref)
     rep = fic.read_info(info)
     assert rep["matches"] == int(ref["pool_size"].sum()) * 8
@@ -137,7 +141,7 @@ def test_encode16_flat_and_extreme_images(engine):
         for K, sigma in ((4, 2), (1, 4), (255, 8)):
             codes = fic.encode(_t(im), _params(sigma, K, -1, engine))
             torch.cuda.synchronize()
-            ref = omatch.encode(im, B=16, sigma=sigma, K=K, n_threads=8)
+            ref = omatch.encode(im, B=16, sigma=sigma, K=K, n_threads=NT)
             _compare_codes(codes, ref)
 
 
@@ -162,7 +166,7 @@ def test_encode16_batched_equals_oracle(engine):
     torch.cuda.synchronize()
     total = 0
     for im, out in zip(imgs, outs):
-        ref = omatch.encode(im, B=16, sigma=4, K=7, n_threads=8)
+        ref = omatch.encode(im, B=16, sigma=4, K=7, n_threads=NT)
         _compare_codes(out, ref)
         total += int(ref["pool_size"].sum()) * 8
     rep = fic.read_info(info)
@@ -171,13 +175,15 @@ def test_encode16_batched_equals_oracle(engine):
 
 @pytest.mark.parametrize("engine", ENGINES)
 def test_encode16_1024_sampled(engine):
-    """1024x1024, stride 4, K = 16 with 16x16 ranges: classification bit-exact, codes on a seeded
-    sample of ranges."""
+    """1024x1024, stride 4, K = 16 with 16x16 ranges: classification bit-exact, codes on 400
+    seeded ranges plus every range the tensor engine re-searched exactly."""
     _need_tensor(engine)
     img = synth.image_1024()
     p = _params(4, 16, -1, engine)
+    ws = torch.empty(fic.encode_workspace_size(1024, 1024, p), dtype=torch.uint8, device="cuda")
     info = fic.new_info("cuda")
-    codes = fic.encode(_t(img), p, info=info)
+    codes = fic.encode(_t(img), p, workspace=ws, info=info)
+    fb = fic.fallback_ranges(1024, 1024, p, ws).cpu().numpy()
     st = fic.classify(_t(img), p)
     torch.cuda.synchronize()
     cls = omatch.classify_image(img, 16, 4, 16)
@@ -185,13 +191,14 @@ def test_encode16_1024_sampled(engine):
     assert np.array_equal(st["dom_bin"].cpu().numpy(), cls["dom_bin"])
     R = 64 * 64
     rng = np.random.default_rng(2016)
-    sample = np.unique(np.concatenate([[0, R - 1, 63, R - 64], rng.choice(R, 40, replace=False)]))
-    ref = omatch.encode(img, B=16, sigma=4, K=16, range_ids=sample, n_threads=8, cls=cls)
+    sample = np.unique(np.concatenate([[0, R - 1, 63, R - 64], rng.choice(R, 400, replace=False), fb]))
+    ref = omatch.encode(img, B=16, sigma=4, K=16, range_ids=sample, n_threads=NT, cls=cls)
     _compare_codes(codes, ref, sample)
     rep = fic.read_info(info)
     ww = odbc.default_half_width(16)
     total = sum(opools.class_pool(b, cls["dom_bin"], ww).size for b in cls["range_bin"])
     assert rep["matches"] == total * 8 and rep["device_error"] == 0
+    assert fb.size == rep["fallback_ranges"]
     if engine == "tensor":
         assert rep["fallback_ranges"] <= R // 20, rep
 
@@ -206,7 +213,7 @@ def _codes_gpu(c):
 def test_decode16_parity_and_adjoint():
     H, W, sigma, iters = 96, 128, 4, 6
     img = synth.fbm_image(71, H, W)
-    codes = omatch.encode(img, B=16, sigma=sigma, K=5, n_threads=8)
+    codes = omatch.encode(img, B=16, sigma=sigma, K=5, n_threads=NT)
     p = fic.EncodeParams(domain_stride=sigma, num_classes=5, block=16)
     for it in (1, iters):
         x = fic.decode(_codes_gpu(codes), H, W, p, it)

@@ -4,6 +4,8 @@ Bars: decoded PSNR within 0.01 dB of the oracle's; iterates within 2e-3 absolute
 FP64 over <= 8 contractive steps of values in [0, 255]); gradients within 1e-4 relative of the
 oracle's FP64 adjoint and of FP64 central finite differences (h = 1e-4).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -13,6 +15,8 @@ from oracle import match as omatch
 from paper_1206_4880_gb300 import fic, synth
 
 pytestmark = pytest.mark.gpu
+
+NT = os.cpu_count() or 1  # oracle threads: every host core
 
 
 def _codes_gpu(c):
@@ -25,7 +29,7 @@ def _codes_gpu(c):
 @pytest.fixture(scope="module")
 def pr1_codes():
     img = synth.pr1_image()
-    return img, omatch.encode(img, B=8, sigma=8, K=8, n_threads=8)
+    return img, omatch.encode(img, B=8, sigma=8, K=8, n_threads=NT)
 
 
 @pytest.mark.parametrize("iters", [0, 1, 2, 5, 8])
@@ -69,7 +73,7 @@ def test_decode_from_given_start(pr1_codes):
 def test_adjoint_parity(sigma):
     H, W, iters = 64, 96, 6
     img = synth.fbm_image(90 + sigma, H, W)
-    codes = omatch.encode(img, B=8, sigma=sigma, K=6, n_threads=8)
+    codes = omatch.encode(img, B=8, sigma=sigma, K=6, n_threads=NT)
     g = np.random.default_rng(sigma).normal(size=(H, W))
     gs_ref, go_ref = odec.decode_adjoint(codes, H, W, 8, sigma, iters, g)
     p = fic.EncodeParams(domain_stride=sigma, num_classes=6)
@@ -92,7 +96,7 @@ def test_adjoint_512_against_finite_differences():
     img = synth.diff_image()
     H = W = 512
     iters = 8
-    codes = omatch.encode(img, B=8, sigma=8, K=16, n_threads=8)
+    codes = omatch.encode(img, B=8, sigma=8, K=16, n_threads=NT)
     cg = _codes_gpu(codes)
     p = fic.EncodeParams(domain_stride=8, num_classes=16)
     base = {k: np.asarray(codes[k], np.float64 if k in ("s", "o") else np.int64)
@@ -181,3 +185,92 @@ def test_refinement_improves_decoded_psnr(pr1_codes):
     assert rep["psnr_refined_quantized"] > rep["psnr_quantized"], rep
     r = refine.refine(cg, torch.from_numpy(img).cuda(), p, steps=3)
     assert float(r["s"].abs().max()) <= 1.0
+
+
+def test_decode_repeated_calls_follow_contents(pr1_codes):
+    """fic_decode replays a cached graph for repeated calls with the same buffers: the result
+    must follow what the code and start buffers hold at each call."""
+    img, codes_a = pr1_codes
+    codes_b = omatch.encode(synth.fbm_image(44, 256, 256), B=8, sigma=8, K=8, n_threads=NT)
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    g = _codes_gpu(codes_a)
+    out = torch.empty(256, 256, dtype=torch.float32, device="cuda")
+    ws = torch.empty(fic.decode_workspace_size(256, 256, p, 6), dtype=torch.uint8, device="cuda")
+    x0 = torch.full((256, 256), 128.0, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(9)
+    for rep in range(3):
+        for codes in (codes_a, codes_b):
+            for k, v in _codes_gpu(codes).items():
+                g[k].copy_(v)
+            start = rng.uniform(0, 255, (256, 256))
+            x0.copy_(torch.from_numpy(start.astype(np.float32)))
+            fic.decode(g, 256, 256, p, 6, x0=x0, out=out, workspace=ws)
+            torch.cuda.synchronize()
+            ref = odec.decode(codes, 256, 256, 8, 8, 6, x0=start.astype(np.float32).astype(np.float64))
+            assert np.max(np.abs(out.cpu().numpy() - ref)) <= 2e-3, rep
+
+
+@pytest.mark.parametrize("block,sigma", [(8, 3), (8, 5), (16, 3), (16, 8)])
+def test_decode_odd_strides_and_unaligned_start(block, sigma):
+    """Odd strides, and a start image and an output that are only 4-byte aligned, take the kernel's
+    scalar-load and scalar-store forms; results equal the oracle's."""
+    H, W = 96, 128
+    img = synth.fbm_image(45 + sigma, H, W)
+    codes = omatch.encode(img, B=block, sigma=sigma, K=4, n_threads=NT)
+    p = fic.EncodeParams(domain_stride=sigma, num_classes=4, block=block)
+    start = np.random.default_rng(sigma).uniform(0, 255, (H, W)).astype(np.float32)
+    big = torch.empty(H * W + 1, dtype=torch.float32, device="cuda")
+    x0 = big[1:].view(H, W)
+    x0.copy_(torch.from_numpy(start))
+    assert x0.data_ptr() % 8 == 4
+    big_out = torch.empty(H * W + 1, dtype=torch.float32, device="cuda")
+    for iters in (1, 4):
+        for out in (None, big_out[1:].view(H, W)):
+            x = fic.decode(_codes_gpu(codes), H, W, p, iters, x0=x0, out=out)
+            torch.cuda.synchronize()
+            ref = odec.decode(codes, H, W, block, sigma, iters, x0=start.astype(np.float64))
+            assert np.max(np.abs(x.cpu().numpy() - ref)) <= 2e-3, iters
+
+
+def test_decode_invalid_codes_give_nan_only_there(pr1_codes):
+    """A code whose domain or isometry is out of range (as written by an encode whose matcher gave
+    up) decodes to NaN over its own range and is never used to index the image."""
+    img, codes = pr1_codes
+    p = fic.EncodeParams(domain_stride=8, num_classes=8)
+    g = _codes_gpu(codes)
+    bad = [0, 77, 1023]
+    g["dom"][bad[0]] = -1
+    g["dom"][bad[1]] = 10 ** 6
+    g["iso"][bad[2]] = 9
+    x = fic.decode(g, 256, 256, p, 1).cpu().numpy()
+    ref = odec.decode(codes, 256, 256, 8, 8, 1)
+    mask = np.zeros((256, 256), bool)
+    for r in bad:
+        ry, rx = divmod(r, 32)
+        mask[8 * ry:8 * ry + 8, 8 * rx:8 * rx + 8] = True
+    assert np.all(np.isnan(x[mask]))
+    assert np.max(np.abs(x[~mask] - ref[~mask])) <= 2e-3
+
+
+@pytest.mark.parametrize("block", [8, 16])
+def test_decode_load_and_store_forms_agree_bitwise(block):
+    """The decode step's 16-byte, pair and single-float load forms and its vector and scalar store
+    forms apply the same operations in the same order: one step from the same start image gives the
+    same bits whichever form the alignment of the buffers selects."""
+    H, W, sigma = 128, 160, 8
+    img = synth.fbm_image(46, H, W)
+    codes = _codes_gpu(omatch.encode(img, B=block, sigma=sigma, K=4, n_threads=NT))
+    p = fic.EncodeParams(domain_stride=sigma, num_classes=4, block=block)
+    start = torch.from_numpy(np.random.default_rng(3).uniform(0, 255, (H, W)).astype(np.float32)).cuda()
+    outs = []
+    for shift_in, shift_out in ((0, 0), (1, 0), (2, 1), (0, 3)):
+        bi = torch.empty(H * W + 4, dtype=torch.float32, device="cuda")
+        bo = torch.empty(H * W + 4, dtype=torch.float32, device="cuda")
+        x0 = bi[shift_in:shift_in + H * W].view(H, W)
+        x0.copy_(start)
+        out = bo[shift_out:shift_out + H * W].view(H, W)
+        fic.decode(codes, H, W, p, 1, x0=x0, out=out)
+        torch.cuda.synchronize()
+        outs.append(out.clone())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])

@@ -4,6 +4,8 @@ Bars: block moments, box counts, FD bit patterns and classes bit-exact; pool ord
 exact; chosen (domain, isometry) identical; s and o within 1e-6 (they are formed from the same
 exact integers, so in practice equal); sse within 1e-9 relative.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -16,6 +18,7 @@ from paper_1206_4880_gb300 import fic, synth
 pytestmark = pytest.mark.gpu
 
 ENGINES = ["simt", "tensor"]
+NT = os.cpu_count() or 1  # oracle threads: every host core
 
 # (H, W, sigma, K, w, seed): small ragged cases spanning several tensor tiles, odd strides
 SMALL = [
@@ -112,7 +115,7 @@ def test_encode_parity_small(case, engine):
     info = fic.new_info("cuda")
     codes = fic.encode(_t(img), _params(sigma, K, w, engine), info=info)
     torch.cuda.synchronize()
-    ref = omatch.encode(img, B=8, sigma=sigma, K=K, w=None if w < 0 else w, n_threads=8)
+    ref = omatch.encode(img, B=8, sigma=sigma, K=K, w=None if w < 0 else w, n_threads=NT)
     _compare_codes(codes, ref)
     rep = fic.read_info(info)
     assert rep["matches"] == int(ref["pool_size"].sum()) * 8
@@ -137,7 +140,7 @@ def test_encode_flat_and_edge_images(engine):
         for K, sigma in ((4, 2), (1, 4), (255, 8)):
             codes = fic.encode(_t(im), _params(sigma, K, -1, engine))
             torch.cuda.synchronize()
-            ref = omatch.encode(im, B=8, sigma=sigma, K=K, n_threads=8)
+            ref = omatch.encode(im, B=8, sigma=sigma, K=K, n_threads=NT)
             _compare_codes(codes, ref)
 
 
@@ -149,7 +152,7 @@ def test_encode_padded_pitch():
     assert t.stride(0) == 96
     codes = fic.encode(t, _params(4, 6, -1))
     torch.cuda.synchronize()
-    ref = omatch.encode(img, B=8, sigma=4, K=6, n_threads=8)
+    ref = omatch.encode(img, B=8, sigma=4, K=6, n_threads=NT)
     _compare_codes(codes, ref)
 
 
@@ -168,15 +171,19 @@ def test_encode_deterministic(engine):
 @pytest.mark.parametrize("block", [8, 16])
 def test_encode_schedule_independent(block):
     """The persistent tensor matchers hand out work items from a global counter, so which CTA
-    scores which item changes from run to run, and items_per_sm changes how the chunks are cut
-    into items: the codes must not change with either."""
+    scores which item changes from run to run; items_per_sm and group_chunks change how the chunks
+    are cut into items and groups, and pipeline_stages the depth of the operand ring: the codes must
+    not change with any of them."""
     _need_tensor("tensor")
     img = _t(synth.fbm_image(41, 1024, 768))
     sigma, K = 4, (16 if block == 8 else 12)
     base, items = None, []
-    for ipsm in (1, 5, 32, 64, 32):
+    stages = (3, 4) if block == 8 else (4, 5)
+    variants = [(1, 0, 0), (5, 0, 0), (32, 0, 0), (64, 0, 0), (32, 0, 0),
+                (24, 4, stages[0]), (24, 128, stages[1]), (8, 1, stages[0])]
+    for ipsm, gch, stg in variants:
         p = fic.EncodeParams(domain_stride=sigma, num_classes=K, engine="tensor", block=block,
-                             items_per_sm=ipsm)
+                             items_per_sm=ipsm, group_chunks=gch, pipeline_stages=stg)
         info = fic.new_info("cuda")
         codes = fic.encode(img, p, info=info)
         torch.cuda.synchronize()
@@ -187,36 +194,74 @@ def test_encode_schedule_independent(block):
             base = codes
             continue
         for k in base:
-            assert torch.equal(base[k], codes[k]), (ipsm, k)
+            assert torch.equal(base[k], codes[k]), (ipsm, gch, stg, k)
     assert items[0] < items[3], items  # the item counts really differ
 
 
-@pytest.mark.parametrize("engine", ENGINES)
-def test_encode_1024_sampled(engine):
-    """The 1024x1024, stride-4, K=16 workload at full size, in the bench's launch
-    configuration: classification bit-exact everywhere, codes on a seeded range sample."""
-    _need_tensor(engine)
+@pytest.fixture(scope="module")
+def oracle_1024():
+    """The oracle's codes of every range of the 1024x1024, stride-4, K = 16 workload (about a
+    minute on 16 host cores), computed once for both engines."""
     img = synth.image_1024()
+    cls = omatch.classify_image(img, 8, 4, 16)
+    ref = omatch.encode(img, B=8, sigma=4, K=16, n_threads=NT, cls=cls)
+    return img, cls, ref
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_encode_1024_full(engine, oracle_1024):
+    """The 1024x1024, stride-4, K=16 workload at full size, in the bench's launch configuration:
+    classification bit-exact everywhere and all 16384 codes equal to the oracle's; the ranges the
+    tensor engine had to re-search exactly are among them."""
+    _need_tensor(engine)
+    img, cls, ref = oracle_1024
     p = _params(4, 16, -1, engine)
+    H, W = img.shape
+    ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device="cuda")
     info = fic.new_info("cuda")
-    codes = fic.encode(_t(img), p, info=info)
+    codes = fic.encode(_t(img), p, workspace=ws, info=info)
+    fb = fic.fallback_ranges(H, W, p, ws).cpu().numpy()
     st = fic.classify(_t(img), p)
     torch.cuda.synchronize()
-    cls = omatch.classify_image(img, 8, 4, 16)
     assert np.array_equal(st["range_bin"].cpu().numpy(), cls["range_bin"])
     assert np.array_equal(st["dom_bin"].cpu().numpy(), cls["dom_bin"])
-    rng = np.random.default_rng(2000)
-    R = 128 * 128
-    sample = np.unique(np.concatenate([[0, R - 1, 127, R - 128], rng.choice(R, 60, replace=False)]))
-    ref = omatch.encode(img, B=8, sigma=4, K=16, range_ids=sample, n_threads=8, cls=cls)
-    _compare_codes(codes, ref, sample)
+    _compare_codes(codes, ref)
     rep = fic.read_info(info)
-    ww = odbc.default_half_width(16)
-    total = sum(opools.class_pool(b, cls["dom_bin"], ww).size for b in cls["range_bin"])
-    assert rep["matches"] == total * 8
+    assert rep["matches"] == int(ref["pool_size"].sum()) * 8
     assert rep["device_error"] == 0
+    R = 128 * 128
+    assert fb.size == rep["fallback_ranges"]
     if engine == "tensor":
-        assert rep["fallback_ranges"] <= R // 20, rep
+        assert 0 < fb.size <= R // 20, rep
+        assert np.unique(fb).size == fb.size and fb.min() >= 0 and fb.max() < R
+    else:
+        assert fb.size == 0
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_encode_batched_bench_subset(engine):
+    """The first eight images of the benchmark's 64-image batch (sides 1536, 512, 768, 2048, 512,
+    1024, 384, 2048; stride 8, K = 16) in one fic_encode_batched call: images up to 1024x1024
+    compared with the oracle on every range, the larger ones on 400 seeded ranges (corners
+    included) each."""
+    _need_tensor(engine)
+    imgs = synth.batch_images(64)[:8]
+    p = _params(8, 16, -1, engine)
+    info = fic.new_info("cuda")
+    outs = fic.encode_batched([_t(im) for im in imgs], p, info=info)
+    torch.cuda.synchronize()
+    assert fic.read_info(info)["device_error"] == 0
+    for k, (im, out) in enumerate(zip(imgs, outs)):
+        H, W = im.shape
+        R = (H // 8) * (W // 8)
+        if H <= 1024:
+            sample = None
+        else:
+            rng = np.random.default_rng(3100 + k)
+            sample = np.unique(np.concatenate([[0, R - 1, W // 8 - 1, R - W // 8],
+                                               rng.choice(R, 400, replace=False)]))
+        ref = omatch.encode(im, B=8, sigma=8, K=16, range_ids=sample, n_threads=NT)
+        _compare_codes(out, ref, sample)
 
 
 def test_full_search_simt_equals_k1_tensor():
@@ -242,7 +287,7 @@ def test_encode_batched_equals_oracle(engine):
     torch.cuda.synchronize()
     total = 0
     for im, out in zip(imgs, outs):
-        ref = omatch.encode(im, B=8, sigma=4, K=7, n_threads=8)
+        ref = omatch.encode(im, B=8, sigma=4, K=7, n_threads=NT)
         _compare_codes(out, ref)
         total += int(ref["pool_size"].sum()) * 8
     rep = fic.read_info(info)
@@ -269,7 +314,7 @@ def test_encode_literal_window(case, engine):
     st = fic.classify(_t(img), p)
     po = fic.build_pools(st, H, W, p)
     torch.cuda.synchronize()
-    ref = omatch.encode(img, B=8, sigma=sigma, K=K, mode="literal", n_threads=8)
+    ref = omatch.encode(img, B=8, sigma=sigma, K=K, mode="literal", n_threads=NT)
     _compare_codes(codes, ref)
     assert fic.read_info(info)["matches"] == int(ref["pool_size"].sum()) * 8
     cls = ref["cls"]
@@ -294,7 +339,7 @@ def test_conci_two_groups(engine):
     p = fic.EncodeParams(domain_stride=4, num_classes=2, half_width=0, engine=engine)
     codes = fic.encode(_t(img), p)
     torch.cuda.synchronize()
-    ref = omatch.encode(img, B=8, sigma=4, K=2, w=0, n_threads=8)
+    ref = omatch.encode(img, B=8, sigma=4, K=2, w=0, n_threads=NT)
     _compare_codes(codes, ref)
 
 

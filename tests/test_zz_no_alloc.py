@@ -30,20 +30,36 @@ def _call_static(codes, H, W, p, iters, x0, out):
                                  ctypes.c_void_p(out.data_ptr()), stream)
 
 
-def test_decode_static_matches_decode_on_two_calls():
+@pytest.fixture(scope="module", params=[8, 16])
+def coded(request):
+    """Codes of a 256 x 320 image for 8x8 or 16x16 ranges, and a random start image."""
+    B = request.param
     H, W = 256, 320
     img = synth.fbm_image(321, H, W)
-    p = fic.EncodeParams(domain_stride=8, num_classes=8, engine="simt")
+    p = fic.EncodeParams(domain_stride=8, num_classes=8, engine="simt", block=B)
     codes = fic.encode(torch.from_numpy(img).cuda(), p)
     x0 = torch.from_numpy(np.random.default_rng(5).uniform(0, 255, (H, W)).astype(np.float32)).cuda()
-    for iters, start in ((8, None), (5, x0)):
-        ref = fic.decode(codes, H, W, p, iters, x0=start)
+    return H, W, p, codes, x0
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 8])
+@pytest.mark.parametrize("with_x0", [False, True])
+def test_decode_static_matches_decode_on_two_calls(coded, iters, with_x0):
+    """Two calls in a row (the second sees the scratch the first left behind) each equal
+    fic_decode: iters = 0 copies or fills the start image, iters = 1 writes the output directly,
+    even and odd counts end the ping-pong in the output buffer."""
+    H, W, p, codes, x0 = coded
+    start = x0 if with_x0 else None
+    ref = fic.decode(codes, H, W, p, iters, x0=start)
+    for _ in range(2):
         out = torch.full((H, W), float("nan"), dtype=torch.float32, device="cuda")
         st = _call_static(codes, H, W, p, iters, start, out)
         assert st == fic.FIC_OK, fic.load().fic_last_error()
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert torch.max(torch.abs(out - ref)).item() <= 2e-3
+    if iters == 0:
+        assert torch.equal(out, x0 if with_x0 else torch.full_like(out, 128.0))
 
 
 def test_decode_static_refuses_images_beyond_its_scratch():
