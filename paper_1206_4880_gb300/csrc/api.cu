@@ -11,14 +11,14 @@
 #include "fic_internal.cuh"
 
 namespace fic {
-cudaError_t launch_dom_csr(const Geo &g, const int32_t *dom, const double *s, int32_t *cnt, int32_t *off,
-                           int32_t *cursor, int32_t *list, cudaStream_t st);
-cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const int32_t *off,
-                                  const int32_t *list, const float *lam, float *lam_prev,
-                                  cudaStream_t st);
+size_t adjoint_csr_ints(const Geo &g);
+size_t adjoint_entries(const Geo &g);
+cudaError_t launch_dom_csr(const Geo &g, const fic_codes &c, const AdjointCsr &a, cudaStream_t st);
+cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const AdjointCsr &a, const float *lam,
+                                  float *lam_prev, cudaStream_t st);
 cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *x, const float *lam,
-                                 double *gs, double *go, cudaStream_t st);
-cudaError_t launch_grads_out(int R, const double *gs64, const double *go64, float *gs, float *go,
+                                 float2 *gs, float2 *go, cudaStream_t st);
+cudaError_t launch_grads_out(int R, const float2 *gsf, const float2 *gof, float *gs, float *go,
                              cudaStream_t st);
 cudaError_t launch_quality(const float *x, const uint8_t *ref, int H, int W, int pitch, double *out,
                            cudaStream_t st);
@@ -167,6 +167,7 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
     g->literal = (p->flags & FIC_FLAG_LITERAL_WINDOW) ? 1 : 0;
     g->fRx = make_fastdiv((uint32_t)g->nRx);
     g->fDx = make_fastdiv((uint32_t)g->nDx);
+    g->fS = make_fastdiv((uint32_t)g->sigma);
     g->group_chunks = p->group_chunks > 0 ? p->group_chunks : (B == 16 ? 16 : 64);
     g->stages = p->pipeline_stages;
     return FIC_OK;
@@ -864,9 +865,12 @@ size_t fic_decode_workspace_size(const fic_geom *gm, const fic_params *p, int32_
     c.take<float>(img * (size_t)nseg);        // checkpoints
     c.take<float>(img * (size_t)(ck));        // segment iterates
     c.take<float>(2 * img);                   // adjoint vectors
-    c.take<int32_t>(3 * (size_t)g.Dn + 1);    // CSR counts, offsets, cursors
-    c.take<int32_t>(g.R);                     // CSR list
-    c.take<double>(2 * (size_t)g.R);          // FP64 gradient accumulators
+    c.take<int32_t>(adjoint_csr_ints(g));     // domain -> ranges index: keys, list, sort buffers,
+                                              // segment starts, radix histograms
+    c.take<uint8_t>(g.R);                     // radix digits
+    c.take<int4>(adjoint_entries(g));         // packed (range, isometry, s / 4) per list position
+    c.take<float>((size_t)g.R * g.n);         // per-range cell blocks of W^T
+    c.take<float2>(2 * (size_t)g.R);          // float-float gradient accumulators
     return c.off + 256;
 }
 
@@ -1010,19 +1014,26 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
     float *ckpt = c.take<float>(img * (size_t)nseg);
     float *seg = c.take<float>(img * (size_t)ck);
     float *lam = c.take<float>(2 * img);
-    int32_t *cnt = c.take<int32_t>(g.Dn);
-    int32_t *off = c.take<int32_t>(g.Dn + 1);
-    int32_t *cursor = c.take<int32_t>(g.Dn);
-    int32_t *list = c.take<int32_t>(g.R);
-    double *g64 = c.take<double>(2 * (size_t)g.R);
+    AdjointCsr csr;
+    int32_t *ints = c.take<int32_t>(adjoint_csr_ints(g));
+    csr.key = ints;
+    csr.list = ints + g.R;
+    csr.t1 = ints + 2 * (size_t)g.R;
+    csr.t2 = ints + 3 * (size_t)g.R;
+    csr.off = ints + 4 * (size_t)g.R;
+    csr.counts = csr.off + g.Dn + 1;
+    csr.digit = c.take<uint8_t>(g.R);
+    csr.ent = c.take<int4>(adjoint_entries(g));
+    csr.acc = c.take<float>((size_t)g.R * g.n);
+    float2 *gacc = c.take<float2>(2 * (size_t)g.R);  // float-float gradient accumulators
     (void)pingpong;
     g_launches = 0;
-    FIC_TRY(cudaMemsetAsync(g64, 0, sizeof(double) * 2 * g.R, st), "memset");
+    FIC_TRY(cudaMemsetAsync(gacc, 0, sizeof(float2) * 2 * g.R, st), "memset");
     if (iters == 0) {
-        FIC_TRY(launch_grads_out(g.R, g64, g64 + g.R, grad_s, grad_o, st), "grads_out");
+        FIC_TRY(launch_grads_out(g.R, gacc, gacc + g.R, grad_s, grad_o, st), "grads_out");
         return FIC_OK;
     }
-    FIC_TRY(launch_dom_csr(g, codes->dom, codes->s, cnt, off, cursor, list, st), "csr");
+    FIC_TRY(launch_dom_csr(g, *codes, csr, st), "csr");
     // forward: checkpoints x_0, x_ck, x_2ck, ...
     if (x0) FIC_TRY(cudaMemcpyAsync(ckpt, x0, img * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy");
     else FIC_TRY(launch_fill(ckpt, img, 128.f, st), "fill");
@@ -1043,16 +1054,16 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
         for (int i = 1; i < len; ++i)
             FIC_TRY(launch_decode_step(*codes, g, seg_ptr(c0, i - 1), seg_ptr(c0, i), st), "decode_step");
         for (int i = len - 1; i >= 0; --i) {
-            FIC_TRY(launch_adjoint_grads(g, *codes, seg_ptr(c0, i), lcur, g64, g64 + g.R, st), "grads");
+            FIC_TRY(launch_adjoint_grads(g, *codes, seg_ptr(c0, i), lcur, gacc, gacc + g.R, st), "grads");
             if (c0 > 0 || i > 0) {
-                FIC_TRY(launch_adjoint_gather(g, *codes, off, list, lcur, lprev, st), "gather");
+                FIC_TRY(launch_adjoint_gather(g, *codes, csr, lcur, lprev, st), "gather");
                 float *t = lcur;
                 lcur = lprev;
                 lprev = t;
             }
         }
     }
-    FIC_TRY(launch_grads_out(g.R, g64, g64 + g.R, grad_s, grad_o, st), "grads_out");
+    FIC_TRY(launch_grads_out(g.R, gacc, gacc + g.R, grad_s, grad_o, st), "grads_out");
     return FIC_OK;
 }
 

@@ -5,9 +5,9 @@
 // One Jacobi step: x_{k+1}[p] = s_r * D(x_k, d_r)[src_{t_r}(p)] + o_r for every pixel p of range
 // r, with D the 2x2 average of the 2B x 2B domain. Adjoint of the linear part W:
 // (W^T l)[q] = sum over ranges r whose domain covers q of (s_r / 4) * l[p_r(q)], where p_r(q)
-// is the range pixel whose source cell contains q. It is evaluated as a gather per pixel q over
-// the (at most (2B/sigma)^2) domains covering q and, through a domain -> ranges CSR whose
-// segments are sorted, over the ranges using each domain: no atomics, so the result does not
+// is the range pixel whose source cell contains q. It is formed per domain (the sum over the
+// domain's ranges, in increasing id, for each of its cells) and then per pixel (the sum over the
+// at most (2B/sigma)^2 domains covering it, in row-major order): no atomics, so the result does not
 // depend on scheduling.
 #include "fic_internal.cuh"
 
@@ -23,6 +23,53 @@ cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st) {
     k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, v);
     ++g_launches;
     return cudaGetLastError();
+}
+
+// The B x B 2x2 averages of the 2B x 2B block at src (row stride W) into cw (shared memory), by the
+// lanes of one warp. LD = 4: 16-byte loads, each the top or bottom row of two adjacent cells (src
+// and W keep every vector 16-byte aligned); 2: aligned pairs; 1: single floats. The sum order
+// ((x00 + x01) + x10) + x11 and the scaling by 1/4 are the same in every form.
+template <int B, int LD>
+__device__ __forceinline__ void load_cells(const float *__restrict__ src, int W, int lane, float *cw) {
+    constexpr int NC = B * B / 32;
+    if constexpr (LD == 4) {
+#pragma unroll
+        for (int k = 0; k < NC / 2; ++k) {
+            const int q = lane + 32 * k, cy = q / (B / 2), cp = q % (B / 2);  // cells (cy, 2cp), (cy, 2cp + 1)
+            const float *p = src + (size_t)(2 * cy) * W + 4 * cp;
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(p + W));
+            *reinterpret_cast<float2 *>(&cw[cy * B + 2 * cp]) =
+                make_float2((((a.x + a.y) + b.x) + b.y) * 0.25f, (((a.z + a.w) + b.z) + b.w) * 0.25f);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const int c = lane + 32 * k, cy = c / B, cx = c % B;
+            const float *p = src + (size_t)(2 * cy) * W + 2 * cx;
+            float v;
+            if constexpr (LD == 2) {
+                const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+                const float2 b = __ldg(reinterpret_cast<const float2 *>(p + W));
+                v = (((a.x + a.y) + b.x) + b.y) * 0.25f;
+            } else {
+                v = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + W)) + __ldg(p + W + 1)) * 0.25f;
+            }
+            cw[c] = v;
+        }
+    }
+}
+
+// Warp-uniform constants of src_t(py, px) = c0 + ky py + kx px, the index of the source cell of
+// pixel (py, px) under isometry t (iso_src, which is affine in the pixel coordinates).
+template <int B>
+__device__ __forceinline__ void iso_affine(int t, int &c0, int &ky, int &kx) {
+    constexpr int N = B - 1;
+    const bool swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
+    const int sgy = fy ? -1 : 1, sgx = fx ? -1 : 1;
+    c0 = (fy ? N * B : 0) + (fx ? N : 0);
+    ky = swap ? sgx : sgy * B;
+    kx = swap ? sgy * B : sgx;
 }
 
 // One warp per range r: the warp reads the 2B x 2B source domain of x_k, forms the B x B averages
@@ -60,38 +107,10 @@ __global__ void __launch_bounds__(32 * kDecodeWarps)
     const float sr = (float)__ldg(s + r), orr = (float)__ldg(o + r);
     const float *src = x + (size_t)(dq * g.sigma) * g.W + (d - dq * g.nDx) * g.sigma;
     float *cw = cell[warp];
-    if constexpr (LD == 4) {
-#pragma unroll
-        for (int k = 0; k < NC / 2; ++k) {
-            const int q = lane + 32 * k, cy = q / (B / 2), cp = q % (B / 2);  // cells (cy, 2cp), (cy, 2cp + 1)
-            const float4 *p = reinterpret_cast<const float4 *>(src + (size_t)(2 * cy) * g.W + 4 * cp);
-            const float4 a = __ldg(p), b = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(p) + g.W));
-            *reinterpret_cast<float2 *>(&cw[cy * B + 2 * cp]) =
-                make_float2((((a.x + a.y) + b.x) + b.y) * 0.25f, (((a.z + a.w) + b.z) + b.w) * 0.25f);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            const int c = lane + 32 * k, cy = c / B, cx = c % B;
-            const float *p = src + (size_t)(2 * cy) * g.W + 2 * cx;
-            float v;
-            if (LD == 2) {
-                const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
-                const float2 b = __ldg(reinterpret_cast<const float2 *>(p + g.W));
-                v = (((a.x + a.y) + b.x) + b.y) * 0.25f;
-            } else {
-                v = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + g.W)) + __ldg(p + g.W + 1)) * 0.25f;
-            }
-            cw[c] = v;
-        }
-    }
+    load_cells<B, LD>(src, g.W, lane, cw);
     __syncwarp();
-    // src_t(py, px) = sy B + sx with (sy, sx) from iso_src: affine in (py, px)
-    constexpr int N = B - 1;
-    const bool swap = (0xCA >> t) & 1, fy = (0xA6 >> t) & 1, fx = (0x9C >> t) & 1;
-    const int sgy = fy ? -1 : 1, sgx = fx ? -1 : 1;
-    const int c0 = (fy ? N * B : 0) + (fx ? N : 0);
-    const int ky = swap ? sgx : sgy * B, kx = swap ? sgy * B : sgx;
+    int c0, ky, kx;
+    iso_affine<B>(t, c0, ky, kx);
 #pragma unroll
     for (int k = 0; k < NC / PV; ++k) {
         const int p0 = PV * (lane + 32 * k), py = p0 / B, px = p0 % B;
@@ -108,6 +127,62 @@ __global__ void __launch_bounds__(32 * kDecodeWarps)
 #pragma unroll
             for (int i = 0; i < PV; ++i) q[i] = v[i];
         }
+    }
+}
+
+// The same step for 8x8 ranges with 16-byte source loads: one half-warp per range, so one warp's
+// instructions keep two ranges' loads in flight. Lane hl of a half loads the top and bottom rows of
+// cell pairs hl and hl + 16 (cell rows hl / 4 and hl / 4 + 4) and writes four adjacent pixels.
+template <bool VS>
+__global__ void __launch_bounds__(32 * kDecodeWarps)
+    k_decode_step8h(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                    const double *__restrict__ s, const double *__restrict__ o, const float *__restrict__ x,
+                    float *__restrict__ y) {
+    __shared__ __align__(16) float cell[2 * kDecodeWarps][64];
+    const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
+    const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
+    const int r = blockIdx.x * (2 * kDecodeWarps) + hw;
+    if (r >= g.R) return;  // whole half-warps leave together; only half-warp barriers follow
+    const int d = __ldg(dom + r), t = __ldg(iso + r);
+    const int rq = fdiv(r, g.fRx), dq = fdiv(d, g.fDx);
+    float *dst = y + (size_t)(rq * 8) * g.W + (r - rq * g.nRx) * 8;
+    if (!valid_code(g, d, t)) {  // an invalid code (an encode that gave up): NaN pixels, no read
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            dst[(size_t)((hl + 16 * k) / 8) * g.W + (hl + 16 * k) % 8] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const float sr = (float)__ldg(s + r), orr = (float)__ldg(o + r);
+    const float *src = x + (size_t)(dq * g.sigma) * g.W + (d - dq * g.nDx) * g.sigma;
+    float *cw = cell[hw];
+    float4 a[2], b[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int q = hl + 16 * k, cy = q >> 2, cp = q & 3;  // cells (cy, 2cp), (cy, 2cp + 1)
+        const float *p = src + (size_t)(2 * cy) * g.W + 4 * cp;
+        a[k] = __ldg(reinterpret_cast<const float4 *>(p));
+        b[k] = __ldg(reinterpret_cast<const float4 *>(p + g.W));
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int q = hl + 16 * k, cy = q >> 2, cp = q & 3;
+        *reinterpret_cast<float2 *>(&cw[cy * 8 + 2 * cp]) =
+            make_float2((((a[k].x + a[k].y) + b[k].x) + b[k].y) * 0.25f, (((a[k].z + a[k].w) + b[k].z) + b[k].w) * 0.25f);
+    }
+    __syncwarp(hmask);
+    int c0, ky, kx;
+    iso_affine<8>(t, c0, ky, kx);
+    const int py = hl >> 1, px = 4 * (hl & 1);
+    const int s0 = c0 + ky * py + kx * px;
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = fmaf(sr, cw[s0 + i * kx], orr);
+    float *q = dst + (size_t)py * g.W + px;
+    if constexpr (VS) {
+        *reinterpret_cast<float4 *>(q) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = v[i];
     }
 }
 
@@ -141,10 +216,17 @@ cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x,
     const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
     const int ld = (g.sigma % 4 == 0 && xa % 16 == 0) ? 4 : (g.sigma % 2 == 0 && xa % 8 == 0) ? 2 : 1;
     const bool vs = ya % (g.B == 16 ? 16 : 8) == 0;
-    if (g.B == 16)
+    if (g.B == 16) {
         decode_step_b<16>(ld, vs, blocks, g, c, x, y, st);
-    else
+    } else if (ld == 4) {
+        const unsigned hblocks = (unsigned)((g.R + 2 * kDecodeWarps - 1) / (2 * kDecodeWarps));
+        if (ya % 16 == 0)
+            k_decode_step8h<true><<<hblocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+        else
+            k_decode_step8h<false><<<hblocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
+    } else {
         decode_step_b<8>(ld, vs, blocks, g, c, x, y, st);
+    }
     ++g_launches;
     return cudaGetLastError();
 }
@@ -183,195 +265,350 @@ cudaError_t launch_decode_step_scaled(const fic_codes &c, const Geo &g, int z, c
 }
 
 // ---- adjoint -------------------------------------------------------------------------------
-// domain -> ranges CSR: cnt[d] = #ranges using d with s != 0 (a range with s = 0 contributes
-// nothing to W^T l, and flat ranges, which all take the pool's smallest domain id, would otherwise
-// pile onto one domain); off = exclusive scan; list sorted per segment.
-__global__ void k_dom_count(Geo g, const int32_t *__restrict__ dom, const double *__restrict__ s, int32_t *cnt) {
+// W^T l (the adjoint of the linear part of one step) in two deterministic phases over the
+// domain -> ranges index of the ranges that contribute (s != 0 and a valid code: a range with
+// s = 0 contributes nothing, and flat ranges, which all take their pool's smallest domain, would
+// otherwise pile onto a few domains):
+//   cells: per listed range r (one warp each), its B x B cell block C_r[c] = (s_r / 4) l[p_r(c)],
+//          p_r(c) the pixel of range r whose source cell under t_r is c, stored at r's list position;
+//   pixels: (W^T l)[q] = sum over the domains d covering q, in row-major order, and over d's ranges
+//          in increasing id, of C_r[cell of q in d].
+// With an even stride every covering domain's cells are aligned 2x2 pixel blocks, so the sum is
+// the same for the four pixels of each aligned 2x2 block and is formed once per block.
+// The index is list = the range ids stably sorted by domain (a byte-wise radix sort) with
+// off[d] = the first position of a domain >= d (off[Dn] = the number of listed ranges).
+__global__ void k_csr_keys(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                           const double *__restrict__ s, int32_t *__restrict__ key) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < g.R && s[r] != 0.0 && valid_code(g, dom[r], 0)) atomicAdd(&cnt[dom[r]], 1);
+    if (r < g.R) key[r] = (s[r] != 0.0 && valid_code(g, dom[r], iso[r])) ? dom[r] : g.Dn;
 }
 
-// Single-block exclusive scan of cnt[0..n) into off[0..n], chunk by chunk.
-__global__ void k_scan_single(const int32_t *__restrict__ cnt, int n, int32_t *__restrict__ off,
-                              int32_t *__restrict__ cursor) {
-    __shared__ int buf[1024];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += 1024) {
-        const int i = base + threadIdx.x;
-        const int v = i < n ? cnt[i] : 0;
-        buf[threadIdx.x] = v;
-        __syncthreads();
-        for (int s = 1; s < 1024; s <<= 1) {
-            const int a = threadIdx.x >= s ? buf[threadIdx.x - s] : 0;
-            __syncthreads();
-            buf[threadIdx.x] += a;
-            __syncthreads();
-        }
-        const int incl = buf[threadIdx.x];
-        if (i < n) {
-            off[i] = carry + incl - v;
-            cursor[i] = carry + incl - v;
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) off[n] = carry;
+// The sorted keys (for the segment starts) and, per list position, the range's packed entry
+// (id, isometry, s / 4) that the cells phase reads at every step.
+__global__ void k_csr_sorted_keys(int n, const int32_t *__restrict__ key, const int32_t *__restrict__ list,
+                                  const int32_t *__restrict__ iso, const double *__restrict__ s,
+                                  int32_t *__restrict__ skey, int4 *__restrict__ ent) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int r = list[j];
+    skey[j] = key[r];
+    ent[j] = make_int4(r, iso[r] & 7, __float_as_int((float)s[r] * 0.25f), 0);
 }
 
-__global__ void k_dom_fill(Geo g, const int32_t *__restrict__ dom, const double *__restrict__ s, int32_t *cursor,
-                           int32_t *__restrict__ list) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < g.R && s[r] != 0.0 && valid_code(g, dom[r], 0)) list[atomicAdd(&cursor[dom[r]], 1)] = r;
-}
-
-// Insertion-sort each domain's segment so the gather order is fixed.
-__global__ void k_dom_sortseg(int Dn, const int32_t *__restrict__ off, int32_t *__restrict__ list) {
+// off[d] = the number of sorted keys below d, for d = 0 .. Dn (binary search).
+__global__ void k_csr_offsets(int n, int Dn, const int32_t *__restrict__ skey, int32_t *__restrict__ off) {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= Dn) return;
-    const int a = off[d], b = off[d + 1];
-    for (int i = a + 1; i < b; ++i) {
-        const int v = list[i];
-        int j = i - 1;
-        while (j >= a && list[j] > v) {
-            list[j + 1] = list[j];
-            --j;
-        }
-        list[j + 1] = v;
+    if (d > Dn) return;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (skey[mid] < d)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    off[d] = lo;
+}
+
+// Phase "cells": one warp per listed range.
+template <int B>
+__global__ void __launch_bounds__(256)
+    k_adjoint_cells(Geo g, const int4 *__restrict__ ent, const int32_t *__restrict__ off,
+                    const float *__restrict__ lam, float *__restrict__ acc) {
+    constexpr int NC = B * B / 32;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (k >= g.R) return;
+    const int n = __ldg(off + g.Dn);  // listed ranges (the rest of the list holds the others)
+    const int4 e = __ldg(ent + k);
+    if (k >= n) return;
+    const int r = e.x, t = e.y;
+    const float sc = __int_as_float(e.z);
+    const int rq = fdiv(r, g.fRx);
+    const float *lr = lam + (size_t)(rq * B) * g.W + (r - rq * g.nRx) * B;
+    // the pixel p with src_t(p) = c is p = src_{t^-1}(c)
+    int c0, ky, kx;
+    iso_affine<B>(t == 1 ? 3 : (t == 3 ? 1 : t), c0, ky, kx);
+    float *dst = acc + (size_t)k * (B * B);
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        const int c = lane + 32 * m, p = c0 + ky * (c / B) + kx * (c % B);
+        dst[c] = sc * __ldg(lr + (size_t)(p / B) * g.W + p % B);
     }
 }
 
-// l_prev = W^T l, one thread per pixel q.
-template <int B>
-__global__ void k_adjoint_gather(Geo g, const int32_t *__restrict__ iso, const double *__restrict__ s,
-                                 const int32_t *__restrict__ off, const int32_t *__restrict__ list,
-                                 const float *__restrict__ lam, float *__restrict__ lam_prev) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= g.H * g.W) return;
-    const int qy = idx / g.W, qx = idx - qy * g.W;
-    // domains (dy, dx) on the stride grid with dy <= qy < dy + 2B, likewise x
-    const int jy_hi = min(qy / g.sigma, g.nDy - 1), jx_hi = min(qx / g.sigma, g.nDx - 1);
-    const int jy_lo = max(0, (qy - (2 * B - 1) + g.sigma - 1) / g.sigma);
-    const int jx_lo = max(0, (qx - (2 * B - 1) + g.sigma - 1) / g.sigma);
-    float acc = 0.f;
-    for (int jy = jy_lo; jy <= jy_hi; ++jy) {
-        const int dy = jy * g.sigma;
-        const int cy = (qy - dy) >> 1;
-        for (int jx = jx_lo; jx <= jx_hi; ++jx) {
-            const int dx = jx * g.sigma;
-            const int cx = (qx - dx) >> 1;
-            const int d = jy * g.nDx + jx;
-            for (int k = off[d]; k < off[d + 1]; ++k) {
-                const int r = list[k];
-                const int t = iso[r] & 7;  // listed ranges have a valid domain; a bad isometry
-                                           // makes the range's own gradients NaN (k_adjoint_grads)
-                // range pixel p with src_t(p) = (cy, cx): p = src_{t^-1}(cy, cx)
-                const int tinv = (t == 1) ? 3 : (t == 3 ? 1 : t);
-                int py, px;
-                iso_src(B, tinv, cy, cx, py, px);
-                const int rq = fdiv(r, g.fRx);
-                const int ry = rq * B, rx = (r - rq * g.nRx) * B;
-                acc = fmaf((float)s[r] * 0.25f, lam[(size_t)(ry + py) * g.W + rx + px], acc);
+// The sum of phase "pixels" for pixel (qy, qx) over the domains (jy, jx) covering it, row-major,
+// and each domain's ranges in list order. MJ > 0: at most MJ domains cover a coordinate per axis,
+// and every covering domain's segment bounds are loaded before any cell; MJ = 0: any number.
+template <int B, int MJ>
+__device__ __forceinline__ float adjoint_sum(const Geo &g, const int32_t *__restrict__ off,
+                                             const float *__restrict__ acc, int jy_lo, int jy_hi, int jx_lo,
+                                             int jx_hi, int qy, int qx) {
+    float a = 0.f;
+    if constexpr (MJ > 0) {
+        int o0[MJ * MJ], o1[MJ * MJ];
+#pragma unroll
+        for (int u = 0; u < MJ; ++u)
+#pragma unroll
+            for (int v = 0; v < MJ; ++v) {
+                const bool in = jy_lo + u <= jy_hi && jx_lo + v <= jx_hi;
+                const int d = (jy_lo + u) * g.nDx + jx_lo + v;
+                o0[u * MJ + v] = in ? __ldg(off + d) : 0;
+                o1[u * MJ + v] = in ? __ldg(off + d + 1) : 0;
             }
+#pragma unroll
+        for (int u = 0; u < MJ; ++u)
+#pragma unroll
+            for (int v = 0; v < MJ; ++v) {
+                const float *cp = acc + ((qy - (jy_lo + u) * g.sigma) >> 1) * B + ((qx - (jx_lo + v) * g.sigma) >> 1);
+                for (int k = o0[u * MJ + v]; k < o1[u * MJ + v]; ++k) a += __ldg(cp + (size_t)k * (B * B));
+            }
+        return a;
+    }
+    for (int jy = jy_lo; jy <= jy_hi; ++jy) {
+        const int cy = (qy - jy * g.sigma) >> 1;
+        for (int jx = jx_lo; jx <= jx_hi; ++jx) {
+            const int d = jy * g.nDx + jx;
+            const int o1 = __ldg(off + d + 1);
+            const float *cp = acc + cy * B + ((qx - jx * g.sigma) >> 1);
+            for (int k = __ldg(off + d); k < o1; ++k) a += __ldg(cp + (size_t)k * (B * B));
         }
     }
-    lam_prev[idx] = acc;
+    return a;
 }
 
-// grad_s[r] += sum_p l[p] * T(D x)[p], grad_o[r] += sum_p l[p]; one warp per range. The terms
-// are formed in FP32 and summed in FP64 (the sums cancel heavily: terms of a few hundred add up
-// to gradients of order one), into per-range FP64 accumulators.
+// First and last domain index along one axis covering coordinate q (domains at j * sigma span
+// 2B pixels).
 template <int B>
-__global__ void k_adjoint_grads(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
-                                const float *__restrict__ x, const float *__restrict__ lam,
-                                double *__restrict__ gs, double *__restrict__ go) {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void covering(const Geo &g, int q, int n, int &lo, int &hi) {
+    hi = min(fdiv(q, g.fS), n - 1);
+    const int num = q - (2 * B - 1) + g.sigma - 1;
+    lo = num > 0 ? fdiv(num, g.fS) : 0;
+}
+
+// Phase "pixels", odd stride: l_prev = W^T l, one thread per pixel, blockIdx.y striding over rows.
+template <int B, int MJ>
+__global__ void __launch_bounds__(256)
+    k_adjoint_gather(Geo g, const int32_t *__restrict__ off, const float *__restrict__ acc,
+                     float *__restrict__ lam_prev) {
+    const int qx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qx >= g.W) return;
+    int jx_lo, jx_hi;
+    covering<B>(g, qx, g.nDx, jx_lo, jx_hi);
+    for (int qy = blockIdx.y; qy < g.H; qy += gridDim.y) {
+        int jy_lo, jy_hi;
+        covering<B>(g, qy, g.nDy, jy_lo, jy_hi);
+        lam_prev[(size_t)qy * g.W + qx] = adjoint_sum<B, MJ>(g, off, acc, jy_lo, jy_hi, jx_lo, jx_hi, qy, qx);
+    }
+}
+
+// Phase "pixels", even stride: one thread per aligned 2x2 pixel block (bx, by), whose four pixels
+// lie in the same cell of every covering domain and receive the same sum.
+template <int B, int MJ>
+__global__ void __launch_bounds__(256)
+    k_adjoint_gather2(Geo g, const int32_t *__restrict__ off, const float *__restrict__ acc,
+                      float *__restrict__ lam_prev) {
+    const int bx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * bx >= g.W) return;
+    const int qx = 2 * bx;
+    int jx_lo, jx_hi;
+    covering<B>(g, qx, g.nDx, jx_lo, jx_hi);
+    for (int by = blockIdx.y; 2 * by < g.H; by += gridDim.y) {
+        const int qy = 2 * by;
+        int jy_lo, jy_hi;
+        covering<B>(g, qy, g.nDy, jy_lo, jy_hi);
+        const float a = adjoint_sum<B, MJ>(g, off, acc, jy_lo, jy_hi, jx_lo, jx_hi, qy, qx);
+        float *q = lam_prev + (size_t)qy * g.W + qx;
+        *reinterpret_cast<float2 *>(q) = make_float2(a, a);
+        *reinterpret_cast<float2 *>(q + g.W) = make_float2(a, a);
+    }
+}
+
+// Float-float accumulation: hi + lo carries the running sum with about 44 significant bits
+// (error-free two-sum of Knuth; exact products from the fused multiply-add residual).
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// a += (bh, bl): the high parts are added with their exact rounding error (two-sum), which goes into
+// the low part with bl; the pair is renormalised once at the end (ff_norm). The low part only
+// collects rounding errors, so its own rounding is of the order of the squared unit roundoff.
+__device__ __forceinline__ void ff_add(FF &a, float bh, float bl) {
+    float s, e;
+    two_sum(a.hi, bh, s, e);
+    a.hi = s;
+    a.lo = (a.lo + bl) + e;
+}
+__device__ __forceinline__ void ff_norm(FF &a) {
+    float s, e;
+    two_sum(a.hi, a.lo, s, e);
+    a.hi = s;
+    a.lo = e;
+}
+
+// grad_s[r] += sum_p l[p] T(D x)[p], grad_o[r] += sum_p l[p]: one warp per range, the domain's
+// averages staged in shared memory as in the decode step, exact FP32 products summed in float-float
+// per lane, across the warp and into the per-range float-float accumulators (the sums cancel
+// heavily: terms of a few hundred add up to gradients of order one; FP64 arithmetic, a small
+// fraction of the FP32 rate on this part, is not used).
+template <int B, int LD>
+__global__ void __launch_bounds__(32 * kDecodeWarps)
+    k_adjoint_grads(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                    const float *__restrict__ x, const float *__restrict__ lam, float2 *__restrict__ gs,
+                    float2 *__restrict__ go) {
+    constexpr int NC = B * B / 32;
+    constexpr int PV = B == 8 ? 2 : 4;
+    __shared__ __align__(16) float cell[kDecodeWarps][B * B];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * kDecodeWarps + warp;
     if (r >= g.R) return;
-    const int d = dom[r], t = iso[r];
+    const int d = __ldg(dom + r), t = __ldg(iso + r);
     if (!valid_code(g, d, t)) {  // an invalid code: NaN gradients, no read
-        if (lane == 0) gs[r] = go[r] = __longlong_as_double(0x7ff8000000000000LL);
+        if (lane == 0) gs[r] = go[r] = make_float2(__int_as_float(0x7fc00000), 0.f);
         return;
     }
     const int rq = fdiv(r, g.fRx), dq = fdiv(d, g.fDx);
-    const int ry = rq * B, rx = (r - rq * g.nRx) * B;
-    const int dy = dq * g.sigma, dx = (d - dq * g.nDx) * g.sigma;
-    double a_s = 0.0, a_o = 0.0;
+    const float *lr = lam + (size_t)(rq * B) * g.W + (r - rq * g.nRx) * B;
+    float *cw = cell[warp];
+    load_cells<B, LD>(x + (size_t)(dq * g.sigma) * g.W + (d - dq * g.nDx) * g.sigma, g.W, lane, cw);
+    __syncwarp();
+    int c0, ky, kx;
+    iso_affine<B>(t, c0, ky, kx);
+    FF ss{0.f, 0.f}, so{0.f, 0.f};
 #pragma unroll
-    for (int h = 0; h < B * B / 32; ++h) {
-        const int p = lane + 32 * h;
-        const int y = p / B, xx = p % B;
-        int sy, sx;
-        iso_src(B, t, y, xx, sy, sx);
-        const float *q = x + (size_t)(dy + 2 * sy) * g.W + dx + 2 * sx;
-        const float v = (((q[0] + q[1]) + q[g.W]) + q[g.W + 1]) * 0.25f;
-        const float l = lam[(size_t)(ry + y) * g.W + rx + xx];
-        a_s += (double)l * (double)v;
-        a_o += (double)l;
+    for (int k = 0; k < NC / PV; ++k) {
+        const int p0 = PV * (lane + 32 * k), py = p0 / B, px = p0 % B;
+        const int s0 = c0 + ky * py + kx * px;
+        float l[PV];
+        if constexpr (PV == 2) {
+            const float2 v2 = *reinterpret_cast<const float2 *>(lr + (size_t)py * g.W + px);
+            l[0] = v2.x;
+            l[1] = v2.y;
+        } else {
+            const float4 v4 = *reinterpret_cast<const float4 *>(lr + (size_t)py * g.W + px);
+            l[0] = v4.x;
+            l[1] = v4.y;
+            l[2] = v4.z;
+            l[3] = v4.w;
+        }
+#pragma unroll
+        for (int i = 0; i < PV; ++i) {
+            const float v = cw[s0 + i * kx];
+            const float ph = l[i] * v;
+            ff_add(ss, ph, fmaf(l[i], v, -ph));
+            ff_add(so, l[i], 0.f);
+        }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        a_s += __shfl_xor_sync(0xffffffffu, a_s, off);
-        a_o += __shfl_xor_sync(0xffffffffu, a_o, off);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float sh = __shfl_xor_sync(0xffffffffu, ss.hi, o), sl = __shfl_xor_sync(0xffffffffu, ss.lo, o);
+        const float oh = __shfl_xor_sync(0xffffffffu, so.hi, o), ol = __shfl_xor_sync(0xffffffffu, so.lo, o);
+        ff_add(ss, sh, sl);
+        ff_add(so, oh, ol);
     }
     if (lane == 0) {
-        gs[r] += a_s;
-        go[r] += a_o;
+        FF a{gs[r].x, gs[r].y}, b{go[r].x, go[r].y};
+        ff_add(a, ss.hi, ss.lo);
+        ff_add(b, so.hi, so.lo);
+        ff_norm(a);
+        ff_norm(b);
+        gs[r] = make_float2(a.hi, a.lo);
+        go[r] = make_float2(b.hi, b.lo);
     }
 }
 
-__global__ void k_grads_out(int R, const double *__restrict__ gs64, const double *__restrict__ go64,
+__global__ void k_grads_out(int R, const float2 *__restrict__ gsf, const float2 *__restrict__ gof,
                             float *__restrict__ gs, float *__restrict__ go) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < R) {
-        gs[r] = (float)gs64[r];
-        go[r] = (float)go64[r];
+        gs[r] = gsf[r].x + gsf[r].y;
+        go[r] = gof[r].x + gof[r].y;
     }
 }
 
-cudaError_t launch_dom_csr(const Geo &g, const int32_t *dom, const double *s, int32_t *cnt, int32_t *off,
-                           int32_t *cursor, int32_t *list, cudaStream_t st) {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * g.Dn, st))) return e;
-    k_dom_count<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, s, cnt);
+size_t adjoint_csr_ints(const Geo &g) { return (size_t)g.Dn + 1 + 4 * (size_t)g.R + radix_counts_ints(g.R); }
+size_t adjoint_entries(const Geo &g) { return (size_t)g.R; }
+
+cudaError_t launch_dom_csr(const Geo &g, const fic_codes &c, const AdjointCsr &a, cudaStream_t st) {
+    const unsigned gr = (unsigned)((g.R + 255) / 256);
+    k_csr_keys<<<gr, 256, 0, st>>>(g, c.dom, c.iso, c.s, a.key);
     ++g_launches;
-    k_scan_single<<<1, 1024, 0, st>>>(cnt, g.Dn, off, cursor);
+    cudaError_t e = launch_radix_sort(a.key, g.R, (uint32_t)g.Dn, a.list, a.t1, a.t2, a.digit, a.counts, st);
+    if (e) return e;
+    k_csr_sorted_keys<<<gr, 256, 0, st>>>(g.R, a.key, a.list, c.iso, c.s, a.t1, a.ent);
     ++g_launches;
-    k_dom_fill<<<(g.R + 255) / 256, 256, 0, st>>>(g, dom, s, cursor, list);
-    ++g_launches;
-    k_dom_sortseg<<<(g.Dn + 255) / 256, 256, 0, st>>>(g.Dn, off, list);
+    k_csr_offsets<<<(unsigned)((g.Dn + 1 + 255) / 256), 256, 0, st>>>(g.R, g.Dn, a.t1, a.off);
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const int32_t *off,
-                                  const int32_t *list, const float *lam, float *lam_prev,
-                                  cudaStream_t st) {
-    const int n = g.H * g.W;
-    if (g.B == 16)
-        k_adjoint_gather<16><<<(n + 255) / 256, 256, 0, st>>>(g, c.iso, c.s, off, list, lam, lam_prev);
+// The pixel phase for this geometry: the 2x2-block form for even strides, with every covering
+// domain's bounds loaded first when at most 2 or 4 domains cover a coordinate per axis.
+template <int B, int MJ>
+void gather_px(const Geo &g, const AdjointCsr &a, float *lam_prev, cudaStream_t st) {
+    const bool even = g.sigma % 2 == 0;  // lam_prev is a workspace buffer: 8-byte aligned
+    const int cols = even ? g.W / 2 : g.W, rows = even ? g.H / 2 : g.H;
+    const dim3 px((unsigned)((cols + 255) / 256), (unsigned)min(rows, 65535));
+    if (even)
+        k_adjoint_gather2<B, MJ><<<px, 256, 0, st>>>(g, a.off, a.acc, lam_prev);
     else
-        k_adjoint_gather<8><<<(n + 255) / 256, 256, 0, st>>>(g, c.iso, c.s, off, list, lam, lam_prev);
-    ++g_launches;
+        k_adjoint_gather<B, MJ><<<px, 256, 0, st>>>(g, a.off, a.acc, lam_prev);
+}
+
+template <int B>
+void adjoint_gather_b(const Geo &g, const AdjointCsr &a, const float *lam, float *lam_prev, cudaStream_t st) {
+    const unsigned cells = (unsigned)(((long long)g.R * 32 + 255) / 256);
+    k_adjoint_cells<B><<<cells, 256, 0, st>>>(g, a.ent, a.off, lam, a.acc);
+    // covering domains per axis: at most ceil(2B / sigma)
+    const int mj = (2 * B + g.sigma - 1) / g.sigma;
+    if (mj <= 2)
+        gather_px<B, 2>(g, a, lam_prev, st);
+    else if (mj <= 4)
+        gather_px<B, 4>(g, a, lam_prev, st);
+    else
+        gather_px<B, 0>(g, a, lam_prev, st);
+}
+
+cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const AdjointCsr &a, const float *lam,
+                                  float *lam_prev, cudaStream_t st) {
+    (void)c;
+    if (g.B == 16)
+        adjoint_gather_b<16>(g, a, lam, lam_prev, st);
+    else
+        adjoint_gather_b<8>(g, a, lam, lam_prev, st);
+    g_launches += 2;
     return cudaGetLastError();
+}
+
+template <int B>
+void adjoint_grads_b(int ld, unsigned blocks, const Geo &g, const fic_codes &c, const float *x, const float *lam,
+                     float2 *gs, float2 *go, cudaStream_t st) {
+    if (ld == 4)
+        k_adjoint_grads<B, 4><<<blocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
+    else if (ld == 2)
+        k_adjoint_grads<B, 2><<<blocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
+    else
+        k_adjoint_grads<B, 1><<<blocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
 }
 
 cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *x, const float *lam,
-                                 double *gs, double *go, cudaStream_t st) {
-    const long long threads = (long long)g.R * 32;
+                                 float2 *gs, float2 *go, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((g.R + kDecodeWarps - 1) / kDecodeWarps);
+    const uintptr_t xa = (uintptr_t)x;
+    const int ld = (g.sigma % 4 == 0 && xa % 16 == 0) ? 4 : (g.sigma % 2 == 0 && xa % 8 == 0) ? 2 : 1;
     if (g.B == 16)
-        k_adjoint_grads<16><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
+        adjoint_grads_b<16>(ld, blocks, g, c, x, lam, gs, go, st);
     else
-        k_adjoint_grads<8><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, x, lam, gs, go);
+        adjoint_grads_b<8>(ld, blocks, g, c, x, lam, gs, go, st);
     ++g_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_grads_out(int R, const double *gs64, const double *go64, float *gs, float *go,
-                             cudaStream_t st) {
-    k_grads_out<<<(R + 255) / 256, 256, 0, st>>>(R, gs64, go64, gs, go);
+cudaError_t launch_grads_out(int R, const float2 *gsf, const float2 *gof, float *gs, float *go, cudaStream_t st) {
+    k_grads_out<<<(R + 255) / 256, 256, 0, st>>>(R, gsf, gof, gs, go);
     ++g_launches;
     return cudaGetLastError();
 }

@@ -41,7 +41,7 @@ struct Geo {
     int nDy, nDx, Dn;    // domain grid
     int K, w;            // classes and pool half-width (Section 3.1 Eq. 2-3)
     int literal;         // 1: Eq. 3 window on FD values (FIC_FLAG_LITERAL_WINDOW)
-    FastDiv fRx, fDx;    // division by nRx and by nDx
+    FastDiv fRx, fDx, fS;  // division by nRx, by nDx and by sigma
     int group_chunks;    // tensor engine: chunk cap of a domain group
     int stages;          // tensor engine: B-operand ring stages (0: the kernel's default)
 };
@@ -453,6 +453,19 @@ cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encod
 cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,
                                cudaStream_t st);
 cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st);
+// Domain -> ranges index of the adjoint (decode.cu): key[R], list[R] (range ids sorted by domain),
+// t1[R], t2[R] sort buffers, off[Dn + 1] segment starts, digit[R] bytes, counts (radix
+// histograms), acc[R * B * B] per-domain accumulated cells (at each domain's segment start).
+struct AdjointCsr {
+    int32_t *key, *list, *t1, *t2, *off, *counts;
+    uint8_t *digit;
+    int4 *ent;   // [R] per list position: (range id, isometry, s / 4 as float bits, 0)
+    float *acc;
+};
+// Stable sort of 0 .. n-1 by key (pools.cu); scratch sizes: see launch_radix_sort.
+size_t radix_counts_ints(int n);
+cudaError_t launch_radix_sort(const int32_t *key, int n, uint32_t key_max, int32_t *perm, int32_t *t1, int32_t *t2,
+                              uint8_t *digit, int32_t *counts, cudaStream_t st);
 // Validates the geometry and parameters of one image and derives its grids (the checks every entry
 // point applies); sets the thread's error message on failure.
 fic_status make_geometry(const fic_geom *gm, const fic_params *p, Geo *g);

@@ -254,4 +254,58 @@ cudaError_t launch_pools_windows(const Geo &g, const EncodeBufs &b, cudaStream_t
 
 int sort_buckets(const Geo &g) { return g.literal ? fd_ranks().n : g.K; }
 
+// ---- stable LSD radix sort of int keys, one byte per counting-sort pass ----------------------
+// digit[i] = byte `shift / 8` of key[perm[i]] (of key[i] when perm is null).
+__global__ void k_radix_digit(const int32_t *__restrict__ key, const int32_t *__restrict__ perm, int n, int shift,
+                              uint8_t *__restrict__ digit) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) digit[i] = (uint8_t)((uint32_t)key[perm ? perm[i] : i] >> shift);
+}
+
+// out[j] = perm[order[j]]: the pass's stable order of positions, as indices into the keys.
+__global__ void k_radix_compose(const int32_t *__restrict__ perm, const int32_t *__restrict__ order, int n,
+                                int32_t *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = perm[order[j]];
+}
+
+size_t radix_counts_ints(int n) { return (size_t)((n + kSortChunk - 1) / kSortChunk) * 256 + 257; }
+
+// perm = the indices 0 .. n-1 ordered stably by key (0 <= key <= key_max): one counting-sort pass
+// per byte of key_max, least significant first; each pass sorts stably by its byte the order the
+// previous passes produced. Scratch: digit[n] bytes, t1[n], t2[n] ints, counts[radix_counts_ints(n)].
+cudaError_t launch_radix_sort(const int32_t *key, int n, uint32_t key_max, int32_t *perm, int32_t *t1, int32_t *t2,
+                              uint8_t *digit, int32_t *counts, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int passes = 1;
+    while (passes < 4 && (key_max >> (8 * passes)) != 0) ++passes;
+    const int nblk = (n + kSortChunk - 1) / kSortChunk;
+    int32_t *bin_off = counts + (size_t)nblk * 256;  // the scatter's class offsets, not used here
+    const unsigned g = (unsigned)((n + 255) / 256);
+    // buffers: perm, t1, t2. The first pass's order is the current order; every later pass sorts
+    // into one free buffer and composes into the other, which becomes current (perm on the last
+    // pass when it is free, so that no copy is needed)
+    int32_t *buf[3] = {perm, t1, t2};
+    int cur = -1;
+    for (int pass = 0; pass < passes; ++pass) {
+        k_radix_digit<<<g, 256, 0, st>>>(key, cur < 0 ? nullptr : buf[cur], n, 8 * pass, digit);
+        ++g_launches;
+        if (cur < 0) {
+            cur = passes == 1 ? 0 : 1;
+            cudaError_t e = counting_sort(digit, n, 256, counts, buf[cur], bin_off, st);
+            if (e) return e;
+            continue;
+        }
+        const int nxt = (pass == passes - 1 && cur != 0) ? 0 : (cur == 1 ? 2 : 1);
+        const int ord = 3 - cur - nxt;
+        cudaError_t e = counting_sort(digit, n, 256, counts, buf[ord], bin_off, st);
+        if (e) return e;
+        k_radix_compose<<<g, 256, 0, st>>>(buf[cur], buf[ord], n, buf[nxt]);
+        ++g_launches;
+        cur = nxt;
+    }
+    if (cur != 0) return cudaMemcpyAsync(perm, buf[cur], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
+}
+
 }  // namespace fic
