@@ -27,6 +27,8 @@
  *    returns FIC_ERR_INVALID_ARG (or FIC_ERR_WORKSPACE) and enqueues nothing.
  *  - A launch failure returns FIC_ERR_CUDA. fic_last_error() returns a message for the last
  *    failure on the calling thread.
+ *  - Each entry point marks its host call with an NVTX range named after it (seen by profilers
+ *    that record NVTX; nothing is recorded otherwise).
  *  - Images are row-major uint8 with row pitch `pitch` >= W bytes. Ranges are numbered
  *    row-major: range r covers rows (r / (W/B))*B .. +B-1 and columns (r % (W/B))*B .. +B-1.
  *    Domains are numbered row-major over the stride grid: domain d has its top-left pixel at

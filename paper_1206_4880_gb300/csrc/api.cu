@@ -443,6 +443,7 @@ static fic_status carve_batch(const fic_geom *geoms, int n, const fic_params *p,
 
 fic_status fic_classify(const uint8_t *img, const fic_geom *gm, const fic_params *p,
                         const fic_blockstats *out, void *ws, size_t bytes, void *stream) {
+    NvtxRange nvtx_range("fic_classify");
     std::vector<Geo> gv;
     std::vector<EncodeBufs> bv;
     TcBatch tb;
@@ -473,6 +474,7 @@ fic_status fic_classify(const uint8_t *img, const fic_geom *gm, const fic_params
 
 fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *gm, const fic_params *p,
                            const fic_pools *out, void *ws, size_t bytes, void *stream) {
+    NvtxRange nvtx_range("fic_build_pools");
     std::vector<Geo> gv;
     std::vector<EncodeBufs> bv;
     TcBatch tb;
@@ -742,6 +744,7 @@ extern "C" {
 fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *p,
                       const fic_codes *out, fic_encode_info *info, void *ws, size_t bytes,
                       void *stream) {
+    NvtxRange nvtx_range("fic_encode");
     const uint8_t *imgs[1] = {img};
     if (!out) return fail(FIC_ERR_INVALID_ARG, "null code pointer");
     cudaStream_t st = (cudaStream_t)stream;
@@ -776,6 +779,7 @@ fic_status fic_encode(const uint8_t *img, const fic_geom *gm, const fic_params *
 
 fic_status fic_encode_fallback_ranges(const fic_geom *gm, const fic_params *p, void *ws, size_t bytes,
                                       int32_t *ids, int32_t max_ids, int32_t *count, void *stream) {
+    NvtxRange nvtx_range("fic_encode_fallback_ranges");
     std::vector<Geo> gv;
     std::vector<EncodeBufs> bv;
     TcBatch tb;
@@ -793,10 +797,12 @@ fic_status fic_encode_fallback_ranges(const fic_geom *gm, const fic_params *p, v
 fic_status fic_encode_batched(const uint8_t *const *imgs, const fic_geom *geoms, int32_t n,
                               const fic_params *p, const fic_codes *outs, fic_encode_info *info,
                               void *ws, size_t bytes, void *stream) {
+    NvtxRange nvtx_range("fic_encode_batched");
     return encode_batch(imgs, geoms, n, p, outs, info, ws, bytes, stream);
 }
 
 fic_status fic_quality(const float *x, const uint8_t *ref, const fic_geom *gm, double *out, void *stream) {
+    NvtxRange nvtx_range("fic_quality");
     if (!x || !ref || !gm || !out) return fail(FIC_ERR_INVALID_ARG, "null pointer");
     if (gm->H < 1 || gm->W < 1 || gm->pitch < gm->W) return fail(FIC_ERR_INVALID_ARG, "bad geometry");
     g_launches = 0;
@@ -806,6 +812,7 @@ fic_status fic_quality(const float *x, const uint8_t *ref, const fic_geom *gm, d
 
 fic_status fic_quantize(const fic_codes *in, int32_t n, int32_t bits_s, int32_t bits_o, uint16_t *q_s,
                         uint16_t *q_o, double *header, const fic_codes *out, void *stream) {
+    NvtxRange nvtx_range("fic_quantize");
     if (!in || !in->dom || !in->iso || !in->s || !in->o || !out || !out->dom || !out->iso || !out->s ||
         !out->o || !q_s || !q_o || !header)
         return fail(FIC_ERR_INVALID_ARG, "null pointer");
@@ -836,6 +843,7 @@ fic_status fic_profile_read(float *ms, int32_t n, int32_t *launches) {
 }
 
 fic_status fic_check(void *stream) {
+    NvtxRange nvtx_range("fic_check");
     FIC_TRY(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
     int32_t v = 0;
     FIC_TRY(cudaMemcpyFromSymbol(&v, g_device_error, sizeof v), "reading the device error word");
@@ -924,6 +932,7 @@ extern "C" {
 fic_status fic_decode(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
                       int32_t iters, const float *x0, float *out, void *ws, size_t bytes,
                       void *stream) {
+    NvtxRange nvtx_range("fic_decode");
     Geo g{};
     fic_status s = make_geo(gm, p, &g);
     if (s != FIC_OK) return s;
@@ -961,6 +970,7 @@ size_t fic_decode_scaled_workspace_size(const fic_geom *gm, const fic_params *p,
 
 fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *gm, const fic_params *p, int32_t scale,
                              int32_t iters, const float *x0, float *out, void *ws, size_t bytes, void *stream) {
+    NvtxRange nvtx_range("fic_decode_scaled");
     Geo g{};
     fic_status s = make_geo(gm, p, &g);
     if (s != FIC_OK) return s;
@@ -996,6 +1006,7 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
                                int32_t iters, int32_t ckpt_every, const float *x0,
                                const float *grad_out, float *grad_s, float *grad_o, void *ws,
                                size_t bytes, void *stream) {
+    NvtxRange nvtx_range("fic_decode_backward");
     Geo g{};
     fic_status s = make_geo(gm, p, &g);
     if (s != FIC_OK) return s;

@@ -64,6 +64,7 @@ cudaError_t scratch_for_current_device(float **ptr) {
 extern "C" fic_status fic_decode_static(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
                                         int32_t iters, const float *x0, float *out, void *stream) {
     using namespace fic;
+    NvtxRange nvtx_range("fic_decode_static");
     // geometry and parameters pass the same checks, and give the same grids, as in fic_decode
     Geo g{};
     const fic_status gs = make_geometry(gm, p, &g);

@@ -3,6 +3,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/fic.h"
@@ -10,6 +11,15 @@
 namespace fic {
 
 constexpr int kMaxClasses = 255;
+
+// An NVTX range named after the entry point for the duration of a host call (what a profiler's
+// timeline shows as the call's enqueue time; nothing is recorded unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Kernels launched by the current fic_* call on this thread (reset at each entry point).
 extern thread_local int g_launches;
