@@ -532,9 +532,17 @@ def large(args, dev):
     peaks, peak_src = _peaks()
     peak = float(peaks["bf16_tflops"])
     res = {"image": "4096x4096 seeded fBm+edges (seed 5000); stride-8 domains, K=32, w=10"}
+    from paper_1206_4880_gb300 import autotune
     for B in (8, 16):
         p = fic.EncodeParams(domain_stride=8, num_classes=32, half_width=-1, engine=args.engine, block=B)
         R, Dn = fic.counts(H, W, p)
+        # the tile pipeline and schedule shapes on this single large image (operands beyond L2)
+        tune = None
+        if args.engine == "tensor":
+            best, tms, noise = autotune.tune([img], p, reps=2, use_cache=False)
+            tune = {"variant": best, "ms": tms, "noise_ms": noise,
+                    "spread_ms": max(tms.values()) - min(tms.values())}
+            torch.cuda.empty_cache()
         ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)
         info = fic.new_info(dev)
         out = fic.encode(img, p, workspace=ws, info=info)
@@ -568,6 +576,8 @@ def large(args, dev):
                         "fallback_ranges": rep["fallback_ranges"], "work_items": rep["work_items"],
                         "device_error": rep["device_error"], "psnr_db": psnr,
                         **decode_rates(out, H, W, p, flush, float(peaks["hbm_gbs"]))}
+        if tune is not None:
+            res[f"b{B}"]["autotune"] = tune
         del ws, out
     res["peak_source"] = f"{peak_src} bf16 dense burst x nominal fp16/bf16 ratio 1.0"
     return res

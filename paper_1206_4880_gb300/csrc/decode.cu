@@ -130,59 +130,85 @@ __global__ void __launch_bounds__(32 * kDecodeWarps)
     }
 }
 
-// The same step for 8x8 ranges with 16-byte source loads: one half-warp per range, so one warp's
-// instructions keep two ranges' loads in flight. Lane hl of a half loads the top and bottom rows of
-// cell pairs hl and hl + 16 (cell rows hl / 4 and hl / 4 + 4) and writes four adjacent pixels.
+// The same step for 8x8 ranges with 16-byte source loads: one half-warp per NR ranges (ranges
+// hw, hw + 16, ... of the block's 16 NR), with every range's code and source rows loaded before
+// any is used, so one warp's instructions keep 2 NR ranges' loads in flight. Lane hl of a half
+// loads the top and bottom rows of cell pairs hl and hl + 16 (cell rows hl / 4 and hl / 4 + 4) of
+// each range and writes four adjacent pixels of each.
+constexpr int kDecodeNR = 2;
+
 template <bool VS>
 __global__ void __launch_bounds__(32 * kDecodeWarps)
     k_decode_step8h(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
                     const double *__restrict__ s, const double *__restrict__ o, const float *__restrict__ x,
                     float *__restrict__ y) {
-    __shared__ __align__(16) float cell[2 * kDecodeWarps][64];
+    constexpr int NR = kDecodeNR, HW = 2 * kDecodeWarps;
+    __shared__ __align__(16) float cell[HW][NR][64];
     const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
     const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
-    const int r = blockIdx.x * (2 * kDecodeWarps) + hw;
-    if (r >= g.R) return;  // whole half-warps leave together; only half-warp barriers follow
-    const int d = __ldg(dom + r), t = __ldg(iso + r);
-    const int rq = fdiv(r, g.fRx), dq = fdiv(d, g.fDx);
-    float *dst = y + (size_t)(rq * 8) * g.W + (r - rq * g.nRx) * 8;
-    if (!valid_code(g, d, t)) {  // an invalid code (an encode that gave up): NaN pixels, no read
+    int r[NR], d[NR], t[NR];
+    bool use[NR];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            dst[(size_t)((hl + 16 * k) / 8) * g.W + (hl + 16 * k) % 8] = __int_as_float(0x7fc00000);
-        return;
+    for (int k = 0; k < NR; ++k) {
+        r[k] = blockIdx.x * (HW * NR) + k * HW + hw;
+        d[k] = t[k] = 0;
+        use[k] = false;
+        if (r[k] < g.R) {
+            d[k] = __ldg(dom + r[k]);
+            t[k] = __ldg(iso + r[k]);
+            use[k] = valid_code(g, d[k], t[k]);
+        }
     }
-    const float sr = (float)__ldg(s + r), orr = (float)__ldg(o + r);
-    const float *src = x + (size_t)(dq * g.sigma) * g.W + (d - dq * g.nDx) * g.sigma;
-    float *cw = cell[hw];
-    float4 a[2], b[2];
+    float4 a[NR][2], b[NR][2];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int q = hl + 16 * k, cy = q >> 2, cp = q & 3;  // cells (cy, 2cp), (cy, 2cp + 1)
-        const float *p = src + (size_t)(2 * cy) * g.W + 4 * cp;
-        a[k] = __ldg(reinterpret_cast<const float4 *>(p));
-        b[k] = __ldg(reinterpret_cast<const float4 *>(p + g.W));
+    for (int k = 0; k < NR; ++k) {
+        if (!use[k]) continue;
+        const int dq = fdiv(d[k], g.fDx);
+        const float *src = x + (size_t)(dq * g.sigma) * g.W + (d[k] - dq * g.nDx) * g.sigma;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = hl + 16 * h, cy = q >> 2, cp = q & 3;  // cells (cy, 2cp), (cy, 2cp + 1)
+            const float *p = src + (size_t)(2 * cy) * g.W + 4 * cp;
+            a[k][h] = __ldg(reinterpret_cast<const float4 *>(p));
+            b[k][h] = __ldg(reinterpret_cast<const float4 *>(p + g.W));
+        }
     }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int q = hl + 16 * k, cy = q >> 2, cp = q & 3;
-        *reinterpret_cast<float2 *>(&cw[cy * 8 + 2 * cp]) =
-            make_float2((((a[k].x + a[k].y) + b[k].x) + b[k].y) * 0.25f, (((a[k].z + a[k].w) + b[k].z) + b[k].w) * 0.25f);
+    for (int k = 0; k < NR; ++k) {
+        if (!use[k]) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = hl + 16 * h, cy = q >> 2, cp = q & 3;
+            *reinterpret_cast<float2 *>(&cell[hw][k][cy * 8 + 2 * cp]) =
+                make_float2((((a[k][h].x + a[k][h].y) + b[k][h].x) + b[k][h].y) * 0.25f,
+                            (((a[k][h].z + a[k][h].w) + b[k][h].z) + b[k][h].w) * 0.25f);
+        }
     }
     __syncwarp(hmask);
-    int c0, ky, kx;
-    iso_affine<8>(t, c0, ky, kx);
-    const int py = hl >> 1, px = 4 * (hl & 1);
-    const int s0 = c0 + ky * py + kx * px;
-    float v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = fmaf(sr, cw[s0 + i * kx], orr);
-    float *q = dst + (size_t)py * g.W + px;
-    if constexpr (VS) {
-        *reinterpret_cast<float4 *>(q) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
+    for (int k = 0; k < NR; ++k) {
+        if (r[k] >= g.R) continue;
+        const int rq = fdiv(r[k], g.fRx);
+        const int py = hl >> 1, px = 4 * (hl & 1);
+        float *q = y + (size_t)(rq * 8 + py) * g.W + (r[k] - rq * g.nRx) * 8 + px;
+        float v[4];
+        if (use[k]) {
+            const float sr = (float)__ldg(s + r[k]), orr = (float)__ldg(o + r[k]);
+            int c0, ky, kx;
+            iso_affine<8>(t[k], c0, ky, kx);
+            const int s0 = c0 + ky * py + kx * px;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) q[i] = v[i];
+            for (int i = 0; i < 4; ++i) v[i] = fmaf(sr, cell[hw][k][s0 + i * kx], orr);
+        } else {  // an invalid code (an encode that gave up): NaN pixels, no read
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = __int_as_float(0x7fc00000);
+        }
+        if constexpr (VS) {
+            *reinterpret_cast<float4 *>(q) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = v[i];
+        }
     }
 }
 
@@ -219,7 +245,7 @@ cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x,
     if (g.B == 16) {
         decode_step_b<16>(ld, vs, blocks, g, c, x, y, st);
     } else if (ld == 4) {
-        const unsigned hblocks = (unsigned)((g.R + 2 * kDecodeWarps - 1) / (2 * kDecodeWarps));
+        const unsigned hblocks = (unsigned)((g.R + 2 * kDecodeWarps * kDecodeNR - 1) / (2 * kDecodeWarps * kDecodeNR));
         if (ya % 16 == 0)
             k_decode_step8h<true><<<hblocks, 32 * kDecodeWarps, 0, st>>>(g, c.dom, c.iso, c.s, c.o, x, y);
         else
