@@ -310,7 +310,8 @@ def run_ours(args, wl, world, rank, local):
     H, W = img_np.shape
     img = torch.from_numpy(img_np).to(dev)
     p = fic.EncodeParams(domain_stride=wl["sigma"], num_classes=wl["K"], half_width=wl["w"],
-                         engine=args.engine, block=wl["block"])
+                         engine=args.engine, block=wl["block"], pipeline_stages=args.pipeline_stages,
+                         group_chunks=args.group_chunks, items_per_sm=args.items_per_sm)
     R, Dn = fic.counts(H, W, p)
     ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)
     out = fic.alloc_codes(R, dev)
@@ -428,6 +429,8 @@ def run_ours(args, wl, world, rank, local):
                         else "u8 pixels; f32 FMA on exact integers, int64 gains, f64 codes",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "engine": args.engine,
+                   "shape": {"pipeline_stages": args.pipeline_stages, "group_chunks": args.group_chunks,
+                             "items_per_sm": args.items_per_sm},
                    "l2": "flushed (256 MiB write) before every step, untimed",
                    "launch": "one fic_encode call captured in a CUDA graph, replayed per step; stage and "
                              "matcher times from replays of a capture with the library's stage events",
@@ -816,6 +819,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--pipeline-stages", type=int, default=0, help="tensor matcher ring stages (0: library default)")
+    ap.add_argument("--group-chunks", type=int, default=0, help="chunks per domain group (0: library default)")
+    ap.add_argument("--items-per-sm", type=int, default=0, help="work items per SM (0: library default)")
     ap.add_argument("--case", choices=("decode", "backward", "classify"), default=None,
                     help="time one stage alone on the workload (for profiling) instead of the encode")
     args = ap.parse_args()
