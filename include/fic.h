@@ -96,7 +96,7 @@ typedef struct {
                               (block 16). Smaller groups need a larger workspace (size queries take
                               it into account). */
     int32_t pipeline_stages; /* tensor engine: shared-memory stages of the streamed domain operand,
-                                3 or 4 (block 8), 4 or 5 (block 16); 0 selects 4 (block 8) or 5
+                                3 or 4 (block 8), 4 or 5 (block 16); 0 selects 3 (block 8) or 4
                                 (block 16). Results do not depend on it. */
 } fic_params;
 

@@ -290,8 +290,8 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->dom_key = c.take<uint8_t>(g.Dn);
         b->range_key = c.take<uint8_t>(g.R);
         // per-block class histograms: of the domain sort and of the range sort
-        b->sort_counts = c.take<int32_t>((size_t)sort_blocks * 256);
-        b->sort_offs = c.take<int32_t>((size_t)sort_blocks * 256);
+        b->sort_counts = c.take<int32_t>(sort_counts_ints(sort_blocks * kSortChunk));
+        b->sort_offs = c.take<int32_t>(sort_counts_ints(sort_blocks * kSortChunk));
         b->fallback = c.take<int32_t>(g.R);
         b->fb_best = c.take<FallbackBest>(g.R);
         b->counters = img_counters ? img_counters + 8 * k : nullptr;

@@ -338,8 +338,8 @@ struct EncodeBufs {
     int32_t *dom_order, *bin_off, *range_order, *rbin_off, *win_lo, *win_hi;
     uint8_t *dom_key, *range_key;  // [Dn], [R] sort keys (class, or FD rank in literal mode)
     int nbuckets;          // sort buckets: K, or the number of distinct FD values
-    int32_t *sort_counts;  // [nblk][256] per-block class histograms of the domain sort
-    int32_t *sort_offs;    // [nblk][256] the same for the range sort
+    int32_t *sort_counts;  // [256][nblk rounded up to 4] per-block class histograms of the domain sort
+    int32_t *sort_offs;    // the same for the range sort
     // tensor engine: this image's slice of the batch-wide arrays (TcBatch)
     __half *A_mat;         // [R_pad][n]   range pixels - a, class-sorted ranges
     __half *B_mat;         // [8 Dn_aux][n] T_t(S_d) - c, class-sorted domains x isometries
@@ -397,7 +397,10 @@ __device__ __forceinline__ void poison_code(const fic_codes &out, int r) {
     out.sse[r] = nan;
 }
 
-constexpr int kSortChunk = 1024;  // elements per counting-sort block
+constexpr int kSortChunk = 1024;  // elements per counting-sort block (4 per histogram thread)
+// ints of a counting sort's block histograms for n keys: 256 classes x the block count rounded up
+// to a multiple of 4
+inline size_t sort_counts_ints(int n) { return (size_t)(((n + kSortChunk - 1) / kSortChunk + 3) & ~3) * 256; }
 constexpr int kTileM = 128;       // rows of one MMA (ranges per B = 8 range tile)
 constexpr int kTileDom = 32;      // domains per accumulator tile (8 isometries -> N = 256)
 constexpr int kChunkTiles = 16;   // accumulator tiles per chunk (the re-search granule)

@@ -16,81 +16,87 @@
 
 namespace fic {
 
-// Per-block class histograms: counts[blk * 256 + k].
-__global__ void k_sort_hist(const uint8_t *__restrict__ keys, int n, int32_t *__restrict__ counts) {
+// Per-block class histograms of kSortChunk keys each, stored class-major: counts[k * nb4 + blk],
+// nb4 = the block count rounded up to a multiple of 4 (pad entries zero), so that one class's
+// counts over all blocks are contiguous 16-byte vectors for the scatter.
+__global__ void __launch_bounds__(256) k_sort_hist(const uint8_t *__restrict__ keys, int n, int nb4,
+                                                   int32_t *__restrict__ counts) {
     __shared__ int h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    h[threadIdx.x] = 0;
     __syncthreads();
     const int base = blockIdx.x * kSortChunk;
-    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x)
-        if (base + i < n) atomicAdd(&h[keys[base + i]], 1);
+    const int i0 = base + 4 * threadIdx.x;  // four keys per thread: kSortChunk = 4 x 256
+    if (i0 + 3 < n) {
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(keys + i0));  // base is 4-aligned
+#pragma unroll
+        for (int k = 0; k < 4; ++k) atomicAdd(&h[(w >> (8 * k)) & 0xFFu], 1);
+    } else {
+        for (int i = i0; i < n && i < i0 + 4; ++i) atomicAdd(&h[keys[i]], 1);
+    }
     __syncthreads();
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) counts[blockIdx.x * 256 + k] = h[k];
+    counts[(size_t)threadIdx.x * nb4 + blockIdx.x] = h[threadIdx.x];
+    if (blockIdx.x == gridDim.x - 1)
+        for (int b = gridDim.x; b < nb4; ++b) counts[(size_t)threadIdx.x * nb4 + b] = 0;
 }
 
 // Stable scatter: block b places its kSortChunk keys, in index order, after the elements of the
-// same class from blocks < b. Each block first forms its own bases from every block's histogram:
+// same class from blocks < b. Threads 0..255 first form the bases from every block's histogram:
 // thread k sums class k over the blocks before b and over all blocks, an exclusive scan of the
 // totals gives the class starts (block 0 also stores them as bin_off[0 .. K], bin_off[K] = n).
-// Within a 256-element step, a thread's rank among equal keys is (earlier warps' counts) +
-// (earlier lanes with the same key).
-__global__ void __launch_bounds__(256) k_sort_scatter(const uint8_t *__restrict__ keys, int n, int nblk, int K,
-                                                      const int32_t *__restrict__ counts,
-                                                      int32_t *__restrict__ order, int32_t *__restrict__ bin_off) {
+// One thread per key: its rank among equal keys is (earlier warps' counts of the key) + (earlier
+// lanes with the same key).
+__global__ void __launch_bounds__(kSortChunk) k_sort_scatter(const uint8_t *__restrict__ keys, int n, int nb4,
+                                                             int K, const int32_t *__restrict__ counts,
+                                                             int32_t *__restrict__ order,
+                                                             int32_t *__restrict__ bin_off) {
+    constexpr int NW = kSortChunk / 32;
     __shared__ int run[256];
-    __shared__ int wc[8][256];
+    __shared__ int wtot[8];
+    __shared__ int wc[NW][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    {
-        int tot = 0, before = 0;
-#pragma unroll 4
-        for (int b = 0; b < nblk; ++b) {
-            const int c = counts[b * 256 + tid];
-            tot += c;
-            before += b < (int)blockIdx.x ? c : 0;
+    for (int j = tid; j < NW * 256; j += kSortChunk) (&wc[0][0])[j] = 0;
+    int tot = 0, incl = 0, before = 0;
+    if (tid < 256) {
+        const int4 *col = reinterpret_cast<const int4 *>(counts + (size_t)tid * nb4);
+        const int b0 = blockIdx.x;
+#pragma unroll 8
+        for (int q = 0; q < nb4 / 4; ++q) {
+            const int4 v = __ldg(col + q);
+            const int bb = 4 * q;
+            tot += (v.x + v.y) + (v.z + v.w);
+            before += (bb < b0 ? v.x : 0) + (bb + 1 < b0 ? v.y : 0) + (bb + 2 < b0 ? v.z : 0) + (bb + 3 < b0 ? v.w : 0);
         }
-        // exclusive scan of the class totals over the 256 classes
-        int incl = tot;
+        // exclusive scan of the class totals over the 256 classes (warps 0..7)
+        incl = tot;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += v;
         }
-        if (lane == 31) wc[0][warp] = incl;
-        __syncthreads();
+        if (lane == 31) wtot[warp] = incl;
+    }
+    const int i = blockIdx.x * kSortChunk + tid;
+    const bool valid = i < n;
+    const int key = valid ? (int)keys[i] : 256 + lane;  // invalid lanes never match others
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    __syncthreads();  // wc zeroed, wtot written
+    if (valid && rank == 0) wc[warp][key] = __popc(peers);
+    if (tid < 256) {
         int wbase = 0;
-        for (int w = 0; w < warp; ++w) wbase += wc[0][w];
+        for (int w = 0; w < warp; ++w) wbase += wtot[w];
         const int start = wbase + incl - tot;
         run[tid] = start + before;
         if (blockIdx.x == 0) {
             if (tid < K) bin_off[tid] = start;
             if (tid == 0) bin_off[K] = n;
         }
-        __syncthreads();
     }
-    const int base = blockIdx.x * kSortChunk;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int sub = 0; sub < kSortChunk; sub += 256) {
-#pragma unroll
-        for (int w = 0; w < 8; ++w) wc[w][tid] = 0;
-        __syncthreads();
-        const int i = base + sub + tid;
-        const bool valid = i < n;
-        const int key = valid ? (int)keys[i] : 256 + lane;  // invalid lanes never match others
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[warp][key] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            int pos = run[key] + rank;
-            for (int w = 0; w < warp; ++w) pos += wc[w][key];
-            order[pos] = i;
-        }
-        __syncthreads();
-        int add = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) add += wc[w][tid];
-        run[tid] += add;
-        __syncthreads();
+    __syncthreads();
+    if (valid) {
+        int pos = run[key] + rank;
+        for (int w = 0; w < warp; ++w) pos += wc[w][key];
+        order[pos] = i;
     }
 }
 
@@ -200,9 +206,10 @@ __global__ void k_windows_literal(Geo g, const double *__restrict__ rfd, const d
 static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *counts, int32_t *order,
                                  int32_t *bin_off, cudaStream_t st) {
     const int nblk = (n + kSortChunk - 1) / kSortChunk;
-    k_sort_hist<<<nblk, 256, 0, st>>>(keys, n, counts);
+    const int nb4 = (nblk + 3) & ~3;
+    k_sort_hist<<<nblk, 256, 0, st>>>(keys, n, nb4, counts);
     ++g_launches;
-    k_sort_scatter<<<nblk, 256, 0, st>>>(keys, n, nblk, K, counts, order, bin_off);
+    k_sort_scatter<<<nblk, kSortChunk, 0, st>>>(keys, n, nb4, K, counts, order, bin_off);
     ++g_launches;
     return cudaGetLastError();
 }
@@ -269,7 +276,7 @@ __global__ void k_radix_compose(const int32_t *__restrict__ perm, const int32_t 
     if (j < n) out[j] = perm[order[j]];
 }
 
-size_t radix_counts_ints(int n) { return (size_t)((n + kSortChunk - 1) / kSortChunk) * 256 + 257; }
+size_t radix_counts_ints(int n) { return sort_counts_ints(n) + 257; }
 
 // perm = the indices 0 .. n-1 ordered stably by key (0 <= key <= key_max): one counting-sort pass
 // per byte of key_max, least significant first; each pass sorts stably by its byte the order the
@@ -279,8 +286,7 @@ cudaError_t launch_radix_sort(const int32_t *key, int n, uint32_t key_max, int32
     if (n <= 0) return cudaSuccess;
     int passes = 1;
     while (passes < 4 && (key_max >> (8 * passes)) != 0) ++passes;
-    const int nblk = (n + kSortChunk - 1) / kSortChunk;
-    int32_t *bin_off = counts + (size_t)nblk * 256;  // the scatter's class offsets, not used here
+    int32_t *bin_off = counts + sort_counts_ints(n);  // the scatter's class offsets, not used here
     const unsigned g = (unsigned)((n + 255) / 256);
     // buffers: perm, t1, t2. The first pass's order is the current order; every later pass sorts
     // into one free buffer and composes into the other, which becomes current (perm on the last
