@@ -12,6 +12,7 @@
 
 namespace fic {
 size_t adjoint_csr_ints(const Geo &g);
+size_t adjoint_off_ints(const Geo &g);
 size_t adjoint_entries(const Geo &g);
 cudaError_t launch_dom_csr(const Geo &g, const fic_codes &c, const AdjointCsr &a, cudaStream_t st);
 cudaError_t launch_adjoint_gather(const Geo &g, const fic_codes &c, const AdjointCsr &a, const float *lam,
@@ -1032,7 +1033,7 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
     csr.t1 = ints + 2 * (size_t)g.R;
     csr.t2 = ints + 3 * (size_t)g.R;
     csr.off = ints + 4 * (size_t)g.R;
-    csr.counts = csr.off + g.Dn + 1;
+    csr.counts = csr.off + adjoint_off_ints(g);  // 16-byte aligned (the workspace is 256-byte aligned)
     csr.digit = c.take<uint8_t>(g.R);
     csr.ent = c.take<int4>(adjoint_entries(g));
     csr.acc = c.take<float>((size_t)g.R * g.n);

@@ -555,7 +555,10 @@ __global__ void k_grads_out(int R, const float2 *__restrict__ gsf, const float2 
     }
 }
 
-size_t adjoint_csr_ints(const Geo &g) { return (size_t)g.Dn + 1 + 4 * (size_t)g.R + radix_counts_ints(g.R); }
+// Dn + 1 segment starts, padded to a multiple of 4 ints so that the radix histograms after them
+// start on a 16-byte boundary (the counting sort reads them as 16-byte vectors).
+size_t adjoint_off_ints(const Geo &g) { return ((size_t)g.Dn + 1 + 3) & ~(size_t)3; }
+size_t adjoint_csr_ints(const Geo &g) { return 4 * (size_t)g.R + adjoint_off_ints(g) + radix_counts_ints(g.R); }
 size_t adjoint_entries(const Geo &g) { return (size_t)g.R; }
 
 cudaError_t launch_dom_csr(const Geo &g, const fic_codes &c, const AdjointCsr &a, cudaStream_t st) {

@@ -19,15 +19,15 @@ namespace fic {
 // Per-block class histograms of kSortChunk keys each, stored class-major: counts[k * nb4 + blk],
 // nb4 = the block count rounded up to a multiple of 4 (pad entries zero), so that one class's
 // counts over all blocks are contiguous 16-byte vectors for the scatter.
-__global__ void __launch_bounds__(256) k_sort_hist(const uint8_t *__restrict__ keys, int n, int nb4,
+__global__ void __launch_bounds__(256) k_sort_hist(const uint8_t *__restrict__ keys, int n, int nb4, bool words,
                                                    int32_t *__restrict__ counts) {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     const int base = blockIdx.x * kSortChunk;
     const int i0 = base + 4 * threadIdx.x;  // four keys per thread: kSortChunk = 4 x 256
-    if (i0 + 3 < n) {
-        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(keys + i0));  // base is 4-aligned
+    if (words && i0 + 3 < n) {  // words: keys is 4-byte aligned, so keys + i0 is
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(keys + i0));
 #pragma unroll
         for (int k = 0; k < 4; ++k) atomicAdd(&h[(w >> (8 * k)) & 0xFFu], 1);
     } else {
@@ -207,7 +207,10 @@ static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *cou
                                  int32_t *bin_off, cudaStream_t st) {
     const int nblk = (n + kSortChunk - 1) / kSortChunk;
     const int nb4 = (nblk + 3) & ~3;
-    k_sort_hist<<<nblk, 256, 0, st>>>(keys, n, nb4, counts);
+    // the scatter reads each class's histogram row as 16-byte vectors
+    if ((uintptr_t)counts % 16 != 0) return cudaErrorMisalignedAddress;
+    const bool words = (uintptr_t)keys % 4 == 0;
+    k_sort_hist<<<nblk, 256, 0, st>>>(keys, n, nb4, words, counts);
     ++g_launches;
     k_sort_scatter<<<nblk, kSortChunk, 0, st>>>(keys, n, nb4, K, counts, order, bin_off);
     ++g_launches;
