@@ -508,6 +508,22 @@ def batched(args, dev):
         b.record()
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
+    # the same batch by full search (K = 1), library default shapes, one call per step
+    pf = fic.EncodeParams(domain_stride=8, num_classes=1, engine=args.engine)
+    wsf = torch.empty(fic.encode_batched_workspace_size(shapes, pf), dtype=torch.uint8, device=dev)
+    infof = fic.new_info(dev)
+    outsf = fic.encode_batched(imgs, pf, workspace=wsf, info=infof)
+    full_matches = fic.read_info(infof)["matches"]
+    fms = []
+    for k in range(3):
+        flush.fill_(k & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fic.encode_batched(imgs, pf, outs=outsf, workspace=wsf)
+        b.record()
+        torch.cuda.synchronize()
+        fms.append(a.elapsed_time(b))
+    del wsf, outsf
     fic.profile_enable(True)
     med = statistics.median(ms)
     sides = sorted({int(t.shape[0]) for t in imgs})
@@ -517,6 +533,7 @@ def batched(args, dev):
             "matches_per_step": rep["matches"], "ms_per_step": med, "steps": steps,
             "matches_per_s": rep["matches"] / (med / 1e3), "fallback_ranges": rep["fallback_ranges"],
             "work_items": rep["work_items"], "variant": best,
+            "full_search_matches": full_matches, "full_search_ms": statistics.median(fms),
             "autotune_ms": tune_ms, "autotune_noise_ms": tune_noise,
             "autotune_spread_ms": max(tune_ms.values()) - min(tune_ms.values()), "autotune_s": tune_s}
 
@@ -526,6 +543,8 @@ def large(args, dev):
     against 16x16 domains and 16x16 ranges against 32x32 domains, each one fic_encode per step,
     L2 flushed before every step; with the decoded PSNR of each pass (8 iterations)."""
     import torch
+
+    import dataclasses
 
     from paper_1206_4880_gb300 import fic, synth
     img_np = synth.large_image()
@@ -567,6 +586,21 @@ def large(args, dev):
         x = fic.decode(out, H, W, p, 8)
         psnr = fic.quality(x, img)[1]
         med, mmatch, mcls = statistics.median(ms), statistics.median(mm), statistics.median(mc)
+        # the same engine's full search (K = 1) on the same image, with its decoded PSNR
+        pf = dataclasses.replace(p, num_classes=1)
+        wsf = torch.empty(fic.encode_workspace_size(H, W, pf), dtype=torch.uint8, device=dev)
+        outf = fic.encode(img, pf, workspace=wsf)
+        fms = []
+        for k in range(3):
+            flush.fill_(k & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fic.encode(img, pf, out=outf, workspace=wsf)
+            b.record()
+            torch.cuda.synchronize()
+            fms.append(a.elapsed_time(b))
+        psnr_full = fic.quality(fic.decode(outf, H, W, pf, 8), img)[1]
+        del wsf, outf
         tf = rep["matches"] * flops_per_match(B) / (mmatch / 1e3) / 1e12
         cls_bytes = classify_bytes(H, W, B, R, Dn)
         res[f"b{B}"] = {"ranges": R, "domains": Dn, "matches_per_step": rep["matches"],
@@ -578,6 +612,7 @@ def large(args, dev):
                         "classify_frac_of_hbm": cls_bytes / (mcls / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
                         "fallback_ranges": rep["fallback_ranges"], "work_items": rep["work_items"],
                         "device_error": rep["device_error"], "psnr_db": psnr,
+                        "full_search_ms": statistics.median(fms), "full_search_psnr_db": psnr_full,
                         **decode_rates(out, H, W, p, flush, float(peaks["hbm_gbs"]))}
         if tune is not None:
             res[f"b{B}"]["autotune"] = tune

@@ -123,3 +123,26 @@ def test_no_cpu_fallback_without_gpu():
     img = torch.zeros(64, 64, dtype=torch.uint8)
     with pytest.raises(ValueError):
         fic.encode(img, fic.EncodeParams())
+
+
+def test_fallback_ranges_and_check_validate_on_the_host():
+    """fic_encode_fallback_ranges refuses bad arguments before any launch; fic_check reports a
+    CUDA failure (no device here) or, on a GPU machine, nothing pending."""
+    import torch
+
+    lib = fic.load()
+    p = fic.EncodeParams(domain_stride=4, num_classes=8).c()
+    g = fic.geom(64, 64)
+    n = ctypes.c_int32(0)
+    assert lib.fic_encode_fallback_ranges(None, ctypes.byref(p), None, 0, None, 0, ctypes.byref(n), None) \
+        == fic.FIC_ERR_INVALID_ARG
+    assert lib.fic_encode_fallback_ranges(ctypes.byref(g), ctypes.byref(p), None, 0, None, 0, ctypes.byref(n),
+                                          None) == fic.FIC_ERR_WORKSPACE
+    buf = ctypes.create_string_buffer(64)
+    assert lib.fic_encode_fallback_ranges(ctypes.byref(g), ctypes.byref(p), buf, 64, None, 0, ctypes.byref(n),
+                                          None) == fic.FIC_ERR_WORKSPACE
+    bad = fic.EncodeParams(domain_stride=4, num_classes=8, pipeline_stages=7).c()
+    assert lib.fic_encode_fallback_ranges(ctypes.byref(g), ctypes.byref(bad), buf, 64, None, 0,
+                                          ctypes.byref(n), None) == fic.FIC_ERR_INVALID_ARG
+    expected = fic.FIC_OK if torch.cuda.is_available() else fic.FIC_ERR_CUDA
+    assert lib.fic_check(None) == expected
