@@ -22,7 +22,7 @@
 // (else the range is re-searched exactly on CUDA cores).
 //
 // Kernel shape: persistent, one CTA per SM, 10 warps: warp 0 issues TMA loads (A tile 128 x 64,
-// B tiles 256 x 64, 128-byte swizzle, 4-stage ring), warp 1 owns TMEM (two 128 x 256 FP32
+// B tiles 256 x 64, 128-byte swizzle, a 3-stage ring by default), warp 1 owns TMEM (two 128 x 256 FP32
 // accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16, four per tile), warps 2-9
 // (one thread per TMEM lane = range row, two warps per row group, one per column half) drain the
 // accumulators with tcgen05.ld. Every wait is
