@@ -270,16 +270,28 @@ __global__ void __launch_bounds__(kSimtThreads, 2)
             }
             __syncthreads();
             const int nf = sh.n_flagged, nsg = sh.n_single;
-            for (int f = 0; f < nf; ++f) {
-                const int cc = sh.flagged[f] + c_lo;
-                const int j0 = max(ri.y, cc * kChunkDom);
-                const int j1 = min(ri.z, (cc + 1) * kChunkDom);
-                for (int j = j0 + threadIdx.x; j < j1; j += kSimtThreads)
-                    scan_domain<B>(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
-            }
-            for (int f = threadIdx.x; f < 16 * nsg; f += kSimtThreads) {
-                const int j = sh.single[f >> 4] + (f & 15);
-                if (j >= ri.y && j < ri.z) scan_domain<B>(sh, dom_order[j - dom_off], A, domS, dsum, dsumsq, b);
+            // every position of the flagged chunks, then of the flagged groups, as one sequence that
+            // each thread walks with stride kSimtThreads; the next domain's id is loaded while the
+            // current domain is scanned, so a domain costs one dependent load round instead of two
+            auto pos_at = [&](int u) -> int {  // u-th position of the sequence, or -1 (outside the pool)
+                if (u < nf * kChunkDom) {
+                    const int j = (sh.flagged[u / kChunkDom] + c_lo) * kChunkDom + u % kChunkDom;
+                    return (j >= ri.y && j < ri.z) ? j : -1;
+                }
+                u -= nf * kChunkDom;
+                const int j = sh.single[u >> 4] + (u & 15);
+                return (j >= ri.y && j < ri.z) ? j : -1;
+            };
+            const int total = nf * kChunkDom + 16 * nsg;
+            int u = threadIdx.x, j = u < total ? pos_at(u) : -1;
+            int d = j >= 0 ? dom_order[j - dom_off] : -1;
+            while (u < total) {
+                const int un = u + kSimtThreads;
+                const int jn = un < total ? pos_at(un) : -1;
+                const int dn = jn >= 0 ? dom_order[jn - dom_off] : -1;
+                if (d >= 0) scan_domain<B>(sh, d, A, domS, dsum, dsumsq, b);
+                u = un;
+                d = dn;
             }
             __syncthreads();
         }

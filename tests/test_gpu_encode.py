@@ -414,3 +414,29 @@ def test_encode_repeated_calls_replay(engine):
                 fic.profile_enable(False)
             for k in got:
                 assert torch.equal(got[k], ref[k]), (rep, k)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("block,shape,sigma", [
+    (8, (16, 16), 1),    # the smallest image: 4 ranges, one domain
+    (8, (16, 48), 3),    # one domain row
+    (8, (40, 16), 8),    # one domain column
+    (16, (32, 32), 4),   # 16x16 ranges: 4 ranges, one domain
+    (16, (32, 96), 16),  # one domain row, stride 16
+])
+def test_encode_smallest_images(engine, block, shape, sigma):
+    """The degenerate geometries: a single domain, one row or one column of domains; every range's
+    pool is then that set, so the codes are the exact full search (oracle parity), for K = 1 and
+    for K > 1 (one class holds everything)."""
+    _need_tensor(engine)
+    H, W = shape
+    img = synth.fbm_image(97 + H + W, H, W)
+    for K in (1, 6):
+        p = fic.EncodeParams(domain_stride=sigma, num_classes=K, engine=engine, block=block)
+        info = fic.new_info("cuda")
+        codes = fic.encode(_t(img), p, info=info)
+        torch.cuda.synchronize()
+        ref = omatch.encode(img, B=block, sigma=sigma, K=K, n_threads=NT)
+        _compare_codes(codes, ref)
+        rep = fic.read_info(info)
+        assert rep["matches"] == int(ref["pool_size"].sum()) * 8 and rep["device_error"] == 0
