@@ -389,24 +389,55 @@ def run_ours(args, wl, world, rank, local):
         stage_step_ms.append(a.elapsed_time(b))
     fic.profile_enable(False)
 
-    # end to end through the public API with host buffers: H2D image, encode, D2H codes
+    # end to end through the public API with host buffers: every step copies its image in from
+    # pinned host memory, encodes it and copies its codes out, pipelined the way a serving loop
+    # runs: step k+1's image goes in and step k-1's codes come out on copy streams while step k
+    # encodes. Three buffer sets (image, workspace, codes: about 3 x the encode's working set, more
+    # than L2) rotate, so each step finds its data evicted instead of needing an L2 flush.
+    NB = 3
     host_img = torch.from_numpy(img_np).pin_memory()
-    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    imgs2 = [img] + [torch.empty_like(img) for _ in range(NB - 1)]
+    outs2 = [out] + [fic.alloc_codes(R, dev) for _ in range(NB - 1)]
+    wss = [ws] + [torch.empty_like(ws) for _ in range(NB - 1)]
+    host_out = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()} for o in outs2]
     d2h = sum(v.numel() * v.element_size() for v in out.values())
-    e2e_steps = min(args.steps, 50)
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
-    for k in range(e2e_steps):
-        flush.fill_(k & 255)
-        e0[k].record()
-        img.copy_(host_img, non_blocking=True)
-        fic.encode(img, p, out=out, workspace=ws)
-        for key in out:
-            host_out[key].copy_(out[key], non_blocking=True)
-        e1[k].record()
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(NB)]
+    ev_cmp = [torch.cuda.Event() for _ in range(NB)]
+    ev_out = [torch.cuda.Event() for _ in range(NB)]
+    for b in range(NB):  # each buffer set's cached graph exists before the timed region
+        imgs2[b].copy_(img)
+        fic.encode(imgs2[b], p, out=outs2[b], workspace=wss[b], stream=s_cmp)
+        ev_cmp[b].record(s_cmp)
+        ev_out[b].record(s_cmp)
     torch.cuda.synchronize()
-    e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1e3, world)
+    e2e_steps = min(args.steps, 60)
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(s_in)
+    for k in range(e2e_steps):
+        b = k % NB
+        s_in.wait_event(ev_cmp[b])  # the encode that last read imgs2[b] is done
+        with torch.cuda.stream(s_in):
+            imgs2[b].copy_(host_img, non_blocking=True)
+        ev_in[b].record(s_in)
+        s_cmp.wait_event(ev_in[b])
+        s_cmp.wait_event(ev_out[b])  # the codes that last sat in outs2[b] have been copied out
+        fic.encode(imgs2[b], p, out=outs2[b], workspace=wss[b], stream=s_cmp)
+        ev_cmp[b].record(s_cmp)
+        s_out.wait_event(ev_cmp[b])
+        with torch.cuda.stream(s_out):
+            for key in outs2[b]:
+                host_out[b][key].copy_(outs2[b][key], non_blocking=True)
+        ev_out[b].record(s_out)
+    s_in.wait_stream(s_out)
+    e_end.record(s_in)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(e_start.elapsed_time(e_end) / 1e3, world)
     e2e_value = reduce_sum(float(matches) * e2e_steps, world) / e2e_s
+    # the last step's codes as read back on the host equal the device-side codes
+    last = (e2e_steps - 1) % NB
+    e2e_ok = all(torch.equal(host_out[last][k2], outs2[last][k2].cpu()) for k2 in out)
+    del wss[1:], imgs2[1:], outs2[1:]
 
     peaks, peak_src = _peaks()
     mean_match_ms = statistics.mean(match_ms)
@@ -448,7 +479,10 @@ def run_ours(args, wl, world, rank, local):
                      "traffic_unit": "bytes per launch (ncu, profiles/; null once the kernel's sources changed)",
                      "per_launch_ms": mean_match_ms, "peak_source": peak_note},
         "e2e": {"value": e2e_value, "unit": "matches/s", "h2d_bytes_per_step": H * W,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps, "codes_read_back_equal": e2e_ok,
+                "pipelining": "step k+1's image copied in and step k-1's codes copied out on copy streams "
+                              "while step k encodes (encodes in order on one stream); three rotating buffer "
+                              "sets larger than L2 in all, no flush"},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
     }
