@@ -14,11 +14,13 @@
  * Conventions for every entry point:
  *  - Image, code, statistics and workspace pointers are DEVICE pointers owned by the caller.
  *    The library allocates no device memory and frees none; it keeps no state between calls
- *    except a per-device cache of its own kernel attributes, fic_encode's per-thread cache of
- *    captured graphs (see fic_encode) and, for fic_encode_batched and single encodes, eight
- *    internal CUDA streams and events per host thread and device (created on the first batched
- *    call that is not inside a stream capture; the images' per-image stages run on them,
- *    joined back into `stream` by events).
+ *    except a per-device cache of its own kernel attributes, the per-thread caches of captured
+ *    graphs of fic_encode and fic_decode (see there), eight internal CUDA streams and events per
+ *    host thread and device for fic_encode_batched and single encodes (created on the first call
+ *    that is not inside a stream capture; the images' per-image stages run on them, joined back
+ *    into `stream` by events), and two fixed device arrays with their addresses cached per
+ *    device and context: the device error word that fic_check reads and fic_decode_static's
+ *    scratch image.
  *  - `stream` is a cudaStream_t (passed as void*; NULL = the legacy default stream). All work
  *    is enqueued asynchronously on it; nothing synchronises the host.
  *  - Decode workspaces must be 256-byte aligned; encode workspaces may have any alignment (the
