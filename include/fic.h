@@ -42,7 +42,7 @@
  *
  * Supported in this version: B = 8 or 16 (16x16 ranges against 32x32 domains: the paper's
  * method at a second range size, with n = 256 pixels per block), 1 <= sigma, 1 <= K <= 255,
- * s_max = 1.0. The literal FD window (FIC_FLAG_LITERAL_WINDOW) needs B = 8.
+ * s_max = 1.0, the class window or the literal FD window (FIC_FLAG_LITERAL_WINDOW) for both.
  */
 #ifndef FIC_H
 #define FIC_H
@@ -72,8 +72,8 @@ enum {
 /* Pool window (fic_params.flags). Default: the class window |bin_d - bin_r| <= w. With
  * FIC_FLAG_LITERAL_WINDOW the pool is Section 3.1 Eq. 3 on the FD values themselves,
  * Pool(r) = {d : FD_r - D_f <= FD_d <= FD_r + D_f}, D_f = (F_m - F_l) / 3 (Eq. 2), each bound one
- * binary64 operation; domains and ranges are then ordered by FD value instead of class, and
- * num_classes / half_width only shape the reported classes. */
+ * binary64 operation; domains and ranges are then ordered by FD value instead of class (stable:
+ * equal FDs keep ascending ids), and num_classes / half_width only shape the reported classes. */
 #define FIC_FLAG_LITERAL_WINDOW 1
 
 typedef struct {
@@ -129,9 +129,12 @@ typedef struct {
 /* Dynamic pools (Section 3.1 Eq. 3 in class units, replacing the paper's AVL tree by an
  * ordered array: a range query of the tree is a contiguous slice of the class-sorted domains).
  *  dom_order[Dn]   domain ids sorted by (class, id) - the in-order traversal of the tree;
- *  bin_off[257]    (257 entries) dom_order[bin_off[b] .. bin_off[b+1]) holds class b (with
- *                  FIC_FLAG_LITERAL_WINDOW: the b-th smallest distinct FD value that 8x8 box
- *                  counts can produce, up to 245 + 1 entries);
+ *  bin_off[257]    dom_order[bin_off[b] .. bin_off[b+1]) holds class b (257 entries). With
+ *                  FIC_FLAG_LITERAL_WINDOW and B = 8: bucket b holds the b-th smallest distinct FD
+ *                  value that 8x8 box counts can produce (up to 245 + 1 entries used); with B = 16
+ *                  the array needs FIC_LITERAL16_OFFSETS entries, and bucket k holds the blocks whose
+ *                  FD exceeds exactly k of the FDs of the 2245 (N_2, N_8) pairs 16x16 box counts
+ *                  can produce (buckets of values no pair has are empty);
  *  range_order[R]  range ids sorted by (class, id); rbin_off[257] likewise;
  *  win_lo[R], win_hi[R]  Pool(r) = dom_order[win_lo[r] .. win_hi[r]) = the domains with
  *                  |bin_d - bin_r| <= w; when that set is empty the pool is every domain
@@ -139,6 +142,9 @@ typedef struct {
 typedef struct {
     int32_t *dom_order, *bin_off, *range_order, *rbin_off, *win_lo, *win_hi;
 } fic_pools;
+
+/* Entries of fic_pools.bin_off and rbin_off for the literal window with 16x16 blocks. */
+#define FIC_LITERAL16_OFFSETS 2246
 
 /* Fractal code per range r (device arrays of R entries): the best domain id, isometry, contrast
  * s, brightness o (binary64, unquantised) and collage error sse = sum (r - s T_t(D) - o)^2 with

@@ -33,6 +33,8 @@ constexpr int kMaxBatch = 4096;
 
 using namespace fic;
 
+static_assert(FIC_LITERAL16_OFFSETS == kFdPairs16 + 1, "bucket offsets of the 16x16 literal window");
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -141,8 +143,6 @@ fic_status make_geo(const fic_geom *gm, const fic_params *p, Geo *g) {
         return fail(FIC_ERR_INVALID_ARG, "unknown engine %d", p->engine);
     if (p->flags != 0 && p->flags != FIC_FLAG_LITERAL_WINDOW)
         return fail(FIC_ERR_INVALID_ARG, "flags must be 0 or FIC_FLAG_LITERAL_WINDOW");
-    if ((p->flags & FIC_FLAG_LITERAL_WINDOW) && p->block != 8)
-        return fail(FIC_ERR_INVALID_ARG, "the literal FD window is implemented for block 8 only");
     if (p->items_per_sm < 0 || p->items_per_sm > 64)
         return fail(FIC_ERR_INVALID_ARG, "items_per_sm must be in [0, 64]");
     if (p->group_chunks < 0 || p->group_chunks > 1024)
@@ -282,10 +282,13 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->dom_bin = c.take<uint8_t>(g.Dn);
         b->fd_extent = c.take<double>(2);
         b->dom_S = c.take<uint16_t>((size_t)g.Dn * npx);
+        // bucket offsets: K + 1 classes, or one per FD key in literal mode (+ 1)
+        const bool lit16 = g.literal && B == 16;
+        const size_t n_off = lit16 ? (size_t)kFdPairs16 + 1 : (size_t)kMaxClasses + 2;
         b->dom_order = c.take<int32_t>(g.Dn);
-        b->bin_off = c.take<int32_t>(kMaxClasses + 2);
+        b->bin_off = c.take<int32_t>(n_off);
         b->range_order = c.take<int32_t>(g.R);
-        b->rbin_off = c.take<int32_t>(kMaxClasses + 2);
+        b->rbin_off = c.take<int32_t>(n_off);
         b->win_lo = c.take<int32_t>(g.R);
         b->win_hi = c.take<int32_t>(g.R);
         b->dom_key = c.take<uint8_t>(g.Dn);
@@ -295,6 +298,14 @@ size_t encode_workspace(const Geo *gs, int n, EncodeBufs *bs, TcBatch *tb, void 
         b->sort_offs = c.take<int32_t>(sort_counts_ints(sort_blocks * kSortChunk));
         b->fallback = c.take<int32_t>(g.R);
         b->fb_best = c.take<FallbackBest>(g.R);
+        const int nmax = g.R > g.Dn ? g.R : g.Dn;
+        b->lit_key = lit16 ? c.take<int32_t>(nmax) : nullptr;
+        b->lit_t1 = lit16 ? c.take<int32_t>(nmax) : nullptr;
+        b->lit_t2 = lit16 ? c.take<int32_t>(nmax) : nullptr;
+        b->lit_counts = lit16 ? c.take<int32_t>(radix_counts_ints(nmax)) : nullptr;
+        b->lit_rank = lit16 ? c.take<int32_t>(kFdPairs16) : nullptr;
+        b->lit_digit = lit16 ? c.take<uint8_t>(nmax) : nullptr;
+        b->lit_sfd = lit16 ? c.take<double>(g.Dn) : nullptr;
         b->counters = img_counters ? img_counters + 8 * k : nullptr;
         b->matches = img_counters ? reinterpret_cast<long long *>(img_counters + 8 * k + 2) : nullptr;
         b->extent_bits = img_counters ? reinterpret_cast<unsigned long long *>(img_counters + 8 * k + 4) : nullptr;

@@ -340,6 +340,11 @@ struct EncodeBufs {
     int nbuckets;          // sort buckets: K, or the number of distinct FD values
     int32_t *sort_counts;  // [256][nblk rounded up to 4] per-block class histograms of the domain sort
     int32_t *sort_offs;    // the same for the range sort
+    // literal window with 16x16 ranges: FD-rank keys (up to 12 bits) radix-sorted
+    int32_t *lit_key, *lit_t1, *lit_t2, *lit_counts;  // [max(R, Dn)] keys and sort buffers, histograms
+    int32_t *lit_rank;     // [kFdPairs16] key of every (N_2, N_8) pair
+    uint8_t *lit_digit;    // [max(R, Dn)] radix digits
+    double *lit_sfd;       // [Dn] FDs of the FD-sorted domains
     // tensor engine: this image's slice of the batch-wide arrays (TcBatch)
     __half *A_mat;         // [R_pad][n]   range pixels - a, class-sorted ranges
     __half *B_mat;         // [8 Dn_aux][n] T_t(S_d) - c, class-sorted domains x isometries
@@ -397,6 +402,10 @@ __device__ __forceinline__ void poison_code(const fic_codes &out, int r) {
     out.sse[r] = nan;
 }
 
+// 16x16 blocks: FD = (log2 N_2 - log2 N_8) / 2 with 64 <= N_2 <= 512 and 4 <= N_8 <= 8 (box counts
+// at s = 2 and s = 8); the literal window sorts blocks by the rank of their FD among these pairs
+constexpr int kFdN2Lo16 = 64, kFdN2Hi16 = 512, kFdN8Lo16 = 4, kFdN8Hi16 = 8;
+constexpr int kFdPairs16 = (kFdN2Hi16 - kFdN2Lo16 + 1) * (kFdN8Hi16 - kFdN8Lo16 + 1);  // 2245
 constexpr int kSortChunk = 1024;  // elements per counting-sort block (4 per histogram thread)
 // ints of a counting sort's block histograms for n keys: 256 classes x the block count rounded up
 // to a multiple of 4

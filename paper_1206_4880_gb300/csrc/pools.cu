@@ -203,6 +203,129 @@ __global__ void k_windows_literal(Geo g, const double *__restrict__ rfd, const d
     if ((threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long *)matches, (unsigned long long)m);
 }
 
+// ---- literal window with 16x16 blocks ------------------------------------------------------
+// A 16x16 block's FD is (L[N_2] - L[N_8]) / 2 (two binary64 operations, as in classification) with
+// 64 <= N_2 <= 512 and 4 <= N_8 <= 8: 2245 pairs. The key of a pair is the number of pairs whose FD
+// is smaller, so keys order blocks by FD and blocks of equal FD share a key; the keys are formed on
+// the device from the same correctly rounded log2 table, one thread per pair.
+__global__ void __launch_bounds__(256) k_fd_rank16(Log2Tab L, int32_t *__restrict__ rank) {
+    __shared__ double v[kFdPairs16];
+    for (int i = threadIdx.x; i < kFdPairs16; i += blockDim.x) {
+        const int n2 = kFdN2Lo16 + i / (kFdN8Hi16 - kFdN8Lo16 + 1), n8 = kFdN8Lo16 + i % (kFdN8Hi16 - kFdN8Lo16 + 1);
+        v[i] = __dmul_rn(__dsub_rn(L.v[n2], L.v[n8]), 0.5);
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kFdPairs16) return;
+    const double x = v[i];
+    int c = 0;
+    for (int j = 0; j < kFdPairs16; ++j) c += v[j] < x;
+    rank[i] = c;
+}
+
+// key[i] = the FD key of block i from its box counts (N_2, N_4, N_8 per block).
+__global__ void k_fd_keys16(int n, const int32_t *__restrict__ counts, const int32_t *__restrict__ rank,
+                            int32_t *__restrict__ key) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // box counts of 16x16 blocks lie in these ranges; caller-supplied statistics are clamped into
+    // them so that no key is read outside the table
+    const int n2 = min(max(counts[3 * i], kFdN2Lo16), kFdN2Hi16);
+    const int n8 = min(max(counts[3 * i + 2], kFdN8Lo16), kFdN8Hi16);
+    key[i] = rank[(n2 - kFdN2Lo16) * (kFdN8Hi16 - kFdN8Lo16 + 1) + (n8 - kFdN8Lo16)];
+}
+
+// off[k] = the first sorted position whose key is >= k, for k = 0 .. nk (binary search over the
+// keys of the sorted order).
+__global__ void k_key_offsets(int n, int nk, const int32_t *__restrict__ key, const int32_t *__restrict__ order,
+                              int32_t *__restrict__ off) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nk) return;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key[order[mid]] < k)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    off[k] = lo;
+}
+
+// sfd[j] = FD of the j-th domain in FD order.
+__global__ void k_sorted_fd(int n, const double *__restrict__ fd, const int32_t *__restrict__ order,
+                            double *__restrict__ sfd) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) sfd[j] = fd[order[j]];
+}
+
+// Pool window of every range, Eq. 3 on the FD values: the FD-sorted domains with
+// FD_r - D_f <= FD_d <= FD_r + D_f (binary searches over their sorted FDs), every domain when
+// none; these are whole runs of equal FD, so whole key buckets.
+__global__ void k_windows_literal16(Geo g, const double *__restrict__ rfd, const double *__restrict__ fd_extent,
+                                    const double *__restrict__ sfd, int32_t *__restrict__ win_lo,
+                                    int32_t *__restrict__ win_hi, long long *matches) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    long long m = 0;
+    if (r < g.R) {
+        const double Df = __ddiv_rn(__dsub_rn(fd_extent[1], fd_extent[0]), 3.0);
+        const double lo_v = __dsub_rn(rfd[r], Df), hi_v = __dadd_rn(rfd[r], Df);
+        int a = 0, b = g.Dn;  // first position with FD >= lo_v
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (sfd[mid] >= lo_v) b = mid; else a = mid + 1;
+        }
+        int lo = a;
+        a = lo;
+        b = g.Dn;  // first position with FD > hi_v
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (sfd[mid] > hi_v) b = mid; else a = mid + 1;
+        }
+        int hi = a;
+        if (lo >= hi) {
+            lo = 0;
+            hi = g.Dn;
+        }
+        win_lo[r] = lo;
+        win_hi[r] = hi;
+        m = (long long)(hi - lo) * 8;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long *)matches, (unsigned long long)m);
+}
+
+// Domains and ranges of a 16x16 encode in FD order (stable: equal FDs keep ascending ids), their
+// key buckets' offsets and every range's literal window.
+static cudaError_t launch_pools_literal16(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
+    cudaError_t e;
+    k_fd_rank16<<<(kFdPairs16 + 255) / 256, 256, 0, st>>>(log2_table(), b.lit_rank);
+    ++g_launches;
+    struct Side {
+        int n;
+        const int32_t *counts;
+        int32_t *order, *off;
+    } sides[2] = {{g.Dn, b.dom_counts, b.dom_order, b.bin_off}, {g.R, b.range_counts, b.range_order, b.rbin_off}};
+    for (const Side &sd : sides) {
+        k_fd_keys16<<<(sd.n + 255) / 256, 256, 0, st>>>(sd.n, sd.counts, b.lit_rank, b.lit_key);
+        ++g_launches;
+        if ((e = launch_radix_sort(b.lit_key, sd.n, (uint32_t)(kFdPairs16 - 1), sd.order, b.lit_t1, b.lit_t2,
+                                   b.lit_digit, b.lit_counts, st)))
+            return e;
+        k_key_offsets<<<(kFdPairs16 + 1 + 255) / 256, 256, 0, st>>>(sd.n, kFdPairs16, b.lit_key, sd.order, sd.off);
+        ++g_launches;
+        if (sd.order == b.dom_order) {
+            k_sorted_fd<<<(g.Dn + 255) / 256, 256, 0, st>>>(g.Dn, b.dom_fd, b.dom_order, b.lit_sfd);
+            ++g_launches;
+        }
+    }
+    k_windows_literal16<<<(g.R + 255) / 256, 256, 0, st>>>(g, b.range_fd, b.fd_extent, b.lit_sfd, b.win_lo, b.win_hi,
+                                                           b.matches);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
 static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *counts, int32_t *order,
                                  int32_t *bin_off, cudaStream_t st) {
     const int nblk = (n + kSortChunk - 1) / kSortChunk;
@@ -219,6 +342,7 @@ static cudaError_t counting_sort(const uint8_t *keys, int n, int K, int32_t *cou
 
 cudaError_t launch_pools(const Geo &g, const EncodeBufs &b, cudaStream_t st) {
     cudaError_t e;
+    if (g.literal && g.B == 16) return launch_pools_literal16(g, b, st);
     if (g.literal) {
         const FdRanks &fr = fd_ranks();
         RankTab rt;
@@ -262,7 +386,7 @@ cudaError_t launch_pools_windows(const Geo &g, const EncodeBufs &b, cudaStream_t
     return cudaGetLastError();
 }
 
-int sort_buckets(const Geo &g) { return g.literal ? fd_ranks().n : g.K; }
+int sort_buckets(const Geo &g) { return g.literal ? (g.B == 16 ? kFdPairs16 : fd_ranks().n) : g.K; }
 
 // ---- stable LSD radix sort of int keys, one byte per counting-sort pass ----------------------
 // digit[i] = byte `shift / 8` of key[perm[i]] (of key[i] when perm is null).

@@ -18,6 +18,7 @@ FIC_OK, FIC_ERR_INVALID_ARG, FIC_ERR_WORKSPACE, FIC_ERR_CUDA, FIC_ERR_DEVICE_TIM
     FIC_ERR_UNSUPPORTED = range(6)
 ENGINES = {"tensor": 0, "simt": 1}
 FLAG_LITERAL_WINDOW = 1
+LITERAL16_OFFSETS = 2246  # FIC_LITERAL16_OFFSETS
 
 c_i32, c_i64, c_dbl, c_vp, c_size = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -308,12 +309,13 @@ def build_pools(stats: dict, H: int, W: int, p: EncodeParams, workspace=None, st
     R, Dn = counts(H, W, p)
     dev = stats["range_bin"].device
     i32 = torch.int32
-    # bucket offsets: K + 1 entries, or one per distinct FD value (+1) with the literal window;
-    # the library documents 257 as the size that covers both
+    # bucket offsets: K + 1 entries, or one per FD key (+1) with the literal window (257 cover the
+    # classes and the 8x8 literal window; the 16x16 literal window needs LITERAL16_OFFSETS)
+    n_off = LITERAL16_OFFSETS if (p.literal and p.block == 16) else 257
     out = {"dom_order": torch.empty(Dn, dtype=i32, device=dev),
-           "bin_off": torch.empty(257, dtype=i32, device=dev),
+           "bin_off": torch.empty(n_off, dtype=i32, device=dev),
            "range_order": torch.empty(R, dtype=i32, device=dev),
-           "rbin_off": torch.empty(257, dtype=i32, device=dev),
+           "rbin_off": torch.empty(n_off, dtype=i32, device=dev),
            "win_lo": torch.empty(R, dtype=i32, device=dev),
            "win_hi": torch.empty(R, dtype=i32, device=dev)}
     s = BlockStats(*[_p(stats[n]) for n, _ in BlockStats._fields_])

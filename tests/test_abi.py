@@ -52,7 +52,7 @@ def test_workspace_size_and_validation():
     assert _ws_size(1024, 1024, domain_stride=4, num_classes=16) > _ws_size(256, 256)
     for kw in ({"domain_stride": 0}, {"num_classes": 0}, {"num_classes": 256},
                {"block": 12}, {"s_max": 0.5}, {"half_width": -2},
-               {"block": 16, "literal": True}, {"group_chunks": -1}, {"group_chunks": 1025},
+               {"group_chunks": -1}, {"group_chunks": 1025},
                {"pipeline_stages": 2}, {"pipeline_stages": 5}, {"block": 16, "pipeline_stages": 3},
                {"block": 16, "pipeline_stages": 6}):
         assert _ws_size(64, 64, **kw) == 0, kw
@@ -61,6 +61,10 @@ def test_workspace_size_and_validation():
     assert _ws_size(64, 64, block=16) > 0
     assert _ws_size(24, 64, block=16) == 0 and _ws_size(64, 48, block=16) > 0 and _ws_size(16, 64, block=16) == 0
     assert _ws_size(1024, 1024, block=16) > _ws_size(512, 512, block=16)
+    # the literal FD window for both range sizes; the 16x16 one needs its key and sort scratch
+    assert _ws_size(64, 64, literal=True) > 0
+    assert _ws_size(64, 64, block=16, literal=True) > _ws_size(64, 64, block=16)
+    assert fic.LITERAL16_OFFSETS == 2246
     for kw in ({"pipeline_stages": 3}, {"pipeline_stages": 4}, {"block": 16, "pipeline_stages": 4},
                {"block": 16, "pipeline_stages": 5}, {"group_chunks": 1}, {"group_chunks": 1024}):
         assert _ws_size(64, 64, **kw) > 0, kw

@@ -229,3 +229,42 @@ def test_decode16_parity_and_adjoint():
     torch.cuda.synchronize()
     for a, b in ((gs.cpu().numpy(), gs_ref), (go.cpu().numpy(), go_ref)):
         assert np.max(np.abs(a - b)) <= 1e-4 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("case", [c for c in SMALL16 if c[3] > 1])
+def test_encode16_literal_window(case, engine):
+    """Section 3.1 Eq. 3 on the FD values of 16x16 blocks: FD_r - D_f <= FD_d <= FD_r + D_f. The
+    domains and ranges are ordered by FD value (stable), each range's window equals the oracle's
+    literal pool, and the codes equal the oracle's literal-mode codes."""
+    _need_tensor(engine)
+    H, W, sigma, K, w, seed = case
+    img = _img(H, W, seed)
+    p = fic.EncodeParams(domain_stride=sigma, num_classes=K, half_width=w, engine=engine, block=16,
+                         literal=True)
+    info = fic.new_info("cuda")
+    codes = fic.encode(_t(img), p, info=info)
+    st = fic.classify(_t(img), p)
+    po = fic.build_pools(st, H, W, p)
+    torch.cuda.synchronize()
+    ref = omatch.encode(img, B=16, sigma=sigma, K=K, mode="literal", n_threads=NT)
+    _compare_codes(codes, ref)
+    rep = fic.read_info(info)
+    assert rep["matches"] == int(ref["pool_size"].sum()) * 8 and rep["device_error"] == 0
+    cls = ref["cls"]
+    Df = opools.fractal_distance(cls["F_l"], cls["F_m"])
+    dom_order = po["dom_order"].cpu().numpy()
+    assert np.array_equal(dom_order, np.argsort(cls["dom_fd"], kind="stable"))
+    assert np.array_equal(po["range_order"].cpu().numpy(), np.argsort(cls["range_fd"], kind="stable"))
+    lo, hi = po["win_lo"].cpu().numpy(), po["win_hi"].cpu().numpy()
+    for r in range(lo.size):
+        pool = opools.literal_pool(cls["range_fd"][r], cls["dom_fd"], Df)
+        assert np.array_equal(np.sort(dom_order[lo[r]:hi[r]]), pool), r
+    # bucket offsets: monotone, ending at the domain count, buckets of equal FD
+    off = po["bin_off"].cpu().numpy()
+    assert off.size == fic.LITERAL16_OFFSETS and off[0] == 0 and off[-1] == dom_order.size
+    assert np.all(np.diff(off) >= 0)
+    fd_sorted = cls["dom_fd"][dom_order]
+    for k in np.nonzero(np.diff(off))[0]:
+        run = fd_sorted[off[k]:off[k + 1]]
+        assert np.all(run == run[0])
