@@ -201,8 +201,9 @@ __global__ void __launch_bounds__(kSimtThreads)
 
 // Re-search of uncertified ranges of one image. Slot k holds class-sorted position fb_pos[k] and
 // the exact best of its evaluated candidates; the 512-domain chunks of the range's tile whose best
-// FP32 score could still reach that best (score * (1 + 2^-13) + 2^-16 >= best gain / (8 n), the
-// bound the re-evaluation certifies with) are scanned exactly. TM ranges per tile, H key columns
+// FP32 score could still reach that best (score * (1 + 2^-13) + 2^-16 >= best gain / (8 n), less
+// 2^-16 sqrt(64 sum r^2 - A^2) for 8x8 ranges: the bound the re-evaluation certifies with) are
+// scanned exactly. TM ranges per tile, H key columns
 // per row (chunk_max layout [chunk][TM][H] of (best key, runner-up score bits)).
 template <int B, int TM, int H>
 __global__ void __launch_bounds__(kSimtThreads, 2)
@@ -231,10 +232,14 @@ __global__ void __launch_bounds__(kSimtThreads, 2)
         // FP32 with the left side rounded up and the threshold rounded down (so a superset of the
         // exactly flagged chunks; the FP64 threshold's own rounding, 2^-52 relatively, lies well
         // inside the margin's slack). One thread forms the threshold: FP64 throughput is low.
-        if (threadIdx.x == 0)
-            sh.thr = fb.num < 0 ? -1.0f
-                                : __double2float_rd(__ddiv_rn(i128_to_double_rn(fb.num), 8.0 * B * B * (double)fb.den));
         const long long A = ri.x, Bs = rsumsq[r];
+        // with 8x8 ranges the score's own rounding adds 2^-16 sqrt(64 Bs - A^2) to the bound
+        // (k_match_tc); moving it to the threshold's side keeps the flag test one FMA
+        if (threadIdx.x == 0) {
+            double thr = __ddiv_rn(i128_to_double_rn(fb.num), 8.0 * B * B * (double)fb.den);
+            if (B == 8) thr -= (double)__fsqrt_ru(__ll2float_ru(64LL * Bs - A * A)) * (1.0 / 65536.0);
+            sh.thr = fb.num < 0 ? -1.0f : __double2float_rd(thr);
+        }
         const int ig = rng_off + i, row = ig % TM;
         const int4 tw = tile_win[ig / TM];
         const int4 ti = tile_items[ig / TM];

@@ -87,7 +87,11 @@ static_assert(sizeof(TcShared<4>) + 1024 <= 232448, "shared memory per CTA");
 // Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
 // range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
 // s = 128 m^2 / Q + (p - m), m = min(p, Q / 256) (the exact gain / 512 up to the accumulator's
-// and this formula's rounding). The 16 domains form one ranking group (positions jh .. jh + 15,
+// and this formula's rounding), formed as m (m 128 / Q - 1) + p with two FMAs. The inner FMA's
+// result lies in [-1, -1/2], so its rounding errs by at most 2^-25 absolutely and the score by
+// at most m 2^-25 <= p 2^-25 beyond its relative errors; with |P| <= sqrt(Q_r Q) (Cauchy-Schwarz,
+// Q_r = 64 sum r^2 - A^2) and Q <= 64^2 510^2 that is below 2^-16 sqrt(Q_r), a per-range term
+// the certification adds to its margin. The 16 domains form one ranking group (positions jh .. jh + 15,
 // jh a multiple of 16): only the group's largest score goes on, as one 32-bit key (its bits with
 // the low 9 replaced by 511 - the group's offset jrel in its 512-domain chunk), into t1, t2, the
 // two largest group keys of the chunk; the exact re-evaluation evaluates the best group whole, so
@@ -139,7 +143,7 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 // certification margin covers
                 const float p = absmax8(cur + 8 * q);
                 const float mm = fminf(p, qy);
-                float sc = fmaf(mm, mm * qz, p - mm);
+                float sc = fmaf(mm, fmaf(mm, qz, -1.f), p);
                 if (MASK) {
                     const int j = jh + l;
                     sc = (j >= lo_r && j < hi_r) ? sc : -1.f;
@@ -883,10 +887,11 @@ __device__ __forceinline__ void reeval_finish(const ReevalRes &e, int32_t *__res
         // FP32 score formula errs < 20 * 2^-24 relatively, and the accumulator's P / 64 (an exact
         // integer Y plus one rounded correction of magnitude <= 16) errs < 2^-22 (|P / 64| + 16);
         // the score's slope in p is at most 1, so that moves it by < 2^-21 relatively plus
-        // < 2^-18 absolutely
+        // < 2^-18 absolutely; the score's inner FMA adds < 2^-16 sqrt(Q_r) absolutely (epi_half)
         const double u2 = (double)__uint_as_float(e.u2);
+        const double sq = (double)__fsqrt_ru(__ll2float_ru(64LL * e.Bs - e.A * e.A));
         // bound < exact gain / 512, compared as bound * 512 den < gain numerator (no division)
-        certified = (u2 * (1.0 + 1.0 / 8192.0) + 1.0 / 65536.0) * (512.0 * (double)gg.den) < (double)gg.num;
+        certified = (u2 * (1.0 + 1.0 / 8192.0) + (1.0 + sq) / 65536.0) * (512.0 * (double)gg.den) < (double)gg.num;
     }
     if (!certified) {
         const int slot = atomicAdd(&counters[0], 1);
@@ -918,8 +923,8 @@ __device__ __forceinline__ void reeval_finish(const ReevalRes &e, int32_t *__res
 // certifies it: every domain outside the evaluated group has an FP32 score at most the runner-up
 // key's, and an FP32 score is an upper bound of that domain's exact gain / 512 up to a relative
 // 20 * 2^-24 (it is formed from exact integers and 24-bit constants by a handful of
-// single-rounding operations), so if runner-up * (1 + 2^-13) + 2^-16 < exact best, no other domain
-// can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
+// single-rounding operations) and an absolute 2^-16 sqrt(Q_r) (Q_r = 64 sum r^2 - A^2), so if
+// runner-up * (1 + 2^-13) + 2^-16 (1 + sqrt(Q_r)) < exact best, no other domain can win or tie. Otherwise the range is queued with its exact best for k_rescan. Flat ranges
 // (n Bs = A^2) have zero error for every candidate; their code is the smallest domain id of the
 // pool with t = 0.
 __global__ void k_reeval(Geo g, const uint8_t *__restrict__ img, const uint16_t *__restrict__ domS,
