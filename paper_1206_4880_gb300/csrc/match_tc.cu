@@ -24,7 +24,7 @@
 // Kernel shape: persistent, one CTA per SM, 10 warps: warp 0 issues TMA loads (A tile 128 x 64,
 // B tiles 256 x 64, 128-byte swizzle, a 3-stage ring by default), warp 1 owns TMEM (two 128 x 256 FP32
 // accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16, four per tile), warps 2-9
-// (one thread per TMEM lane = range row, two warps per row group, one per column half) drain the
+// (one thread per TMEM lane = range row, two warps per row group, one per accumulator) drain the
 // accumulators with tcgen05.ld. Every wait is
 // bounded by a wall-clock limit; a timeout sets an error word, lets in-flight copies and MMAs
 // finish (bounded), frees TMEM and returns.
@@ -59,7 +59,7 @@ constexpr int kABytes = kTileM * 128;    // 128 rows x 64 fp16
 constexpr int kBBytes = kTileN * 128;    // 256 rows x 64 fp16
 constexpr int kA1Bytes = kTileM * 32;    // 128 rows x 16 fp16 (correction slice)
 constexpr int kB1Bytes = kTileN * 32;    // 256 rows x 16 fp16
-constexpr int kEpiWarps = 8;             // two per TMEM lane group, one per column half
+constexpr int kEpiWarps = 8;             // two per TMEM lane group, one per accumulator
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 constexpr int kTmemCols = 2 * kTileN;    // two accumulators
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16 (0), both K-major,
@@ -84,19 +84,20 @@ template <int S>
 constexpr size_t tc_smem() { return sizeof(TcShared<S>) + 1024; }
 static_assert(sizeof(TcShared<4>) + 1024 <= 232448, "shared memory per CTA");
 
-// Scores of one column half of an accumulator tile: 16 domains x 8 isometries for this thread's
-// range row. Per domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
+// Scores of one accumulator tile: 32 domains x 8 isometries for this thread's range row. Per
+// domain: p = max_t |P_t| / 64, the clamped least-squares gain / 512 of p:
 // s = 128 m^2 / Q + (p - m), m = min(p, Q / 256) (the exact gain / 512 up to the accumulator's
 // and this formula's rounding), formed as m (m 128 / Q - 1) + p with two FMAs. The inner FMA's
 // result lies in [-1, -1/2], so its rounding errs by at most 2^-25 absolutely and the score by
 // at most m 2^-25 <= p 2^-25 beyond its relative errors; with |P| <= sqrt(Q_r Q) (Cauchy-Schwarz,
 // Q_r = 64 sum r^2 - A^2) and Q <= 64^2 510^2 that is below 2^-16 sqrt(Q_r), a per-range term
-// the certification adds to its margin. The 16 domains form one ranking group (positions jh .. jh + 15,
-// jh a multiple of 16): only the group's largest score goes on, as one 32-bit key (its bits with
-// the low 9 replaced by 511 - the group's offset jrel in its 512-domain chunk), into t1, t2, the
-// two largest group keys of the chunk; the exact re-evaluation evaluates the best group whole, so
-// no domain position within a group is kept. MASK: domains outside this row's pool window
-// [lo_r, hi_r) score -1, and a group with none inside gives key 0.
+// the certification adds to its margin. Each 16 domains of the tile form one ranking group
+// (positions jt .. jt + 15 and jt + 16 .. jt + 31, jt a multiple of 32): only the group's largest
+// score goes on, as one 32-bit key (its bits with the low 9 replaced by 511 - the group's offset
+// in its 512-domain chunk; jrel is the tile's), into t1, t2, the two largest group keys of the
+// chunk; the exact re-evaluation evaluates the best group whole, so no domain position within a
+// group is kept. MASK: domains outside this row's pool window [lo_r, hi_r) score -1, and a group
+// with none inside gives key 0.
 __device__ __forceinline__ float absmax8(const uint32_t *v) {
     // a tree of depth two: three independent maxima of magnitudes, then their maximum
     const float a = max3_abs(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]));
@@ -115,15 +116,16 @@ __device__ __forceinline__ uint32_t chunk_key(float sc, uint32_t base) {
 }
 
 template <bool MASK>
-__device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int jh, int jrel, int lo_r, int hi_r,
+__device__ __forceinline__ void epi_tile(uint32_t taddr, const float4 *auxp, int jt, int jrel, int lo_r, int hi_r,
                                          uint32_t &t1, uint32_t &t2) {
-    float gmax = MASK ? -1.f : 0.f;  // the group's largest score
+    float gmax = MASK ? -1.f : 0.f;  // the current group's largest score
     uint32_t va[32], vb[32];
     tmem_ld32(taddr, va);
     tmem_ld_wait(va);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (c < 3) {
+    for (int c = 0; c < 8; ++c) {
+        // columns 32 c .. 32 c + 31 = domains 4 c .. 4 c + 3; the next 32 columns load meanwhile
+        if (c < 7) {
             if (c & 1)
                 tmem_ld32(taddr + (c + 1) * 32, va);
             else
@@ -145,24 +147,28 @@ __device__ __forceinline__ void epi_half(uint32_t taddr, const float4 *auxp, int
                 const float mm = fminf(p, qy);
                 float sc = fmaf(mm, fmaf(mm, qz, -1.f), p);
                 if (MASK) {
-                    const int j = jh + l;
+                    const int j = jt + l;
                     sc = (j >= lo_r && j < hi_r) ? sc : -1.f;
                 }
                 sv[q] = sc;
             }
         }
-        // one link of the running group maximum per stage
+        // one link of the running group maximum per 4 domains
         gmax = max3f(gmax, max3f(sv[0], sv[1], sv[2]), sv[3]);
-        if (c < 3) {
+        if ((c & 3) == 3) {
+            // the group of domains 16 (c >> 2) .. + 15 is complete
+            uint32_t key = chunk_key(gmax, 511u - (uint32_t)(jrel + 16 * (c >> 2)));
+            if (MASK && gmax < 0.f) key = 0u;  // no domain of the group in the window
+            top2u(t1, t2, key);
+            gmax = MASK ? -1.f : 0.f;
+        }
+        if (c < 7) {
             if (c & 1)
                 tmem_ld_wait(va);
             else
                 tmem_ld_wait(vb);
         }
     }
-    uint32_t key = chunk_key(gmax, 511u - (uint32_t)jrel);
-    if (MASK && gmax < 0.f) key = 0u;  // no domain of the group in the window
-    top2u(t1, t2, key);
 }
 
 }  // namespace
@@ -526,7 +532,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&sh.full_a[s], 1);
             mbar_init(&sh.empty_a[s], 1);
             mbar_init(&sh.tfull[s], 1);
-            mbar_init(&sh.tempty[s], kEpiWarps);
+            mbar_init(&sh.tempty[s], kEpiWarps / 2);  // the accumulator's four warps
             mbar_init(&sh.aux_ready[s], 32 * kEpiWarps);
         }
         for (int s = 0; s < S; ++s) {
@@ -640,13 +646,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
     } else {
-        // ---- epilogue: warps 2..9. Warp w reads TMEM lane group (w & 3) (range rows) and column
-        // half (w - 2) >> 2 of every accumulator tile (16 domains x 8 isometries).
+        // ---- epilogue: warps 2..9. Warp w reads TMEM lane group (w & 3) (range rows) of every
+        // tile of accumulator (w - 2) >> 2 (whole tiles: 32 domains x 8 isometries), so the tiles
+        // alternate between the two warp sets and each warp's fixed cost per tile serves 32 domains.
+        // The set is the "half" of the chunk and item keys: each set ranks the groups of its tiles.
         const int ew = warp - 2;
         const int lg = warp & 3;
         const int half = ew >> 2;
         const int row = lg * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(half * (kTileN / 2));
+        const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
         uint32_t gt = 0, lc = 0;  // accumulator tiles and chunks this CTA has processed
         bool ok = true;
         for (uint32_t li = 0; ok; ++li) {
@@ -682,20 +690,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (!ok) break;
                 // the chunk's two best 32-bit keys, folded into the 64-bit keys once per chunk
                 uint32_t t1 = 0, t2 = 0;
-                const int jrel0 = jc - cabs * kChunkDom + half * (kTileDom / 2);
+                const int jrel0 = jc - cabs * kChunkDom;
                 for (int k = 0; k < ntc; ++k, ++gt) {
                     const int acc = gt & 1;
+                    if (acc != half) continue;  // the other set's tile
                     ok = __all_sync(0xffffffffu, mbar_wait(&sh.tfull[acc], (gt >> 1) & 1, abort_flag));
                     if (!ok) break;
                     tc_fence_after();
-                    const int jh = jc + k * kTileDom + half * (kTileDom / 2);
-                    const float4 *auxp = &sh.aux[ab][(k * kTileDom + half * (kTileDom / 2)) / 2];
+                    const int jt = jc + k * kTileDom;
+                    const float4 *auxp = &sh.aux[ab][(k * kTileDom) / 2];
                     const uint32_t taddr = tbase + acc * kTileN;
                     const int jrel = jrel0 + k * kTileDom;
-                    if (jh >= f_lo && jh + kTileDom / 2 <= f_hi)
-                        epi_half<false>(taddr, auxp, jh, jrel, lo_r, hi_r, t1, t2);
+                    if (jt >= f_lo && jt + kTileDom <= f_hi)
+                        epi_tile<false>(taddr, auxp, jt, jrel, lo_r, hi_r, t1, t2);
                     else
-                        epi_half<true>(taddr, auxp, jh, jrel, lo_r, hi_r, t1, t2);
+                        epi_tile<true>(taddr, auxp, jt, jrel, lo_r, hi_r, t1, t2);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh.tempty[acc]);
@@ -887,7 +896,7 @@ __device__ __forceinline__ void reeval_finish(const ReevalRes &e, int32_t *__res
         // FP32 score formula errs < 20 * 2^-24 relatively, and the accumulator's P / 64 (an exact
         // integer Y plus one rounded correction of magnitude <= 16) errs < 2^-22 (|P / 64| + 16);
         // the score's slope in p is at most 1, so that moves it by < 2^-21 relatively plus
-        // < 2^-18 absolutely; the score's inner FMA adds < 2^-16 sqrt(Q_r) absolutely (epi_half)
+        // < 2^-18 absolutely; the score's inner FMA adds < 2^-16 sqrt(Q_r) absolutely (epi_tile)
         const double u2 = (double)__uint_as_float(e.u2);
         const double sq = (double)__fsqrt_ru(__ll2float_ru(64LL * e.Bs - e.A * e.A));
         // bound < exact gain / 512, compared as bound * 512 den < gain numerator (no division)
