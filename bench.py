@@ -655,6 +655,20 @@ def large(args, dev):
     return res
 
 
+def decode_figures(H, W, R, iters, ms, hbm_gbs):
+    """fic_decode's figures. With an even stride the steps before the last run on the plane of 2x2
+    averages, which stays in L2, so the DRAM traffic a decode must make is its output (4 B per
+    pixel) and its codes (24 B per range); the full-resolution iteration moves 8 B per pixel per
+    step, and `full_res_roofline_ms` is the time that traffic takes at the measured HBM peak."""
+    dram = 4 * H * W + 24 * R
+    full = iters * H * W * 8
+    return {"decode_iters": iters, "decode_ms": ms,
+            "decode_dram_bytes": dram, "decode_dram_gbs": dram / (ms / 1e3) / 1e9,
+            "decode_full_res_bytes": full,
+            "decode_full_res_roofline_ms": full / (hbm_gbs * 1e9) * 1e3,
+            "decode_speedup_over_full_res_roofline": full / (hbm_gbs * 1e9) * 1e3 / ms}
+
+
 def classify_bytes(H, W, B, R, Dn):
     """Algorithmic bytes of the classification stage: every pixel read once; per range its sum,
     sum of squares, box counts, FD and class written; per domain the same plus its B x B block of
@@ -695,10 +709,8 @@ def decode_rates(codes, H, W, p, flush, hbm_gbs, iters=8, ckpt=2, reps=5):
 
     dec_ms = timed(lambda: fic.decode(codes, H, W, p, iters, out=out, workspace=ws))
     bwd_ms = timed(lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, g, workspace=ws))
-    dec_b = iters * H * W * 8
     bwd_b = iters * H * W * 16
-    return {"decode_iters": iters, "decode_ms": dec_ms, "decode_gbs": dec_b / (dec_ms / 1e3) / 1e9,
-            "decode_frac_of_hbm": dec_b / (dec_ms / 1e3) / 1e9 / hbm_gbs,
+    return {**decode_figures(H, W, codes["dom"].numel(), iters, dec_ms, hbm_gbs),
             "backward_ms": bwd_ms, "backward_gbs": bwd_b / (bwd_ms / 1e3) / 1e9,
             "backward_frac_of_hbm": bwd_b / (bwd_ms / 1e3) / 1e9 / hbm_gbs}
 
@@ -744,14 +756,13 @@ def diff(args, dev):
     psnr2 = fic.quality(x2, up)[1]
     rep = refine.refine_and_quantize(codes, img, p, bits_s=5, bits_o=7, iters=iters)
     peaks, peak_src = _peaks()
-    dec_bytes = iters * H * W * 8      # read + write one FP32 image per iteration
     bwd_bytes = iters * H * W * 16     # forward recompute + adjoint gather, per iteration
     return {"workload": "512x512 seeded fBm+edges (seed 4000), stride 8, K=16; 8 iterations, checkpoint every 2",
-            "decode_ms": dec_ms, "decode_gbs": dec_bytes / (dec_ms / 1e3) / 1e9,
+            **decode_figures(H, W, codes["dom"].numel(), iters, dec_ms, float(peaks["hbm_gbs"])),
             "backward_ms": bwd_ms, "backward_gbs": bwd_bytes / (bwd_ms / 1e3) / 1e9,
             "hbm_peak_gbs": float(peaks["hbm_gbs"]),
             "note": "the 1 MiB image is L2-resident and each call is a chain of small launches; "
-                    "GB/s are algorithmic bytes over time",
+                    "the backward GB/s are algorithmic bytes over time",
             "psnr_decoded_db": psnr, "psnr_decoded_2x_db": psnr2, **rep}
 
 
@@ -849,7 +860,7 @@ def run_case(args, wl, local):
         out = torch.empty(H, W, dtype=torch.float32, device=dev)
         if args.case == "decode":
             fn = lambda: fic.decode(codes, H, W, p, iters, out=out, workspace=ws)  # noqa: E731
-            nbytes = iters * H * W * 8
+            nbytes = 4 * H * W + 24 * R  # the output and the codes: the plane steps stay in L2
         else:
             gout = torch.randn(H, W, dtype=torch.float32, device=dev)
             fn = lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, gout, workspace=ws)  # noqa: E731
@@ -872,8 +883,11 @@ def run_case(args, wl, local):
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     med = statistics.median(ms)
-    print(json.dumps({"case": args.case, "workload": args.workload, "ms": med, "algorithmic_bytes": nbytes,
-                      "gbs": nbytes / (med / 1e3) / 1e9}))
+    line = {"case": args.case, "workload": args.workload, "ms": med, "algorithmic_bytes": nbytes,
+            "gbs": nbytes / (med / 1e3) / 1e9}
+    if args.case == "decode":
+        line.update(decode_figures(H, W, R, 8, med, float(_peaks()[0]["hbm_gbs"])))
+    print(json.dumps(line))
     return 0
 
 

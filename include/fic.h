@@ -251,6 +251,9 @@ size_t fic_decode_workspace_size(const fic_geom *g, const fic_params *p, int32_t
 /* Section 1: decoding. x_0 = x0 (H*W float, row-major, dense) or 128 everywhere when x0 is
  * NULL; x_{k+1}[range r] = s_r T_{t_r}(D(x_k, dom_r)) + o_r for all ranges from x_k (Jacobi),
  * D the 2x2 average of the 2B x 2B domain; `out` (H*W float) receives x_iters, unclamped.
+ * With an even domain stride the steps before the last run on the plane of 2x2 averages of x_k
+ * (a quarter of the pixels; the same iterates in exact arithmetic, rounded in another order) and
+ * only the last step writes full-resolution pixels.
  * iters >= 0. Workspace: fic_decode_workspace_size. Codes whose domain or isometry is out of range
  * (such as the invalid codes of an encode whose matcher gave up) give NaN pixels for their range.
  * Like fic_encode, the first call with a given argument set on a host thread captures its

@@ -903,7 +903,7 @@ static fic_status check_codes(const fic_codes *c) {
 }  // extern "C"
 
 namespace {
-// Enqueues x_iters = W^iters(x_0) (ping-pong between `out` and `tmp`, landing in `out`).
+// Enqueues x_iters = W^iters(x_0) into `out` (`tmp`: H * W floats of scratch).
 fic_status decode_enqueue(const fic_codes &codes, const Geo &g, int iters, const float *x0, float *out, float *tmp,
                           cudaStream_t st) {
     const size_t img = (size_t)g.H * g.W;
@@ -913,18 +913,7 @@ fic_status decode_enqueue(const fic_codes &codes, const Geo &g, int iters, const
         else FIC_TRY(launch_fill(out, img, 128.f, st), "fill");
         return FIC_OK;
     }
-    // step k writes out when (iters-1-k) is even, tmp otherwise, so x_iters lands in out
-    const float *cur = x0;
-    if (!x0) {
-        float *init = ((iters - 1) % 2 == 0) ? tmp : out;
-        FIC_TRY(launch_fill(init, img, 128.f, st), "fill");
-        cur = init;
-    }
-    for (int k = 0; k < iters; ++k) {
-        float *dst = ((iters - 1 - k) % 2 == 0) ? out : tmp;
-        FIC_TRY(launch_decode_step(codes, g, cur, dst, st), "decode_step");
-        cur = dst;
-    }
+    FIC_TRY(launch_decode_iterate(codes, g, iters, x0, out, tmp, st), "decode");
     return FIC_OK;
 }
 

@@ -257,6 +257,268 @@ cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x,
     return cudaGetLastError();
 }
 
+// ---- iterating on the plane of 2x2 averages --------------------------------------------------
+// With an even stride every domain starts at even coordinates, so its contracted block D(x_k, d)
+// is the B x B window at (dy / 2, dx / 2) of the plane P_k of 2x2 averages of x_k
+// (P_k[i][j] = the mean of x_k over rows 2i, 2i + 1 and columns 2j, 2j + 1). x_{k+1} depends on
+// x_k only through P_k, and the 2x2 averages of a range's pixels at step k + 1 are
+//   P_{k+1}[cell (u, v) of r] = s_r E[src'_t(u, v)] + o_r,
+// E the 2x2 averages of r's window of P_k and src' the isometry of the (B/2)-square: an isometry
+// of the B-square maps aligned 2x2 pixel blocks onto aligned 2x2 cell blocks, and averaging
+// commutes with the map's affine part. So the iteration runs on P (a quarter of the pixels; the
+// two planes stay in L2 up to 4096 x 4096 images) and only the last step writes x:
+//   x_K[p] = s_r P_{K-1}[(dy / 2, dx / 2) + src_t(p)] + o_r.
+// In exact arithmetic this is the Jacobi iteration of the maps; in FP32 it rounds in another order
+// (s times the mean of four cells plus o, where the full-resolution steps average four results of
+// s times a cell plus o). With one step it is the full-resolution step bit for bit: the first
+// plane holds the same averages, summed in the same order.
+constexpr int kHalfThreads = 128;
+
+// P = the 2x2 averages of x (H x W, row stride W), two outputs per thread. V4: x is 16-byte
+// aligned, so each pair's two source rows are two float4 loads; else single floats, same sums.
+template <bool V4>
+__global__ void __launch_bounds__(kHalfThreads) k_pool2(const float *__restrict__ x, int W, float *__restrict__ P) {
+    const int Wh = W / 2, i = blockIdx.y, j = 2 * (blockIdx.x * kHalfThreads + threadIdx.x);
+    if (j >= Wh) return;  // Wh is a multiple of 4 (W is a multiple of B >= 8), so j + 1 < Wh
+    const float *a = x + (size_t)(2 * i) * W + 2 * j;
+    float v0, v1;
+    if constexpr (V4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(a));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(a + W));
+        v0 = (((t.x + t.y) + b.x) + b.y) * 0.25f;
+        v1 = (((t.z + t.w) + b.z) + b.w) * 0.25f;
+    } else {
+        v0 = (((__ldg(a) + __ldg(a + 1)) + __ldg(a + W)) + __ldg(a + W + 1)) * 0.25f;
+        v1 = (((__ldg(a + 2) + __ldg(a + 3)) + __ldg(a + W + 2)) + __ldg(a + W + 3)) * 0.25f;
+    }
+    *reinterpret_cast<float2 *>(P + (size_t)i * Wh + j) = make_float2(v0, v1);
+}
+
+// Each code once per decoding call, for the steps on the plane: (offset of the range's B x B window
+// in P, or -1 for an invalid code; isometry; s and o rounded to FP32 bits). The steps then read one
+// 16-byte record per range and convert nothing: an FP64 -> FP32 conversion runs on the FP64 pipe,
+// a small fraction of the FP32 rate on this part, and every lane converting its range's
+// coefficients at every step had been a large share of a step's time.
+__global__ void k_pack_codes(Geo g, const int32_t *__restrict__ dom, const int32_t *__restrict__ iso,
+                             const double *__restrict__ s, const double *__restrict__ o, int4 *__restrict__ pk) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.R) return;
+    const int d = dom[r], t = iso[r];
+    if (!valid_code(g, d, t)) {
+        pk[r] = make_int4(-1, 0, 0, 0);
+        return;
+    }
+    const int dq = fdiv(d, g.fDx);
+    const int off = ((dq * g.sigma) / 2) * (g.W / 2) + ((d - dq * g.nDx) * g.sigma) / 2;
+    pk[r] = make_int4(off, t, __float_as_int((float)s[r]), __float_as_int((float)o[r]));
+}
+
+template <int B>
+struct PlaneShape {
+    static constexpr int T = B == 8 ? 16 : 32;  // threads per range
+    static constexpr int G = 256 / T;           // groups per block
+    static constexpr int NR = B == 8 ? 4 : 2;   // ranges per group
+};
+
+// One step on the plane, by a group of T threads per NR ranges (T = 16 for B = 8, a warp for
+// B = 16; in each of the NR rounds consecutive groups take consecutive ranges, so a warp's stores
+// cover adjacent ranges of one range row); every range's record and source loads are issued before
+// any is used. Lane l of a group forms the cells c = l + T j of the range's (B/2) x (B/2) grid of
+// 2x2 means E of its window, row-major (each from two aligned float2 loads when V2 — the stride is
+// a multiple of 4, so every window column is even — else four single loads; the lanes of one cell
+// row read one contiguous run), summed ((w00 + w01) + w10) + w11 and scaled by 1/4, then writes
+// the cells (u, v) = c of P_{k+1}: s * E[src'_t(u, v)] + o, taking E[src'] from the lane that
+// formed it by a warp shuffle. C0: the plane is 128 everywhere (the mid-grey start, whose 2x2
+// means are 128 exactly), so nothing is read.
+template <int B, bool V2, bool C0>
+__global__ void __launch_bounds__(256)
+    k_plane_half(Geo g, const int4 *__restrict__ pk, const float *__restrict__ P, float *__restrict__ y) {
+    constexpr int T = PlaneShape<B>::T, G = PlaneShape<B>::G, NR = PlaneShape<B>::NR;
+    constexpr int OB = B / 2, J = OB * OB / T;  // cells per lane: 1 (B = 8), 2 (B = 16)
+    const int grp = threadIdx.x / T, l = threadIdx.x % T, gbase = (threadIdx.x & 31) & ~(T - 1);
+    const unsigned gmask = T == 32 ? 0xffffffffu : (0xFFFFu << (threadIdx.x & 16));
+    const int Wh = g.W / 2;
+    int r[NR];
+    int4 c[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        r[k] = (blockIdx.x * NR + k) * G + grp;
+        c[k] = r[k] < g.R ? __ldg(pk + r[k]) : make_int4(-1, 0, 0, 0);
+    }
+    float e[NR][J];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) e[k][j] = 128.f;
+        if (C0 || c[k].x < 0) continue;  // an invalid code (an encode that gave up): no read
+        const float *w = P + c[k].x;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = l + T * j, cy = q / OB, cx = q % OB;
+            const float *p = w + (size_t)(2 * cy) * Wh + 2 * cx;
+            if constexpr (V2) {
+                const float2 lo = __ldg(reinterpret_cast<const float2 *>(p));
+                const float2 hi = __ldg(reinterpret_cast<const float2 *>(p + Wh));
+                e[k][j] = (((lo.x + lo.y) + hi.x) + hi.y) * 0.25f;
+            } else {
+                e[k][j] = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + Wh)) + __ldg(p + Wh + 1)) * 0.25f;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const bool live = r[k] < g.R;
+        const int rq = live ? fdiv(r[k], g.fRx) : 0;
+        float *dst = y + (size_t)(rq * OB) * Wh + (r[k] - rq * g.nRx) * OB;
+        const float sr = __int_as_float(c[k].z), orr = __int_as_float(c[k].w);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = l + T * j, u = q / OB, v = q % OB;
+            int sy, sx;
+            iso_src(OB, c[k].y, u, v, sy, sx);
+            const int src = sy * OB + sx;  // the cell to take: lane src % T, register src / T
+            float val = __shfl_sync(gmask, e[k][0], gbase + src % T);
+            if constexpr (J == 2) {
+                const float hi = __shfl_sync(gmask, e[k][1], gbase + src % T);
+                val = src >= T ? hi : val;
+            }
+            if (live) dst[(size_t)u * Wh + v] = c[k].x >= 0 ? fmaf(sr, val, orr) : __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+// The last step: the B x B pixels of x_K, s * window[src_t(py, px)] + o, by the same groups; the
+// group copies each range's window into shared memory (float2 loads when V2), then every lane
+// writes B * B / T pixels (eight adjacent lanes cover 32 contiguous bytes of a pixel row).
+template <int B, bool V2, bool C0>
+__global__ void __launch_bounds__(256)
+    k_plane_final(Geo g, const int4 *__restrict__ pk, const float *__restrict__ P, float *__restrict__ y) {
+    constexpr int T = PlaneShape<B>::T, G = PlaneShape<B>::G, NR = PlaneShape<B>::NR;
+    __shared__ __align__(16) float win[G][NR][B * B];
+    const int grp = threadIdx.x / T, l = threadIdx.x % T;
+    const unsigned gmask = T == 32 ? 0xffffffffu : (0xFFFFu << (threadIdx.x & 16));
+    const int Wh = g.W / 2;
+    int r[NR];
+    int4 c[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        r[k] = (blockIdx.x * NR + k) * G + grp;
+        c[k] = r[k] < g.R ? __ldg(pk + r[k]) : make_int4(-1, 0, 0, 0);
+    }
+    if constexpr (!C0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            if (c[k].x < 0) continue;  // an invalid code: no read
+            const float *w = P + c[k].x;
+            float *wn = win[grp][k];
+            if constexpr (V2) {
+#pragma unroll
+                for (int q = l; q < B * B / 2; q += T) {
+                    const int row = q / (B / 2), c2 = q % (B / 2);
+                    *reinterpret_cast<float2 *>(&wn[row * B + 2 * c2]) =
+                        __ldg(reinterpret_cast<const float2 *>(w + (size_t)row * Wh + 2 * c2));
+                }
+            } else {
+#pragma unroll
+                for (int q = l; q < B * B; q += T) wn[q] = __ldg(w + (size_t)(q / B) * Wh + q % B);
+            }
+        }
+        __syncwarp(gmask);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        if (r[k] >= g.R) continue;
+        const int rq = fdiv(r[k], g.fRx);
+        float *dst = y + (size_t)(rq * B) * g.W + (r[k] - rq * g.nRx) * B;
+        const float sr = __int_as_float(c[k].z), orr = __int_as_float(c[k].w);
+        const float *wn = win[grp][k];
+#pragma unroll
+        for (int q = l; q < B * B; q += T) {
+            const int u = q / B, v = q % B;
+            float val = __int_as_float(0x7fc00000);  // an invalid code: NaN pixels
+            if (c[k].x >= 0) {
+                int sy, sx;
+                iso_src(B, c[k].y, u, v, sy, sx);
+                val = fmaf(sr, C0 ? 128.f : wn[sy * B + sx], orr);
+            }
+            dst[(size_t)u * g.W + v] = val;
+        }
+    }
+}
+
+template <int B, bool FINAL>
+void launch_plane_step(bool v2, bool c0, const Geo &g, const int4 *pk, const float *P, float *y, cudaStream_t st) {
+    constexpr int per_block = PlaneShape<B>::G * PlaneShape<B>::NR;
+    const unsigned blocks = (unsigned)((g.R + per_block - 1) / per_block);
+    if constexpr (!FINAL) {
+        if (c0) k_plane_half<B, false, true><<<blocks, 256, 0, st>>>(g, pk, P, y);
+        else if (v2) k_plane_half<B, true, false><<<blocks, 256, 0, st>>>(g, pk, P, y);
+        else k_plane_half<B, false, false><<<blocks, 256, 0, st>>>(g, pk, P, y);
+    } else {
+        if (c0) k_plane_final<B, false, true><<<blocks, 256, 0, st>>>(g, pk, P, y);
+        else if (v2) k_plane_final<B, true, false><<<blocks, 256, 0, st>>>(g, pk, P, y);
+        else k_plane_final<B, false, false><<<blocks, 256, 0, st>>>(g, pk, P, y);
+    }
+}
+
+bool decode_on_plane(const Geo &g) { return g.sigma % 2 == 0 && g.H <= 65535; }
+
+cudaError_t launch_decode_iterate(const fic_codes &c, const Geo &g, int iters, const float *x0, float *out,
+                                  float *tmp, cudaStream_t st) {
+    const size_t img = (size_t)g.H * g.W;
+    if (iters <= 0) return cudaErrorInvalidValue;
+    if (!decode_on_plane(g)) {
+        // odd strides: full-resolution steps, ping-pong between out and tmp ending in out
+        const float *cur = x0;
+        cudaError_t e = cudaSuccess;
+        if (!x0) {
+            float *init = ((iters - 1) % 2 == 0) ? tmp : out;
+            e = launch_fill(init, img, 128.f, st);
+            cur = init;
+        }
+        for (int k = 0; k < iters && e == cudaSuccess; ++k) {
+            float *dst = ((iters - 1 - k) % 2 == 0) ? out : tmp;
+            e = launch_decode_step(c, g, cur, dst, st);
+            cur = dst;
+        }
+        return e;
+    }
+    // two planes of img / 4 floats in tmp (offset img bytes: a multiple of 256), then the packed
+    // codes (R int4 <= img / 16 floats); with no x0 the first step reads the constant start
+    // instead of a plane
+    const int Wh = g.W / 2, Hh = g.H / 2;
+    float *pa = tmp, *pb = tmp + img / 4;
+    int4 *pk = reinterpret_cast<int4 *>(tmp + img / 2);
+    k_pack_codes<<<(unsigned)((g.R + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, pk);
+    ++g_launches;
+    cudaError_t e = cudaGetLastError();
+    if (x0 && e == cudaSuccess) {
+        const dim3 grid((unsigned)((Wh / 2 + kHalfThreads - 1) / kHalfThreads), (unsigned)Hh);
+        if ((uintptr_t)x0 % 16 == 0)
+            k_pool2<true><<<grid, kHalfThreads, 0, st>>>(x0, g.W, pa);
+        else
+            k_pool2<false><<<grid, kHalfThreads, 0, st>>>(x0, g.W, pa);
+        ++g_launches;
+        e = cudaGetLastError();
+    }
+    const bool v2 = g.sigma % 4 == 0;
+    bool c0 = !x0;
+    for (int k = 1; k < iters && e == cudaSuccess; ++k, c0 = false) {
+        if (g.B == 16) launch_plane_step<16, false>(v2, c0, g, pk, pa, pb, st);
+        else launch_plane_step<8, false>(v2, c0, g, pk, pa, pb, st);
+        ++g_launches;
+        e = cudaGetLastError();
+        float *t = pa;
+        pa = pb;
+        pb = t;
+    }
+    if (e != cudaSuccess) return e;
+    if (g.B == 16) launch_plane_step<16, true>(v2, c0, g, pk, pa, out, st);
+    else launch_plane_step<8, true>(v2, c0, g, pk, pa, out, st);
+    ++g_launches;
+    return cudaGetLastError();
+}
+
 // Resolution-independent step (Section 1): the codes of an H x W encoding applied on the
 // (zH) x (zW) grid; range r covers the (Bz)^2 block at z times its position, domain d the (2Bz)^2
 // block at z times its position, contracted by 2x2 averaging, with the isometries of the

@@ -3,8 +3,9 @@
 // Some callers cannot call cudaMalloc: applications that reserve all device memory up front and
 // hand libraries only the buffers they need (engines and media frameworks that own the memory
 // budget), and latency-critical loops in which an allocation could block on, or synchronise,
-// the device. fic_decode needs one image of scratch besides its output (the second buffer of the
-// Jacobi iteration), which those callers cannot provide on demand. This variant keeps that
+// the device. fic_decode needs one image of scratch besides its output (the two planes of 2x2
+// averages it iterates on, or with odd strides the second buffer of the Jacobi iteration), which
+// those callers cannot provide on demand. This variant keeps that
 // scratch in a fixed array in the library's device memory instead: every GPU that loads the
 // library holds the array (kStaticDecodeMaxPixels floats, 4 MiB) until the process exits.
 //
@@ -94,19 +95,8 @@ extern "C" fic_status fic_decode_static(const fic_codes *codes, const fic_geom *
         e = x0 ? cudaMemcpyAsync(out, x0, img * sizeof(float), cudaMemcpyDeviceToDevice, st)
                : launch_fill(out, img, 128.f, st);
     } else {
-        // step k writes `out` when (iters - 1 - k) is even, the scratch otherwise, so the last
-        // iterate lands in `out`; with no x0 the start image (128) goes where step 0 reads
-        const float *cur = x0;
-        if (!x0) {
-            float *init = ((iters - 1) % 2 == 0) ? tmp : out;
-            e = launch_fill(init, img, 128.f, st);
-            cur = init;
-        }
-        for (int k = 0; k < iters && e == cudaSuccess; ++k) {
-            float *dst = ((iters - 1 - k) % 2 == 0) ? out : tmp;
-            e = launch_decode_step(*codes, g, cur, dst, st);
-            cur = dst;
-        }
+        // the same launches as fic_decode, with the fixed array as its scratch
+        e = launch_decode_iterate(*codes, g, iters, x0, out, tmp, st);
     }
     if (e != cudaSuccess) {
         set_error(cudaGetErrorString(e));

@@ -474,6 +474,11 @@ cudaError_t launch_info(const EncodeBufs *b, int n, const TcBatch &tb, fic_encod
 // decode
 cudaError_t launch_decode_step(const fic_codes &c, const Geo &g, const float *x, float *y,
                                cudaStream_t st);
+// x_iters of the Jacobi iteration from x0 (NULL: 128 everywhere) into out, iters >= 1; tmp holds
+// H * W floats of scratch. Even strides iterate on the plane of 2x2 averages and write x only at
+// the last step; odd strides take full-resolution steps.
+cudaError_t launch_decode_iterate(const fic_codes &c, const Geo &g, int iters, const float *x0, float *out,
+                                  float *tmp, cudaStream_t st);
 cudaError_t launch_fill(float *x, size_t n, float v, cudaStream_t st);
 // Domain -> ranges index of the adjoint (decode.cu): key[R], list[R] (range ids sorted by domain),
 // t1[R], t2[R] sort buffers, off[Dn + 1] segment starts, digit[R] bytes, counts (radix
