@@ -1038,7 +1038,6 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
     csr.ent = c.take<int4>(adjoint_entries(g));
     csr.acc = c.take<float>((size_t)g.R * g.n);
     float2 *gacc = c.take<float2>(2 * (size_t)g.R);  // float-float gradient accumulators
-    (void)pingpong;
     g_launches = 0;
     FIC_TRY(cudaMemsetAsync(gacc, 0, sizeof(float2) * 2 * g.R, st), "memset");
     if (iters == 0) {
@@ -1046,6 +1045,16 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
         return FIC_OK;
     }
     FIC_TRY(launch_dom_csr(g, *codes, csr, st), "csr");
+    if (decode_on_plane(g)) {
+        // even strides: checkpoints, recomputation and every step but the last on the plane of
+        // 2x2 averages, as fic_decode iterates (the packed codes go where the full-resolution
+        // ping-pong buffer would)
+        FIC_TRY(launch_backward_plane(*codes, g, csr, iters, ck, x0, grad_out, ckpt, seg, lam,
+                                      reinterpret_cast<int4 *>(pingpong), gacc, gacc + g.R, st),
+                "backward_plane");
+        FIC_TRY(launch_grads_out(g.R, gacc, gacc + g.R, grad_s, grad_o, st), "grads_out");
+        return FIC_OK;
+    }
     // forward: checkpoints x_0, x_ck, x_2ck, ...
     if (x0) FIC_TRY(cudaMemcpyAsync(ckpt, x0, img * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy");
     else FIC_TRY(launch_fill(ckpt, img, 128.f, st), "fill");

@@ -598,19 +598,21 @@ __global__ void k_csr_offsets(int n, int Dn, const int32_t *__restrict__ skey, i
     off[d] = lo;
 }
 
-// Phase "cells": one warp per listed range.
-template <int B>
+// Phase "cells": one warp per listed range (B = 4: its first 16 lanes). MUL = 4 gives s_r l[p_r(c)]
+// (the transpose of a map without the 2x2 averaging: the packed entry holds s_r / 4, and the
+// product by 4 is exact).
+template <int B, int MUL = 1>
 __global__ void __launch_bounds__(256)
     k_adjoint_cells(Geo g, const int4 *__restrict__ ent, const int32_t *__restrict__ off,
                     const float *__restrict__ lam, float *__restrict__ acc) {
-    constexpr int NC = B * B / 32;
+    constexpr int NC = (B * B + 31) / 32;
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (k >= g.R) return;
     const int n = __ldg(off + g.Dn);  // listed ranges (the rest of the list holds the others)
     const int4 e = __ldg(ent + k);
     if (k >= n) return;
     const int r = e.x, t = e.y;
-    const float sc = __int_as_float(e.z);
+    const float sc = __int_as_float(e.z) * (float)MUL;
     const int rq = fdiv(r, g.fRx);
     const float *lr = lam + (size_t)(rq * B) * g.W + (r - rq * g.nRx) * B;
     // the pixel p with src_t(p) = c is p = src_{t^-1}(c)
@@ -620,17 +622,21 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
         const int c = lane + 32 * m, p = c0 + ky * (c / B) + kx * (c % B);
-        dst[c] = sc * __ldg(lr + (size_t)(p / B) * g.W + p % B);
+        if (B * B >= 32 || c < B * B) dst[c] = sc * __ldg(lr + (size_t)(p / B) * g.W + p % B);
     }
 }
 
 // The sum of phase "pixels" for pixel (qy, qx) over the domains (jy, jx) covering it, row-major,
 // and each domain's ranges in list order. MJ > 0: at most MJ domains cover a coordinate per axis,
 // and every covering domain's segment bounds are loaded before any cell; MJ = 0: any number.
-template <int B, int MJ>
+// WIN: the domains are windows of side 2B whose cells are single pixels (2B x 2B cells per range,
+// cell (qy - jy sigma, qx - jx sigma)), the transpose of a map without the 2x2 averaging.
+template <int B, int MJ, bool WIN = false>
 __device__ __forceinline__ float adjoint_sum(const Geo &g, const int32_t *__restrict__ off,
                                              const float *__restrict__ acc, int jy_lo, int jy_hi, int jx_lo,
                                              int jx_hi, int qy, int qx) {
+    constexpr int CB = WIN ? 2 * B : B;  // cells per side of a domain's block
+    constexpr int SH = WIN ? 0 : 1;
     float a = 0.f;
     if constexpr (MJ > 0) {
         int o0[MJ * MJ], o1[MJ * MJ];
@@ -647,18 +653,18 @@ __device__ __forceinline__ float adjoint_sum(const Geo &g, const int32_t *__rest
         for (int u = 0; u < MJ; ++u)
 #pragma unroll
             for (int v = 0; v < MJ; ++v) {
-                const float *cp = acc + ((qy - (jy_lo + u) * g.sigma) >> 1) * B + ((qx - (jx_lo + v) * g.sigma) >> 1);
-                for (int k = o0[u * MJ + v]; k < o1[u * MJ + v]; ++k) a += __ldg(cp + (size_t)k * (B * B));
+                const float *cp = acc + ((qy - (jy_lo + u) * g.sigma) >> SH) * CB + ((qx - (jx_lo + v) * g.sigma) >> SH);
+                for (int k = o0[u * MJ + v]; k < o1[u * MJ + v]; ++k) a += __ldg(cp + (size_t)k * (CB * CB));
             }
         return a;
     }
     for (int jy = jy_lo; jy <= jy_hi; ++jy) {
-        const int cy = (qy - jy * g.sigma) >> 1;
+        const int cy = (qy - jy * g.sigma) >> SH;
         for (int jx = jx_lo; jx <= jx_hi; ++jx) {
             const int d = jy * g.nDx + jx;
             const int o1 = __ldg(off + d + 1);
-            const float *cp = acc + cy * B + ((qx - jx * g.sigma) >> 1);
-            for (int k = __ldg(off + d); k < o1; ++k) a += __ldg(cp + (size_t)k * (B * B));
+            const float *cp = acc + cy * CB + ((qx - jx * g.sigma) >> SH);
+            for (int k = __ldg(off + d); k < o1; ++k) a += __ldg(cp + (size_t)k * (CB * CB));
         }
     }
     return a;
@@ -674,7 +680,7 @@ __device__ __forceinline__ void covering(const Geo &g, int q, int n, int &lo, in
 }
 
 // Phase "pixels", odd stride: l_prev = W^T l, one thread per pixel, blockIdx.y striding over rows.
-template <int B, int MJ>
+template <int B, int MJ, bool WIN = false>
 __global__ void __launch_bounds__(256)
     k_adjoint_gather(Geo g, const int32_t *__restrict__ off, const float *__restrict__ acc,
                      float *__restrict__ lam_prev) {
@@ -685,7 +691,7 @@ __global__ void __launch_bounds__(256)
     for (int qy = blockIdx.y; qy < g.H; qy += gridDim.y) {
         int jy_lo, jy_hi;
         covering<B>(g, qy, g.nDy, jy_lo, jy_hi);
-        lam_prev[(size_t)qy * g.W + qx] = adjoint_sum<B, MJ>(g, off, acc, jy_lo, jy_hi, jx_lo, jx_hi, qy, qx);
+        lam_prev[(size_t)qy * g.W + qx] = adjoint_sum<B, MJ, WIN>(g, off, acc, jy_lo, jy_hi, jx_lo, jx_hi, qy, qx);
     }
 }
 
@@ -901,6 +907,209 @@ cudaError_t launch_adjoint_grads(const Geo &g, const fic_codes &c, const float *
 cudaError_t launch_grads_out(int R, const float2 *gsf, const float2 *gof, float *gs, float *go, cudaStream_t st) {
     k_grads_out<<<(R + 255) / 256, 256, 0, st>>>(R, gsf, gof, gs, go);
     ++g_launches;
+    return cudaGetLastError();
+}
+
+// ---- the adjoint on the plane of 2x2 averages ------------------------------------------------
+// With an even stride one step is x_{k+1} = M P_k + b, P_k = A x_k the plane of 2x2 averages and M
+// the per-range map s_r T_t of its window, so with nu_k = dL/dP_k = M^T l_{k+1}:
+//   nu_{K-1} = M^T l_K (l_K = dL/dx_K, full resolution),
+//   nu_k = H^T nu_{k+1} for k < K - 1, H = A M the plane step, which is the fractal map of ranges
+//   B/2 and windows B on the plane at stride sigma/2 (so W^T's two phases on the plane geometry);
+// and the gradient terms of step k, from l_{k+1} = A^T nu_{k+1} (nu_{k+1} / 4 over each 2x2 block):
+//   k < K - 1: grad_s_r += sum over the cells c of r of nu_{k+1}[c] E_k[src'_t(c)] (E_k the 2x2 means
+//              of r's window of P_k), grad_o_r += sum_c nu_{k+1}[c];
+//   k = K - 1: grad_s_r += sum over the pixels p of r of l_K[p] P_{K-1}[window + src_t(p)],
+//              grad_o_r += sum_p l_K[p].
+// The checkpoints and the recomputed iterates are planes, and only the last step reads full-
+// resolution data (l_K).
+
+// Gradient terms of one step, a group of T lanes per range (as the plane steps): FINAL = false
+// takes lam = nu_{k+1} (a plane) and the 2x2 means of the window of P = P_k (each lane the cells
+// l + T j in row-major order, E[src'] fetched from the lane that formed it by a shuffle); FINAL =
+// true takes lam = l_K (full resolution) and the window of P = P_{K-1} directly. Exact FP32
+// products summed in float-float per lane, across the group and into the per-range accumulators.
+template <int B, bool FINAL, bool V2>
+__global__ void __launch_bounds__(256)
+    k_plane_grads(Geo g, const int4 *__restrict__ pk, const float *__restrict__ P, const float *__restrict__ lam,
+                  float2 *__restrict__ gs, float2 *__restrict__ go) {
+    constexpr int T = PlaneShape<B>::T, G = PlaneShape<B>::G;
+    constexpr int OB = B / 2, J = OB * OB / T, JF = B * B / T;
+    const int grp = threadIdx.x / T, l = threadIdx.x % T, gbase = (threadIdx.x & 31) & ~(T - 1);
+    const unsigned gmask = T == 32 ? 0xffffffffu : (0xFFFFu << (threadIdx.x & 16));
+    const int r = blockIdx.x * G + grp;
+    if (r >= g.R) return;  // whole groups leave together
+    const int4 c = __ldg(pk + r);
+    if (c.x < 0) {  // an invalid code: NaN gradients, no read
+        if (l == 0) gs[r] = go[r] = make_float2(__int_as_float(0x7fc00000), 0.f);
+        return;
+    }
+    const int Wh = g.W / 2;
+    const int rq = fdiv(r, g.fRx), rx = r - rq * g.nRx;
+    const float *w = P + c.x;
+    FF ss{0.f, 0.f}, so{0.f, 0.f};
+    if constexpr (FINAL) {
+#pragma unroll
+        for (int j = 0; j < JF; ++j) {
+            const int q = l + T * j, py = q / B, px = q % B;
+            int sy, sx;
+            iso_src(B, c.y, py, px, sy, sx);
+            const float v = __ldg(w + (size_t)sy * Wh + sx);
+            const float lv = __ldg(lam + (size_t)(rq * B + py) * g.W + rx * B + px);
+            const float ph = lv * v;
+            ff_add(ss, ph, fmaf(lv, v, -ph));
+            ff_add(so, lv, 0.f);
+        }
+    } else {
+        float e[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = l + T * j, cy = q / OB, cx = q % OB;
+            const float *p = w + (size_t)(2 * cy) * Wh + 2 * cx;
+            if constexpr (V2) {
+                const float2 lo = __ldg(reinterpret_cast<const float2 *>(p));
+                const float2 hi = __ldg(reinterpret_cast<const float2 *>(p + Wh));
+                e[j] = (((lo.x + lo.y) + hi.x) + hi.y) * 0.25f;
+            } else {
+                e[j] = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + Wh)) + __ldg(p + Wh + 1)) * 0.25f;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = l + T * j, u = q / OB, v = q % OB;
+            int sy, sx;
+            iso_src(OB, c.y, u, v, sy, sx);
+            const int src = sy * OB + sx;  // the cell to take: lane src % T, register src / T
+            float val = __shfl_sync(gmask, e[0], gbase + src % T);
+            if constexpr (J == 2) {
+                const float hi = __shfl_sync(gmask, e[1], gbase + src % T);
+                val = src >= T ? hi : val;
+            }
+            const float lv = __ldg(lam + (size_t)(rq * OB + u) * Wh + rx * OB + v);
+            const float ph = lv * val;
+            ff_add(ss, ph, fmaf(lv, val, -ph));
+            ff_add(so, lv, 0.f);
+        }
+    }
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) {
+        const float sh = __shfl_xor_sync(gmask, ss.hi, o), sl = __shfl_xor_sync(gmask, ss.lo, o);
+        const float oh = __shfl_xor_sync(gmask, so.hi, o), ol = __shfl_xor_sync(gmask, so.lo, o);
+        ff_add(ss, sh, sl);
+        ff_add(so, oh, ol);
+    }
+    if (l == 0) {
+        FF a{gs[r].x, gs[r].y}, b{go[r].x, go[r].y};
+        ff_add(a, ss.hi, ss.lo);
+        ff_add(b, so.hi, so.lo);
+        ff_norm(a);
+        ff_norm(b);
+        gs[r] = make_float2(a.hi, a.lo);
+        go[r] = make_float2(b.hi, b.lo);
+    }
+}
+
+// The plane geometry of H: ranges B/2 and windows B on the (H/2) x (W/2) plane at stride sigma/2,
+// the same range and domain grids.
+static Geo plane_geo(const Geo &g) {
+    Geo p = g;
+    p.H = g.H / 2;
+    p.W = g.W / 2;
+    p.pitch = p.W;
+    p.B = g.B / 2;
+    p.n = p.B * p.B;
+    p.sigma = g.sigma / 2;
+    p.fS = make_fastdiv((uint32_t)p.sigma);
+    return p;
+}
+
+template <int B>
+static void plane_grads(bool fin, bool v2, const Geo &g, const int4 *pk, const float *P, const float *lam,
+                        float2 *gs, float2 *go, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((g.R + PlaneShape<B>::G - 1) / PlaneShape<B>::G);
+    if (fin) k_plane_grads<B, true, false><<<blocks, 256, 0, st>>>(g, pk, P, lam, gs, go);
+    else if (v2) k_plane_grads<B, false, true><<<blocks, 256, 0, st>>>(g, pk, P, lam, gs, go);
+    else k_plane_grads<B, false, false><<<blocks, 256, 0, st>>>(g, pk, P, lam, gs, go);
+}
+
+// nu_{K-1} = M^T l_K: cell blocks s_r l_K[p_r(c)] of B x B window pixels per listed range, then
+// per plane pixel the sum over the covering windows (side B at stride sigma/2) and their ranges.
+template <int B>
+static void plane_mt(const Geo &g, const Geo &gp, const AdjointCsr &a, const float *lK, float *nu,
+                     cudaStream_t st) {
+    const unsigned cells = (unsigned)(((long long)g.R * 32 + 255) / 256);
+    k_adjoint_cells<B, 4><<<cells, 256, 0, st>>>(g, a.ent, a.off, lK, a.acc);
+    const int mj = (B + gp.sigma - 1) / gp.sigma;  // covering windows per axis: at most ceil(B / (sigma/2))
+    const dim3 px((unsigned)((gp.W + 255) / 256), (unsigned)min(gp.H, 65535));
+    if (mj <= 2)
+        k_adjoint_gather<B / 2, 2, true><<<px, 256, 0, st>>>(gp, a.off, a.acc, nu);
+    else if (mj <= 4)
+        k_adjoint_gather<B / 2, 4, true><<<px, 256, 0, st>>>(gp, a.off, a.acc, nu);
+    else
+        k_adjoint_gather<B / 2, 0, true><<<px, 256, 0, st>>>(gp, a.off, a.acc, nu);
+}
+
+template <int B>
+static void plane_ht(const Geo &gp, const AdjointCsr &a, const float *nu, float *nu_prev, cudaStream_t st) {
+    // H^T on the plane: W^T's two phases with ranges B/2 (cells (s_r / 4) nu[p_r(c)], 2x2 blocks)
+    adjoint_gather_b<B / 2>(gp, a, nu, nu_prev, st);
+}
+
+cudaError_t launch_backward_plane(const fic_codes &c, const Geo &g, const AdjointCsr &a, int iters, int ck,
+                                  const float *x0, const float *grad_out, float *ckpt, float *seg, float *nu,
+                                  int4 *pk, float2 *gs, float2 *go, cudaStream_t st) {
+    const size_t pl = (size_t)g.H * g.W / 4;  // floats per plane (a multiple of 64)
+    const int nseg = (iters + ck - 1) / ck;
+    const Geo gp = plane_geo(g);
+    const bool v2 = g.sigma % 4 == 0;
+    k_pack_codes<<<(unsigned)((g.R + 255) / 256), 256, 0, st>>>(g, c.dom, c.iso, c.s, c.o, pk);
+    ++g_launches;
+    // P_0 into the first checkpoint
+    if (x0) {
+        const dim3 grid((unsigned)((g.W / 4 + kHalfThreads - 1) / kHalfThreads), (unsigned)(g.H / 2));
+        if ((uintptr_t)x0 % 16 == 0)
+            k_pool2<true><<<grid, kHalfThreads, 0, st>>>(x0, g.W, ckpt);
+        else
+            k_pool2<false><<<grid, kHalfThreads, 0, st>>>(x0, g.W, ckpt);
+        ++g_launches;
+    } else {
+        cudaError_t e = launch_fill(ckpt, pl, 128.f, st);
+        if (e != cudaSuccess) return e;
+    }
+    auto plane = [&](int c0, int i) -> float * { return i == 0 ? ckpt + (size_t)c0 * pl : seg + (size_t)i * pl; };
+    auto step = [&](const float *src, float *dst) {
+        if (g.B == 16) launch_plane_step<16, false>(v2, false, g, pk, src, dst, st);
+        else launch_plane_step<8, false>(v2, false, g, pk, src, dst, st);
+        ++g_launches;
+    };
+    for (int c0 = 0; c0 + 1 < nseg; ++c0)
+        for (int i = 1; i <= ck; ++i) step(plane(c0, i - 1), i == ck ? ckpt + (size_t)(c0 + 1) * pl : plane(c0, i));
+    float *ncur = nu, *nprev = nu + pl;
+    bool fin = true;  // the first reverse step is the last forward step
+    for (int c0 = nseg - 1; c0 >= 0; --c0) {
+        const int len = (c0 == nseg - 1) ? iters - c0 * ck : ck;
+        for (int i = 1; i < len; ++i) step(plane(c0, i - 1), plane(c0, i));
+        for (int i = len - 1; i >= 0; --i) {
+            const float *lam = fin ? grad_out : ncur;
+            if (g.B == 16) plane_grads<16>(fin, v2, g, pk, plane(c0, i), lam, gs, go, st);
+            else plane_grads<8>(fin, v2, g, pk, plane(c0, i), lam, gs, go, st);
+            ++g_launches;
+            if (c0 > 0 || i > 0) {
+                if (fin) {
+                    if (g.B == 16) plane_mt<16>(g, gp, a, grad_out, ncur, st);
+                    else plane_mt<8>(g, gp, a, grad_out, ncur, st);
+                } else {
+                    if (g.B == 16) plane_ht<16>(gp, a, ncur, nprev, st);
+                    else plane_ht<8>(gp, a, ncur, nprev, st);
+                    float *t = ncur;
+                    ncur = nprev;
+                    nprev = t;
+                }
+                g_launches += 2;
+            }
+            fin = false;
+        }
+    }
     return cudaGetLastError();
 }
 

@@ -489,6 +489,14 @@ struct AdjointCsr {
     int4 *ent;   // [R] per list position: (range id, isometry, s / 4 as float bits, 0)
     float *acc;
 };
+// The adjoint of `iters` decoding steps for an even stride, on the plane of 2x2 averages:
+// checkpoints every ck steps (ckpt: nseg planes, seg: ck planes, nu: 2 planes, pk: R records;
+// planes are H * W / 4 floats), the gradient terms accumulated into gs, go (float-float per range).
+// The domain -> ranges index `a` must be built first.
+cudaError_t launch_backward_plane(const fic_codes &c, const Geo &g, const AdjointCsr &a, int iters, int ck,
+                                  const float *x0, const float *grad_out, float *ckpt, float *seg, float *nu,
+                                  int4 *pk, float2 *gs, float2 *go, cudaStream_t st);
+bool decode_on_plane(const Geo &g);
 // Stable sort of 0 .. n-1 by key (pools.cu); scratch sizes: see launch_radix_sort.
 size_t radix_counts_ints(int n);
 cudaError_t launch_radix_sort(const int32_t *key, int n, uint32_t key_max, int32_t *perm, int32_t *t1, int32_t *t2,
