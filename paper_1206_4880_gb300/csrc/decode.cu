@@ -598,15 +598,17 @@ __global__ void k_csr_offsets(int n, int Dn, const int32_t *__restrict__ skey, i
     off[d] = lo;
 }
 
-// Phase "cells": one warp per listed range (B = 4: its first 16 lanes). MUL = 4 gives s_r l[p_r(c)]
+// Phase "cells": one warp per listed range (B = 4: one half-warp). MUL = 4 gives s_r l[p_r(c)]
 // (the transpose of a map without the 2x2 averaging: the packed entry holds s_r / 4, and the
 // product by 4 is exact).
 template <int B, int MUL = 1>
 __global__ void __launch_bounds__(256)
     k_adjoint_cells(Geo g, const int4 *__restrict__ ent, const int32_t *__restrict__ off,
                     const float *__restrict__ lam, float *__restrict__ acc) {
-    constexpr int NC = (B * B + 31) / 32;
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    constexpr int LPR = B * B >= 32 ? 32 : B * B;  // lanes per range
+    constexpr int NC = B * B / LPR;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = tid / LPR, lane = tid % LPR;
     if (k >= g.R) return;
     const int n = __ldg(off + g.Dn);  // listed ranges (the rest of the list holds the others)
     const int4 e = __ldg(ent + k);
@@ -621,8 +623,8 @@ __global__ void __launch_bounds__(256)
     float *dst = acc + (size_t)k * (B * B);
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
-        const int c = lane + 32 * m, p = c0 + ky * (c / B) + kx * (c % B);
-        if (B * B >= 32 || c < B * B) dst[c] = sc * __ldg(lr + (size_t)(p / B) * g.W + p % B);
+        const int c = lane + LPR * m, p = c0 + ky * (c / B) + kx * (c % B);
+        dst[c] = sc * __ldg(lr + (size_t)(p / B) * g.W + p % B);
     }
 }
 
@@ -857,7 +859,7 @@ void gather_px(const Geo &g, const AdjointCsr &a, float *lam_prev, cudaStream_t 
 
 template <int B>
 void adjoint_gather_b(const Geo &g, const AdjointCsr &a, const float *lam, float *lam_prev, cudaStream_t st) {
-    const unsigned cells = (unsigned)(((long long)g.R * 32 + 255) / 256);
+    const unsigned cells = (unsigned)(((long long)g.R * (B * B >= 32 ? 32 : B * B) + 255) / 256);
     k_adjoint_cells<B><<<cells, 256, 0, st>>>(g, a.ent, a.off, lam, a.acc);
     // covering domains per axis: at most ceil(2B / sigma)
     const int mj = (2 * B + g.sigma - 1) / g.sigma;
@@ -924,19 +926,26 @@ cudaError_t launch_grads_out(int R, const float2 *gsf, const float2 *gof, float 
 // The checkpoints and the recomputed iterates are planes, and only the last step reads full-
 // resolution data (l_K).
 
-// Gradient terms of one step, a group of T lanes per range (as the plane steps): FINAL = false
-// takes lam = nu_{k+1} (a plane) and the 2x2 means of the window of P = P_k (each lane the cells
-// l + T j in row-major order, E[src'] fetched from the lane that formed it by a shuffle); FINAL =
-// true takes lam = l_K (full resolution) and the window of P = P_{K-1} directly. Exact FP32
+// Gradient terms of one step, a group of TG lanes per range (4 for 8x8 ranges, 8 for 16x16, so
+// that a lane sums several terms before the float-float reduction across the group): FINAL =
+// false takes lam = nu_{k+1} (a plane) and, for each cell (u, v) of the range, the 2x2 mean of the
+// window of P = P_k at src'_t(u, v) (two aligned float2 loads when V2, else four single loads);
+// FINAL = true takes lam = l_K (full resolution) and the window of P = P_{K-1} directly. Exact FP32
 // products summed in float-float per lane, across the group and into the per-range accumulators.
+template <int B>
+struct GradShape {
+    static constexpr int TG = B == 8 ? 4 : 8;  // lanes per range
+    static constexpr int G = 256 / TG;         // ranges per block
+};
+
 template <int B, bool FINAL, bool V2>
 __global__ void __launch_bounds__(256)
     k_plane_grads(Geo g, const int4 *__restrict__ pk, const float *__restrict__ P, const float *__restrict__ lam,
                   float2 *__restrict__ gs, float2 *__restrict__ go) {
-    constexpr int T = PlaneShape<B>::T, G = PlaneShape<B>::G;
-    constexpr int OB = B / 2, J = OB * OB / T, JF = B * B / T;
-    const int grp = threadIdx.x / T, l = threadIdx.x % T, gbase = (threadIdx.x & 31) & ~(T - 1);
-    const unsigned gmask = T == 32 ? 0xffffffffu : (0xFFFFu << (threadIdx.x & 16));
+    constexpr int TG = GradShape<B>::TG, G = GradShape<B>::G;
+    constexpr int OB = B / 2, J = OB * OB / TG, JF = B * B / TG;
+    const int grp = threadIdx.x / TG, l = threadIdx.x % TG;
+    const unsigned gmask = ((1u << TG) - 1u) << ((threadIdx.x & 31) & ~(TG - 1));
     const int r = blockIdx.x * G + grp;
     if (r >= g.R) return;  // whole groups leave together
     const int4 c = __ldg(pk + r);
@@ -951,7 +960,7 @@ __global__ void __launch_bounds__(256)
     if constexpr (FINAL) {
 #pragma unroll
         for (int j = 0; j < JF; ++j) {
-            const int q = l + T * j, py = q / B, px = q % B;
+            const int q = l + TG * j, py = q / B, px = q % B;
             int sy, sx;
             iso_src(B, c.y, py, px, sy, sx);
             const float v = __ldg(w + (size_t)sy * Wh + sx);
@@ -961,38 +970,28 @@ __global__ void __launch_bounds__(256)
             ff_add(so, lv, 0.f);
         }
     } else {
-        float e[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-            const int q = l + T * j, cy = q / OB, cx = q % OB;
-            const float *p = w + (size_t)(2 * cy) * Wh + 2 * cx;
+            const int q = l + TG * j, u = q / OB, v = q % OB;
+            int sy, sx;
+            iso_src(OB, c.y, u, v, sy, sx);
+            const float *p = w + (size_t)(2 * sy) * Wh + 2 * sx;
+            float e;
             if constexpr (V2) {
                 const float2 lo = __ldg(reinterpret_cast<const float2 *>(p));
                 const float2 hi = __ldg(reinterpret_cast<const float2 *>(p + Wh));
-                e[j] = (((lo.x + lo.y) + hi.x) + hi.y) * 0.25f;
+                e = (((lo.x + lo.y) + hi.x) + hi.y) * 0.25f;
             } else {
-                e[j] = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + Wh)) + __ldg(p + Wh + 1)) * 0.25f;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int q = l + T * j, u = q / OB, v = q % OB;
-            int sy, sx;
-            iso_src(OB, c.y, u, v, sy, sx);
-            const int src = sy * OB + sx;  // the cell to take: lane src % T, register src / T
-            float val = __shfl_sync(gmask, e[0], gbase + src % T);
-            if constexpr (J == 2) {
-                const float hi = __shfl_sync(gmask, e[1], gbase + src % T);
-                val = src >= T ? hi : val;
+                e = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + Wh)) + __ldg(p + Wh + 1)) * 0.25f;
             }
             const float lv = __ldg(lam + (size_t)(rq * OB + u) * Wh + rx * OB + v);
-            const float ph = lv * val;
-            ff_add(ss, ph, fmaf(lv, val, -ph));
+            const float ph = lv * e;
+            ff_add(ss, ph, fmaf(lv, e, -ph));
             ff_add(so, lv, 0.f);
         }
     }
 #pragma unroll
-    for (int o = T / 2; o > 0; o >>= 1) {
+    for (int o = TG / 2; o > 0; o >>= 1) {
         const float sh = __shfl_xor_sync(gmask, ss.hi, o), sl = __shfl_xor_sync(gmask, ss.lo, o);
         const float oh = __shfl_xor_sync(gmask, so.hi, o), ol = __shfl_xor_sync(gmask, so.lo, o);
         ff_add(ss, sh, sl);
@@ -1026,7 +1025,7 @@ static Geo plane_geo(const Geo &g) {
 template <int B>
 static void plane_grads(bool fin, bool v2, const Geo &g, const int4 *pk, const float *P, const float *lam,
                         float2 *gs, float2 *go, cudaStream_t st) {
-    const unsigned blocks = (unsigned)((g.R + PlaneShape<B>::G - 1) / PlaneShape<B>::G);
+    const unsigned blocks = (unsigned)((g.R + GradShape<B>::G - 1) / GradShape<B>::G);
     if (fin) k_plane_grads<B, true, false><<<blocks, 256, 0, st>>>(g, pk, P, lam, gs, go);
     else if (v2) k_plane_grads<B, false, true><<<blocks, 256, 0, st>>>(g, pk, P, lam, gs, go);
     else k_plane_grads<B, false, false><<<blocks, 256, 0, st>>>(g, pk, P, lam, gs, go);
