@@ -210,8 +210,12 @@ def _codes_gpu(c):
             "o": torch.from_numpy(np.asarray(c["o"], np.float64)).cuda()}
 
 
-def test_decode16_parity_and_adjoint():
-    H, W, sigma, iters = 96, 128, 4, 6
+@pytest.mark.parametrize("sigma", [4, 8, 2, 6])
+def test_decode16_parity_and_adjoint(sigma):
+    """Decoding and its adjoint with 16x16 ranges. Even strides run on the plane of 2x2 averages:
+    sigma = 4 and 8 with float2 window loads and 2x2-block transposes (sigma / 2 even), 2 and 6
+    with single loads and per-pixel transposes (sigma / 2 odd)."""
+    H, W, iters = 96, 128, 6
     img = synth.fbm_image(71, H, W)
     codes = omatch.encode(img, B=16, sigma=sigma, K=5, n_threads=NT)
     p = fic.EncodeParams(domain_stride=sigma, num_classes=5, block=16)

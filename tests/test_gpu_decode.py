@@ -69,7 +69,7 @@ def test_decode_from_given_start(pr1_codes):
         assert np.max(np.abs(x.cpu().numpy() - ref)) <= 2e-3
 
 
-@pytest.mark.parametrize("sigma", [8, 4, 3, 2, 1])
+@pytest.mark.parametrize("sigma", [8, 4, 6, 3, 2, 1])
 def test_adjoint_parity(sigma):
     H, W, iters = 64, 96, 6
     img = synth.fbm_image(90 + sigma, H, W)
@@ -214,10 +214,11 @@ def test_decode_repeated_calls_follow_contents(pr1_codes):
             assert np.max(np.abs(out.cpu().numpy() - ref)) <= 2e-3, rep
 
 
-@pytest.mark.parametrize("block,sigma", [(8, 3), (8, 5), (16, 3), (16, 8)])
+@pytest.mark.parametrize("block,sigma", [(8, 3), (8, 5), (16, 3), (16, 8), (8, 6), (8, 2)])
 def test_decode_odd_strides_and_unaligned_start(block, sigma):
-    """Odd strides, and a start image and an output that are only 4-byte aligned, take the kernel's
-    scalar-load and scalar-store forms; results equal the oracle's."""
+    """Odd strides, and a start image and an output that are only 4-byte aligned, take the kernels'
+    scalar-load and scalar-store forms (odd strides: full-resolution steps; even strides: the plane
+    of 2x2 averages, with single loads when sigma / 2 is odd); results equal the oracle's."""
     H, W = 96, 128
     img = synth.fbm_image(45 + sigma, H, W)
     codes = omatch.encode(img, B=block, sigma=sigma, K=4, n_threads=NT)
