@@ -280,7 +280,11 @@ fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *g, const fi
 /* Adjoint of fic_decode with respect to the per-range contrast and brightness: given
  * grad_out = dL/dx_iters (H*W float), writes grad_s[r] = dL/ds_r and grad_o[r] = dL/do_r
  * (R floats each). Iterates are recomputed from checkpoints kept every `ckpt_every` (>= 1)
- * iterations. W^T is applied as a deterministic gather (no floating-point atomics). */
+ * iterations. W^T is applied as a deterministic gather (no floating-point atomics), so the
+ * result does not depend on scheduling or on ckpt_every. With an even domain stride the
+ * checkpoints, the recomputation and every reverse step but the last (the one that reads
+ * grad_out) run on the plane of 2x2 averages, as in fic_decode. Workspace:
+ * fic_decode_workspace_size with the same iters and ckpt_every. */
 fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *g, const fic_params *p,
                                int32_t iters, int32_t ckpt_every, const float *x0,
                                const float *grad_out, float *grad_s, float *grad_o,
