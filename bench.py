@@ -707,8 +707,11 @@ def decode_rates(codes, H, W, p, flush, hbm_gbs, iters=8, ckpt=2, reps=5):
             ms.append(a.elapsed_time(b))
         return statistics.median(ms)
 
+    R = codes["dom"].numel()
+    gs = torch.empty(R, dtype=torch.float32, device=dev)
+    go = torch.empty(R, dtype=torch.float32, device=dev)
     dec_ms = timed(lambda: fic.decode(codes, H, W, p, iters, out=out, workspace=ws))
-    bwd_ms = timed(lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, g, workspace=ws))
+    bwd_ms = timed(lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, g, workspace=ws, grad_s=gs, grad_o=go))
     bwd_b = iters * H * W * 16
     return {**decode_figures(H, W, codes["dom"].numel(), iters, dec_ms, hbm_gbs),
             "backward_ms": bwd_ms, "backward_gbs": bwd_b / (bwd_ms / 1e3) / 1e9,
@@ -747,8 +750,10 @@ def diff(args, dev):
             ms.append(a.elapsed_time(b))
         return statistics.median(ms)
 
+    gs = torch.empty(codes["dom"].numel(), dtype=torch.float32, device=dev)
+    go = torch.empty_like(gs)
     dec_ms = timed(lambda: fic.decode(codes, H, W, p, iters, out=out, workspace=ws))
-    bwd_ms = timed(lambda: fic.decode_backward(codes, H, W, p, iters, ck, g, workspace=ws))
+    bwd_ms = timed(lambda: fic.decode_backward(codes, H, W, p, iters, ck, g, workspace=ws, grad_s=gs, grad_o=go))
     x = fic.decode(codes, H, W, p, iters)
     psnr = fic.quality(x, img)[1]
     x2 = fic.decode_scaled(codes, H, W, p, 2, iters)
@@ -863,7 +868,10 @@ def run_case(args, wl, local):
             nbytes = 4 * H * W + 24 * R  # the output and the codes: the plane steps stay in L2
         else:
             gout = torch.randn(H, W, dtype=torch.float32, device=dev)
-            fn = lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, gout, workspace=ws)  # noqa: E731
+            gs = torch.empty(R, dtype=torch.float32, device=dev)
+            go = torch.empty_like(gs)
+            fn = lambda: fic.decode_backward(codes, H, W, p, iters, ckpt, gout, workspace=ws,  # noqa: E731
+                                             grad_s=gs, grad_o=go)
             nbytes = iters * H * W * 16
     else:
         ws = torch.empty(fic.encode_workspace_size(H, W, p), dtype=torch.uint8, device=dev)

@@ -284,7 +284,10 @@ fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *g, const fi
  * result does not depend on scheduling or on ckpt_every. With an even domain stride the
  * checkpoints, the recomputation and every reverse step but the last (the one that reads
  * grad_out) run on the plane of 2x2 averages, as in fic_decode. Workspace:
- * fic_decode_workspace_size with the same iters and ckpt_every. */
+ * fic_decode_workspace_size with the same iters and ckpt_every. Like fic_decode, the first call
+ * with a given argument set on a host thread captures its launches into a CUDA graph that later
+ * calls with the same arguments replay (4 argument sets per thread; calls on a stream the caller is
+ * capturing run directly). */
 fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *g, const fic_params *p,
                                int32_t iters, int32_t ckpt_every, const float *x0,
                                const float *grad_out, float *grad_s, float *grad_o,

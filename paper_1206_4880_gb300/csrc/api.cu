@@ -664,9 +664,10 @@ static fic_status encode_batch(const uint8_t *const *imgs, const fic_geom *geoms
 }  // extern "C"
 
 // ---- repeated calls: one cached CUDA graph per argument set ----------------------------------
-// A fic_encode or fic_decode call whose arguments (pointers, geometry, parameters, device) equal an
-// earlier call's on this host thread replays that call's captured graph: one launch instead of the
-// stage kernels, memsets and stream forks (encode) or of the iterations (decode). The graph embeds
+// A fic_encode, fic_decode or fic_decode_backward call whose arguments (pointers, geometry,
+// parameters, device) equal an earlier call's on this host thread replays that call's captured
+// graph: one launch instead of the stage kernels, memsets and stream forks (encode), of the
+// iterations (decode) or of the index build, recomputation and reverse steps (adjoint). The graph embeds
 // every pointer and parameter, so equal arguments mean the same work on whatever the buffers hold
 // now.
 namespace {
@@ -1003,21 +1004,13 @@ fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *gm, const f
     return FIC_OK;
 }
 
-fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
-                               int32_t iters, int32_t ckpt_every, const float *x0,
-                               const float *grad_out, float *grad_s, float *grad_o, void *ws,
-                               size_t bytes, void *stream) {
-    NvtxRange nvtx_range("fic_decode_backward");
-    Geo g{};
-    fic_status s = make_geo(gm, p, &g);
-    if (s != FIC_OK) return s;
-    if ((s = check_codes(codes)) != FIC_OK) return s;
-    if (!grad_out || !grad_s || !grad_o || iters < 0 || ckpt_every < 1)
-        return fail(FIC_ERR_INVALID_ARG, "null gradient pointer, iters < 0 or ckpt_every < 1");
-    if (!ws || (uintptr_t)ws % 256) return fail(FIC_ERR_WORKSPACE, "workspace null or misaligned");
-    const size_t need = fic_decode_workspace_size(gm, p, iters, ckpt_every);
-    if (bytes < need) return fail(FIC_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", bytes, need);
-    cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+// Enqueues the adjoint of fic_decode_backward (arguments already checked) on st.
+fic_status backward_enqueue(const fic_codes *codes, const Geo &g, int32_t iters, int32_t ckpt_every,
+                            const float *x0, const float *grad_out, float *grad_s, float *grad_o, void *ws,
+                            size_t bytes, cudaStream_t st) {
     const size_t img = (size_t)g.H * g.W;
     const int ck = ckpt_every;
     const int nseg = iters > 0 ? (iters + ck - 1) / ck : 1;
@@ -1086,6 +1079,59 @@ fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const
     }
     FIC_TRY(launch_grads_out(g.R, gacc, gacc + g.R, grad_s, grad_o, st), "grads_out");
     return FIC_OK;
+}
+
+
+struct BackwardKey {
+    fic_codes codes;
+    fic_geom g;
+    fic_params p;
+    const void *x0, *grad_out, *grad_s, *grad_o, *ws;
+    size_t bytes;
+    int iters, ckpt, dev;
+};
+thread_local GraphCacheT<BackwardKey> g_backward_graphs;
+}  // namespace
+
+extern "C" {
+
+fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *gm, const fic_params *p,
+                               int32_t iters, int32_t ckpt_every, const float *x0,
+                               const float *grad_out, float *grad_s, float *grad_o, void *ws,
+                               size_t bytes, void *stream) {
+    NvtxRange nvtx_range("fic_decode_backward");
+    Geo g{};
+    fic_status s = make_geo(gm, p, &g);
+    if (s != FIC_OK) return s;
+    if ((s = check_codes(codes)) != FIC_OK) return s;
+    if (!grad_out || !grad_s || !grad_o || iters < 0 || ckpt_every < 1)
+        return fail(FIC_ERR_INVALID_ARG, "null gradient pointer, iters < 0 or ckpt_every < 1");
+    if (!ws || (uintptr_t)ws % 256) return fail(FIC_ERR_WORKSPACE, "workspace null or misaligned");
+    const size_t need = fic_decode_workspace_size(gm, p, iters, ckpt_every);
+    if (bytes < need) return fail(FIC_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = -1;
+    if (!cacheable(st, &dev))
+        return backward_enqueue(codes, g, iters, ckpt_every, x0, grad_out, grad_s, grad_o, ws, bytes, st);
+    BackwardKey k;
+    memset(&k, 0, sizeof k);  // padding included: keys compare as bytes
+    k.codes = *codes;
+    k.g = *gm;
+    k.p = *p;
+    k.x0 = x0;
+    k.grad_out = grad_out;
+    k.grad_s = grad_s;
+    k.grad_o = grad_o;
+    k.ws = ws;
+    k.bytes = bytes;
+    k.iters = iters;
+    k.ckpt = ckpt_every;
+    k.dev = dev;
+    return replay_or_capture(
+        g_backward_graphs, k, dev, st, []() { return FIC_OK; },
+        [&](cudaStream_t cap) {
+            return backward_enqueue(codes, g, iters, ckpt_every, x0, grad_out, grad_s, grad_o, ws, bytes, cap);
+        });
 }
 
 }  // extern "C"

@@ -418,11 +418,17 @@ def decode_scaled(codes: dict, H: int, W: int, p: EncodeParams, scale: int, iter
 
 
 def decode_backward(codes: dict, H: int, W: int, p: EncodeParams, iters: int, ckpt_every: int,
-                    grad_out: torch.Tensor, x0=None, workspace=None, stream=None):
+                    grad_out: torch.Tensor, x0=None, workspace=None, stream=None, grad_s=None, grad_o=None):
+    """dL/ds and dL/do of `iters` decoding steps given dL/dx (fic_decode_backward); grad_s and
+    grad_o, when given, are R float32 device tensors that receive them (reused buffers let repeated
+    calls replay the library's cached graph)."""
     dev = codes["dom"].device
     R, _ = counts(H, W, p)
-    gs = torch.empty(R, dtype=torch.float32, device=dev)
-    go = torch.empty(R, dtype=torch.float32, device=dev)
+    gs = torch.empty(R, dtype=torch.float32, device=dev) if grad_s is None else grad_s
+    go = torch.empty(R, dtype=torch.float32, device=dev) if grad_o is None else grad_o
+    for t in (gs, go):
+        if t.dtype != torch.float32 or t.numel() != R or not t.is_contiguous() or t.device != dev:
+            raise ValueError("grad_s and grad_o must be contiguous float32 tensors of R entries on the codes' device")
     if workspace is None:
         workspace = torch.empty(decode_workspace_size(H, W, p, iters, ckpt_every),
                                 dtype=torch.uint8, device=dev)

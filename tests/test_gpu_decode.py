@@ -214,6 +214,33 @@ def test_decode_repeated_calls_follow_contents(pr1_codes):
             assert np.max(np.abs(out.cpu().numpy() - ref)) <= 2e-3, rep
 
 
+@pytest.mark.parametrize("sigma", [8, 3])
+def test_backward_repeated_calls_follow_contents(pr1_codes, sigma):
+    """fic_decode_backward replays a cached graph for repeated calls with the same buffers: the
+    gradients must follow what the code and gradient buffers hold at each call."""
+    H, W, iters, ck = 64, 96, 5, 2
+    codes = [omatch.encode(synth.fbm_image(60 + k, H, W), B=8, sigma=sigma, K=4, n_threads=NT) for k in (0, 1)]
+    p = fic.EncodeParams(domain_stride=sigma, num_classes=4)
+    g = _codes_gpu(codes[0])
+    R = g["dom"].numel()
+    gout = torch.empty(H, W, dtype=torch.float32, device="cuda")
+    gs = torch.empty(R, dtype=torch.float32, device="cuda")
+    go = torch.empty_like(gs)
+    ws = torch.empty(fic.decode_workspace_size(H, W, p, iters, ck), dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(13)
+    for rep in range(2):
+        for c in codes:
+            for k, v in _codes_gpu(c).items():
+                g[k].copy_(v)
+            up = rng.normal(size=(H, W))
+            gout.copy_(torch.from_numpy(up.astype(np.float32)))
+            fic.decode_backward(g, H, W, p, iters, ck, gout, workspace=ws, grad_s=gs, grad_o=go)
+            torch.cuda.synchronize()
+            gs_ref, go_ref = odec.decode_adjoint(c, H, W, 8, sigma, iters, up.astype(np.float32).astype(np.float64))
+            for a, b in ((gs.cpu().numpy(), gs_ref), (go.cpu().numpy(), go_ref)):
+                assert np.max(np.abs(a - b)) <= 1e-4 * np.max(np.abs(b)), rep
+
+
 @pytest.mark.parametrize("block,sigma", [(8, 3), (8, 5), (16, 3), (16, 8), (8, 6), (8, 2)])
 def test_decode_odd_strides_and_unaligned_start(block, sigma):
     """Odd strides, and a start image and an output that are only 4-byte aligned, take the kernels'
