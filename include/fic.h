@@ -186,11 +186,12 @@ fic_status fic_build_pools(const fic_blockstats *st, const fic_geom *g, const fi
  * bounded (2 s); if one gives up, the kernel stops without leaving work in flight, every code of
  * the call is written as invalid (dom = iso = -1, s = o = sse = NaN), info->device_error (when
  * `info` is given) is FIC_ERR_DEVICE_TIMEOUT, and the next fic_check on the device returns
- * FIC_ERR_DEVICE_TIMEOUT. The call itself returns before the GPU runs, so it cannot report this. The first call with a given argument set (pointers, geometry, parameters, device) on a
- * host thread captures its work into a CUDA graph on a private stream; later calls with the same
- * arguments replay that graph on `stream` (up to 4 argument sets per thread, least recently used
- * replaced). Calls with profiling on, or on a stream the caller is capturing, run the stages
- * directly. */
+ * FIC_ERR_DEVICE_TIMEOUT. The call itself returns before the GPU runs, so it cannot report this.
+ * The first call with a given argument set (pointers, geometry, parameters, device) on a host
+ * thread runs its stages directly; the second captures its work into a CUDA graph on a private
+ * stream, and it and later calls with the same arguments replay that graph on `stream` (up to 4
+ * argument sets per thread, least recently used replaced). Calls with profiling on, or on a
+ * stream the caller is capturing, run the stages directly. */
 fic_status fic_encode(const uint8_t *img, const fic_geom *g, const fic_params *p,
                       const fic_codes *out, fic_encode_info *info, void *workspace,
                       size_t workspace_bytes, void *stream);
@@ -256,9 +257,9 @@ size_t fic_decode_workspace_size(const fic_geom *g, const fic_params *p, int32_t
  * only the last step writes full-resolution pixels.
  * iters >= 0. Workspace: fic_decode_workspace_size. Codes whose domain or isometry is out of range
  * (such as the invalid codes of an encode whose matcher gave up) give NaN pixels for their range.
- * Like fic_encode, the first call with a given argument set on a host thread captures its
- * iterations into a CUDA graph; later calls with the same arguments replay it (4 argument sets per
- * thread; calls on a stream the caller is capturing run the steps directly). */
+ * Like fic_encode, the second call with a given argument set on a host thread captures its
+ * launches into a CUDA graph (the first runs them directly); later calls with the same arguments
+ * replay it (4 argument sets per thread; calls on a stream the caller is capturing run directly). */
 fic_status fic_decode(const fic_codes *codes, const fic_geom *g, const fic_params *p,
                       int32_t iters, const float *x0, float *out, void *workspace,
                       size_t workspace_bytes, void *stream);
@@ -284,10 +285,9 @@ fic_status fic_decode_scaled(const fic_codes *codes, const fic_geom *g, const fi
  * result does not depend on scheduling or on ckpt_every. With an even domain stride the
  * checkpoints, the recomputation and every reverse step but the last (the one that reads
  * grad_out) run on the plane of 2x2 averages, as in fic_decode. Workspace:
- * fic_decode_workspace_size with the same iters and ckpt_every. Like fic_decode, the first call
- * with a given argument set on a host thread captures its launches into a CUDA graph that later
- * calls with the same arguments replay (4 argument sets per thread; calls on a stream the caller is
- * capturing run directly). */
+ * fic_decode_workspace_size with the same iters and ckpt_every. Like fic_decode, repeated calls
+ * with the same arguments replay a CUDA graph of the launches, captured at the second such call
+ * (4 argument sets per thread; calls on a stream the caller is capturing run directly). */
 fic_status fic_decode_backward(const fic_codes *codes, const fic_geom *g, const fic_params *p,
                                int32_t iters, int32_t ckpt_every, const float *x0,
                                const float *grad_out, float *grad_s, float *grad_o,

@@ -682,11 +682,16 @@ struct GraphCacheT {
     };
     Entry e[kGraphCache];
     unsigned long long tick = 0;
+    Key seen[kGraphCache];  // argument sets met once and run directly: the next such call captures
+    bool seen_valid[kGraphCache] = {};
+    int seen_next = 0;
 };
 thread_local cudaStream_t g_capture_stream[kMaxDevices] = {};  // private capture streams
 
-// Replays the graph cached for `k`, or captures enqueue(capture stream) into a new one (after
-// prepare(), which creates whatever must exist before a capture begins) and replays that. Keys
+// Replays the graph cached for `k`; else, the first time an argument set is met, runs
+// enqueue(st) directly and remembers the set, and the second time captures enqueue(capture
+// stream) into a new graph (after prepare(), which creates whatever must exist before a capture
+// begins) and replays that, so calls whose buffers change every time never pay for a capture. Keys
 // compare as bytes, padding included, so callers zero them before filling them in.
 template <class Key, class Prepare, class Enqueue>
 fic_status replay_or_capture(GraphCacheT<Key> &cache, const Key &k, int dev, cudaStream_t st, Prepare prepare,
@@ -700,6 +705,15 @@ fic_status replay_or_capture(GraphCacheT<Key> &cache, const Key &k, int dev, cud
         if (!victim || !e.exec || (victim->exec && e.used < victim->used)) victim = &e;
     }
     if (!hit) {
+        bool seen = false;
+        for (int i = 0; i < kGraphCache && !seen; ++i)
+            seen = cache.seen_valid[i] && memcmp(&cache.seen[i], &k, sizeof k) == 0;
+        if (!seen) {
+            const int i = cache.seen_next++ % kGraphCache;
+            cache.seen[i] = k;
+            cache.seen_valid[i] = true;
+            return enqueue(st);
+        }
         const fic_status ps = prepare();
         if (ps != FIC_OK) return ps;
         cudaStream_t &cap = g_capture_stream[dev];
