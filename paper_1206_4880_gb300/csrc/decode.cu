@@ -1008,6 +1008,97 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The gradient terms of a step k < K - 1 and the cell phase of H^T nu_{k+1} in one pass, a group
+// of LPR lanes per list position of the domain -> ranges index (LPR = 16 for 8x8 ranges, a warp for
+// 16x16; every range has a position, the listed ones first): lane l holds the cells l + LPR m of
+// range r's (B/2) x (B/2) grid of nu_{k+1} in row-major order, forms the gradient terms of those
+// cells against the 2x2 means of r's window of P_k (as k_plane_grads), and, when r is listed,
+// writes the cell block (s_r / 4) nu_{k+1}[p_r(c)] of its position (as k_adjoint_cells on the
+// plane geometry), taking nu_{k+1}[p_r(c)] from the lane that holds it by a shuffle.
+template <int B, bool V2>
+__global__ void __launch_bounds__(256)
+    k_plane_grads_cells(Geo g, const int4 *__restrict__ pk, const int4 *__restrict__ ent,
+                        const int32_t *__restrict__ off, const float *__restrict__ P,
+                        const float *__restrict__ lam, float *__restrict__ acc, float2 *__restrict__ gs,
+                        float2 *__restrict__ go) {
+    constexpr int OB = B / 2, NCELL = OB * OB, LPR = NCELL >= 32 ? 32 : NCELL, M = NCELL / LPR;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kpos = tid / LPR, l = tid % LPR;
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << ((threadIdx.x & 31) & ~(LPR - 1)));
+    const int gbase = (threadIdx.x & 31) & ~(LPR - 1);
+    if (kpos >= g.R) return;  // whole groups leave together
+    const int n = __ldg(off + g.Dn);  // listed ranges
+    const int4 e = __ldg(ent + kpos);
+    const int r = e.x;
+    const int4 c = __ldg(pk + r);
+    const int Wh = g.W / 2;
+    const int rq = fdiv(r, g.fRx), rx = r - rq * g.nRx;
+    float nv[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int q = l + LPR * m;
+        nv[m] = __ldg(lam + (size_t)(rq * OB + q / OB) * Wh + rx * OB + q % OB);
+    }
+    if (kpos < n) {
+        // the cell block of this list position: cell q of the window block takes nu at the range
+        // cell p = src'_{t^-1}(q)
+        const float sc = __int_as_float(e.z);
+        int c0, ky, kx;
+        iso_affine<OB>(e.y == 1 ? 3 : (e.y == 3 ? 1 : e.y), c0, ky, kx);
+        float *dst = acc + (size_t)kpos * NCELL;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int q = l + LPR * m, p = c0 + ky * (q / OB) + kx * (q % OB);
+            float v = __shfl_sync(gmask, nv[0], gbase + p % LPR);
+            if constexpr (M == 2) {
+                const float hi = __shfl_sync(gmask, nv[1], gbase + p % LPR);
+                v = p >= LPR ? hi : v;
+            }
+            dst[q] = sc * v;
+        }
+    }
+    if (c.x < 0) {  // an invalid code: NaN gradients, no read
+        if (l == 0) gs[r] = go[r] = make_float2(__int_as_float(0x7fc00000), 0.f);
+        return;
+    }
+    const float *w = P + c.x;
+    FF ss{0.f, 0.f}, so{0.f, 0.f};
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int q = l + LPR * m;
+        int sy, sx;
+        iso_src(OB, c.y, q / OB, q % OB, sy, sx);
+        const float *p = w + (size_t)(2 * sy) * Wh + 2 * sx;
+        float ev;
+        if constexpr (V2) {
+            const float2 lo = __ldg(reinterpret_cast<const float2 *>(p));
+            const float2 hi = __ldg(reinterpret_cast<const float2 *>(p + Wh));
+            ev = (((lo.x + lo.y) + hi.x) + hi.y) * 0.25f;
+        } else {
+            ev = (((__ldg(p) + __ldg(p + 1)) + __ldg(p + Wh)) + __ldg(p + Wh + 1)) * 0.25f;
+        }
+        const float ph = nv[m] * ev;
+        ff_add(ss, ph, fmaf(nv[m], ev, -ph));
+        ff_add(so, nv[m], 0.f);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) {
+        const float sh = __shfl_xor_sync(gmask, ss.hi, o), sl = __shfl_xor_sync(gmask, ss.lo, o);
+        const float oh = __shfl_xor_sync(gmask, so.hi, o), ol = __shfl_xor_sync(gmask, so.lo, o);
+        ff_add(ss, sh, sl);
+        ff_add(so, oh, ol);
+    }
+    if (l == 0) {
+        FF a{gs[r].x, gs[r].y}, b{go[r].x, go[r].y};
+        ff_add(a, ss.hi, ss.lo);
+        ff_add(b, so.hi, so.lo);
+        ff_norm(a);
+        ff_norm(b);
+        gs[r] = make_float2(a.hi, a.lo);
+        go[r] = make_float2(b.hi, b.lo);
+    }
+}
+
 // The plane geometry of H: ranges B/2 and windows B on the (H/2) x (W/2) plane at stride sigma/2,
 // the same range and domain grids.
 static Geo plane_geo(const Geo &g) {
@@ -1048,10 +1139,23 @@ static void plane_mt(const Geo &g, const Geo &gp, const AdjointCsr &a, const flo
         k_adjoint_gather<B / 2, 0, true><<<px, 256, 0, st>>>(gp, a.off, a.acc, nu);
 }
 
+
+// A reverse step k < K - 1 with its transpose: gradient terms and H^T's cell phase in one launch,
+// then H^T's pixel phase on the plane geometry.
 template <int B>
-static void plane_ht(const Geo &gp, const AdjointCsr &a, const float *nu, float *nu_prev, cudaStream_t st) {
-    // H^T on the plane: W^T's two phases with ranges B/2 (cells (s_r / 4) nu[p_r(c)], 2x2 blocks)
-    adjoint_gather_b<B / 2>(gp, a, nu, nu_prev, st);
+static void plane_step_back(bool v2, const Geo &g, const Geo &gp, const AdjointCsr &a, const int4 *pk, const float *P,
+                            const float *nu, float *nu_prev, float2 *gs, float2 *go, cudaStream_t st) {
+    constexpr int OB = B / 2, LPR = OB * OB >= 32 ? 32 : OB * OB;
+    const unsigned blocks = (unsigned)(((long long)g.R * LPR + 255) / 256);
+    if (v2) k_plane_grads_cells<B, true><<<blocks, 256, 0, st>>>(g, pk, a.ent, a.off, P, nu, a.acc, gs, go);
+    else k_plane_grads_cells<B, false><<<blocks, 256, 0, st>>>(g, pk, a.ent, a.off, P, nu, a.acc, gs, go);
+    const int mj = (2 * OB + gp.sigma - 1) / gp.sigma;
+    if (mj <= 2)
+        gather_px<OB, 2>(gp, a, nu_prev, st);
+    else if (mj <= 4)
+        gather_px<OB, 4>(gp, a, nu_prev, st);
+    else
+        gather_px<OB, 0>(gp, a, nu_prev, st);
 }
 
 cudaError_t launch_backward_plane(const fic_codes &c, const Geo &g, const AdjointCsr &a, int iters, int ck,
@@ -1089,22 +1193,25 @@ cudaError_t launch_backward_plane(const fic_codes &c, const Geo &g, const Adjoin
         const int len = (c0 == nseg - 1) ? iters - c0 * ck : ck;
         for (int i = 1; i < len; ++i) step(plane(c0, i - 1), plane(c0, i));
         for (int i = len - 1; i >= 0; --i) {
-            const float *lam = fin ? grad_out : ncur;
-            if (g.B == 16) plane_grads<16>(fin, v2, g, pk, plane(c0, i), lam, gs, go, st);
-            else plane_grads<8>(fin, v2, g, pk, plane(c0, i), lam, gs, go, st);
-            ++g_launches;
-            if (c0 > 0 || i > 0) {
-                if (fin) {
+            const bool more = c0 > 0 || i > 0;  // a transpose is needed (not the first step)
+            if (fin || !more) {
+                // the last step's terms (full-resolution l_K), or the first step's (no transpose)
+                const float *lam = fin ? grad_out : ncur;
+                if (g.B == 16) plane_grads<16>(fin, v2, g, pk, plane(c0, i), lam, gs, go, st);
+                else plane_grads<8>(fin, v2, g, pk, plane(c0, i), lam, gs, go, st);
+                ++g_launches;
+                if (fin && more) {
                     if (g.B == 16) plane_mt<16>(g, gp, a, grad_out, ncur, st);
                     else plane_mt<8>(g, gp, a, grad_out, ncur, st);
-                } else {
-                    if (g.B == 16) plane_ht<16>(gp, a, ncur, nprev, st);
-                    else plane_ht<8>(gp, a, ncur, nprev, st);
-                    float *t = ncur;
-                    ncur = nprev;
-                    nprev = t;
+                    g_launches += 2;
                 }
+            } else {
+                if (g.B == 16) plane_step_back<16>(v2, g, gp, a, pk, plane(c0, i), ncur, nprev, gs, go, st);
+                else plane_step_back<8>(v2, g, gp, a, pk, plane(c0, i), ncur, nprev, gs, go, st);
                 g_launches += 2;
+                float *t = ncur;
+                ncur = nprev;
+                nprev = t;
             }
             fin = false;
         }
