@@ -214,6 +214,26 @@ def test_decode_repeated_calls_follow_contents(pr1_codes):
             assert np.max(np.abs(out.cpu().numpy() - ref)) <= 2e-3, rep
 
 
+@pytest.mark.parametrize("block,sigma", [(8, 8), (8, 3), (16, 4)])
+def test_adjoint_from_given_start(block, sigma):
+    """The adjoint of decoding from a given start image (its 2x2 averages form the first plane when
+    the stride is even) equals the FP64 oracle's."""
+    H, W, iters = 64, 96, 4
+    codes = omatch.encode(synth.fbm_image(80 + sigma, H, W), B=block, sigma=sigma, K=4, n_threads=NT)
+    p = fic.EncodeParams(domain_stride=sigma, num_classes=4, block=block)
+    rng = np.random.default_rng(21)
+    start = rng.uniform(0, 255, (H, W)).astype(np.float32)
+    up = rng.normal(size=(H, W))
+    gs, go = fic.decode_backward(_codes_gpu(codes), H, W, p, iters, 2,
+                                 torch.from_numpy(up.astype(np.float32)).cuda(),
+                                 x0=torch.from_numpy(start).cuda())
+    torch.cuda.synchronize()
+    gs_ref, go_ref = odec.decode_adjoint(codes, H, W, block, sigma, iters, up.astype(np.float32).astype(np.float64),
+                                         x0=start.astype(np.float64))
+    for a, b in ((gs.cpu().numpy(), gs_ref), (go.cpu().numpy(), go_ref)):
+        assert np.max(np.abs(a - b)) <= 1e-4 * np.max(np.abs(b))
+
+
 @pytest.mark.parametrize("sigma", [8, 3])
 def test_backward_repeated_calls_follow_contents(pr1_codes, sigma):
     """fic_decode_backward replays a cached graph for repeated calls with the same buffers: the
