@@ -392,30 +392,36 @@ def run_ours(args, wl, world, rank, local):
     # end to end through the public API with host buffers: every step copies its image in from
     # pinned host memory, encodes it and copies its codes out, pipelined the way a serving loop
     # runs: step k+1's image goes in and step k-1's codes come out on copy streams while step k
-    # encodes. Three buffer sets (image, workspace, codes: about 3 x the encode's working set, more
-    # than L2) rotate, so each step finds its data evicted instead of needing an L2 flush.
-    NB = 3
+    # encodes, and consecutive encodes alternate between two streams, so one image's
+    # classification, pools and packing (small kernels) run beside the previous image's matcher
+    # on the SM resources it leaves free. Four buffer sets (image, workspace, codes: about 4 x the
+    # encode's working set, more than L2) rotate, so each step finds its data evicted instead of
+    # needing an L2 flush.
+    NB = 4
     host_img = torch.from_numpy(img_np).pin_memory()
     imgs2 = [img] + [torch.empty_like(img) for _ in range(NB - 1)]
     outs2 = [out] + [fic.alloc_codes(R, dev) for _ in range(NB - 1)]
     wss = [ws] + [torch.empty_like(ws) for _ in range(NB - 1)]
     host_out = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()} for o in outs2]
     d2h = sum(v.numel() * v.element_size() for v in out.values())
-    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    s_cmps = [torch.cuda.Stream(), torch.cuda.Stream()]
     ev_in = [torch.cuda.Event() for _ in range(NB)]
     ev_cmp = [torch.cuda.Event() for _ in range(NB)]
     ev_out = [torch.cuda.Event() for _ in range(NB)]
     for b in range(NB):  # each buffer set's cached graph exists before the timed region
         imgs2[b].copy_(img)
-        fic.encode(imgs2[b], p, out=outs2[b], workspace=wss[b], stream=s_cmp)
-        ev_cmp[b].record(s_cmp)
-        ev_out[b].record(s_cmp)
+        for _ in range(2):  # the library captures an argument set's graph at its second call
+            fic.encode(imgs2[b], p, out=outs2[b], workspace=wss[b], stream=s_cmps[0])
+        ev_cmp[b].record(s_cmps[0])
+        ev_out[b].record(s_cmps[0])
     torch.cuda.synchronize()
     e2e_steps = min(args.steps, 60)
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_start.record(s_in)
     for k in range(e2e_steps):
         b = k % NB
+        s_cmp = s_cmps[k % 2]
         s_in.wait_event(ev_cmp[b])  # the encode that last read imgs2[b] is done
         with torch.cuda.stream(s_in):
             imgs2[b].copy_(host_img, non_blocking=True)
@@ -481,7 +487,8 @@ def run_ours(args, wl, world, rank, local):
         "e2e": {"value": e2e_value, "unit": "matches/s", "h2d_bytes_per_step": H * W,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "codes_read_back_equal": e2e_ok,
                 "pipelining": "step k+1's image copied in and step k-1's codes copied out on copy streams "
-                              "while step k encodes (encodes in order on one stream); three rotating buffer "
+                              "while step k encodes; consecutive encodes on two alternating streams (one "
+                              "image's pre-matcher stages beside the previous image's matcher); four rotating buffer "
                               "sets larger than L2 in all, no flush"},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
