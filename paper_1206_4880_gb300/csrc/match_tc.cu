@@ -72,9 +72,10 @@ struct TcShared {
     uint8_t B[S][kBBytes];
     uint8_t A1[2][kA1Bytes];
     uint8_t B1[S][kB1Bytes];
-    float4 aux[2][kChunkDom / 2];  // (Q / 256, 128 / Q) of two domains per entry: current, next chunk
+    // (Q / 256, 128 / Q) of two domains per entry, per epilogue warp set: current, next chunk
+    float4 aux[2][2][kChunkDom / 2];
     unsigned long long full_a[2], empty_a[2], full_b[S], empty_b[S], tfull[2],
-        tempty[2], aux_ready[2], drain, item_full[kItemRing], item_empty[kItemRing],
+        tempty[2], aux_ready[2][2], drain, item_full[kItemRing], item_empty[kItemRing],
         never;  // completed by nothing: the forced wait of the testing hook (fic_debug_stall_matcher)
     int item_id[kItemRing];  // work items fetched by the producer, in this CTA's order (-1: none left)
     uint32_t tmem_base;
@@ -533,7 +534,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&sh.empty_a[s], 1);
             mbar_init(&sh.tfull[s], 1);
             mbar_init(&sh.tempty[s], kEpiWarps / 2);  // the accumulator's four warps
-            mbar_init(&sh.aux_ready[s], 32 * kEpiWarps);
+            mbar_init(&sh.aux_ready[0][s], 32 * kEpiWarps / 2);  // one warp set each
+            mbar_init(&sh.aux_ready[1][s], 32 * kEpiWarps / 2);
         }
         for (int s = 0; s < S; ++s) {
             mbar_init(&sh.full_b[s], 1);
@@ -680,13 +682,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int jc = w.y + k0 * kTileDom;
                 const int cabs = jc / kChunkDom;
                 ntc = min(nt - k0, ((cabs + 1) * kChunkDom - jc) / kTileDom);
-                // per-domain constants of this chunk into shared memory (double-buffered by chunk
-                // parity; a thread reaches chunk lc + 2 only after every thread has left chunk lc)
+                // per-domain constants of this chunk into the set's shared buffer (double-buffered
+                // by chunk parity; a thread reaches chunk lc + 2 only after every thread of its set
+                // has left chunk lc). Each set keeps its own copy, so the sets, which drain
+                // alternate tiles, do not wait for each other at chunk boundaries.
                 const int ab = lc & 1;
-                for (int k = ew * 32 + lane; k < ntc * kTileDom / 2; k += 32 * kEpiWarps)
-                    sh.aux[ab][k] = __ldg(&dom_aux[jc / 2 + k]);  // dom_aux holds float2 pairs here
-                mbar_arrive(&sh.aux_ready[ab]);
-                ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[ab], (lc >> 1) & 1, abort_flag));
+                for (int k = (ew & 3) * 32 + lane; k < ntc * kTileDom / 2; k += 32 * (kEpiWarps / 2))
+                    sh.aux[half][ab][k] = __ldg(&dom_aux[jc / 2 + k]);  // dom_aux holds float2 pairs here
+                mbar_arrive(&sh.aux_ready[half][ab]);
+                ok = __all_sync(0xffffffffu, mbar_wait(&sh.aux_ready[half][ab], (lc >> 1) & 1, abort_flag));
                 if (!ok) break;
                 // the chunk's two best 32-bit keys, folded into the 64-bit keys once per chunk
                 uint32_t t1 = 0, t2 = 0;
@@ -698,7 +702,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (!ok) break;
                     tc_fence_after();
                     const int jt = jc + k * kTileDom;
-                    const float4 *auxp = &sh.aux[ab][(k * kTileDom) / 2];
+                    const float4 *auxp = &sh.aux[half][ab][(k * kTileDom) / 2];
                     const uint32_t taddr = tbase + acc * kTileN;
                     const int jrel = jrel0 + k * kTileDom;
                     if (jt >= f_lo && jt + kTileDom <= f_hi)
