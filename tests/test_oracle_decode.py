@@ -149,3 +149,40 @@ def test_scaled_decode_pins():
     assert np.allclose(down, x1, rtol=0, atol=1e-9)
     x3 = decode.decode_scaled(c, H, W, 8, 4, 3, 3)
     assert np.allclose(x3.reshape(H, 3, W, 3).mean(axis=(1, 3)), decode.decode(c, H, W, 8, 4, 3), atol=1e-9)
+
+
+def _pool2(x):
+    return (x[0::2, 0::2] + x[0::2, 1::2] + x[1::2, 0::2] + x[1::2, 1::2]) / 4.0
+
+
+@pytest.mark.parametrize("B,sigma", [(8, 8), (8, 4), (8, 2), (8, 6), (16, 4), (16, 8), (16, 2)])
+def test_plane_of_averages_iteration(B, sigma):
+    """With an even stride the Jacobi iterates' 2x2 averages follow their own iteration on the
+    half-size plane: P_{k+1}[cells of r] = s_r T_t(pool2(window of P_k at the domain's half
+    position)) + o_r, and x_K = s_r T_t(window of P_{K-1}) + o_r. The decoder's plane form rests on
+    this identity; here it is checked against the oracle's full-resolution iteration in binary64."""
+    rng = np.random.default_rng(1000 * B + sigma)
+    H, W = (48, 64) if B == 8 else (64, 96)
+    codes = _random_codes(rng, H, W, B, sigma, 0.9)
+    x0 = rng.uniform(0, 255, (H, W))
+    iters = 4
+    xs = [x0]
+    for _ in range(iters):
+        xs.append(decode.decode_step(xs[-1], codes, B, sigma))
+    R = geometry.n_ranges(H, W, B)
+    hb = B // 2
+    P = _pool2(x0)
+    for k in range(iters):
+        assert np.max(np.abs(P - _pool2(xs[k]))) <= 1e-9, k
+        nxt = np.empty_like(P)
+        last = np.empty_like(x0)
+        for r in range(R):
+            dy, dx = geometry.domain_origin(H, W, B, sigma, int(codes["dom"][r]))
+            ry, rx = geometry.range_origin(H, W, B, r)
+            win = P[dy // 2:dy // 2 + B, dx // 2:dx // 2 + B]
+            t, s, o = int(codes["iso"][r]), codes["s"][r], codes["o"][r]
+            nxt[ry // 2:ry // 2 + hb, rx // 2:rx // 2 + hb] = s * geometry.isometry(_pool2(win), t) + o
+            last[ry:ry + B, rx:rx + B] = s * geometry.isometry(win, t) + o
+        # the full-resolution step from the plane alone
+        assert np.max(np.abs(last - xs[k + 1])) <= 1e-9, k
+        P = nxt
