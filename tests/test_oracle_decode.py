@@ -186,3 +186,65 @@ def test_plane_of_averages_iteration(B, sigma):
         # the full-resolution step from the plane alone
         assert np.max(np.abs(last - xs[k + 1])) <= 1e-9, k
         P = nxt
+
+
+def _iso_scatter(out, q0y, q0x, vals, t):
+    """out[q0 + src_t(p)] += vals[p] for the p of a square block (the transpose of
+    geometry.isometry restricted to a window at q0)."""
+    n = vals.shape[0]
+    for y in range(n):
+        for x in range(n):
+            sy, sx = geometry.iso_source(n, t, y, x)
+            out[q0y + sy, q0x + sx] += vals[y, x]
+
+
+@pytest.mark.parametrize("B,sigma", [(8, 8), (8, 2), (16, 4)])
+def test_plane_of_averages_adjoint(B, sigma):
+    """The adjoint on the plane (nu_k = dL/dP_k: nu_{K-1} = M^T dL/dx_K, nu_k = H^T nu_{k+1}, the
+    last step's gradient terms from dL/dx_K and the window of P_{K-1}, the others from nu_{k+1} and
+    the 2x2 means of the windows of P_k) equals the oracle's full-resolution adjoint."""
+    rng = np.random.default_rng(77 * B + sigma)
+    H, W = (48, 64) if B == 8 else (64, 96)
+    codes = _random_codes(rng, H, W, B, sigma, 0.9)
+    x0 = rng.uniform(0, 255, (H, W))
+    g = rng.normal(size=(H, W))
+    iters = 4
+    gs_ref, go_ref = decode.decode_adjoint(codes, H, W, B, sigma, iters, g, x0=x0)
+    R = geometry.n_ranges(H, W, B)
+    hb = B // 2
+    geo = []
+    for r in range(R):
+        dy, dx = geometry.domain_origin(H, W, B, sigma, int(codes["dom"][r]))
+        ry, rx = geometry.range_origin(H, W, B, r)
+        geo.append((dy // 2, dx // 2, ry, rx, int(codes["iso"][r]), codes["s"][r], codes["o"][r]))
+    # forward on the plane
+    Ps = [_pool2(x0)]
+    for _ in range(iters - 1):
+        P, nxt = Ps[-1], np.empty_like(Ps[-1])
+        for wy, wx, ry, rx, t, s, o in geo:
+            nxt[ry // 2:ry // 2 + hb, rx // 2:rx // 2 + hb] = s * geometry.isometry(_pool2(P[wy:wy + B, wx:wx + B]), t) + o
+        Ps.append(nxt)
+    gs, go = np.zeros(R), np.zeros(R)
+    # the last step: terms from dL/dx_K, then nu_{K-1} = M^T dL/dx_K
+    P = Ps[-1]
+    nu = np.zeros_like(P)
+    for r, (wy, wx, ry, rx, t, s, o) in enumerate(geo):
+        lr = g[ry:ry + B, rx:rx + B]
+        gs[r] += np.sum(lr * geometry.isometry(P[wy:wy + B, wx:wx + B], t))
+        go[r] += np.sum(lr)
+        _iso_scatter(nu, wy, wx, s * lr, t)
+    # the other steps, on the plane
+    for k in range(iters - 2, -1, -1):
+        P = Ps[k]
+        prev = np.zeros_like(P)
+        for r, (wy, wx, ry, rx, t, s, o) in enumerate(geo):
+            nr = nu[ry // 2:ry // 2 + hb, rx // 2:rx // 2 + hb]
+            gs[r] += np.sum(nr * geometry.isometry(_pool2(P[wy:wy + B, wx:wx + B]), t))
+            go[r] += np.sum(nr)
+            # H^T: each cell's value, times s / 4, to the four plane pixels of its 2x2 source block
+            blk = np.zeros((hb, hb))
+            _iso_scatter(blk, 0, 0, (s / 4.0) * nr, t)
+            prev[wy:wy + B, wx:wx + B] += np.repeat(np.repeat(blk, 2, 0), 2, 1)
+        nu = prev
+    for a, b in ((gs, gs_ref), (go, go_ref)):
+        assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(b))
