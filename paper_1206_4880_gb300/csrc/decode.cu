@@ -659,17 +659,18 @@ __device__ __forceinline__ float adjoint_sum(const Geo &g, const int32_t *__rest
                 for (int k = o0[u * MJ + v]; k < o1[u * MJ + v]; ++k) a += __ldg(cp + (size_t)k * (CB * CB));
             }
         return a;
-    }
-    for (int jy = jy_lo; jy <= jy_hi; ++jy) {
-        const int cy = (qy - jy * g.sigma) >> SH;
-        for (int jx = jx_lo; jx <= jx_hi; ++jx) {
-            const int d = jy * g.nDx + jx;
-            const int o1 = __ldg(off + d + 1);
-            const float *cp = acc + cy * CB + ((qx - jx * g.sigma) >> SH);
-            for (int k = __ldg(off + d); k < o1; ++k) a += __ldg(cp + (size_t)k * (CB * CB));
+    } else {
+        for (int jy = jy_lo; jy <= jy_hi; ++jy) {
+            const int cy = (qy - jy * g.sigma) >> SH;
+            for (int jx = jx_lo; jx <= jx_hi; ++jx) {
+                const int d = jy * g.nDx + jx;
+                const int o1 = __ldg(off + d + 1);
+                const float *cp = acc + cy * CB + ((qx - jx * g.sigma) >> SH);
+                for (int k = __ldg(off + d); k < o1; ++k) a += __ldg(cp + (size_t)k * (CB * CB));
+            }
         }
+        return a;
     }
-    return a;
 }
 
 // First and last domain index along one axis covering coordinate q (domains at j * sigma span
